@@ -1,0 +1,214 @@
+"""FP64 CPU oracle for block nAIR (arXiv 1704.05001) -- test infrastructure only.
+
+The oracle is a plain C restatement of the method (``nair_oracle.c``), built
+with gcc and loaded with ctypes.  Only the tests, the smoke check and the
+benchmark's CPU-baseline leg may use it; the GPU library never imports it and
+shares no code with it.  Every function in the C file cites the passage of
+the paper it follows.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nair_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "singular block", 3: "not converged",
+          4: "breakdown", 5: "out of memory"}
+
+# level arrays exported by orc_level_get
+A_RP, A_CI, A_V, DINV, CF, IPC, D_RP, D_CI, D_V, R_RP, R_CI, R_V, STRONG, LAM, L_RP, L_CI, L_V = range(17)
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no contraction of multiply-adds)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            D = ctypes.c_double
+            lib.orc_setup.restype = P
+            lib.orc_setup.argtypes = [I, I, P, P, P, D, D, I, I, I, I, I, ctypes.c_ulonglong,
+                                      ctypes.POINTER(I)]
+            lib.orc_free.argtypes = [P]
+            lib.orc_num_levels.argtypes = [P]
+            lib.orc_level_sizes.argtypes = [P, I, P]
+            lib.orc_level_get.argtypes = [P, I, I, P]
+            lib.orc_solve.argtypes = [P, P, P, I, I, I, I, D, P, I, ctypes.POINTER(I),
+                                      ctypes.POINTER(I), ctypes.POINTER(D)]
+            lib.orc_vcycle.argtypes = [P, P, P, I, I]
+            lib.orc_block_inverse.argtypes = [I, P, P]
+            lib.orc_transpose.argtypes = [I, I, P, P, P, P, P, P]
+            lib.orc_gradients.argtypes = [I, I, P, P, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__(f"oracle {where}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+DEFAULTS = dict(theta=0.1, filter_tol=1e-4, filter_targets=3, neumann_degree=1, max_levels=25,
+                max_coarse=None, max_dense=4096, seed=0, f_sweeps=None, c_sweeps=1,
+                restart=50, maxiter=500, tol=1e-10)
+
+
+def default_max_coarse(b):
+    """Coarsest level: at most max(2, 192 // b) elements (dense solve of <= ~192 unknowns)."""
+    return max(2, 192 // b)
+
+
+class Hierarchy:
+    """An oracle hierarchy built from a block-CSR matrix (host arrays)."""
+
+    def __init__(self, row_ptr, col, vals, **params):
+        lib = _load()
+        p = dict(DEFAULTS)
+        p.update(params)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        self.b = vals.shape[-1]
+        if p["max_coarse"] is None:
+            p["max_coarse"] = default_max_coarse(self.b)
+        if p["f_sweeps"] is None:
+            p["f_sweeps"] = p["neumann_degree"] + 1
+        self.params = p
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(col, dtype=np.int32)
+        self.E = len(rp) - 1
+        st = ctypes.c_int(0)
+        self._h = lib.orc_setup(self.E, self.b, _p(rp), _p(ci), _p(vals), p["theta"],
+                                p["filter_tol"], p["filter_targets"], p["neumann_degree"],
+                                p["max_levels"], p["max_coarse"], p["max_dense"], p["seed"],
+                                ctypes.byref(st))
+        if not self._h:
+            raise OracleError(st.value, "setup")
+        self.nlev = lib.orc_num_levels(self._h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _load().orc_free(h)
+            self._h = None
+
+    def sizes(self, l):
+        out = np.zeros(9, dtype=np.int64)
+        _load().orc_level_sizes(self._h, l, _p(out))
+        keys = ["E", "nnzb", "nC", "nF", "L_nnzb", "D_nnzb", "R_nnzb", "AP_nnzb", "coarsest"]
+        return dict(zip(keys, (int(v) for v in out)))
+
+    def _get(self, l, which, shape, dtype):
+        out = np.zeros(shape, dtype=dtype)
+        if out.size:
+            _load().orc_level_get(self._h, l, which, _p(out))
+        return out
+
+    def level(self, l):
+        """All arrays of level l (host copies)."""
+        s = self.sizes(l)
+        b = self.b
+        E, nC, nF = s["E"], s["nC"], s["nF"]
+        d = dict(s)
+        d["row_ptr"] = self._get(l, A_RP, E + 1, np.int32)
+        d["col"] = self._get(l, A_CI, s["nnzb"], np.int32)
+        d["vals"] = self._get(l, A_V, (s["nnzb"], b, b), np.float64)
+        d["dinv"] = self._get(l, DINV, (E, b, b), np.float64)
+        if not s["coarsest"] or nC + nF == E:
+            d["cf"] = self._get(l, CF, E, np.int8)
+            d["strong"] = self._get(l, STRONG, s["nnzb"], np.uint8)
+            d["lam"] = self._get(l, LAM, E, np.int32)
+        if not s["coarsest"]:
+            d["ipc"] = self._get(l, IPC, E, np.int32)
+            d["D_rp"] = self._get(l, D_RP, nF + 1, np.int32)
+            d["D_ci"] = self._get(l, D_CI, s["D_nnzb"], np.int32)
+            d["D_v"] = self._get(l, D_V, (s["D_nnzb"], b, b), np.float64)
+            d["R_rp"] = self._get(l, R_RP, nC + 1, np.int32)
+            d["R_ci"] = self._get(l, R_CI, s["R_nnzb"], np.int32)
+            d["R_v"] = self._get(l, R_V, (s["R_nnzb"], b, b), np.float64)
+            d["L_rp"] = self._get(l, L_RP, nF + 1, np.int32)
+            d["L_ci"] = self._get(l, L_CI, s["L_nnzb"], np.int32)
+            d["L_v"] = self._get(l, L_V, (s["L_nnzb"], b, b), np.float64)
+        return d
+
+    def solve(self, rhs, x0=None, **over):
+        p = dict(self.params)
+        p.update(over)
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.zeros_like(rhs) if x0 is None else np.array(x0, dtype=np.float64)
+        cap = p["maxiter"] + p["maxiter"] // max(1, p["restart"]) + 4
+        hist = np.zeros(cap)
+        hl = ctypes.c_int(0)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0)
+        st = _load().orc_solve(self._h, _p(rhs), _p(x), p["f_sweeps"], p["c_sweeps"], p["restart"],
+                               p["maxiter"], p["tol"], _p(hist), cap, ctypes.byref(hl),
+                               ctypes.byref(it), ctypes.byref(rr))
+        return dict(x=x, status=st, history=hist[:hl.value].copy(), iterations=it.value,
+                    relres=rr.value)
+
+    def vcycle(self, f, f_sweeps=None, c_sweeps=None):
+        p = self.params
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        x = np.zeros_like(f)
+        _load().orc_vcycle(self._h, _p(f), _p(x),
+                           p["f_sweeps"] if f_sweeps is None else f_sweeps,
+                           p["c_sweeps"] if c_sweeps is None else c_sweeps)
+        return x
+
+
+def block_inverse(A):
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    X = np.zeros_like(A)
+    st = _load().orc_block_inverse(A.shape[0], _p(A), _p(X))
+    if st:
+        raise OracleError(st, "block inverse")
+    return X
+
+
+def transpose(row_ptr, col, vals):
+    """Block transpose of a block-CSR matrix."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col, dtype=np.int32)
+    v = np.ascontiguousarray(vals, dtype=np.float64)
+    E = len(rp) - 1
+    b = v.shape[-1]
+    trp = np.zeros(E + 1, dtype=np.int32)
+    tci = np.zeros(len(ci), dtype=np.int32)
+    tv = np.zeros_like(v)
+    _load().orc_transpose(E, b, _p(rp), _p(ci), _p(v), _p(trp), _p(tci), _p(tv))
+    return trp, tci, tv
+
+
+def gradients(mass, lam, x):
+    """(dJ/dsigma per element, dJ/dq per DOF) from the adjoint solution lam."""
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    E, b, _ = mass.shape
+    gs = np.zeros(E)
+    gq = np.zeros(E * b)
+    _load().orc_gradients(E, b, _p(mass), _p(lam), _p(x), _p(gs), _p(gq))
+    return gs, gq

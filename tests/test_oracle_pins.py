@@ -1,0 +1,428 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: dense
+inverses and Schur complements (numpy), closed forms, exact-solver special
+cases and the invariants the paper states.  No test here needs a GPU.
+"""
+import numpy as np
+import pytest
+
+import dgtransport as D
+from conftest import bsr_dense
+
+
+def tiny(name="C1", N=4, p=1, **kw):
+    return D.make_problem(name, N=N, p=p, **kw)
+
+
+def dof_sets(cf, b):
+    F = np.nonzero(cf == 0)[0]
+    C = np.nonzero(cf == 1)[0]
+    fd = (F[:, None] * b + np.arange(b)[None, :]).ravel()
+    cd = (C[:, None] * b + np.arange(b)[None, :]).ravel()
+    return F, C, fd, cd
+
+
+def block_forward_substitution(P):
+    """x* for a block lower-triangular system (Sec. 2.1: forward solve)."""
+    b = P["b"]
+    E = P["E"]
+    x = np.zeros(P["n"])
+    rhs = P["rhs"]
+    for i in range(E):
+        s = rhs[i * b:(i + 1) * b].copy()
+        dblk = None
+        for k in range(P["row_ptr"][i], P["row_ptr"][i + 1]):
+            j = P["col"][k]
+            if j < i:
+                s -= P["vals"][k] @ x[j * b:(j + 1) * b]
+            elif j == i:
+                dblk = P["vals"][k]
+            else:
+                raise AssertionError("not block lower triangular")
+        x[i * b:(i + 1) * b] = np.linalg.solve(dblk, s)
+    return x
+
+
+def chain(n, c=0.5):
+    """1D upwind chain, b = 1: x_i - c x_{i-1} = f_i."""
+    rp = [0]
+    col = []
+    vals = []
+    for i in range(n):
+        if i > 0:
+            col.append(i - 1)
+            vals.append(-c)
+        col.append(i)
+        vals.append(1.0)
+        rp.append(len(col))
+    return (np.array(rp, dtype=np.int32), np.array(col, dtype=np.int32),
+            np.array(vals, dtype=np.float64).reshape(-1, 1, 1))
+
+
+# -----------------------------------------------------------------------------
+# generator
+# -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 6])
+def test_generator_reproduces_constant_solution(p):
+    """u = 1 with sigma = q = 1 and inflow g = 1 lies in P_p: DG is exact."""
+    P = tiny("C3", N=5, p=p, g=1.0)
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    u = np.linalg.solve(A, P["rhs"])
+    assert np.max(np.abs(u - 1.0)) < 1e-10
+
+
+def test_generator_structure():
+    P = D.make_problem("C1")
+    b, p = P["b"], P["p"]
+    faces = 3 * 32 * 32 - 2 * 32
+    # one upwind coupling per interior face, (p+1)^2 nonzeros each
+    assert P["nnzb"] == P["E"] + faces
+    assert np.count_nonzero(P["vals"]) == P["E"] * b * b + faces * (p + 1) ** 2
+    rows = np.repeat(np.arange(P["E"]), np.diff(P["row_ptr"]))
+    assert np.all(P["col"] <= rows)          # block lower triangular (topological order)
+    assert abs(P["mass"].sum() - 1.0) < 1e-12  # sum of element areas
+
+
+# -----------------------------------------------------------------------------
+# a1: block inverse
+# -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("b", [1, 3, 6, 10, 28])
+def test_block_inverse_matches_dense_inverse(oracle_lib, b):
+    r = np.random.default_rng(b)
+    for trial in range(5):
+        A = r.standard_normal((b, b))
+        if trial == 0:
+            A = A + 3 * b * np.eye(b)
+        X = oracle_lib.block_inverse(A)
+        assert np.linalg.norm(X @ A - np.eye(b)) <= 1e-11 * np.linalg.cond(A)
+        assert np.allclose(X, np.linalg.inv(A), rtol=1e-9, atol=1e-12 * np.abs(X).max())
+
+
+def test_block_inverse_singular(oracle_lib):
+    A = np.ones((3, 3))
+    with pytest.raises(oracle_lib.OracleError):
+        oracle_lib.block_inverse(A)
+
+
+# -----------------------------------------------------------------------------
+# a2 / a3: strength and C/F splitting
+# -----------------------------------------------------------------------------
+
+def test_cf_star_by_hand(oracle_lib):
+    """Points 1..4 depend only on point 0: lambda_0 = 4, others 0 -> C F F F F."""
+    n = 5
+    rp = [0, 1]
+    col = [0]
+    vals = [2.0]
+    for i in range(1, n):
+        col += [0, i]
+        vals += [-1.0, 2.0]
+        rp.append(len(col))
+    H = oracle_lib.Hierarchy(np.array(rp), np.array(col), np.array(vals).reshape(-1, 1, 1),
+                             max_coarse=1, max_levels=2, filter_targets=0)
+    lev = H.level(0)
+    assert lev["cf"].tolist() == [1, 0, 0, 0, 0]
+    assert lev["lam"].tolist() == [4, 0, 0, 0, 0]
+    assert lev["ipc"].tolist() == [0, 0, 0, 0, 0]
+
+
+def test_strength_rule_by_hand(oracle_lib):
+    """Row 2 of a 3-point system: |a_20| = 1, |a_21| = 0.05; theta = 0.1 keeps only 0."""
+    rp = np.array([0, 1, 3, 6], dtype=np.int32)
+    col = np.array([0, 0, 1, 0, 1, 2], dtype=np.int32)
+    vals = np.array([1.0, -0.5, 1.0, -1.0, -0.05, 1.0]).reshape(-1, 1, 1)
+    H = oracle_lib.Hierarchy(rp, col, vals, theta=0.1, max_coarse=1, max_levels=2)
+    s = H.level(0)["strong"].tolist()
+    assert s == [0, 1, 0, 1, 0, 0]
+    # theta = 0.3: |a_21|^2 = 0.0025 < 0.09 -> still weak; theta = 0.01 -> strong
+    H2 = oracle_lib.Hierarchy(rp, col, vals, theta=0.01, max_coarse=1, max_levels=2)
+    assert H2.level(0)["strong"].tolist() == [0, 1, 0, 1, 1, 0]
+
+
+@pytest.mark.parametrize("name,N,p", [("C1", 8, 1), ("C2", 8, 2), ("C3", 6, 3)])
+def test_cf_invariants(oracle_lib, name, N, p):
+    P = tiny(name, N=N, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], max_coarse=4)
+    for l in range(H.nlev - 1):
+        lev = H.level(l)
+        cf, strong, rp, col = lev["cf"], lev["strong"].astype(bool), lev["row_ptr"], lev["col"]
+        E = lev["E"]
+        assert set(np.unique(cf)) <= {0, 1}
+        lam = np.zeros(E, dtype=np.int64)
+        for i in range(E):
+            for k in range(rp[i], rp[i + 1]):
+                if strong[k]:
+                    lam[col[k]] += 1
+        assert np.array_equal(lam, lev["lam"])
+        for i in range(E):
+            if cf[i] == 0:
+                has_c = any(strong[k] and cf[col[k]] == 1 for k in range(rp[i], rp[i + 1]))
+                assert has_c or lam[i] == 0
+        # one-point interpolation: strongest strong C neighbour, smallest index on ties
+        cidx = np.cumsum(cf) - 1
+        for i in range(E):
+            if cf[i] == 1:
+                assert lev["ipc"][i] == cidx[i]
+                continue
+            cands = [(k, col[k]) for k in range(rp[i], rp[i + 1]) if strong[k] and cf[col[k]] == 1]
+            if not cands:
+                assert lev["ipc"][i] == -1
+                continue
+            nrm = [np.sum(lev["vals"][k] ** 2) for k, _ in cands]
+            best = max(nrm)
+            # norms equal up to summation rounding: accept any near-maximal candidate
+            ok = [cidx[j] for (k, j), s in zip(cands, nrm) if s >= best * (1 - 1e-12)]
+            assert lev["ipc"][i] in ok
+
+
+# -----------------------------------------------------------------------------
+# a4 / a5 / a7: Neumann series, ideal restriction, Schur complement
+# -----------------------------------------------------------------------------
+
+def two_level(oracle_lib, P, **kw):
+    par = dict(max_levels=2, max_coarse=1, max_dense=100000)
+    par.update(kw)
+    return oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], **par)
+
+
+def dense_L(A, cf, strong, rp, col, b):
+    """L = I - D_ff^{-1} A_ff^S over strong F-F blocks, built directly (numpy)."""
+    F = np.nonzero(cf == 0)[0]
+    fpos = {int(e): k for k, e in enumerate(F)}
+    nF = len(F)
+    Lm = np.zeros((nF * b, nF * b))
+    for a, i in enumerate(F):
+        Dii = A[i * b:(i + 1) * b, i * b:(i + 1) * b]
+        Di = np.linalg.inv(Dii)
+        for k in range(rp[i], rp[i + 1]):
+            j = col[k]
+            if j != i and strong[k] and cf[j] == 0:
+                c = fpos[int(j)]
+                Lm[a * b:(a + 1) * b, c * b:(c + 1) * b] = -Di @ A[i * b:(i + 1) * b, j * b:(j + 1) * b]
+    return Lm
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+@pytest.mark.parametrize("name,p", [("C1", 1), ("C3", 2), ("C2", 2)])
+def test_neumann_error_identity(oracle_lib, name, p, k):
+    """I - Delta A^S_ff = L^{k+1} for any degree k (Sec. 4.1), unfiltered."""
+    P = tiny(name, N=4, p=p)
+    H = two_level(oracle_lib, P, neumann_degree=k, filter_targets=0, theta=0.1)
+    lev = H.level(0)
+    b = P["b"]
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    Lm = dense_L(A, lev["cf"], lev["strong"], lev["row_ptr"], lev["col"], b)
+    nF = lev["nF"]
+    Dg = np.zeros_like(Lm)
+    F = np.nonzero(lev["cf"] == 0)[0]
+    for a, i in enumerate(F):
+        Dg[a * b:(a + 1) * b, a * b:(a + 1) * b] = A[i * b:(i + 1) * b, i * b:(i + 1) * b]
+    AS = Dg @ (np.eye(nF * b) - Lm)   # A_ff restricted to strong blocks
+    Delta = bsr_dense(lev["D_rp"], lev["D_ci"], lev["D_v"], nF, nF)
+    lhs = np.eye(nF * b) - Delta @ AS
+    rhs = np.linalg.matrix_power(Lm, k + 1)
+    assert np.max(np.abs(lhs - rhs)) <= 1e-12 * max(1.0, np.max(np.abs(rhs)))
+    Ld = bsr_dense(lev["L_rp"], lev["L_ci"], lev["L_v"], nF, nF)
+    assert np.max(np.abs(Ld - Lm)) <= 1e-13 * max(1.0, np.abs(Lm).max())
+
+
+def longest_ff_path(lev):
+    """d_f: longest path in the F-F graph of L (footnote to Eq. neumann)."""
+    nF = lev["nF"]
+    depth = np.zeros(nF, dtype=np.int64)
+    for i in range(nF):
+        for k in range(lev["L_rp"][i], lev["L_rp"][i + 1]):
+            j = lev["L_ci"][k]
+            assert j < i   # lower triangular in the F order
+            depth[i] = max(depth[i], depth[j] + 1)
+    return int(depth.max()) if nF else 0
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_exact_neumann_gives_ideal_restriction_and_schur(oracle_lib, p):
+    """theta = 0, no filtering, k >= d_f on triangular A: Delta = A_ff^{-1},
+    R = R_ideal and K = R A P = K_A (Eq. neumann, Lemma ideal restriction)."""
+    P = tiny("C1", N=4, p=p)
+    b = P["b"]
+    H = two_level(oracle_lib, P, neumann_degree=40, filter_targets=0, theta=0.0)
+    lev = H.level(0)
+    assert longest_ff_path(lev) <= 40
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    F, C, fd, cd = dof_sets(lev["cf"], b)
+    Aff, Afc, Acf, Acc = A[np.ix_(fd, fd)], A[np.ix_(fd, cd)], A[np.ix_(cd, fd)], A[np.ix_(cd, cd)]
+    Affi = np.linalg.inv(Aff)
+    Delta = bsr_dense(lev["D_rp"], lev["D_ci"], lev["D_v"], len(F), len(F))
+    assert np.max(np.abs(Delta - Affi)) <= 1e-12 * np.abs(Affi).max()
+    Rcf = bsr_dense(lev["R_rp"], lev["R_ci"], lev["R_v"], len(C), len(F))
+    Rid = -Acf @ Affi
+    assert np.max(np.abs(Rcf - Rid)) <= 1e-12 * max(1.0, np.abs(Rid).max())
+    KA = Acc - Acf @ Affi @ Afc
+    K = bsr_dense(H.level(1)["row_ptr"], H.level(1)["col"], H.level(1)["vals"], len(C), len(C))
+    assert np.max(np.abs(K - KA)) <= 1e-12 * np.abs(KA).max()
+
+
+@pytest.mark.parametrize("name,p,k", [("C1", 1, 1), ("C2", 2, 2), ("C3", 3, 1)])
+def test_galerkin_product_and_wap_identity(oracle_lib, name, p, k):
+    """K equals R A P formed densely from the oracle's R and P (Eq. rap), and
+    K - K_A = delta_R A_ff^{-1} delta_P (Sec. 3.3)."""
+    P = tiny(name, N=4, p=p)
+    b = P["b"]
+    H = two_level(oracle_lib, P, neumann_degree=k, filter_targets=0, theta=0.1)
+    lev = H.level(0)
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    F, C, fd, cd = dof_sets(lev["cf"], b)
+    nC, nF = len(C), len(F)
+    Rcf = bsr_dense(lev["R_rp"], lev["R_ci"], lev["R_v"], nC, nF)
+    W = np.zeros((nF * b, nC * b))
+    for a, i in enumerate(F):
+        J = lev["ipc"][i]
+        if J >= 0:
+            W[a * b:(a + 1) * b, J * b:(J + 1) * b] = np.eye(b)
+    Aff, Afc, Acf, Acc = A[np.ix_(fd, fd)], A[np.ix_(fd, cd)], A[np.ix_(cd, fd)], A[np.ix_(cd, cd)]
+    K_dense = Rcf @ Aff @ W + Acf @ W + Rcf @ Afc + Acc
+    K = bsr_dense(H.level(1)["row_ptr"], H.level(1)["col"], H.level(1)["vals"], nC, nC)
+    scale = np.abs(K_dense).max()
+    assert np.max(np.abs(K - K_dense)) <= 1e-12 * scale
+    KA = Acc - Acf @ np.linalg.inv(Aff) @ Afc
+    dR = Rcf @ Aff + Acf
+    dP = Aff @ W + Afc
+    assert np.max(np.abs((K_dense - KA) - dR @ np.linalg.inv(Aff) @ dP)) <= 1e-10 * scale
+
+
+def test_chain_closed_form(oracle_lib):
+    """1D upwind chain: R_ideal and the Schur complement have closed forms
+    R_{c,f} = c^{c-f} and K_{c,c'} = -c^{c-c'} (c' the previous C point)."""
+    n = 40
+    cval = 0.5
+    rp, col, vals = chain(n, cval)
+    H = oracle_lib.Hierarchy(rp, col, vals, theta=0.0, filter_targets=0, neumann_degree=n,
+                             max_levels=2, max_coarse=1)
+    lev = H.level(0)
+    cf = lev["cf"]
+    C = np.nonzero(cf == 1)[0]
+    F = np.nonzero(cf == 0)[0]
+    fpos = {int(f): a for a, f in enumerate(F)}
+    K = bsr_dense(H.level(1)["row_ptr"], H.level(1)["col"], H.level(1)["vals"], len(C), len(C))
+    R = bsr_dense(lev["R_rp"], lev["R_ci"], lev["R_v"], len(C), len(F))
+    for a, c in enumerate(C):
+        assert K[a, a] == 1.0
+        prev = C[C < c]
+        for a2 in range(len(C)):
+            if a2 != a:
+                want = -(cval ** (c - prev[-1])) if (len(prev) and C[a2] == prev[-1]) else 0.0
+                assert abs(K[a, a2] - want) <= 1e-15
+        lo = prev[-1] if len(prev) else -1
+        for f in F:
+            want = cval ** (c - f) if lo < f < c else 0.0
+            assert abs(R[a, fpos[int(f)]] - want) <= 1e-15
+
+
+# -----------------------------------------------------------------------------
+# a9 - a14: cycle
+# -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_exact_settings_one_vcycle_solves(oracle_lib, p):
+    """R_ideal at every level plus enough F-Jacobi sweeps to be exact on the
+    nilpotent F block: one V-cycle from zero solves A x = f (Lemma ideal
+    restriction, applied recursively)."""
+    P = tiny("C1", N=6, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], theta=0.0, filter_targets=0,
+                             neumann_degree=80, max_coarse=2, f_sweeps=80, c_sweeps=1)
+    assert H.nlev >= 3
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    x = H.vcycle(P["rhs"])
+    xs = np.linalg.solve(A, P["rhs"])
+    assert np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_error_propagation_is_strictly_block_lower_triangular(oracle_lib):
+    """Remark (nilpotent error propagation): with truncated Neumann R and Jacobi
+    F-relaxation on a triangular A, the multilevel error propagation
+    E = I - M^{-1} A is strictly block lower triangular, hence nilpotent."""
+    P = tiny("C1", N=4, p=1)
+    b, n, E = P["b"], P["n"], P["E"]
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=1, max_coarse=2)
+    assert H.nlev >= 3
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    Minv = np.stack([H.vcycle(e) for e in np.eye(n)], axis=1)
+    Em = np.eye(n) - Minv @ A
+    scale = np.abs(Em).max()
+    for i in range(E):
+        blk = Em[i * b:(i + 1) * b, i * b:]
+        assert np.abs(blk).max() <= 1e-13 * scale
+    assert np.abs(np.linalg.matrix_power(Em, E)).max() <= 1e-10 * scale
+
+
+# -----------------------------------------------------------------------------
+# a15: FGMRES
+# -----------------------------------------------------------------------------
+
+def test_fgmres_triangular_matches_forward_substitution(oracle_lib):
+    P = D.make_problem("C1")
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=1)
+    r = H.solve(P["rhs"])
+    assert r["status"] == 0
+    xs = block_forward_substitution(P)
+    assert np.linalg.norm(r["x"] - xs) <= 1e-9 * np.linalg.norm(xs)
+    assert r["relres"] <= 1e-10
+    h = r["history"]
+    assert np.all(np.diff(h) <= 1e-14)    # GMRES residuals never increase
+    assert h[-1] <= 1e-10 and h[0] == 1.0
+
+
+@pytest.mark.parametrize("name,N,p", [("C2", 8, 2), ("C3", 6, 3)])
+def test_fgmres_matches_dense_solve(oracle_lib, name, N, p):
+    P = tiny(name, N=N, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=2, max_coarse=4)
+    r = H.solve(P["rhs"], restart=5)
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    xs = np.linalg.solve(A, P["rhs"])
+    assert r["status"] == 0 and r["relres"] <= 1e-10
+    assert np.linalg.norm(r["x"] - xs) <= 1e-8 * np.linalg.norm(xs)
+
+
+# -----------------------------------------------------------------------------
+# a16: adjoint
+# -----------------------------------------------------------------------------
+
+def test_transpose_and_adjoint_gradients(oracle_lib):
+    """A^T lambda = w by nAIR on A^T; gradients of J = w . x against central
+    finite differences of dense solves."""
+    P = D.make_problem("C2", N=4, keep_parts=True)
+    b, E, n = P["b"], P["E"], P["n"]
+    trp, tci, tv = oracle_lib.transpose(P["row_ptr"], P["col"], P["vals"])
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    assert np.array_equal(bsr_dense(trp, tci, tv), A.T)
+    w = D.functional_weights(n)
+    Hf = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=2, max_coarse=4)
+    Ht = oracle_lib.Hierarchy(trp, tci, tv, neumann_degree=2, max_coarse=4)
+    x = Hf.solve(P["rhs"], tol=1e-13)["x"]
+    lam = Ht.solve(w, tol=1e-13)["x"]
+    gs, gq = oracle_lib.gradients(P["mass"], lam, x)
+
+    def J(sig, q):
+        vals = P["vals0"].copy()
+        vals[P["diag_pos"]] += sig[:, None, None] * P["mass"]
+        Ad = bsr_dense(P["row_ptr"], P["col"], vals)
+        rhs = np.einsum("eij,ej->ei", P["mass"], q.reshape(E, b)).ravel()
+        return w @ np.linalg.solve(Ad, rhs)
+
+    sig0 = P["sigma"].copy()
+    q0 = P["q"].copy()
+    eps = 1e-6
+    for e in [0, 5, E - 1]:
+        sp, sm = sig0.copy(), sig0.copy()
+        sp[e] += eps
+        sm[e] -= eps
+        fd = (J(sp, q0) - J(sm, q0)) / (2 * eps)
+        assert abs(fd - gs[e]) <= 1e-6 * max(1.0, abs(fd))
+    for i in [0, 7, n - 1]:
+        qp, qm = q0.copy(), q0.copy()
+        qp[i] += eps
+        qm[i] -= eps
+        fd = (J(sig0, qp) - J(sig0, qm)) / (2 * eps)
+        assert abs(fd - gq[i]) <= 1e-6 * max(1.0, abs(fd))
