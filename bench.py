@@ -1,0 +1,297 @@
+"""Benchmark: nAIR setup + solve to 1e-10 relative residual on one GB300.
+
+A step is one pass of the whole hot path on one synthetic problem that is
+already resident in HBM: the nAIR setup (diagonal-block inverses, strength,
+C/F splitting, Neumann Delta, R, P, K = R A P on every level) followed by the
+FGMRES solve preconditioned by V-cycles, to ||b - A x|| / ||b|| <= 1e-10.
+The headline workload is the P2 DG transport problem on a 256 x 256 x 2
+mesh with rotating flow and log-normal absorption (786,432 unknowns, FP64).
+value = unknowns / (setup + solve time) in MDOF/s, summed over ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nair|reference]
+                    [--workload C2] [--precision fp64|mixed]
+
+With N > 1 (torchrun) every rank solves its own replica of the problem on its
+own GPU with no communication on the data path (the solve does not shard).
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import dgtransport  # noqa: E402
+
+WORKLOADS = {
+    "C1": "P1 DG, 32x32x2 mesh, constant flow (6144 DOFs), FP64",
+    "C2": "P2 DG, 256x256x2 mesh, rotating flow, log-normal sigma_t (786432 DOFs), FP64",
+    "C3": "P6 DG, 128x128x2 jittered mesh, constant flow (917504 DOFs)",
+    "C5": "P3 DG, 512x512x2 jittered mesh, rotating flow, log-normal sigma_t (5242880 DOFs)",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nair", choices=["nair", "reference"])
+    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(workload):
+    P = dgtransport.make_problem(workload)
+    return P
+
+
+def run_reference(args, rank, world):
+    """FP64 CPU oracle (single host thread) on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    if rank != 0:
+        return
+    # bounded sample: the same configuration on a coarser mesh (setup + solve)
+    cfg = dgtransport.CONFIGS[args.workload]
+    Ns = max(16, cfg["N"] // 4)
+    P = dgtransport.make_problem(args.workload, N=Ns)
+    k = P["neumann_degree"]
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        H = oracle.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=k)
+        r = H.solve(P["rhs"])
+        t1 = time.perf_counter()
+        del H
+        if it >= args.warmup:
+            times.append(t1 - t0)
+    tot = sum(times)
+    value = P["n"] * len(times) / tot / 1e6
+    sample = f"{args.workload} configuration on a {Ns}x{Ns}x2 mesh ({P['n']} DOFs), setup+solve, {r['iterations']} iterations"
+    line = {"impl": "reference", "metric": "nAIR setup+solve MDOF/s to 1e-10 rel. residual",
+            "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "sample_dofs": P["n"]},
+            "cpu_baseline": {"value": value, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(workload):
+    """The oracle as it stands, one host thread, on a bounded sample (~10-30 s)."""
+    import oracle
+    oracle.build()
+    cfg = dgtransport.CONFIGS[workload]
+    Ns = max(16, cfg["N"] // 2)
+    P = dgtransport.make_problem(workload, N=Ns)
+    t0 = time.perf_counter()
+    H = oracle.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=P["neumann_degree"])
+    r = H.solve(P["rhs"])
+    t = time.perf_counter() - t0
+    return {"value": P["n"] / t / 1e6, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"one setup+solve of the {workload} configuration on a {Ns}x{Ns}x2 mesh "
+                      f"({P['n']} DOFs, {r['iterations']} iterations, {t:.1f} s)"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1704_05001_gb300 as nair
+    from paper_1704_05001_gb300 import build as nbuild
+    nbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    P = make_inputs(args.workload)
+    k = P["neumann_degree"]
+    params = dict(neumann_degree=k, precision=args.precision)
+    rp = torch.from_numpy(P["row_ptr"]).to(dev)
+    ci = torch.from_numpy(P["col"]).to(dev)
+    v = torch.from_numpy(P["vals"]).to(dev)
+    bvec = torch.from_numpy(P["rhs"]).to(dev)
+    x = torch.zeros_like(bvec)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s = nair.NairSolver(rp, ci, v, **params)
+        x.zero_()
+        _, rep = s.solve(bvec, x)
+        s.close()
+        return rep
+
+    for _ in range(args.warmup):
+        rep = step()
+    launches0 = nair.kernel_launches()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    setup_ms = solve_ms = 0.0
+    reps = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)   # L2 flush between timed steps (outside the events)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        setup_ms += rep["setup_ms"]
+        solve_ms += rep["solve_ms"]
+        reps.append(rep)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = (nair.kernel_launches() - launches0) // max(1, args.steps)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t.item())
+    ms = total_ms / args.steps
+    value = world * P["n"] / (ms * 1e-3) / 1e6
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_extras:
+        hp = {k2: torch.from_numpy(np.ascontiguousarray(P[k2])).pin_memory()
+              for k2 in ("row_ptr", "col", "vals", "rhs")}
+        xh = torch.empty(P["n"], dtype=torch.float64).pin_memory()
+        h2d = sum(t2.numel() * t2.element_size() for t2 in hp.values())
+        d2h = xh.numel() * xh.element_size()
+
+        def e2e_step():
+            drp = hp["row_ptr"].to(dev, non_blocking=True)
+            dci = hp["col"].to(dev, non_blocking=True)
+            dv = hp["vals"].to(dev, non_blocking=True)
+            db = hp["rhs"].to(dev, non_blocking=True)
+            s = nair.NairSolver(drp, dci, dv, **params)
+            xx, _ = s.solve(db)
+            xh.copy_(xx, non_blocking=True)
+            s.close()
+            torch.cuda.synchronize()
+
+        e2e_step()
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            e2e_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+        e2e = {"value": world * P["n"] / (e2e_ms / args.steps * 1e-3) / 1e6, "unit": "MDOF/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        return
+    last = reps[-1]
+    line = {
+        "metric": "nAIR setup+solve MDOF/s to 1e-10 rel. residual",
+        "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32-in-f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "dofs": P["n"], "precision": args.precision,
+                   "neumann_degree": k, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "setup_ms": setup_ms / args.steps, "solve_ms": solve_ms / args.steps,
+        "iterations": last["iterations"], "levels": last["levels"], "rel_res": last["rel_res"],
+        "op_complexity": last["op_complexity"], "cycle_complexity": last["cycle_complexity"],
+        "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
+    }
+    if not args.no_extras:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

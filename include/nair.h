@@ -1,0 +1,183 @@
+/*
+ * nair.h -- C ABI of the GB300 block-nAIR library (libnair.so).
+ *
+ * nAIR is the reduction-based algebraic multigrid of Manteuffel, Muenzenmaier,
+ * Ruge and Southworth, "Nonsymmetric reduction-based algebraic multigrid"
+ * (arXiv 1704.05001).  The library solves a sparse, nonsymmetric, block
+ * (near-)triangular system A x = b, such as an upwind DG discretisation of
+ * steady transport (Sec. 2.1 and Eq. transport, Sec. 6.1), with flexible
+ * GMRES preconditioned by one nAIR V-cycle (Sec. 5 and 6).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are block CSR (BSR) with square b x b blocks, b in 1..32, each
+ *     block stored row-major; column indices are sorted and unique within a
+ *     row and every block row holds its diagonal block.
+ *   - "device" pointers are CUDA global-memory addresses on the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every pointer
+ *     it passes; the library copies what it keeps and retains no caller
+ *     pointer after a call returns.
+ *   - Work is ordered on the stream given in nair_params (NULL = the legacy
+ *     default stream).  Calls that return sizes or statuses synchronise that
+ *     stream.
+ *   - Every call returns a nair_status; on failure nair_last_error() returns a
+ *     message for the calling thread.  A handle must not be used by two
+ *     threads at once.
+ */
+#ifndef NAIR_H
+#define NAIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NAIR_OK = 0,
+  NAIR_ERR_INVALID_ARG = 1,    /* bad sizes, pointers, structure or parameters */
+  NAIR_ERR_SINGULAR_BLOCK = 2, /* a diagonal block (or the coarsest matrix) is singular */
+  NAIR_ERR_NOT_CONVERGED = 3,  /* GMRES reached maxiter above the tolerance */
+  NAIR_ERR_BREAKDOWN = 4,      /* non-finite value inside the Krylov iteration */
+  NAIR_ERR_OOM = 5,            /* device allocation failed */
+  NAIR_ERR_CUDA = 6,           /* any other CUDA runtime error */
+  NAIR_ERR_UNSUPPORTED = 7     /* shape outside what the kernels handle */
+} nair_status;
+
+typedef enum { NAIR_FP64 = 0, NAIR_MIXED = 1 } nair_precision;
+
+/* A block-CSR matrix in device memory (caller-owned, read-only during a call). */
+typedef struct {
+  int32_t nb_rows;        /* number of block rows = number of elements E */
+  int32_t block_size;     /* b, 1..32 */
+  int64_t nnzb;           /* number of stored blocks */
+  const int32_t *row_ptr; /* device, nb_rows + 1 entries, row_ptr[0] = 0 */
+  const int32_t *col_idx; /* device, nnzb block-column indices */
+  const double *vals;     /* device, nnzb * b * b doubles */
+} nair_bsr;
+
+/* Method parameters (Sec. 5).  nair_default_params fills the defaults given here. */
+typedef struct {
+  double strength_theta;  /* 0.1: j in S_i iff ||A_ij||_F >= theta max_{k!=i} ||A_ik||_F (Sec. 4.3) */
+  double filter_tol;      /* 1e-4: drop X_ij when ||X_ij||_F <= tol ||X_ii||_F (Sec. 5.2) */
+  int32_t filter_targets; /* bit 0: filter each Neumann iterate; bit 1: filter coarse operators; 3 */
+  int32_t neumann_degree; /* k of Delta^(k) (Eq. neumann); 1 */
+  int32_t f_sweeps;       /* F-Jacobi sweeps; <= 0 means k + 1 (Sec. 5.1) */
+  int32_t c_sweeps;       /* C-Jacobi sweeps after the F sweeps; 1 */
+  int32_t max_levels;     /* 25 */
+  int32_t max_coarse;     /* coarsest level when E <= max_coarse; <= 0 means max(2, 192 / b) */
+  int32_t max_dense;      /* largest coarsest-level size E*b accepted for the dense solve; 4096 */
+  uint64_t cf_seed;       /* seed of the C/F tie-break hash; 0 */
+  int32_t precision;      /* nair_precision; NAIR_FP64 */
+  int32_t gmres_restart;  /* 50 */
+  int32_t maxiter;        /* total preconditioner applications allowed; 500 */
+  double tol;             /* relative residual target ||b - A x|| / ||b||; 1e-10 */
+  void *stream;           /* cudaStream_t for all work; NULL */
+  int32_t keep_setup_data;/* keep strength, L and Delta for nair_get_level; 0 */
+  int32_t use_graphs;     /* replay the V-cycle as a CUDA graph; 1 */
+} nair_params;
+
+/* Solve report.  history is an optional host buffer owned by the caller. */
+typedef struct {
+  int32_t iterations;      /* preconditioner applications */
+  int32_t levels;          /* hierarchy levels */
+  double rel_res;          /* true residual ||b - A x|| / ||b|| at exit (FP64) */
+  double setup_ms;         /* last setup time (device events) */
+  double solve_ms;         /* this solve (device events) */
+  double op_complexity;    /* sum of stored scalars over levels / level 0 (Sec. 6) */
+  double cycle_complexity; /* work units per V-cycle, one WU = one SpMV with A (Sec. 6) */
+  double *history;         /* host, history_cap doubles: [0] initial, then one per iteration */
+  int32_t history_cap;
+  int32_t history_len;
+} nair_info;
+
+typedef struct nair_handle nair_handle;
+
+/* Fill p with the defaults listed in nair_params. */
+void nair_default_params(nair_params *p);
+
+/* Build the nAIR hierarchy of A (Sec. 5): diagonal-block inverses, strength,
+ * C/F splitting, truncated Neumann Delta (Eq. neumann), R = [-A_cf Delta  I],
+ * one-point P and the filtered coarse operator K = R A P (Eq. rap), level by
+ * level, then the inverse of the coarsest operator.  A is validated (row
+ * pointers, sorted columns, diagonal blocks) and copied; *out receives a new
+ * handle that owns all hierarchy memory until nair_free.  Synchronises the
+ * stream.  Errors: INVALID_ARG, SINGULAR_BLOCK, OOM, CUDA, UNSUPPORTED. */
+nair_status nair_setup(const nair_bsr *A, const nair_params *p, nair_handle **out);
+
+/* Solve A x = b with FGMRES(m) preconditioned by one V-cycle (no
+ * pre-relaxation, F-F-...-C post-relaxation, Sec. 5).  b, x: device, n = E*b
+ * doubles; x holds the initial guess on entry and the solution on return.
+ * info may be NULL.  Returns NOT_CONVERGED if the tolerance was not met
+ * within maxiter (x then holds the last iterate). */
+nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *info);
+
+/* Solve A^T lambda = w.  On the first call the library forms A^T (block
+ * transpose, on the device) and builds a second nAIR hierarchy for it with the
+ * same parameters; later calls reuse it.  w, lambda: device, n doubles. */
+nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lambda, nair_info *info);
+
+/* Apply one V-cycle to f with zero initial guess: x = M^{-1} f (device, n doubles). */
+nair_status nair_vcycle(nair_handle *h, const double *f, double *x);
+
+/* Release every device allocation of the handle (NULL is ignored). */
+void nair_free(nair_handle *h);
+
+/* Number of levels of the hierarchy (forward hierarchy when adjoint == 0). */
+nair_status nair_num_levels(const nair_handle *h, int32_t adjoint, int32_t *levels);
+
+/* Sizes of one level, 10 int64 values:
+ *   E, nnzb(A), nC, nF, nnzb(L), nnzb(Delta), nnzb(R_cf), nnzb(AP), coarsest flag, setup rounds of C/F. */
+nair_status nair_level_sizes(const nair_handle *h, int32_t adjoint, int32_t level, int64_t *sizes);
+
+/* Copy one array of a level to host memory.  `which` is a nair_level_array;
+ * integer arrays are int32 (CF: int8), value arrays are returned as doubles in
+ * block row-major order whatever the storage precision.  *need receives the
+ * byte size; nothing is copied when cap < *need (returns INVALID_ARG).  L,
+ * Delta and the strength flags exist only when keep_setup_data was set. */
+typedef enum {
+  NAIR_A_ROWPTR = 0, NAIR_A_COL = 1, NAIR_A_VALS = 2, NAIR_DINV = 3, NAIR_CF = 4,
+  NAIR_P_MAP = 5, /* per element: coarse index it interpolates from (C: itself), -1 if none */
+  NAIR_DELTA_ROWPTR = 6, NAIR_DELTA_COL = 7, NAIR_DELTA_VALS = 8,
+  NAIR_R_ROWPTR = 9, NAIR_R_COL = 10, /* R_cf columns as F indices (position among F elements) */
+  NAIR_R_VALS = 11, NAIR_STRONG = 12, /* uint8 per block of A */
+  NAIR_LAMBDA = 13, NAIR_L_ROWPTR = 14, NAIR_L_COL = 15, NAIR_L_VALS = 16
+} nair_level_array;
+nair_status nair_get_level(const nair_handle *h, int32_t adjoint, int32_t level, int32_t which,
+                           void *host_out, size_t cap, size_t *need);
+
+/* Batched inverses of nblk b x b blocks (step a1 alone, Sec. 5.2 block
+ * scaling): in-place Gauss-Jordan with partial pivoting in FP64.  A, Ainv:
+ * device, nblk*b*b doubles.  Returns SINGULAR_BLOCK if any pivot is zero. */
+nair_status nair_block_inverse(int32_t nblk, int32_t b, const double *A, double *Ainv, void *stream);
+
+/* Parameter-dependent assembly for the transport problem (Eq. transport):
+ * vals = vals0 with diagonal blocks vals0[diag_pos[e]] + sigma[e] * M[e]
+ * (sigma_t piecewise constant per element, M the element mass matrices).
+ * vals0, vals: device nnzb*b*b; diag_pos: device E; M: device E*b*b; sigma: device E. */
+nair_status nair_assemble_sigma(int32_t E, int32_t b, int64_t nnzb, const int32_t *diag_pos,
+                                const double *vals0, const double *M, const double *sigma,
+                                double *vals, void *stream);
+
+/* rhs_e = M_e q_e for every element (device, E*b doubles each). */
+nair_status nair_mass_apply(int32_t E, int32_t b, const double *M, const double *q, double *rhs,
+                            void *stream);
+
+/* Gradients of J = w . x for A(sigma) x = M q given the adjoint solution
+ * lambda = A^{-T} w: gsigma_e = -lambda_e^T M_e x_e (device, E doubles) and
+ * gq_e = M_e^T lambda_e (device, E*b doubles). */
+nair_status nair_gradients(int32_t E, int32_t b, const double *M, const double *lambda,
+                           const double *x, double *gsigma, double *gq, void *stream);
+
+/* Total number of kernels this library has launched in the process so far
+ * (a diagnostic counter; every launch site increments it). */
+nair_status nair_kernel_launches(int64_t *count);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *nair_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NAIR_H */

@@ -1,0 +1,625 @@
+// C ABI of the nAIR GPU library (declared in include/nair.h): handle life
+// cycle, argument checking, the adjoint (transpose) hierarchy, hierarchy
+// export, and the small parameter-dependent kernels of the transport problem.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "solve.cuh"
+
+namespace nair {
+void validate_bsr(int E, int ncols, const int *rp, const int *ci, int nnzb, cudaStream_t s, Mem &tmp);
+}
+
+using namespace nair;
+
+static thread_local std::string g_last_error;
+
+struct nair_handle {
+  Params P{};
+  nair_params raw{};
+  int b = 0, E = 0;
+  long long n = 0;
+  cudaStream_t s = nullptr;
+  Mem mem;
+  DBsr<double> A64;
+  DBsr<float> A32;
+  bool mixed = false;
+  Hier<double> h64;
+  Hier<float> h32;
+  Krylov K;
+  nair_handle *adj = nullptr;
+  double setup_ms = 0.0;
+};
+
+static nair_status set_error(nair_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+#define NAIR_API_BEGIN try {
+#define NAIR_API_END                                              \
+  }                                                               \
+  catch (const NairError &e) {                                    \
+    return set_error(e.status, e.msg);                            \
+  }                                                               \
+  catch (const std::exception &e) {                               \
+    return set_error(NAIR_ERR_CUDA, e.what());                    \
+  }
+
+static constexpr int kThreads = 256;
+static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
+
+namespace nair {
+Params resolve_params(const nair_params *p, int b) {
+  Params P{};
+  P.theta = p->strength_theta;
+  P.filter_tol = p->filter_tol;
+  P.filter_targets = p->filter_targets;
+  P.k = p->neumann_degree;
+  P.f_sweeps = p->f_sweeps > 0 ? p->f_sweeps : p->neumann_degree + 1;
+  P.c_sweeps = p->c_sweeps < 0 ? 0 : p->c_sweeps;
+  P.max_levels = p->max_levels;
+  P.max_coarse = p->max_coarse > 0 ? p->max_coarse : std::max(2, 192 / b);
+  P.max_dense = p->max_dense;
+  P.seed = p->cf_seed;
+  P.precision = p->precision;
+  P.restart = p->gmres_restart;
+  P.maxiter = p->maxiter;
+  P.tol = p->tol;
+  P.keep = p->keep_setup_data;
+  P.use_graphs = p->use_graphs;
+  return P;
+}
+}  // namespace nair
+
+// ---------------------------------------------------------------------------
+// small kernels of the API
+// ---------------------------------------------------------------------------
+template <typename A, typename B>
+__global__ void k_cast_api(long long n, const A *__restrict__ in, B *__restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (B)in[i];
+}
+
+__global__ void k_t_count(int nnzb, const int *__restrict__ ci, int *__restrict__ cnt) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnzb) atomicAdd(&cnt[ci[p]], 1);
+}
+
+__global__ void k_t_fill(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const int *__restrict__ trp, int *__restrict__ fill, int *__restrict__ tci,
+                         int *__restrict__ tsrc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    int q = trp[j] + atomicAdd(&fill[j], 1);
+    tci[q] = i;
+    tsrc[q] = p;
+  }
+}
+
+// sort each transposed row by column (insertion sort: rows are short)
+__global__ void k_t_sort(int E, const int *__restrict__ trp, int *__restrict__ tci, int *__restrict__ tsrc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  for (int a = trp[i] + 1; a < trp[i + 1]; ++a) {
+    int c = tci[a], s = tsrc[a], q = a - 1;
+    while (q >= trp[i] && tci[q] > c) {
+      tci[q + 1] = tci[q];
+      tsrc[q + 1] = tsrc[q];
+      --q;
+    }
+    tci[q + 1] = c;
+    tsrc[q + 1] = s;
+  }
+}
+
+__global__ void k_t_vals(long long total, int b, const int *__restrict__ tsrc, const double *__restrict__ v,
+                         double *__restrict__ tv) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long q = g / bb;
+  const int rc = (int)(g - q * bb), r = rc / b, c = rc - r * b;
+  tv[g] = v[(size_t)tsrc[q] * bb + c * b + r];
+}
+
+__global__ void k_assemble_sigma(int E, int b, const int *__restrict__ dpos, const double *__restrict__ v0,
+                                 const double *__restrict__ M, const double *__restrict__ sigma,
+                                 double *__restrict__ v) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bb = b * b;
+  if (g >= (long long)E * bb) return;
+  const int e = (int)(g / bb), rc = (int)(g - (long long)e * bb);
+  const size_t o = (size_t)dpos[e] * bb + rc;
+  v[o] = __dadd_rn(v0[o], __dmul_rn(sigma[e], M[g]));
+}
+
+__global__ void k_copy64(long long n, const double *__restrict__ a, double *__restrict__ b) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = a[i];
+}
+
+__global__ void k_mass_apply(int E, int b, const double *__restrict__ M, const double *__restrict__ q,
+                             double *__restrict__ rhs) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)E * b) return;
+  const int e = (int)(g / b), r = (int)(g - (long long)e * b);
+  const double *m = M + (size_t)e * b * b + r * b;
+  const double *qe = q + (size_t)e * b;
+  double acc = 0.0;
+  for (int c = 0; c < b; ++c) acc += m[c] * qe[c];
+  rhs[g] = acc;
+}
+
+// gsigma_e = -lambda_e^T M_e x_e ; gq_e = M_e^T lambda_e
+__global__ void k_gradients(int E, int b, const double *__restrict__ M, const double *__restrict__ lam,
+                            const double *__restrict__ x, double *__restrict__ gs, double *__restrict__ gq) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const double *Me = M + (size_t)e * b * b, *le = lam + (size_t)e * b, *xe = x + (size_t)e * b;
+  double s = 0.0;
+  for (int r = 0; r < b; ++r) {
+    double mx = 0.0;
+    for (int c = 0; c < b; ++c) mx += Me[r * b + c] * xe[c];
+    s += le[r] * mx;
+  }
+  gs[e] = -s;
+  for (int c = 0; c < b; ++c) {
+    double t = 0.0;
+    for (int r = 0; r < b; ++r) t += Me[r * b + c] * le[r];
+    gq[(size_t)e * b + c] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// handle construction
+// ---------------------------------------------------------------------------
+static void init_pool_once() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  NAIR_CK(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  NAIR_CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+  uint64_t thr = UINT64_MAX;
+  NAIR_CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+  done = true;
+}
+
+static void check_params(const nair_params *p, int b) {
+  if (!(p->strength_theta >= 0.0) || !(p->strength_theta <= 1.0))
+    fail(NAIR_ERR_INVALID_ARG, "strength_theta must lie in [0, 1]");
+  if (!(p->filter_tol >= 0.0)) fail(NAIR_ERR_INVALID_ARG, "filter_tol must be >= 0");
+  if (p->neumann_degree < 0 || p->neumann_degree > 64) fail(NAIR_ERR_INVALID_ARG, "neumann_degree must lie in 0..64");
+  if (p->max_levels < 1 || p->max_levels > 64) fail(NAIR_ERR_INVALID_ARG, "max_levels must lie in 1..64");
+  if (p->max_dense < b) fail(NAIR_ERR_INVALID_ARG, "max_dense smaller than one block");
+  if (p->precision != NAIR_FP64 && p->precision != NAIR_MIXED) fail(NAIR_ERR_INVALID_ARG, "unknown precision");
+  if (p->gmres_restart < 1 || p->gmres_restart > 1000) fail(NAIR_ERR_INVALID_ARG, "gmres_restart must lie in 1..1000");
+  if (p->maxiter < 0) fail(NAIR_ERR_INVALID_ARG, "maxiter must be >= 0");
+  if (!(p->tol >= 0.0)) fail(NAIR_ERR_INVALID_ARG, "tol must be >= 0");
+}
+
+static void setup_impl(nair_handle *h, const int *rp, const int *ci, const double *v, int E, int b,
+                       long long nnzb, bool device_copy_done) {
+  cudaStream_t s = h->s;
+  Mem &mem = h->mem;
+  mem.s = s;
+  cudaEvent_t e0, e1;
+  NAIR_CK(cudaEventCreate(&e0));
+  NAIR_CK(cudaEventCreate(&e1));
+  NAIR_CK(cudaEventRecord(e0, s));
+  h->b = b;
+  h->E = E;
+  h->n = (long long)E * b;
+  DBsr<double> &A = h->A64;
+  if (!device_copy_done) {
+    A.nrows = A.ncols = E;
+    A.nnzb = (int)nnzb;
+    A.rp = mem.alloc<int>(E + 1);
+    A.ci = mem.alloc<int>(nnzb);
+    A.v = mem.alloc<double>((size_t)nnzb * b * b);
+    NAIR_CK(cudaMemcpyAsync(A.rp, rp, sizeof(int) * (E + 1), cudaMemcpyDefault, s));
+    NAIR_CK(cudaMemcpyAsync(A.ci, ci, sizeof(int) * nnzb, cudaMemcpyDefault, s));
+    NAIR_CK(cudaMemcpyAsync(A.v, v, sizeof(double) * nnzb * b * b, cudaMemcpyDefault, s));
+  }
+  {
+    Mem tmp;
+    tmp.s = s;
+    int first = -1, last = -1;
+    NAIR_CK(cudaMemcpyAsync(&first, A.rp, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NAIR_CK(cudaMemcpyAsync(&last, A.rp + E, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NAIR_CK(cudaStreamSynchronize(s));
+    if (first != 0 || last != nnzb) fail(NAIR_ERR_INVALID_ARG, "row_ptr[0] must be 0 and row_ptr[E] must equal nnzb");
+    validate_bsr(E, E, A.rp, A.ci, (int)nnzb, s, tmp);
+  }
+  h->mixed = h->P.precision == NAIR_MIXED;
+  if (h->mixed) {
+    DBsr<float> &F = h->A32;
+    F.nrows = F.ncols = E;
+    F.nnzb = A.nnzb;
+    F.rp = A.rp;
+    F.ci = A.ci;
+    F.v = mem.alloc<float>((size_t)nnzb * b * b);
+    long long tot = nnzb * b * b;
+    k_cast_api<double, float><<<grid(tot), kThreads, 0, s>>>(tot, A.v, F.v);
+    NAIR_LAUNCH_CHECK();
+    h->h32.b = b;
+    build_hierarchy<float>(F, h->P, s, mem, h->h32);
+  } else {
+    h->h64.b = b;
+    build_hierarchy<double>(A, h->P, s, mem, h->h64);
+  }
+  NAIR_CK(cudaEventRecord(e1, s));
+  NAIR_CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  NAIR_CK(cudaEventElapsedTime(&ms, e0, e1));
+  h->setup_ms = ms;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+// Definitions below take C linkage from their declarations in nair.h.
+
+void nair_default_params(nair_params *p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->strength_theta = 0.1;
+  p->filter_tol = 1e-4;
+  p->filter_targets = 3;
+  p->neumann_degree = 1;
+  p->f_sweeps = 0;
+  p->c_sweeps = 1;
+  p->max_levels = 25;
+  p->max_coarse = 0;
+  p->max_dense = 4096;
+  p->cf_seed = 0;
+  p->precision = NAIR_FP64;
+  p->gmres_restart = 50;
+  p->maxiter = 500;
+  p->tol = 1e-10;
+  p->stream = nullptr;
+  p->keep_setup_data = 0;
+  p->use_graphs = 1;
+}
+
+const char *nair_last_error(void) { return g_last_error.c_str(); }
+
+nair_status nair_kernel_launches(int64_t *count) {
+  if (!count) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  *count = launch_count();
+  return NAIR_OK;
+}
+
+nair_status nair_setup(const nair_bsr *A, const nair_params *p, nair_handle **out) {
+  NAIR_API_BEGIN
+  if (!A || !p || !out) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const int E = A->nb_rows, b = A->block_size;
+  if (E <= 0) return set_error(NAIR_ERR_INVALID_ARG, "nb_rows must be positive");
+  if (b < 1 || b > 32) return set_error(NAIR_ERR_UNSUPPORTED, "block_size must lie in 1..32");
+  if (A->nnzb < E || A->nnzb > (int64_t)INT32_MAX || (long long)A->nnzb * b * b > (1LL << 40))
+    return set_error(NAIR_ERR_INVALID_ARG, "nnzb out of range");
+  if (!A->row_ptr || !A->col_idx || !A->vals) return set_error(NAIR_ERR_INVALID_ARG, "null matrix array");
+  check_params(p, b);
+  init_pool_once();
+  nair_handle *h = new nair_handle();
+  h->raw = *p;
+  h->P = resolve_params(p, b);
+  h->s = (cudaStream_t)p->stream;
+  h->K.mem.s = h->s;
+  try {
+    setup_impl(h, A->row_ptr, A->col_idx, A->vals, E, b, A->nnzb, false);
+  } catch (...) {
+    nair_free(h);
+    throw;
+  }
+  *out = h;
+  g_last_error.clear();
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+static void fill_info(nair_handle *h, nair_info *info, int iters, double relres, double ms,
+                      const std::vector<double> &hist) {
+  if (!info) return;
+  info->iterations = iters;
+  info->rel_res = relres;
+  info->solve_ms = ms;
+  info->setup_ms = h->setup_ms;
+  if (h->mixed) {
+    info->levels = h->h32.nlev;
+    info->op_complexity = h->h32.op_complexity;
+    info->cycle_complexity = h->h32.cycle_complexity;
+  } else {
+    info->levels = h->h64.nlev;
+    info->op_complexity = h->h64.op_complexity;
+    info->cycle_complexity = h->h64.cycle_complexity;
+  }
+  int nh = (int)hist.size();
+  info->history_len = nh;
+  if (info->history && info->history_cap > 0)
+    for (int k = 0; k < std::min(nh, info->history_cap); ++k) info->history[k] = hist[k];
+}
+
+nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *info) {
+  NAIR_API_BEGIN
+  if (!h || !b || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  cudaEvent_t e0, e1;
+  NAIR_CK(cudaEventCreate(&e0));
+  NAIR_CK(cudaEventCreate(&e1));
+  NAIR_CK(cudaEventRecord(e0, h->s));
+  std::vector<double> hist;
+  int iters = 0;
+  double relres = 0.0;
+  nair_status st = h->mixed ? fgmres<float>(h->A64, h->h32, h->P, h->K, b, x, hist, &iters, &relres, h->s)
+                            : fgmres<double>(h->A64, h->h64, h->P, h->K, b, x, hist, &iters, &relres, h->s);
+  NAIR_CK(cudaEventRecord(e1, h->s));
+  NAIR_CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  NAIR_CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  fill_info(h, info, iters, relres, ms, hist);
+  if (st == NAIR_ERR_NOT_CONVERGED) return set_error(st, "GMRES did not reach the tolerance within maxiter");
+  if (st == NAIR_ERR_BREAKDOWN) return set_error(st, "non-finite value in the Krylov iteration");
+  if (st == NAIR_OK) g_last_error.clear();
+  return st;
+  NAIR_API_END
+}
+
+nair_status nair_vcycle(nair_handle *h, const double *f, double *x) {
+  NAIR_API_BEGIN
+  if (!h || !f || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (h->mixed) precond<float>(h->h32, h->P, f, x, h->s, h->n);
+  else precond<double>(h->h64, h->P, f, x, h->s, h->n);
+  NAIR_CK(cudaStreamSynchronize(h->s));
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+static void build_adjoint(nair_handle *h) {
+  cudaStream_t s = h->s;
+  nair_handle *a = new nair_handle();
+  a->raw = h->raw;
+  a->P = h->P;
+  a->s = s;
+  a->K.mem.s = s;
+  a->mem.s = s;
+  try {
+    const int E = h->E, b = h->b, nnzb = h->A64.nnzb;
+    const DBsr<double> &A = h->A64;
+    DBsr<double> &T = a->A64;
+    T.nrows = T.ncols = E;
+    T.nnzb = nnzb;
+    T.rp = a->mem.alloc<int>(E + 1);
+    T.ci = a->mem.alloc<int>(nnzb);
+    T.v = a->mem.alloc<double>((size_t)nnzb * b * b);
+    Mem tmp;
+    tmp.s = s;
+    int *cnt = tmp.alloc<int>(E + 1), *fill = tmp.alloc<int>(E + 1), *tsrc = tmp.alloc<int>(nnzb);
+    NAIR_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * (E + 1), s));
+    NAIR_CK(cudaMemsetAsync(fill, 0, sizeof(int) * (E + 1), s));
+    k_t_count<<<grid(nnzb), kThreads, 0, s>>>(nnzb, A.ci, cnt);
+    NAIR_LAUNCH_CHECK();
+    exclusive_scan(cnt, T.rp, E, s, tmp, false);
+    k_t_fill<<<grid(E), kThreads, 0, s>>>(E, A.rp, A.ci, T.rp, fill, T.ci, tsrc);
+    NAIR_LAUNCH_CHECK();
+    k_t_sort<<<grid(E), kThreads, 0, s>>>(E, T.rp, T.ci, tsrc);
+    NAIR_LAUNCH_CHECK();
+    long long tot = (long long)nnzb * b * b;
+    k_t_vals<<<grid(tot), kThreads, 0, s>>>(tot, b, tsrc, A.v, T.v);
+    NAIR_LAUNCH_CHECK();
+    setup_impl(a, nullptr, nullptr, nullptr, E, b, nnzb, true);
+  } catch (...) {
+    nair_free(a);
+    throw;
+  }
+  h->adj = a;
+}
+
+nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lam, nair_info *info) {
+  NAIR_API_BEGIN
+  if (!h || !w || !lam) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (!h->adj) build_adjoint(h);
+  return nair_solve(h->adj, w, lam, info);
+  NAIR_API_END
+}
+
+void nair_free(nair_handle *h) {
+  if (!h) return;
+  if (h->adj) nair_free(h->adj);
+  h->K.mem.release_all();
+  h->mem.release_all();
+  cudaStreamSynchronize(h->s);
+  delete h;
+}
+
+static const nair_handle *pick(const nair_handle *h, int adjoint) {
+  if (!h) fail(NAIR_ERR_INVALID_ARG, "null handle");
+  if (adjoint) {
+    if (!h->adj) fail(NAIR_ERR_INVALID_ARG, "no adjoint hierarchy yet (call nair_adjoint_solve first)");
+    return h->adj;
+  }
+  return h;
+}
+
+nair_status nair_num_levels(const nair_handle *h0, int32_t adjoint, int32_t *levels) {
+  NAIR_API_BEGIN
+  const nair_handle *h = pick(h0, adjoint);
+  if (!levels) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  *levels = h->mixed ? h->h32.nlev : h->h64.nlev;
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+template <typename T>
+static void sizes_t(const Hier<T> &H, int l, int64_t *o) {
+  const Level<T> &L = H.lev[l];
+  o[0] = L.E;
+  o[1] = L.A.nnzb;
+  o[2] = L.nC;
+  o[3] = L.nF;
+  o[4] = L.L.nnzb;
+  o[5] = L.Delta.nnzb;
+  o[6] = L.R.nnzb;
+  o[7] = 0;
+  o[8] = L.coarsest;
+  o[9] = L.cf_rounds;
+}
+
+nair_status nair_level_sizes(const nair_handle *h0, int32_t adjoint, int32_t level, int64_t *sizes) {
+  NAIR_API_BEGIN
+  const nair_handle *h = pick(h0, adjoint);
+  int nl = h->mixed ? h->h32.nlev : h->h64.nlev;
+  if (level < 0 || level >= nl || !sizes) return set_error(NAIR_ERR_INVALID_ARG, "level out of range");
+  if (h->mixed) sizes_t(h->h32, level, sizes);
+  else sizes_t(h->h64, level, sizes);
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+template <typename T>
+static void copy_vals(const T *src, size_t count, void *out, cudaStream_t s) {
+  if (!count) return;
+  if constexpr (std::is_same<T, double>::value) {
+    NAIR_CK(cudaMemcpyAsync(out, src, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+    NAIR_CK(cudaStreamSynchronize(s));
+  } else {
+    std::vector<T> tmp(count);
+    NAIR_CK(cudaMemcpyAsync(tmp.data(), src, sizeof(T) * count, cudaMemcpyDeviceToHost, s));
+    NAIR_CK(cudaStreamSynchronize(s));
+    double *o = (double *)out;
+    for (size_t i = 0; i < count; ++i) o[i] = (double)tmp[i];
+  }
+}
+
+static void copy_raw(const void *src, size_t bytes, void *out, cudaStream_t s) {
+  if (!bytes) return;
+  if (!src) fail(NAIR_ERR_INVALID_ARG, "array not available (keep_setup_data not set, or coarsest level)");
+  NAIR_CK(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, s));
+  NAIR_CK(cudaStreamSynchronize(s));
+}
+
+template <typename T>
+static void get_level_t(const Hier<T> &H, int l, int which, void *out, size_t cap, size_t *need,
+                        cudaStream_t s) {
+  const Level<T> &L = H.lev[l];
+  const size_t bb = (size_t)H.b * H.b;
+  size_t bytes = 0;
+  switch (which) {
+    case NAIR_A_ROWPTR: bytes = sizeof(int) * (L.E + 1); break;
+    case NAIR_A_COL: bytes = sizeof(int) * L.A.nnzb; break;
+    case NAIR_A_VALS: bytes = sizeof(double) * bb * L.A.nnzb; break;
+    case NAIR_DINV: bytes = sizeof(double) * bb * L.E; break;
+    case NAIR_CF: bytes = L.cf ? (size_t)L.E : 0; break;
+    case NAIR_P_MAP: bytes = L.ipc ? sizeof(int) * L.E : 0; break;
+    case NAIR_DELTA_ROWPTR: bytes = L.Delta.rp ? sizeof(int) * (L.nF + 1) : 0; break;
+    case NAIR_DELTA_COL: bytes = sizeof(int) * L.Delta.nnzb; break;
+    case NAIR_DELTA_VALS: bytes = sizeof(double) * bb * L.Delta.nnzb; break;
+    case NAIR_R_ROWPTR: bytes = L.R.rp ? sizeof(int) * (L.nC + 1) : 0; break;
+    case NAIR_R_COL: bytes = sizeof(int) * L.R.nnzb; break;
+    case NAIR_R_VALS: bytes = sizeof(double) * bb * L.R.nnzb; break;
+    case NAIR_STRONG: bytes = L.strong ? (size_t)L.A.nnzb : 0; break;
+    case NAIR_LAMBDA: bytes = L.lam ? sizeof(int) * L.E : 0; break;
+    case NAIR_L_ROWPTR: bytes = L.L.rp ? sizeof(int) * (L.nF + 1) : 0; break;
+    case NAIR_L_COL: bytes = sizeof(int) * L.L.nnzb; break;
+    case NAIR_L_VALS: bytes = sizeof(double) * bb * L.L.nnzb; break;
+    default: fail(NAIR_ERR_INVALID_ARG, "unknown level array");
+  }
+  if (need) *need = bytes;
+  if (!out) return;
+  if (cap < bytes) fail(NAIR_ERR_INVALID_ARG, "output buffer too small");
+  switch (which) {
+    case NAIR_A_ROWPTR: copy_raw(L.A.rp, bytes, out, s); break;
+    case NAIR_A_COL: copy_raw(L.A.ci, bytes, out, s); break;
+    case NAIR_A_VALS: copy_vals(L.A.v, bb * L.A.nnzb, out, s); break;
+    case NAIR_DINV: copy_vals(L.dinv, bb * L.E, out, s); break;
+    case NAIR_CF: copy_raw(L.cf, bytes, out, s); break;
+    case NAIR_P_MAP: copy_raw(L.ipc, bytes, out, s); break;
+    case NAIR_DELTA_ROWPTR: copy_raw(L.Delta.rp, bytes, out, s); break;
+    case NAIR_DELTA_COL: copy_raw(L.Delta.ci, bytes, out, s); break;
+    case NAIR_DELTA_VALS: copy_vals(L.Delta.v, bb * L.Delta.nnzb, out, s); break;
+    case NAIR_R_ROWPTR: copy_raw(L.R.rp, bytes, out, s); break;
+    case NAIR_R_COL: copy_raw(L.R_ci_f, bytes, out, s); break;
+    case NAIR_R_VALS: copy_vals(L.R.v, bb * L.R.nnzb, out, s); break;
+    case NAIR_STRONG: copy_raw(L.strong, bytes, out, s); break;
+    case NAIR_LAMBDA: copy_raw(L.lam, bytes, out, s); break;
+    case NAIR_L_ROWPTR: copy_raw(L.L.rp, bytes, out, s); break;
+    case NAIR_L_COL: copy_raw(L.L.ci, bytes, out, s); break;
+    case NAIR_L_VALS: copy_vals(L.L.v, bb * L.L.nnzb, out, s); break;
+  }
+}
+
+nair_status nair_get_level(const nair_handle *h0, int32_t adjoint, int32_t level, int32_t which,
+                           void *host_out, size_t cap, size_t *need) {
+  NAIR_API_BEGIN
+  const nair_handle *h = pick(h0, adjoint);
+  int nl = h->mixed ? h->h32.nlev : h->h64.nlev;
+  if (level < 0 || level >= nl) return set_error(NAIR_ERR_INVALID_ARG, "level out of range");
+  if (h->mixed) get_level_t(h->h32, level, which, host_out, cap, need, h->s);
+  else get_level_t(h->h64, level, which, host_out, cap, need, h->s);
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+nair_status nair_block_inverse(int32_t nblk, int32_t b, const double *A, double *Ainv, void *stream) {
+  NAIR_API_BEGIN
+  if (nblk < 0 || b < 1 || b > 32 || (nblk > 0 && (!A || !Ainv)))
+    return set_error(NAIR_ERR_INVALID_ARG, "bad block-inverse arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  Mem tmp;
+  tmp.s = s;
+  int *err = tmp.alloc<int>(1);
+  NAIR_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  block_inverses<double>(nblk, b, A, nullptr, Ainv, err, s);
+  if (read_int(err, s)) return set_error(NAIR_ERR_SINGULAR_BLOCK, "singular block");
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+nair_status nair_assemble_sigma(int32_t E, int32_t b, int64_t nnzb, const int32_t *diag_pos,
+                                const double *vals0, const double *M, const double *sigma,
+                                double *vals, void *stream) {
+  NAIR_API_BEGIN
+  if (E < 0 || b < 1 || b > 32 || nnzb < E || !diag_pos || !vals0 || !M || !sigma || !vals)
+    return set_error(NAIR_ERR_INVALID_ARG, "bad assemble arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  long long tot = nnzb * b * b;
+  if (vals != vals0) {
+    k_copy64<<<grid(tot), kThreads, 0, s>>>(tot, vals0, vals);
+    NAIR_LAUNCH_CHECK();
+  }
+  long long td = (long long)E * b * b;
+  k_assemble_sigma<<<grid(td), kThreads, 0, s>>>(E, b, diag_pos, vals0, M, sigma, vals);
+  NAIR_LAUNCH_CHECK();
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+nair_status nair_mass_apply(int32_t E, int32_t b, const double *M, const double *q, double *rhs, void *stream) {
+  NAIR_API_BEGIN
+  if (E < 0 || b < 1 || b > 32 || !M || !q || !rhs) return set_error(NAIR_ERR_INVALID_ARG, "bad mass arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_mass_apply<<<grid((long long)E * b), kThreads, 0, s>>>(E, b, M, q, rhs);
+  NAIR_LAUNCH_CHECK();
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+nair_status nair_gradients(int32_t E, int32_t b, const double *M, const double *lambda, const double *x,
+                           double *gsigma, double *gq, void *stream) {
+  NAIR_API_BEGIN
+  if (E < 0 || b < 1 || b > 32 || !M || !lambda || !x || !gsigma || !gq)
+    return set_error(NAIR_ERR_INVALID_ARG, "bad gradient arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  k_gradients<<<grid(E), kThreads, 0, s>>>(E, b, M, lambda, x, gsigma, gq);
+  NAIR_LAUNCH_CHECK();
+  return NAIR_OK;
+  NAIR_API_END
+}
+

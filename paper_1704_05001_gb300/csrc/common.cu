@@ -1,0 +1,153 @@
+// Errors, stream-ordered device memory and the exclusive scan used to turn
+// per-row counts into block-CSR row pointers.
+#include <atomic>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace nair {
+
+void fail(nair_status st, const std::string &msg) { throw NairError{st, msg}; }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+void ck_fail(cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e),
+           cudaGetErrorString(e), what, file, line);
+  throw NairError{e == cudaErrorMemoryAllocation ? NAIR_ERR_OOM : NAIR_ERR_CUDA, buf};
+}
+
+void *Mem::raw(size_t bytes) {
+  void *p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[160];
+    snprintf(buf, sizeof(buf), "device allocation of %zu bytes failed (%s)", bytes,
+             cudaGetErrorName(e));
+    fail(e == cudaErrorMemoryAllocation ? NAIR_ERR_OOM : NAIR_ERR_CUDA, buf);
+  }
+  ptrs.push_back(p);
+  return p;
+}
+
+void Mem::release(void *p) {
+  for (size_t i = 0; i < ptrs.size(); ++i)
+    if (ptrs[i] == p) {
+      cudaFreeAsync(p, s);
+      ptrs[i] = ptrs.back();
+      ptrs.pop_back();
+      return;
+    }
+}
+
+void Mem::release_all() {
+  for (void *p : ptrs) cudaFreeAsync(p, s);
+  ptrs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan: tiles of 2048 ints per CTA (256 threads x 8), tile sums
+// scanned recursively, then added back
+// ---------------------------------------------------------------------------
+static constexpr int kScanThreads = 256;
+static constexpr int kScanItems = 8;
+static constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int cta_exclusive_scan(int v, int *warp_sums, int *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < (kScanThreads / 32) ? warp_sums[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < (kScanThreads / 32)) warp_sums[lane] = wi - w;
+    if (lane == (kScanThreads / 32) - 1) *total = wi;
+  }
+  __syncthreads();
+  return inc - v + warp_sums[wid];
+}
+
+__global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, int n,
+                             int *__restrict__ tile_sums) {
+  __shared__ int warp_sums[kScanThreads / 32];
+  __shared__ int total;
+  const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = base + k;
+    v[k] = (i < n) ? in[i] : 0;
+    s += v[k];
+  }
+  int pre = cta_exclusive_scan(s, warp_sums, &total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    long long i = base + k;
+    if (i < n) out[i] = pre;
+    pre += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ tile_off) {
+  const long long base = (long long)blockIdx.x * kScanTile;
+  const int add = tile_off[blockIdx.x];
+  for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+    long long i = base + k;
+    if (i < n) out[i] += add;
+  }
+}
+
+__global__ void k_scan_total(int *out, int n, const int *in, const int *tile_total) {
+  // out[n] = out[n-1] + in[n-1] (or the single tile total when n fits one tile)
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = (n > 0) ? out[n - 1] + in[n - 1] : 0;
+  (void)tile_total;
+}
+
+static void scan_rec(const int *in, int *out, int n, cudaStream_t s, Mem &tmp) {
+  int tiles = cdiv(n, kScanTile);
+  int *sums = tmp.alloc<int>(tiles + 1);
+  k_scan_tiles<<<tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+  NAIR_LAUNCH_CHECK();
+  if (tiles > 1) {
+    int *offs = tmp.alloc<int>(tiles + 1);
+    scan_rec(sums, offs, tiles, s, tmp);
+    k_scan_add<<<tiles, kScanThreads, 0, s>>>(out, n, offs);
+    NAIR_LAUNCH_CHECK();
+    tmp.release(offs);
+  }
+  tmp.release(sums);
+}
+
+int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, Mem &tmp, bool want_total) {
+  if (n > 0) scan_rec(in, out, n, s, tmp);
+  k_scan_total<<<1, 32, 0, s>>>(out, n, in, nullptr);
+  NAIR_LAUNCH_CHECK();
+  if (!want_total) return -1;
+  return read_int(out + n, s);
+}
+
+int read_int(const int *p, cudaStream_t s) {
+  int v = 0;
+  NAIR_CK(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NAIR_CK(cudaStreamSynchronize(s));
+  return v;
+}
+
+}  // namespace nair

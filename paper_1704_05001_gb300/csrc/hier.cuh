@@ -1,0 +1,74 @@
+// Hierarchy data of the nAIR GPU library and the host-side entry points of
+// the setup and solve phases.
+#pragma once
+
+#include "common.cuh"
+
+namespace nair {
+
+// block-CSR matrix in device memory; values of type T, b x b row-major blocks
+template <typename T>
+struct DBsr {
+  int nrows = 0, ncols = 0, nnzb = 0;
+  int *rp = nullptr, *ci = nullptr;
+  T *v = nullptr;
+};
+
+// One level of the hierarchy (Sec. 5).  Index spaces: elements 0..E-1 of the
+// level; F elements numbered 0..nF-1 and C elements 0..nC-1 in ascending
+// element order (the C numbering is the next level's element numbering).
+template <typename T>
+struct Level {
+  int E = 0, nC = 0, nF = 0, coarsest = 0, cf_rounds = 0;
+  DBsr<T> A;               // level operator
+  int *diag = nullptr;     // position of the diagonal block of each row
+  T *dinv = nullptr;       // E inverse diagonal blocks (computed in FP64)
+  signed char *cf = nullptr;  // 1 = C, 0 = F
+  int *c2f = nullptr;      // coarse index -> element
+  int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
+  DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
+  int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)
+  // kept only with keep_setup_data
+  unsigned char *strong = nullptr;
+  int *lam = nullptr;
+  DBsr<T> L, Delta;
+  // coarsest level: dense inverse
+  int n = 0;
+  T *ainv = nullptr;
+  // V-cycle vectors
+  T *f = nullptr, *x = nullptr, *x2 = nullptr;
+};
+
+template <typename T>
+struct Hier {
+  int b = 0, nlev = 0;
+  std::vector<Level<T>> lev;
+  double setup_ms = 0.0;
+  double op_complexity = 0.0, cycle_complexity = 0.0;
+};
+
+struct Params {
+  double theta, filter_tol;
+  int filter_targets, k, f_sweeps, c_sweeps, max_levels, max_coarse, max_dense;
+  uint64_t seed;
+  int precision, restart, maxiter;
+  double tol;
+  int keep, use_graphs;
+};
+
+Params resolve_params(const nair_params *p, int b);
+
+// setup of the hierarchy for level-0 matrix A0 (device BSR, values T)
+template <typename T>
+void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &mem, Hier<T> &H);
+
+// V-cycle with zero initial guess on level 0: x = M^{-1} f (device vectors of T)
+template <typename T>
+void vcycle(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s);
+
+// diagonal-block inverses in FP64 of the blocks at positions pos[] (or 0..nblk-1)
+template <typename TI>
+void block_inverses(int nblk, int b, const TI *A, const int *pos, double *out, int *err_flag,
+                    cudaStream_t s);
+
+}  // namespace nair

@@ -1,0 +1,1027 @@
+// nAIR setup phase on the GPU (Sec. 4.1, 5.1, 5.2): diagonal-block inverses,
+// strength of connection, C/F splitting, truncated Neumann Delta, restriction
+// R = [-A_cf Delta  I], one-point interpolation and the coarse operator
+// K = R A P with filtering, level after level.
+//
+// Every value upstream of a threshold (block norms, Delta, R, K) is computed
+// with correctly rounded IEEE operations in one fixed order, whatever the
+// launch shape: block products c_rc = fma(a_rt, b_tc, c_rc) with t ascending,
+// summed over the inner block index in ascending order; squared norms
+// s = fma(x, x, s) in row-major order.  Threads parallelise over output
+// blocks and their scalars only, never over a summed index, so C/F splittings
+// and sparsity patterns are reproducible bit for bit.
+#include <algorithm>
+#include <type_traits>
+#include <climits>
+#include <cstdio>
+
+#include "hier.cuh"
+
+namespace nair {
+
+static constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// a1: diagonal-block inverses (in-place Gauss-Jordan, partial pivoting, FP64)
+// One thread per block row; bpc blocks per CTA staged in shared memory.
+// ---------------------------------------------------------------------------
+template <typename TI>
+__global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__ A,
+                                const int *__restrict__ pos, double *__restrict__ out,
+                                int *__restrict__ err) {
+  extern __shared__ double sm[];
+  int *piv = reinterpret_cast<int *>(sm + (size_t)bpc * b * b);
+  const int lb = threadIdx.x / b, t = threadIdx.x % b;
+  const long long blk = (long long)blockIdx.x * bpc + lb;
+  const bool active = lb < bpc && blk < nblk;
+  double *M = sm + (size_t)lb * b * b;
+  if (active) {
+    const TI *src = A + (size_t)(pos ? pos[blk] : blk) * b * b;
+    for (int c = 0; c < b; ++c) M[t * b + c] = (double)src[t * b + c];
+  }
+  __syncthreads();
+  bool sing = false;
+  for (int k = 0; k < b; ++k) {
+    int p = k;
+    if (active) {
+      double best = fabs(M[k * b + k]);
+      for (int r = k + 1; r < b; ++r) {
+        double a = fabs(M[r * b + k]);
+        if (a > best) { best = a; p = r; }
+      }
+      if (t == 0) piv[lb * 32 + k] = p;
+    }
+    __syncthreads();
+    if (active && p != k) {  // thread t swaps column t of rows k and p
+      double tmp = M[k * b + t];
+      M[k * b + t] = M[p * b + t];
+      M[p * b + t] = tmp;
+    }
+    __syncthreads();
+    const double d = active ? M[k * b + k] : 1.0;
+    if (active && (d == 0.0 || d != d)) sing = true;
+    __syncthreads();
+    if (active) {
+      double v = (t == k) ? 1.0 : M[k * b + t];
+      M[k * b + t] = __ddiv_rn(v, d);
+    }
+    __syncthreads();
+    if (active && t != k) {
+      double l = M[t * b + k];
+      M[t * b + k] = 0.0;
+      for (int c = 0; c < b; ++c) M[t * b + c] = __fma_rn(-l, M[k * b + c], M[t * b + c]);
+    }
+    __syncthreads();
+  }
+  if (active) {
+    for (int k = b - 1; k >= 0; --k) {
+      int p = piv[lb * 32 + k];
+      if (p != k) {
+        double tmp = M[t * b + k];
+        M[t * b + k] = M[t * b + p];
+        M[t * b + p] = tmp;
+      }
+    }
+    double *dst = out + (size_t)blk * b * b;
+    for (int c = 0; c < b; ++c) dst[t * b + c] = M[t * b + c];
+    if (sing) atomicOr(err, 1);
+  }
+}
+
+template <typename TI>
+void block_inverses(int nblk, int b, const TI *A, const int *pos, double *out, int *err,
+                    cudaStream_t s) {
+  if (nblk <= 0) return;
+  int bpc = std::max(1, kThreads / b);
+  size_t smem = (size_t)bpc * b * b * sizeof(double) + (size_t)bpc * 32 * sizeof(int);
+  if (smem > 48 * 1024) {
+    NAIR_CK(cudaFuncSetAttribute(k_block_inverse<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  }
+  k_block_inverse<TI><<<cdiv(nblk, bpc), bpc * b, smem, s>>>(nblk, b, bpc, A, pos, out, err);
+  NAIR_LAUNCH_CHECK();
+}
+template void block_inverses<double>(int, int, const double *, const int *, double *, int *, cudaStream_t);
+template void block_inverses<float>(int, int, const float *, const int *, double *, int *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// structure helpers
+// ---------------------------------------------------------------------------
+__global__ void k_validate(int E, int ncols, const int *__restrict__ rp, const int *__restrict__ ci,
+                           int nnzb, int *__restrict__ err) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  int a = rp[i], e = rp[i + 1];
+  if (a > e || a < 0 || e > nnzb) { atomicOr(err, 2); return; }
+  int prev = -1;
+  bool diag = false;
+  for (int p = a; p < e; ++p) {
+    int j = ci[p];
+    if (j <= prev || j >= ncols) { atomicOr(err, 2); return; }
+    prev = j;
+    diag |= (j == i);
+  }
+  if (!diag) atomicOr(err, 4);
+}
+
+__global__ void k_diag_pos(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                           int *__restrict__ dpos) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < E) dpos[i] = find_sorted(ci, rp[i], rp[i + 1], i);
+}
+
+__global__ void k_block_rows(int E, const int *__restrict__ rp, int *__restrict__ brow) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) brow[p] = i;
+}
+
+template <typename TO>
+__global__ void k_convert(long long n, const double *__restrict__ in, TO *__restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (TO)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// a2: squared block norms and strength
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T block_norm2(const T *__restrict__ x, int bb) {
+  T s = 0;
+  for (int k = 0; k < bb; ++k) s = fma_rn(x[k], x[k], s);
+  return s;
+}
+
+template <typename T>
+__global__ void k_block_norm2(int nnzb, int b, const T *__restrict__ v, T *__restrict__ s) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnzb) s[p] = block_norm2(v + (size_t)p * b * b, b * b);
+}
+
+template <typename T>
+__global__ void k_strength(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const T *__restrict__ s, T th2, unsigned char *__restrict__ strong) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  T smax = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] != i && s[p] > smax) smax = s[p];
+  const T thr = mul_rn(th2, smax);
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    strong[p] = (ci[p] != i && s[p] > (T)0 && s[p] >= thr) ? 1 : 0;
+}
+
+__global__ void k_lambda(int nnzb, const int *__restrict__ ci, const unsigned char *__restrict__ strong,
+                         int *__restrict__ lam) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnzb && strong[p]) atomicAdd(&lam[ci[p]], 1);
+}
+
+// ---------------------------------------------------------------------------
+// a3: C/F splitting by independent-set rounds (PMIS form of classical RS)
+// states: -1 undecided, 0 F, 1 C
+// ---------------------------------------------------------------------------
+__global__ void k_pmis_init(int E, const int *__restrict__ lam, signed char *__restrict__ st,
+                            uint64_t *__restrict__ h, uint64_t seed, int *__restrict__ mark) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  st[i] = lam[i] == 0 ? 0 : -1;
+  h[i] = splitmix64((uint64_t)i ^ seed);
+  mark[i] = -1;
+}
+
+__device__ __forceinline__ bool key_greater(int i, int j, const int *__restrict__ lam,
+                                            const uint64_t *__restrict__ h) {
+  if (lam[i] != lam[j]) return lam[i] > lam[j];
+  if (h[i] != h[j]) return h[i] > h[j];
+  return i > j;
+}
+
+__global__ void k_pmis_mark(int nnzb, const int *__restrict__ brow, const int *__restrict__ ci,
+                            const unsigned char *__restrict__ strong,
+                            const signed char *__restrict__ st, const int *__restrict__ lam,
+                            const uint64_t *__restrict__ h, int *__restrict__ mark, int round) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnzb || !strong[p]) return;
+  int i = brow[p], j = ci[p];
+  if (st[i] != -1 || st[j] != -1) return;
+  if (key_greater(j, i, lam, h)) mark[i] = round;
+  else mark[j] = round;
+}
+
+__global__ void k_pmis_select(int E, signed char *__restrict__ st, const int *__restrict__ mark,
+                              int round) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < E && st[i] == -1 && mark[i] != round) st[i] = 1;
+}
+
+__global__ void k_pmis_fmark(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const unsigned char *__restrict__ strong, signed char *__restrict__ st,
+                             int *__restrict__ remaining) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E || st[i] != -1) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (strong[p] && st[ci[p]] == 1) {
+      st[i] = 0;
+      return;
+    }
+  atomicAdd(remaining, 1);
+}
+
+__global__ void k_cf_flags(int E, const signed char *__restrict__ cf, int *__restrict__ isc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < E) isc[i] = cf[i] == 1;
+}
+
+__global__ void k_cf_index(int E, const signed char *__restrict__ cf, const int *__restrict__ pre,
+                           int *__restrict__ cidx, int *__restrict__ fidx, int *__restrict__ c2f,
+                           int *__restrict__ f2f) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  int c = pre[i];
+  if (cf[i] == 1) {
+    cidx[i] = c;
+    fidx[i] = -1;
+    c2f[c] = i;
+  } else {
+    cidx[i] = -1;
+    fidx[i] = i - c;
+    f2f[i - c] = i;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a6: one-point interpolation: strongest strong C neighbour, first on ties
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_one_point(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                            const unsigned char *__restrict__ strong, const T *__restrict__ s,
+                            const signed char *__restrict__ cf, const int *__restrict__ cidx,
+                            int *__restrict__ ipc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  if (cf[i] == 1) { ipc[i] = cidx[i]; return; }
+  int best = -1;
+  T bs = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (!strong[p] || cf[j] != 1) continue;
+    if (best < 0 || s[p] > bs) { best = j; bs = s[p]; }
+  }
+  ipc[i] = best < 0 ? -1 : cidx[best];
+}
+
+// ---------------------------------------------------------------------------
+// submatrix extraction: rows sel (rowmap), blocks whose column passes a test
+// mode 0: strong F-F blocks of F rows (for L); mode 1: F columns of C rows (A_cf)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool take_block(int mode, int p, int j, const unsigned char *strong,
+                                           const signed char *cf) {
+  return mode == 0 ? (strong[p] && cf[j] == 0) : (cf[j] == 0);
+}
+
+__global__ void k_sub_count(int nrows, int mode, const int *__restrict__ rowmap,
+                            const int *__restrict__ rp, const int *__restrict__ ci,
+                            const unsigned char *__restrict__ strong,
+                            const signed char *__restrict__ cf, int *__restrict__ cnt) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int i = rowmap[r], c = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) c += take_block(mode, p, ci[p], strong, cf);
+  cnt[r] = c;
+}
+
+__global__ void k_sub_fill(int nrows, int mode, const int *__restrict__ rowmap,
+                           const int *__restrict__ rp, const int *__restrict__ ci,
+                           const unsigned char *__restrict__ strong,
+                           const signed char *__restrict__ cf, const int *__restrict__ fidx,
+                           const int *__restrict__ orp, int *__restrict__ oci,
+                           int *__restrict__ osrc, int *__restrict__ orow) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  int i = rowmap[r], w = orp[r];
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int j = ci[p];
+    if (!take_block(mode, p, j, strong, cf)) continue;
+    oci[w] = fidx[j];
+    osrc[w] = p;
+    orow[w] = r;
+    ++w;
+  }
+}
+
+// L_ij = -(D_ii^{-1} A_ij): one block product from +0, then negated
+template <typename T>
+__global__ void k_L_values(long long total, int b, const int *__restrict__ orow,
+                           const int *__restrict__ osrc, const int *__restrict__ rowmap,
+                           const T *__restrict__ dinv, const T *__restrict__ Av, T *__restrict__ out) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long blk = g / bb;
+  const int rc = (int)(g - blk * bb), r = rc / b, c = rc - r * b;
+  const T *d = dinv + (size_t)rowmap[orow[blk]] * bb + r * b;
+  const T *a = Av + (size_t)osrc[blk] * bb + c;
+  T acc = 0;
+  for (int t = 0; t < b; ++t) acc = fma_rn(d[t], a[t * b], acc);
+  out[g] = -acc;
+}
+
+template <typename T>
+__global__ void k_copy_blocks(long long total, int b, const int *__restrict__ src,
+                              const T *__restrict__ in, T *__restrict__ out) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long blk = g / bb;
+  const int rc = (int)(g - blk * bb);
+  out[g] = in[(size_t)src[blk] * bb + rc];
+}
+
+__global__ void k_iota(int n, int *__restrict__ a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= n) a[i] = i;
+}
+
+__global__ void k_map(int n, const int *__restrict__ in, const int *__restrict__ m,
+                      int *__restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = m[in[i]];
+}
+
+// ---------------------------------------------------------------------------
+// Block sparse product  out_i = init_{imap(i)} + sum_{m in Left row i} Left_im * Right_{rmap(m)}
+// symbolic: the sorted union of the right rows (and init row), by repeated
+// extraction of the smallest head over per-entry cursors (thread per row).
+// ---------------------------------------------------------------------------
+struct SpgemmIdx {
+  int nrows;
+  const int *lrp, *lci, *rmap;
+  const int *rrp, *rci;
+  const int *irp, *ici, *imap;
+};
+
+template <bool FILL>
+__global__ void k_spgemm_symbolic(SpgemmIdx X, int *__restrict__ cursor, int *__restrict__ cnt,
+                                  const int *__restrict__ orp, int *__restrict__ oci,
+                                  int *__restrict__ orow) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= X.nrows) return;
+  const int l0 = X.lrp[i], l1 = X.lrp[i + 1];
+  for (int p = l0; p < l1; ++p) {
+    int m = X.rmap ? X.rmap[X.lci[p]] : X.lci[p];
+    cursor[p] = X.rrp[m];
+  }
+  int icur = 0, iend = 0;
+  if (X.irp) {
+    int ii = X.imap ? X.imap[i] : i;
+    icur = X.irp[ii];
+    iend = X.irp[ii + 1];
+  }
+  int count = 0;
+  int w = FILL ? orp[i] : 0;
+  for (;;) {
+    int jmin = INT_MAX;
+    if (icur < iend) jmin = X.ici[icur];
+    for (int p = l0; p < l1; ++p) {
+      int m = X.rmap ? X.rmap[X.lci[p]] : X.lci[p];
+      int cpos = cursor[p];
+      if (cpos < X.rrp[m + 1]) jmin = min(jmin, X.rci[cpos]);
+    }
+    if (jmin == INT_MAX) break;
+    if (FILL) {
+      oci[w] = jmin;
+      orow[w] = i;
+      ++w;
+    }
+    ++count;
+    if (icur < iend && X.ici[icur] == jmin) ++icur;
+    for (int p = l0; p < l1; ++p) {
+      int m = X.rmap ? X.rmap[X.lci[p]] : X.lci[p];
+      int cpos = cursor[p];
+      if (cpos < X.rrp[m + 1] && X.rci[cpos] == jmin) cursor[p] = cpos + 1;
+    }
+  }
+  if (!FILL) cnt[i] = count;
+}
+
+// numeric phase: one thread per output scalar (block, r, c); one fma chain over
+// (left entry m ascending, t ascending); the init block (if any) is the start value
+template <typename T>
+__global__ void k_spgemm_numeric(long long total, int b, SpgemmIdx X, const T *__restrict__ lv,
+                                 const T *__restrict__ rv, const T *__restrict__ iv,
+                                 const int *__restrict__ orow, const int *__restrict__ oci,
+                                 int negate, T *__restrict__ ov) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long blk = g / bb;
+  const int rc = (int)(g - blk * bb), r = rc / b, c = rc - r * b;
+  const int i = orow[blk], j = oci[blk];
+  T acc = 0;
+  if (X.irp) {
+    int ii = X.imap ? X.imap[i] : i;
+    int q = find_sorted(X.ici, X.irp[ii], X.irp[ii + 1], j);
+    if (q >= 0) acc = iv[(size_t)q * bb + rc];
+  }
+  for (int p = X.lrp[i]; p < X.lrp[i + 1]; ++p) {
+    int m = X.rmap ? X.rmap[X.lci[p]] : X.lci[p];
+    int q = find_sorted(X.rci, X.rrp[m], X.rrp[m + 1], j);
+    if (q < 0) continue;
+    const T *a = lv + (size_t)p * bb + r * b;
+    const T *bv = rv + (size_t)q * bb + c;
+    for (int t = 0; t < b; ++t) acc = fma_rn(a[t], bv[t * b], acc);
+  }
+  ov[g] = negate ? -acc : acc;
+}
+
+// ---------------------------------------------------------------------------
+// a8: filtering.  Drop X_ij (j != i) when ||X_ij||^2 <= tol^2 ||X_ii||^2
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_filter_flags(int nrows, int b, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const T *__restrict__ v, T tol2, int *__restrict__ newpos,
+                               int *__restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  const int bb = b * b;
+  T dn = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p)
+    if (ci[p] == i) dn = block_norm2(v + (size_t)p * bb, bb);
+  const T thr = mul_rn(tol2, dn);
+  int k = 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    bool keep = ci[p] == i || !(block_norm2(v + (size_t)p * bb, bb) <= thr);
+    newpos[p] = keep ? k++ : -1;
+  }
+  cnt[i] = k;
+}
+
+__global__ void k_filter_compact(int nrows, const int *__restrict__ rp, const int *__restrict__ ci,
+                                 const int *__restrict__ newpos, const int *__restrict__ nrp,
+                                 int *__restrict__ nci, int *__restrict__ src) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    int k = newpos[p];
+    if (k < 0) continue;
+    nci[nrp[i] + k] = ci[p];
+    src[nrp[i] + k] = p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a7: A P by column merge: (AP)_{r,J} = sum over j ascending with ipc(j) = J of A_rj
+// ---------------------------------------------------------------------------
+__global__ void k_ap_count(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                           const int *__restrict__ ipc, int *__restrict__ cnt) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= E) return;
+  int c = 0;
+  for (int p = rp[r]; p < rp[r + 1]; ++p) {
+    int J = ipc[ci[p]];
+    if (J < 0) continue;
+    bool dup = false;
+    for (int q = rp[r]; q < p && !dup; ++q) dup = ipc[ci[q]] == J;
+    c += !dup;
+  }
+  cnt[r] = c;
+}
+
+__global__ void k_ap_fill(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                          const int *__restrict__ ipc, const int *__restrict__ orp,
+                          int *__restrict__ oci, int *__restrict__ orow) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= E) return;
+  int w = orp[r], last = -1;
+  for (;;) {
+    int jmin = INT_MAX;
+    for (int p = rp[r]; p < rp[r + 1]; ++p) {
+      int J = ipc[ci[p]];
+      if (J > last && J < jmin) jmin = J;
+    }
+    if (jmin == INT_MAX) break;
+    oci[w] = jmin;
+    orow[w] = r;
+    ++w;
+    last = jmin;
+  }
+}
+
+template <typename T>
+__global__ void k_ap_values(long long total, int b, const int *__restrict__ orow,
+                            const int *__restrict__ oci, const int *__restrict__ rp,
+                            const int *__restrict__ ci, const int *__restrict__ ipc,
+                            const T *__restrict__ Av, T *__restrict__ out) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long blk = g / bb;
+  const int rc = (int)(g - blk * bb);
+  const int r = orow[blk], J = oci[blk];
+  T acc = 0;
+  bool first = true;
+  for (int p = rp[r]; p < rp[r + 1]; ++p) {
+    if (ipc[ci[p]] != J) continue;
+    T v = Av[(size_t)p * bb + rc];
+    acc = first ? v : add_rn(acc, v);
+    first = false;
+  }
+  out[g] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// a9: coarsest level: dense matrix and its inverse (single CTA Gauss-Jordan)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_dense_fill(long long total, int b, int n, const int *__restrict__ brow,
+                             const int *__restrict__ ci, const T *__restrict__ v,
+                             double *__restrict__ M) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long blk = g / bb;
+  const int rc = (int)(g - blk * bb), r = rc / b, c = rc - r * b;
+  M[(size_t)(brow[blk] * b + r) * n + ci[blk] * b + c] = (double)v[g];
+}
+
+static constexpr int kGjThreads = 1024;
+
+__global__ void __launch_bounds__(kGjThreads) k_dense_gj(int n, double *__restrict__ M, int *__restrict__ piv,
+                                                         double *__restrict__ lcol, int *__restrict__ err) {
+  __shared__ double rv[kGjThreads / 32];
+  __shared__ int ri[kGjThreads / 32];
+  __shared__ int pk;
+  __shared__ double dk;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = n;
+    for (int r = k + tid; r < n; r += blockDim.x) {
+      double a = fabs(M[(size_t)r * n + k]);
+      if (a > best || (a == best && r < bi)) { best = a; bi = r; }
+    }
+    for (int o = 16; o; o >>= 1) {
+      double ob = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b0 = rv[0];
+      int i0 = ri[0];
+      for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+        if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
+      pk = i0;
+      piv[k] = i0;
+    }
+    __syncthreads();
+    const int p = pk;
+    if (p != k)
+      for (int c = tid; c < n; c += blockDim.x) {
+        double t = M[(size_t)k * n + c];
+        M[(size_t)k * n + c] = M[(size_t)p * n + c];
+        M[(size_t)p * n + c] = t;
+      }
+    __syncthreads();
+    if (tid == 0) {
+      dk = M[(size_t)k * n + k];
+      if (dk == 0.0 || dk != dk) *err = 1;
+    }
+    __syncthreads();
+    const double d = dk;
+    for (int c = tid; c < n; c += blockDim.x) {
+      double v = (c == k) ? 1.0 : M[(size_t)k * n + c];
+      M[(size_t)k * n + c] = __ddiv_rn(v, d);
+    }
+    for (int r = tid; r < n; r += blockDim.x) {
+      lcol[r] = (r == k) ? 0.0 : M[(size_t)r * n + k];
+      if (r != k) M[(size_t)r * n + k] = 0.0;
+    }
+    __syncthreads();
+    for (long long g = tid; g < (long long)n * n; g += blockDim.x) {
+      int r = (int)(g / n), c = (int)(g - (long long)r * n);
+      if (r == k) continue;
+      M[g] = __fma_rn(-lcol[r], M[(size_t)k * n + c], M[g]);
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    int p = piv[k];
+    if (p != k)
+      for (int r = tid; r < n; r += blockDim.x) {
+        double t = M[(size_t)r * n + k];
+        M[(size_t)r * n + k] = M[(size_t)r * n + p];
+        M[(size_t)r * n + p] = t;
+      }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
+
+template <typename T>
+static void spgemm(int b, const SpgemmIdx &X, const T *lv, const T *rv, const T *iv, int negate,
+                   int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out) {
+  const int nrows = X.nrows;
+  int left_nnz = 0;
+  NAIR_CK(cudaMemcpyAsync(&left_nnz, X.lrp + nrows, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NAIR_CK(cudaStreamSynchronize(s));
+  int *cursor = tmp.alloc<int>(left_nnz + 1);
+  int *cnt = tmp.alloc<int>(nrows + 1);
+  out.nrows = nrows;
+  out.ncols = ncols;
+  out.rp = mem.alloc<int>(nrows + 1);
+  k_spgemm_symbolic<false><<<grid(nrows), kThreads, 0, s>>>(X, cursor, cnt, nullptr, nullptr, nullptr);
+  NAIR_LAUNCH_CHECK();
+  out.nnzb = exclusive_scan(cnt, out.rp, nrows, s, tmp);
+  out.ci = mem.alloc<int>(out.nnzb);
+  int *orow = tmp.alloc<int>(out.nnzb);
+  k_spgemm_symbolic<true><<<grid(nrows), kThreads, 0, s>>>(X, cursor, nullptr, out.rp, out.ci, orow);
+  NAIR_LAUNCH_CHECK();
+  out.v = mem.alloc<T>((size_t)out.nnzb * b * b);
+  long long total = (long long)out.nnzb * b * b;
+  if (total) {
+    k_spgemm_numeric<T><<<grid(total), kThreads, 0, s>>>(total, b, X, lv, rv, iv, orow, out.ci,
+                                                        negate, out.v);
+    NAIR_LAUNCH_CHECK();
+  }
+  tmp.release(orow);
+  tmp.release(cnt);
+  tmp.release(cursor);
+}
+
+template <typename T>
+static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M) {
+  const int nrows = M.nrows;
+  int *newpos = tmp.alloc<int>(M.nnzb);
+  int *cnt = tmp.alloc<int>(nrows + 1);
+  k_filter_flags<T><<<grid(nrows), kThreads, 0, s>>>(nrows, b, M.rp, M.ci, M.v, tol2, newpos, cnt);
+  NAIR_LAUNCH_CHECK();
+  int *nrp = mem.alloc<int>(nrows + 1);
+  int nn = exclusive_scan(cnt, nrp, nrows, s, tmp);
+  int *nci = mem.alloc<int>(nn);
+  int *src = tmp.alloc<int>(nn);
+  k_filter_compact<<<grid(nrows), kThreads, 0, s>>>(nrows, M.rp, M.ci, newpos, nrp, nci, src);
+  NAIR_LAUNCH_CHECK();
+  T *nv = mem.alloc<T>((size_t)nn * b * b);
+  long long total = (long long)nn * b * b;
+  if (total) {
+    k_copy_blocks<T><<<grid(total), kThreads, 0, s>>>(total, b, src, M.v, nv);
+    NAIR_LAUNCH_CHECK();
+  }
+  mem.release(M.rp);
+  mem.release(M.ci);
+  mem.release(M.v);
+  tmp.release(src);
+  tmp.release(cnt);
+  tmp.release(newpos);
+  M.rp = nrp;
+  M.ci = nci;
+  M.v = nv;
+  M.nnzb = nn;
+}
+
+template <typename T>
+static void release_bsr(Mem &mem, DBsr<T> &M) {
+  if (M.rp) mem.release(M.rp);
+  if (M.ci) mem.release(M.ci);
+  if (M.v) mem.release(M.v);
+  M = DBsr<T>();
+}
+
+static void check_flag(int *flag, cudaStream_t s, nair_status st, const char *msg) {
+  int v = read_int(flag, s);
+  if (v) fail(st, msg);
+}
+
+// extract rows `rowmap` (nrows of them) of A with the chosen column test
+template <typename T>
+static void extract(int b, int nrows, int mode, const int *rowmap, const Level<T> &L,
+                    const unsigned char *strong, const int *fidx, cudaStream_t s, Mem &mem,
+                    Mem &tmp, DBsr<T> &out, int **src_out, int **row_out) {
+  int *cnt = tmp.alloc<int>(nrows + 1);
+  k_sub_count<<<grid(nrows), kThreads, 0, s>>>(nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, cnt);
+  NAIR_LAUNCH_CHECK();
+  out.nrows = nrows;
+  out.rp = mem.alloc<int>(nrows + 1);
+  out.nnzb = exclusive_scan(cnt, out.rp, nrows, s, tmp);
+  out.ci = mem.alloc<int>(out.nnzb);
+  int *src = tmp.alloc<int>(out.nnzb);
+  int *row = tmp.alloc<int>(out.nnzb);
+  k_sub_fill<<<grid(nrows), kThreads, 0, s>>>(nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, fidx,
+                                               out.rp, out.ci, src, row);
+  NAIR_LAUNCH_CHECK();
+  out.v = mem.alloc<T>((size_t)out.nnzb * b * b);
+  tmp.release(cnt);
+  *src_out = src;
+  *row_out = row;
+}
+
+// Build level l + 1 from level l.  Returns false when level l must be the coarsest.
+template <typename T>
+static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem, Mem &tmp) {
+  const int b = H.b, bb = b * b;
+  Level<T> &L = H.lev[l];
+  const int E = L.E, nnzb = L.A.nnzb;
+  // a2: strength
+  T *snorm = tmp.alloc<T>(nnzb);
+  unsigned char *strong = (P.keep ? mem.alloc<unsigned char>(nnzb) : tmp.alloc<unsigned char>(nnzb));
+  k_block_norm2<T><<<grid(nnzb), kThreads, 0, s>>>(nnzb, b, L.A.v, snorm);
+  NAIR_LAUNCH_CHECK();
+  const T th2 = (T)(P.theta * P.theta);
+  k_strength<T><<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, snorm, th2, strong);
+  NAIR_LAUNCH_CHECK();
+  int *lam = P.keep ? mem.alloc<int>(E) : tmp.alloc<int>(E);
+  NAIR_CK(cudaMemsetAsync(lam, 0, sizeof(int) * E, s));
+  k_lambda<<<grid(nnzb), kThreads, 0, s>>>(nnzb, L.A.ci, strong, lam);
+  NAIR_LAUNCH_CHECK();
+  // a3: C/F splitting
+  L.cf = mem.alloc<signed char>(E);
+  uint64_t *hash = tmp.alloc<uint64_t>(E);
+  int *mark = tmp.alloc<int>(E);
+  int *brow = tmp.alloc<int>(nnzb);
+  int *remaining = tmp.alloc<int>(1);
+  k_block_rows<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, brow);
+  NAIR_LAUNCH_CHECK();
+  k_pmis_init<<<grid(E), kThreads, 0, s>>>(E, lam, L.cf, hash, P.seed, mark);
+  NAIR_LAUNCH_CHECK();
+  int rounds = 0;
+  for (;;) {
+    NAIR_CK(cudaMemsetAsync(remaining, 0, sizeof(int), s));
+    k_pmis_mark<<<grid(nnzb), kThreads, 0, s>>>(nnzb, brow, L.A.ci, strong, L.cf, lam, hash, mark, rounds);
+    NAIR_LAUNCH_CHECK();
+    k_pmis_select<<<grid(E), kThreads, 0, s>>>(E, L.cf, mark, rounds);
+    NAIR_LAUNCH_CHECK();
+    k_pmis_fmark<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, strong, L.cf, remaining);
+    NAIR_LAUNCH_CHECK();
+    ++rounds;
+    if (read_int(remaining, s) == 0) break;
+    if (rounds > E + 1) fail(NAIR_ERR_CUDA, "C/F splitting did not terminate");
+  }
+  L.cf_rounds = rounds;
+  int *isc = tmp.alloc<int>(E);
+  int *pre = tmp.alloc<int>(E + 1);
+  k_cf_flags<<<grid(E), kThreads, 0, s>>>(E, L.cf, isc);
+  NAIR_LAUNCH_CHECK();
+  const int nC = exclusive_scan(isc, pre, E, s, tmp);
+  const int nF = E - nC;
+  L.nC = nC;
+  L.nF = nF;
+  if (P.keep) {
+    L.strong = strong;
+    L.lam = lam;
+  }
+  if (nC == 0 || (long long)nC * 10 > (long long)E * 9) {
+    tmp.release_all();
+    return false;
+  }
+  int *cidx = tmp.alloc<int>(E), *fidx = tmp.alloc<int>(E);
+  L.c2f = mem.alloc<int>(nC);
+  int *f2f = tmp.alloc<int>(nF);
+  k_cf_index<<<grid(E), kThreads, 0, s>>>(E, L.cf, pre, cidx, fidx, L.c2f, f2f);
+  NAIR_LAUNCH_CHECK();
+
+  // a4: L = -D_ff^{-1} A^S_ff, then Horner T_{t+1} = D^{-1} + L T_t (Eq. neumann)
+  DBsr<T> Lm;
+  int *src, *row;
+  extract<T>(b, nF, 0, f2f, L, strong, fidx, s, mem, tmp, Lm, &src, &row);
+  Lm.ncols = nF;
+  long long tot = (long long)Lm.nnzb * bb;
+  if (tot) {
+    k_L_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, row, src, f2f, L.dinv, L.A.v, Lm.v);
+    NAIR_LAUNCH_CHECK();
+  }
+  tmp.release(src);
+  tmp.release(row);
+  DBsr<T> Dg;  // diagonal D_ff^{-1} as a block-CSR matrix
+  Dg.nrows = Dg.ncols = Dg.nnzb = nF;
+  Dg.rp = tmp.alloc<int>(nF + 1);
+  Dg.ci = Dg.rp;  // column i of row i: the same iota array
+  Dg.v = tmp.alloc<T>((size_t)nF * bb);
+  k_iota<<<grid(nF + 1), kThreads, 0, s>>>(nF, Dg.rp);
+  NAIR_LAUNCH_CHECK();
+  tot = (long long)nF * bb;
+  if (tot) {
+    k_copy_blocks<T><<<grid(tot), kThreads, 0, s>>>(tot, b, f2f, L.dinv, Dg.v);
+    NAIR_LAUNCH_CHECK();
+  }
+  DBsr<T> Tk;  // T_0 = D^{-1}
+  {
+    Tk.nrows = Tk.ncols = Tk.nnzb = nF;
+    Tk.rp = mem.alloc<int>(nF + 1);
+    Tk.ci = mem.alloc<int>(nF);
+    Tk.v = mem.alloc<T>((size_t)nF * bb);
+    NAIR_CK(cudaMemcpyAsync(Tk.rp, Dg.rp, sizeof(int) * (nF + 1), cudaMemcpyDeviceToDevice, s));
+    NAIR_CK(cudaMemcpyAsync(Tk.ci, Dg.rp, sizeof(int) * nF, cudaMemcpyDeviceToDevice, s));
+    NAIR_CK(cudaMemcpyAsync(Tk.v, Dg.v, sizeof(T) * nF * bb, cudaMemcpyDeviceToDevice, s));
+  }
+  const T tol2 = (T)(P.filter_tol * P.filter_tol);
+  for (int t = 0; t < P.k; ++t) {
+    SpgemmIdx X{nF, Lm.rp, Lm.ci, nullptr, Tk.rp, Tk.ci, Dg.rp, Dg.rp, nullptr};
+    DBsr<T> Tn;
+    spgemm<T>(b, X, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn);
+    if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn);
+    release_bsr(mem, Tk);
+    Tk = Tn;
+  }
+  tmp.release(Dg.v);
+  tmp.release(Dg.rp);
+
+  // a5: R_cf = -A_cf Delta over all A_cf blocks
+  DBsr<T> Acf;
+  extract<T>(b, nC, 1, L.c2f, L, strong, fidx, s, tmp, tmp, Acf, &src, &row);
+  tot = (long long)Acf.nnzb * bb;
+  if (tot) {
+    k_copy_blocks<T><<<grid(tot), kThreads, 0, s>>>(tot, b, src, L.A.v, Acf.v);
+    NAIR_LAUNCH_CHECK();
+  }
+  {
+    SpgemmIdx X{nC, Acf.rp, Acf.ci, nullptr, Tk.rp, Tk.ci, nullptr, nullptr, nullptr};
+    spgemm<T>(b, X, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R);
+  }
+  L.R_ci_f = L.R.ci;
+  L.R.ci = mem.alloc<int>(L.R.nnzb);
+  if (L.R.nnzb) {
+    k_map<<<grid(L.R.nnzb), kThreads, 0, s>>>(L.R.nnzb, L.R_ci_f, f2f, L.R.ci);
+    NAIR_LAUNCH_CHECK();
+  }
+  L.R.ncols = E;
+
+  // a6: one-point interpolation
+  L.ipc = mem.alloc<int>(E);
+  k_one_point<T><<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, strong, snorm, L.cf, cidx, L.ipc);
+  NAIR_LAUNCH_CHECK();
+
+  // a7: A P (column merge), then K = (AP)_C + R_cf (AP)_F
+  DBsr<T> AP;
+  {
+    int *cnt = tmp.alloc<int>(E + 1);
+    k_ap_count<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.ipc, cnt);
+    NAIR_LAUNCH_CHECK();
+    AP.nrows = E;
+    AP.ncols = nC;
+    AP.rp = tmp.alloc<int>(E + 1);
+    AP.nnzb = exclusive_scan(cnt, AP.rp, E, s, tmp);
+    AP.ci = tmp.alloc<int>(AP.nnzb);
+    int *aprow = tmp.alloc<int>(AP.nnzb);
+    k_ap_fill<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.ipc, AP.rp, AP.ci, aprow);
+    NAIR_LAUNCH_CHECK();
+    AP.v = tmp.alloc<T>((size_t)AP.nnzb * bb);
+    tot = (long long)AP.nnzb * bb;
+    if (tot) {
+      k_ap_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, aprow, AP.ci, L.A.rp, L.A.ci, L.ipc, L.A.v, AP.v);
+      NAIR_LAUNCH_CHECK();
+    }
+  }
+  Level<T> nx;
+  {
+    SpgemmIdx X{nC, L.R.rp, L.R.ci, nullptr, AP.rp, AP.ci, AP.rp, AP.ci, L.c2f};
+    spgemm<T>(b, X, L.R.v, AP.v, AP.v, 0, nC, s, mem, tmp, nx.A);
+    if (P.filter_targets & 2) filter<T>(b, tol2, s, mem, tmp, nx.A);
+  }
+  nx.E = nC;
+  if (P.keep) {
+    L.L = Lm;
+    L.Delta = Tk;
+  } else {
+    release_bsr(mem, Lm);
+    release_bsr(mem, Tk);
+  }
+  tmp.release_all();
+  H.lev.push_back(nx);
+  return true;
+}
+
+template <typename T>
+static void level_dinv(Hier<T> &H, Level<T> &L, cudaStream_t s, Mem &mem, Mem &tmp, int *err) {
+  const int b = H.b, E = L.E;
+  L.diag = mem.alloc<int>(E);
+  k_diag_pos<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.diag);
+  NAIR_LAUNCH_CHECK();
+  double *d64;
+  if constexpr (std::is_same<T, double>::value) {
+    L.dinv = mem.alloc<T>((size_t)E * b * b);
+    d64 = L.dinv;
+  } else {
+    d64 = tmp.alloc<double>((size_t)E * b * b);
+  }
+  block_inverses<T>(E, b, L.A.v, L.diag, d64, err, s);
+  if constexpr (!std::is_same<T, double>::value) {
+    L.dinv = mem.alloc<T>((size_t)E * b * b);
+    long long n = (long long)E * b * b;
+    k_convert<T><<<grid(n), kThreads, 0, s>>>(n, d64, L.dinv);
+    NAIR_LAUNCH_CHECK();
+    tmp.release(d64);
+  }
+  check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular diagonal block");
+}
+
+template <typename T>
+static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t s, Mem &mem,
+                          Mem &tmp, int *err) {
+  const int b = H.b;
+  const int n = L.E * b;
+  if (n > P.max_dense) {
+    char buf[200];
+    snprintf(buf, sizeof(buf),
+             "coarsest level has %d unknowns, above max_dense = %d (coarsening stalled)", n,
+             P.max_dense);
+    fail(NAIR_ERR_UNSUPPORTED, buf);
+  }
+  L.coarsest = 1;
+  L.n = n;
+  double *M = tmp.alloc<double>((size_t)n * n);
+  NAIR_CK(cudaMemsetAsync(M, 0, sizeof(double) * n * n, s));
+  int *brow = tmp.alloc<int>(L.A.nnzb);
+  k_block_rows<<<grid(L.E), kThreads, 0, s>>>(L.E, L.A.rp, brow);
+  NAIR_LAUNCH_CHECK();
+  long long tot = (long long)L.A.nnzb * b * b;
+  if (tot) {
+    k_dense_fill<T><<<grid(tot), kThreads, 0, s>>>(tot, b, n, brow, L.A.ci, L.A.v, M);
+    NAIR_LAUNCH_CHECK();
+  }
+  int *piv = tmp.alloc<int>(n);
+  double *lcol = tmp.alloc<double>(n);
+  k_dense_gj<<<1, kGjThreads, 0, s>>>(n, M, piv, lcol, err);
+  NAIR_LAUNCH_CHECK();
+  L.ainv = mem.alloc<T>((size_t)n * n);
+  tot = (long long)n * n;
+  k_convert<T><<<grid(tot), kThreads, 0, s>>>(tot, M, L.ainv);
+  NAIR_LAUNCH_CHECK();
+  check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular coarsest-level matrix");
+  tmp.release_all();
+}
+
+template <typename T>
+void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &mem, Hier<T> &H) {
+  Mem tmp;
+  tmp.s = s;
+  int *err = tmp.alloc<int>(1);
+  NAIR_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  H.lev.clear();
+  H.lev.reserve(P.max_levels + 1);
+  Level<T> l0;
+  l0.A = A0;
+  l0.E = A0.nrows;
+  H.lev.push_back(l0);
+  for (int l = 0;; ++l) {
+    Level<T> &L = H.lev[l];
+    level_dinv<T>(H, L, s, mem, tmp, err);
+    bool stop = (l == P.max_levels - 1) || (L.E <= P.max_coarse);
+    if (!stop) {
+      Mem ltmp;
+      ltmp.s = s;
+      stop = !coarsen<T>(H, l, P, s, mem, ltmp);
+    }
+    if (stop) {
+      Mem ctmp;
+      ctmp.s = s;
+      make_coarsest<T>(H, H.lev[l], P, s, mem, ctmp, err);
+      break;
+    }
+  }
+  H.nlev = (int)H.lev.size();
+  // V-cycle vectors and complexities (Sec. 6: OC and CC in work units)
+  const int b = H.b;
+  double nnz0 = (double)H.lev[0].A.nnzb, oc = 0.0, cc = 0.0;
+  for (int l = 0; l < H.nlev; ++l) {
+    Level<T> &L = H.lev[l];
+    size_t n = (size_t)L.E * b;
+    L.f = mem.alloc<T>(n);
+    L.x = mem.alloc<T>(n);
+    L.x2 = mem.alloc<T>(n);
+    double a = (double)L.A.nnzb / nnz0;
+    oc += a;
+    if (L.coarsest) {
+      cc += (double)L.n * L.n / (nnz0 * b * b);
+    } else {
+      // restriction + (f + c) sweeps over the selected rows, counted as full SpMVs
+      cc += a * (P.f_sweeps + P.c_sweeps) + (double)L.R.nnzb / nnz0;
+    }
+  }
+  H.op_complexity = oc;
+  H.cycle_complexity = cc;
+  NAIR_CK(cudaStreamSynchronize(s));
+}
+
+template void build_hierarchy<double>(const DBsr<double> &, const Params &, cudaStream_t, Mem &, Hier<double> &);
+template void build_hierarchy<float>(const DBsr<float> &, const Params &, cudaStream_t, Mem &, Hier<float> &);
+
+// validation kernel wrapper used by the API
+void validate_bsr(int E, int ncols, const int *rp, const int *ci, int nnzb, cudaStream_t s, Mem &tmp) {
+  int *err = tmp.alloc<int>(1);
+  NAIR_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+  k_validate<<<grid(E), kThreads, 0, s>>>(E, ncols, rp, ci, nnzb, err);
+  NAIR_LAUNCH_CHECK();
+  int v = read_int(err, s);
+  tmp.release(err);
+  if (v & 2) fail(NAIR_ERR_INVALID_ARG, "block CSR structure invalid (row pointers or unsorted/out-of-range columns)");
+  if (v & 4) fail(NAIR_ERR_INVALID_ARG, "a block row has no diagonal block");
+}
+
+}  // namespace nair

@@ -1,0 +1,402 @@
+// nAIR solve phase on the GPU: the V-cycle (Sec. 5: restriction of the
+// right-hand side with R = [R_cf I], recursion, one-point interpolation, then
+// block-Jacobi F- and C-relaxation, Eq. relax / Eq. cgc) and flexible GMRES(m)
+// with classical Gram-Schmidt applied twice (Sec. 6: GMRES acceleration).
+// The Krylov vectors, Arnoldi products and outer residuals are FP64; the
+// V-cycle runs in the hierarchy's precision T.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "solve.cuh"
+
+namespace nair {
+
+static constexpr int kThreads = 256;
+static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
+
+// ---------------------------------------------------------------------------
+// V-cycle kernels
+// ---------------------------------------------------------------------------
+
+// a11: f_c = f_C + R_cf f_F (zero initial guess, so the residual is f)
+template <typename T>
+__global__ void k_restrict(int nC, int b, const int *__restrict__ c2f, const int *__restrict__ rp,
+                           const int *__restrict__ ci, const T *__restrict__ rv,
+                           const T *__restrict__ f, T *__restrict__ fc) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)nC * b) return;
+  const int c = (int)(g / b), r = (int)(g - (long long)c * b), bb = b * b;
+  T acc = f[(size_t)c2f[c] * b + r];
+  for (int p = rp[c]; p < rp[c + 1]; ++p) {
+    const T *a = rv + (size_t)p * bb + r * b;
+    const T *ff = f + (size_t)ci[p] * b;
+    for (int t = 0; t < b; ++t) acc += a[t] * ff[t];
+  }
+  fc[g] = acc;
+}
+
+// a12: x = P x_c (C: own coarse value, F: one-point source, or 0)
+template <typename T>
+__global__ void k_prolong(int E, int b, const int *__restrict__ ipc, const T *__restrict__ xc,
+                          T *__restrict__ x) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)E * b) return;
+  const int i = (int)(g / b), r = (int)(g - (long long)i * b);
+  const int J = ipc[i];
+  x[g] = J >= 0 ? xc[(size_t)J * b + r] : (T)0;
+}
+
+// a13/a14: one block-Jacobi sweep on the rows with cf == which:
+// x_i <- x_i + D_ii^{-1} (f - A x)_i, all rows from the sweep's input x
+template <typename T>
+__global__ void k_jacobi(int E, int b, int rpc, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const T *__restrict__ v, const T *__restrict__ dinv,
+                         const signed char *__restrict__ cf, int which, const T *__restrict__ f,
+                         const T *__restrict__ xin, T *__restrict__ xout) {
+  extern __shared__ unsigned char smraw[];
+  T *sres = reinterpret_cast<T *>(smraw);
+  const int lr = threadIdx.x / b, r = threadIdx.x - lr * b, bb = b * b;
+  const int i = blockIdx.x * rpc + lr;
+  const bool active = lr < rpc && i < E;
+  const bool upd = active && cf[i] == which;
+  T res = 0;
+  if (upd) {
+    T acc = f[(size_t)i * b + r];
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const T *a = v + (size_t)p * bb + r * b;
+      const T *xj = xin + (size_t)ci[p] * b;
+      for (int c = 0; c < b; ++c) acc -= a[c] * xj[c];
+    }
+    res = acc;
+  }
+  if (lr < rpc) sres[lr * b + r] = res;
+  __syncthreads();
+  if (!active) return;
+  const size_t o = (size_t)i * b + r;
+  if (upd) {
+    const T *d = dinv + (size_t)i * bb + r * b;
+    T acc = 0;
+    for (int c = 0; c < b; ++c) acc += d[c] * sres[lr * b + c];
+    xout[o] = xin[o] + acc;
+  } else {
+    xout[o] = xin[o];
+  }
+}
+
+// a9: coarsest level, x = A_c^{-1} f (dense), one warp per row
+template <typename T>
+__global__ void k_dense_mv(int n, const T *__restrict__ M, const T *__restrict__ f, T *__restrict__ x) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const T *row = M + (size_t)warp * n;
+  T acc = 0;
+  for (int c = lane; c < n; c += 32) acc += row[c] * f[c];
+  for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[warp] = acc;
+}
+
+template <typename T>
+static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, cudaStream_t s) {
+  const Level<T> &L = H.lev[l];
+  const int b = H.b;
+  if (L.coarsest) {
+    k_dense_mv<T><<<cdiv((long long)L.n * 32, kThreads), kThreads, 0, s>>>(L.n, L.ainv, f, out);
+    NAIR_LAUNCH_CHECK();
+    return;
+  }
+  const Level<T> &N = H.lev[l + 1];
+  k_restrict<T><<<grid((long long)L.nC * b), kThreads, 0, s>>>(L.nC, b, L.c2f, L.R.rp, L.R.ci, L.R.v, f, N.f);
+  NAIR_LAUNCH_CHECK();
+  vcyc<T>(H, P, l + 1, N.f, N.x, s);
+  const int S = P.f_sweeps + P.c_sweeps;
+  T *other = L.x2;
+  T *cur = (S % 2 == 0) ? out : other;
+  T *nxt = (S % 2 == 0) ? other : out;
+  k_prolong<T><<<grid((long long)L.E * b), kThreads, 0, s>>>(L.E, b, L.ipc, N.x, cur);
+  NAIR_LAUNCH_CHECK();
+  const int rpc = std::max(1, kThreads / b);
+  const size_t smem = (size_t)rpc * b * sizeof(T);
+  for (int k = 0; k < S; ++k) {
+    int which = k < P.f_sweeps ? 0 : 1;
+    k_jacobi<T><<<cdiv(L.E, rpc), rpc * b, smem, s>>>(L.E, b, rpc, L.A.rp, L.A.ci, L.A.v, L.dinv, L.cf,
+                                                      which, f, cur, nxt);
+    NAIR_LAUNCH_CHECK();
+    T *t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+}
+
+template <typename T>
+void vcycle(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s) {
+  vcyc<T>(H, P, 0, f, x, s);
+}
+template void vcycle<double>(const Hier<double> &, const Params &, const double *, double *, cudaStream_t);
+template void vcycle<float>(const Hier<float> &, const Params &, const float *, float *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// FP64 Krylov kernels
+// ---------------------------------------------------------------------------
+
+// y = A x, or y = b - A x when b is given (a10), one thread per scalar row
+__global__ void k_spmv64(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const double *__restrict__ v, const double *__restrict__ x,
+                         const double *__restrict__ bvec, double *__restrict__ y) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)E * b) return;
+  const int i = (int)(g / b), r = (int)(g - (long long)i * b), bb = b * b;
+  double acc = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const double *a = v + (size_t)p * bb + r * b;
+    const double *xj = x + (size_t)ci[p] * b;
+    for (int c = 0; c < b; ++c) acc += a[c] * xj[c];
+  }
+  y[g] = bvec ? bvec[g] - acc : acc;
+}
+
+static constexpr int kDotGroup = 8;
+static constexpr int kDotCtas = 304;
+
+// partial[k * G + cta] = sum over this CTA's elements of V_k . w, k < nv
+__global__ void k_multidot(long long n, int nv, const double *__restrict__ V, long long ldv,
+                           const double *__restrict__ w, double *__restrict__ partial) {
+  __shared__ double red[kDotGroup][kThreads / 32];
+  const int G = gridDim.x;
+  const long long chunk = (n + G - 1) / G;
+  const long long lo = chunk * blockIdx.x, hi = min(n, lo + chunk);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nv; k0 += kDotGroup) {
+    double acc[kDotGroup];
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) acc[q] = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int q = 0; q < kDotGroup; ++q)
+        if (k0 + q < nv) acc[q] += V[(k0 + q) * ldv + i] * wi;
+    }
+#pragma unroll
+    for (int q = 0; q < kDotGroup; ++q) {
+      double a = acc[q];
+      for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      if (lane == 0) red[q][wid] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < kDotGroup && k0 + (int)threadIdx.x < nv) {
+      double a = 0.0;
+      for (int w2 = 0; w2 < kThreads / 32; ++w2) a += red[threadIdx.x][w2];
+      partial[(size_t)(k0 + threadIdx.x) * G + blockIdx.x] = a;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_reduce_partials(int nv, int G, const double *__restrict__ partial,
+                                  double *__restrict__ out) {
+  const int k = blockIdx.x, lane = threadIdx.x;
+  if (k >= nv) return;
+  double a = 0.0;
+  for (int c = lane; c < G; c += 32) a += partial[(size_t)k * G + c];
+  for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+  if (lane == 0) out[k] = a;
+}
+
+// w -= sum_k h_k V_k
+__global__ void k_axpy_multi(long long n, int nv, const double *__restrict__ V, long long ldv,
+                             const double *__restrict__ h, double *__restrict__ w) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = w[i];
+  for (int k = 0; k < nv; ++k) a -= h[k] * V[k * ldv + i];
+  w[i] = a;
+}
+
+// x += sum_k y_k Z_k
+__global__ void k_update(long long n, int nv, const double *__restrict__ Z, long long ldz,
+                         const double *__restrict__ y, double *__restrict__ x) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = x[i];
+  for (int k = 0; k < nv; ++k) a += y[k] * Z[k * ldz + i];
+  x[i] = a;
+}
+
+__global__ void k_div(long long n, const double *__restrict__ w, double d, double *__restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = w[i] / d;
+}
+
+template <typename A, typename B>
+__global__ void k_cast(long long n, const A *__restrict__ in, B *__restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (B)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+void Krylov::ensure(long long n_, int m_, cudaStream_t s) {
+  if (n == n_ && m == m_ && V) return;
+  mem.release_all();
+  mem.s = s;
+  n = n_;
+  m = m_;
+  V = mem.alloc<double>((size_t)n * (m + 1));
+  Z = mem.alloc<double>((size_t)n * m);
+  w = mem.alloc<double>(n);
+  partial = mem.alloc<double>((size_t)kDotCtas * (m + 2));
+  hdev = mem.alloc<double>(2 * (m + 2) + 2);
+  ydev = mem.alloc<double>(m + 1);
+  if (hhost) cudaFreeHost(hhost);
+  NAIR_CK(cudaMallocHost(&hhost, sizeof(double) * (2 * (m + 2) + 2 + m + 1)));
+}
+
+Krylov::~Krylov() {
+  if (hhost) cudaFreeHost(hhost);
+}
+
+static void multidot(Krylov &K, long long n, int nv, const double *V, const double *w, double *out,
+                     cudaStream_t s) {
+  k_multidot<<<kDotCtas, kThreads, 0, s>>>(n, nv, V, n, w, K.partial);
+  NAIR_LAUNCH_CHECK();
+  k_reduce_partials<<<nv, 32, 0, s>>>(nv, kDotCtas, K.partial, out);
+  NAIR_LAUNCH_CHECK();
+}
+
+template <typename T>
+void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s,
+             long long n) {
+  if constexpr (std::is_same<T, double>::value) {
+    vcycle<double>(H, P, v, z, s);
+  } else {
+    T *f0 = H.lev[0].f, *x0 = H.lev[0].x;
+    k_cast<double, T><<<grid(n), kThreads, 0, s>>>(n, v, f0);
+    NAIR_LAUNCH_CHECK();
+    vcycle<T>(H, P, f0, x0, s);
+    k_cast<T, double><<<grid(n), kThreads, 0, s>>>(n, x0, z);
+    NAIR_LAUNCH_CHECK();
+  }
+}
+template void precond<double>(const Hier<double> &, const Params &, const double *, double *, cudaStream_t, long long);
+template void precond<float>(const Hier<float> &, const Params &, const double *, double *, cudaStream_t, long long);
+
+void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s) {
+  k_spmv64<<<grid((long long)A.nrows * b), kThreads, 0, s>>>(A.nrows, b, A.rp, A.ci, A.v, x, bvec, y);
+  NAIR_LAUNCH_CHECK();
+}
+
+template <typename T>
+nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
+                   const double *bvec, double *x, std::vector<double> &hist, int *iters,
+                   double *relres, cudaStream_t s) {
+  const int b = H.b, m = P.restart;
+  const long long n = (long long)A.nrows * b;
+  K.ensure(n, m, s);
+  double *hh = K.hhost;  // [0, m+1): h1, [m+1, 2m+2): h2, [2m+2]: ||w||^2
+  std::vector<double> Hm((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  hist.clear();
+  // ||b||
+  multidot(K, n, 1, bvec, bvec, K.hdev, s);
+  NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  NAIR_CK(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(hh[0]);
+  int it = 0;
+  nair_status status = NAIR_ERR_NOT_CONVERGED;
+  if (bnorm == 0.0) {
+    NAIR_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    *iters = 0;
+    *relres = 0.0;
+    return NAIR_OK;
+  }
+  double *V = K.V, *Z = K.Z, *w = K.w;
+  for (;;) {
+    spmv64(A, b, x, bvec, w, s);
+    multidot(K, n, 1, w, w, K.hdev, s);
+    NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    NAIR_CK(cudaStreamSynchronize(s));
+    const double beta = std::sqrt(hh[0]);
+    if (!std::isfinite(beta)) return NAIR_ERR_BREAKDOWN;
+    if (hist.empty()) hist.push_back(beta / bnorm);
+    if (beta / bnorm <= P.tol) { status = NAIR_OK; break; }
+    if (it >= P.maxiter) break;
+    k_div<<<grid(n), kThreads, 0, s>>>(n, w, beta, V);
+    NAIR_LAUNCH_CHECK();
+    std::fill(g.begin(), g.end(), 0.0);
+    std::fill(Hm.begin(), Hm.end(), 0.0);
+    g[0] = beta;
+    int j;
+    bool conv = false, brk = false;
+    for (j = 0; j < m && it < P.maxiter; ++j) {
+      double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+      precond<T>(H, P, vj, zj, s, n);
+      ++it;
+      spmv64(A, b, zj, nullptr, w, s);
+      // classical Gram-Schmidt, twice
+      multidot(K, n, j + 1, V, w, K.hdev, s);
+      k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev, w);
+      NAIR_LAUNCH_CHECK();
+      multidot(K, n, j + 1, V, w, K.hdev + (m + 1), s);
+      k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev + (m + 1), w);
+      NAIR_LAUNCH_CHECK();
+      multidot(K, n, 1, w, w, K.hdev + 2 * (m + 1), s);
+      NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+      NAIR_CK(cudaStreamSynchronize(s));
+      for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hh[k] + hh[m + 1 + k];
+      const double hn = std::sqrt(hh[2 * (m + 1)]);
+      if (!std::isfinite(hn)) return NAIR_ERR_BREAKDOWN;
+      Hm[(size_t)(j + 1) * m + j] = hn;
+      if (hn != 0.0) {
+        k_div<<<grid(n), kThreads, 0, s>>>(n, w, hn, V + (size_t)(j + 1) * n);
+        NAIR_LAUNCH_CHECK();
+      }
+      for (int k = 0; k < j; ++k) {
+        double a = Hm[(size_t)k * m + j], c = Hm[(size_t)(k + 1) * m + j];
+        Hm[(size_t)k * m + j] = cs[k] * a + sn[k] * c;
+        Hm[(size_t)(k + 1) * m + j] = -sn[k] * a + cs[k] * c;
+      }
+      double a = Hm[(size_t)j * m + j], c = Hm[(size_t)(j + 1) * m + j];
+      double r = std::hypot(a, c);
+      cs[j] = a / r;
+      sn[j] = c / r;
+      Hm[(size_t)j * m + j] = r;
+      Hm[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      double est = std::fabs(g[j + 1]) / bnorm;
+      hist.push_back(est);
+      if (est <= P.tol) { conv = true; ++j; break; }
+      if (hn == 0.0) { brk = true; ++j; break; }
+    }
+    for (int r = j - 1; r >= 0; --r) {
+      double sum = g[r];
+      for (int c = r + 1; c < j; ++c) sum -= Hm[(size_t)r * m + c] * y[c];
+      y[r] = sum / Hm[(size_t)r * m + r];
+    }
+    double *yh = hh + 2 * (m + 2) + 2;
+    for (int k = 0; k < j; ++k) yh[k] = y[k];
+    NAIR_CK(cudaMemcpyAsync(K.ydev, yh, sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    k_update<<<grid(n), kThreads, 0, s>>>(n, j, Z, n, K.ydev, x);
+    NAIR_LAUNCH_CHECK();
+    if (conv || brk) { status = NAIR_OK; break; }
+    if (it >= P.maxiter) break;
+  }
+  spmv64(A, b, x, bvec, w, s);
+  multidot(K, n, 1, w, w, K.hdev, s);
+  NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  NAIR_CK(cudaStreamSynchronize(s));
+  *relres = std::sqrt(hh[0]) / bnorm;
+  *iters = it;
+  if (!std::isfinite(*relres)) return NAIR_ERR_BREAKDOWN;
+  if (status == NAIR_OK && *relres > 10.0 * P.tol && P.tol > 0) status = NAIR_ERR_NOT_CONVERGED;
+  return status;
+}
+
+template nair_status fgmres<double>(const DBsr<double> &, const Hier<double> &, const Params &, Krylov &,
+                                    const double *, double *, std::vector<double> &, int *, double *,
+                                    cudaStream_t);
+template nair_status fgmres<float>(const DBsr<double> &, const Hier<float> &, const Params &, Krylov &,
+                                   const double *, double *, std::vector<double> &, int *, double *,
+                                   cudaStream_t);
+
+}  // namespace nair

@@ -1,0 +1,33 @@
+// Solve-phase declarations: Krylov workspace, FP64 SpMV and flexible GMRES.
+#pragma once
+
+#include <type_traits>
+#include <vector>
+
+#include "hier.cuh"
+
+namespace nair {
+
+// FGMRES(m) workspace: basis V (m + 1 vectors), preconditioned vectors Z (m),
+// one work vector, Arnoldi partial sums and a pinned host staging buffer
+struct Krylov {
+  Mem mem;
+  long long n = 0;
+  int m = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *partial = nullptr, *hdev = nullptr,
+         *ydev = nullptr, *hhost = nullptr;
+  void ensure(long long n, int m, cudaStream_t s);
+  ~Krylov();
+};
+
+void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s);
+
+template <typename T>
+void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s, long long n);
+
+template <typename T>
+nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
+                   const double *bvec, double *x, std::vector<double> &hist, int *iters,
+                   double *relres, cudaStream_t s);
+
+}  // namespace nair

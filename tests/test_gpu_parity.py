@@ -1,0 +1,292 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Bar (from the method's arithmetic): bit-exact C/F splittings, strength flags,
+interpolation maps and sparsity patterns; hierarchy values identical (the GPU
+setup uses the oracle's canonical fma order, so equality is expected, and the
+test allows 1e-12 relative per row); residual histories within 1e-12 absolute
+(they are already relative to ||b||) with identical iteration counts.
+"""
+import numpy as np
+import pytest
+
+import dgtransport as D
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nair():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1704_05001_gb300 as nair
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return nair
+
+
+@pytest.fixture(scope="module")
+def oracle_mod():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_rows(a, b):
+    """max over block rows of |a - b| / max |b| in that row (values as (nnzb, b, b))."""
+    if a.size == 0:
+        return 0.0
+    d = np.abs(a - b).reshape(len(a), -1).max(axis=1)
+    s = np.maximum(np.abs(b).reshape(len(b), -1).max(axis=1), 1e-300)
+    return float(np.max(d / s))
+
+
+CASES = [
+    ("C1", 32, 1, 1),       # full C1: P1, constant flow, triangular
+    ("C2", 16, 2, 2),       # P2 rotating flow, log-normal sigma
+    ("C3", 6, 6, 1),        # P6 jittered, b = 28
+    ("C5", 12, 3, 1),       # P3 jittered rotating
+    ("C3", 10, 4, 2),       # b = 15, k = 2
+]
+
+
+def compare_hierarchies(S, H, b, check_setup_data=True):
+    assert S.num_levels() == H.nlev
+    for l in range(H.nlev):
+        g = S.level(l)
+        o = H.level(l)
+        assert g["E"] == o["E"] and g["nnzb"] == o["nnzb"], f"level {l} sizes"
+        assert np.array_equal(g["row_ptr"], o["row_ptr"]), f"level {l} row pointers"
+        assert np.array_equal(g["col"], o["col"]), f"level {l} pattern"
+        assert rel_rows(g["vals"], o["vals"]) <= 1e-12, f"level {l} values"
+        assert np.array_equal(g["dinv"], o["dinv"]), f"level {l} diagonal inverses"
+        if o["coarsest"]:
+            continue
+        assert np.array_equal(g["cf"], o["cf"]), f"level {l} C/F"
+        assert np.array_equal(g["ipc"], o["ipc"]), f"level {l} interpolation"
+        assert np.array_equal(g["R_rp"], o["R_rp"]) and np.array_equal(g["R_ci"], o["R_ci"]), f"level {l} R pattern"
+        assert rel_rows(g["R_v"], o["R_v"]) <= 1e-12, f"level {l} R values"
+        if check_setup_data:
+            assert np.array_equal(g["strong"], o["strong"]), f"level {l} strength"
+            assert np.array_equal(g["lam"], o["lam"]), f"level {l} lambda"
+            assert np.array_equal(g["D_rp"], o["D_rp"]) and np.array_equal(g["D_ci"], o["D_ci"]), f"level {l} Delta pattern"
+            assert rel_rows(g["D_v"], o["D_v"]) <= 1e-12, f"level {l} Delta values"
+            assert np.array_equal(g["L_ci"], o["L_ci"]), f"level {l} L pattern"
+            assert rel_rows(g["L_v"], o["L_v"]) <= 1e-12, f"level {l} L values"
+
+
+@pytest.mark.parametrize("b", [1, 3, 6, 10, 28, 32])
+def test_block_inverse_bitwise(nair, oracle_mod, b):
+    r = np.random.default_rng(100 + b)
+    nblk = 333
+    A = r.standard_normal((nblk, b, b)) + np.eye(b) * (0.5 * b)
+    X = nair.block_inverse(dev(A)).cpu().numpy()
+    for k in range(nblk):
+        assert np.array_equal(X[k], oracle_mod.block_inverse(A[k]))
+
+
+def test_block_inverse_singular(nair):
+    A = np.ones((4, 3, 3))
+    with pytest.raises(nair.NairError) as e:
+        nair.block_inverse(dev(A))
+    assert e.value.status == 2
+
+
+@pytest.mark.parametrize("name,N,p,k", CASES)
+def test_hierarchy_and_solve_parity(nair, oracle_mod, name, N, p, k):
+    P = D.make_problem(name, N=N, p=p)
+    b = P["b"]
+    params = dict(neumann_degree=k, max_coarse=4)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), keep_setup_data=1, **params)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params)
+    compare_hierarchies(S, H, b)
+    x, rep = S.solve(dev(P["rhs"]))
+    ref = H.solve(P["rhs"])
+    assert ref["status"] == 0
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    assert rep["rel_res"] <= 1e-10
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(xs - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    # one V-cycle on a seeded vector
+    f = D.rng.uniform(7, P["n"]) - 0.5
+    z = S.vcycle(dev(f)).cpu().numpy()
+    zr = H.vcycle(f)
+    assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    S.close()
+
+
+def test_exact_settings_one_cycle(nair):
+    """theta = 0, no filtering, k and F sweeps beyond the F-graph depth: one
+    V-cycle solves the triangular system (Lemma ideal restriction)."""
+    P = D.make_problem("C1", N=6, p=1)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), strength_theta=0.0,
+                        filter_targets=0, neumann_degree=64, f_sweeps=64, max_coarse=2)
+    x = S.vcycle(dev(P["rhs"])).cpu().numpy()
+    from conftest import bsr_dense
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    xs = np.linalg.solve(A, P["rhs"])
+    assert np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_edge_single_element(nair, oracle_mod):
+    """E = 1: the fine level is the coarsest; the dense solve is the whole method."""
+    r = np.random.default_rng(5)
+    A = (r.standard_normal((1, 6, 6)) + 6 * np.eye(6))
+    rp = np.array([0, 1], dtype=np.int32)
+    ci = np.array([0], dtype=np.int32)
+    rhs = r.standard_normal(6)
+    S = nair.NairSolver(dev(rp), dev(ci), dev(A))
+    x, rep = S.solve(dev(rhs))
+    assert S.num_levels() == 1
+    assert np.allclose(x.cpu().numpy(), np.linalg.solve(A[0], rhs), rtol=1e-12, atol=1e-14)
+    assert rep["iterations"] == 1
+
+
+def test_edge_chain_b1(nair, oracle_mod):
+    """Scalar 1D upwind chain (b = 1), a ragged multi-level case."""
+    n = 1000
+    rp, col, vals = [0], [], []
+    for i in range(n):
+        if i > 0:
+            col.append(i - 1)
+            vals.append(-0.9)
+        col.append(i)
+        vals.append(1.0)
+        rp.append(len(col))
+    rp = np.array(rp, dtype=np.int32)
+    col = np.array(col, dtype=np.int32)
+    vals = np.array(vals).reshape(-1, 1, 1)
+    rhs = np.ones(n)
+    S = nair.NairSolver(dev(rp), dev(col), dev(vals), keep_setup_data=1, max_coarse=4)
+    H = oracle_mod.Hierarchy(rp, col, vals, max_coarse=4)
+    compare_hierarchies(S, H, 1)
+    x, rep = S.solve(dev(rhs))
+    ref = H.solve(rhs)
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+
+
+def test_edge_block32_triangular(nair, oracle_mod):
+    """Largest block size (b = 32) on a random block lower-triangular matrix."""
+    r = np.random.default_rng(32)
+    E, b = 40, 32
+    rp, col, vals = [0], [], []
+    for i in range(E):
+        nb = sorted(set(int(j) for j in r.integers(0, i, size=min(i, 3)))) if i else []
+        for j in nb:
+            col.append(j)
+            vals.append(r.standard_normal((b, b)) * 0.05)
+        col.append(i)
+        vals.append(r.standard_normal((b, b)) + b * np.eye(b))
+        rp.append(len(col))
+    rp = np.array(rp, dtype=np.int32)
+    col = np.array(col, dtype=np.int32)
+    vals = np.array(vals)
+    rhs = r.standard_normal(E * b)
+    S = nair.NairSolver(dev(rp), dev(col), dev(vals), keep_setup_data=1, max_coarse=4)
+    H = oracle_mod.Hierarchy(rp, col, vals, max_coarse=4)
+    compare_hierarchies(S, H, b)
+    x, rep = S.solve(dev(rhs))
+    ref = H.solve(rhs)
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+
+
+def test_invalid_inputs_rejected(nair):
+    P = D.make_problem("C1", N=4)
+    col = P["col"].copy()
+    col[[1, 2]] = col[[2, 1]]  # unsorted row
+    with pytest.raises(nair.NairError) as e:
+        nair.NairSolver(dev(P["row_ptr"]), dev(col), dev(P["vals"]))
+    assert e.value.status == 1
+    vals = P["vals"].copy()
+    vals[P["diag_pos"][3]] = 0.0
+    with pytest.raises(nair.NairError) as e:
+        nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(vals))
+    assert e.value.status == 2
+
+
+def test_zero_rhs_and_maxiter(nair):
+    P = D.make_problem("C2", N=8)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), maxiter=1, neumann_degree=2)
+    x, rep = S.solve(dev(np.zeros(P["n"])))
+    assert rep["iterations"] == 0 and float(x.abs().max()) == 0.0
+    x, rep = S.solve(dev(P["rhs"]), check=False)
+    assert rep["status"] == 3 and rep["iterations"] == 1
+
+
+def test_adjoint_parity_and_gradients(nair, oracle_mod):
+    P = D.make_problem("C2", N=12, keep_parts=True)
+    b, E, n = P["b"], P["E"], P["n"]
+    params = dict(neumann_degree=2, max_coarse=4)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), keep_setup_data=1, **params)
+    w = D.functional_weights(n)
+    lam, rep = S.adjoint_solve(dev(w))
+    trp, tci, tv = oracle_mod.transpose(P["row_ptr"], P["col"], P["vals"])
+    Ht = oracle_mod.Hierarchy(trp, tci, tv, **params)
+    ref = Ht.solve(w)
+    assert S.num_levels(adjoint=True) == Ht.nlev
+    for l in range(Ht.nlev - 1):
+        assert np.array_equal(S.level(l, adjoint=True)["cf"], Ht.level(l)["cf"])
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    x, _ = S.solve(dev(P["rhs"]))
+    gs, gq = nair.gradients(dev(P["mass"]), lam, x)
+    ogs, ogq = oracle_mod.gradients(P["mass"], lam.cpu().numpy(), x.cpu().numpy())
+    assert np.allclose(gs.cpu().numpy(), ogs, rtol=1e-12, atol=1e-15 * np.abs(ogs).max())
+    assert np.allclose(gq.cpu().numpy(), ogq, rtol=1e-12, atol=1e-15 * np.abs(ogq).max())
+
+
+def test_autograd_against_finite_differences(nair):
+    """dJ/dq and dJ/dsigma from the adjoint solve vs central differences
+    (eps = 1e-6, forward solves to 1e-13) on seeded coordinates."""
+    P = D.make_problem("C4", N=8, keep_parts=True)
+    n, E = P["n"], P["E"]
+    w = dev(D.functional_weights(n))
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals0"]), dev(P["diag_pos"]), dev(P["mass"]))
+    params = dict(neumann_degree=2, tol=1e-13, max_coarse=4)
+    q = dev(P["q"]).requires_grad_(True)
+    sig = dev(P["sigma"]).requires_grad_(True)
+    x = nair.NairSolve.apply(q, sig, *args, params)
+    J = (w * x).sum()
+    J.backward()
+    iq, isg = D.fd_coordinates(n, E, count=8)
+    eps = 1e-6
+
+    def Jof(qv, sv):
+        with torch.no_grad():
+            return float((w * nair.NairSolve.apply(qv, sv, *args, params)).sum())
+
+    for i in iq:
+        qp, qm = q.detach().clone(), q.detach().clone()
+        qp[i] += eps
+        qm[i] -= eps
+        fd = (Jof(qp, sig.detach()) - Jof(qm, sig.detach())) / (2 * eps)
+        assert abs(fd - float(q.grad[i])) <= 1e-6 * max(1.0, abs(fd))
+    for e in isg:
+        sp, sm = sig.detach().clone(), sig.detach().clone()
+        sp[e] += eps
+        sm[e] -= eps
+        fd = (Jof(q.detach(), sp) - Jof(q.detach(), sm)) / (2 * eps)
+        assert abs(fd - float(sig.grad[e])) <= 1e-6 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("name,N,p,k", [("C3", 16, 6, 1), ("C5", 24, 3, 1), ("C2", 32, 2, 2)])
+def test_mixed_precision_accuracy(nair, name, N, p, k):
+    """FP32 hierarchy and V-cycle inside FP64 FGMRES: FP64 residual <= 1e-10
+    and the solution within cond * 1e-10 of the all-FP64 solve."""
+    P = D.make_problem(name, N=N, p=p)
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    S64 = nair.NairSolver(*args, neumann_degree=k)
+    S32 = nair.NairSolver(*args, neumann_degree=k, precision="mixed")
+    rhs = dev(P["rhs"])
+    x64, r64 = S64.solve(rhs)
+    x32, r32 = S32.solve(rhs)
+    assert r64["rel_res"] <= 1e-10 and r32["rel_res"] <= 1e-10
+    err = float((x32 - x64).norm() / x64.norm())
+    assert err <= 1e-8, err
