@@ -433,6 +433,9 @@ nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lam, nai
 void nair_free(nair_handle *h) {
   if (!h) return;
   if (h->adj) nair_free(h->adj);
+  cudaStreamSynchronize(h->s);
+  release_graph(h->h64.graph);
+  release_graph(h->h32.graph);
   h->K.mem.release_all();
   h->mem.release_all();
   cudaStreamSynchronize(h->s);

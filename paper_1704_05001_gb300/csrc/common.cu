@@ -11,6 +11,7 @@ void fail(nair_status st, const std::string &msg) { throw NairError{st, msg}; }
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void ck_fail(cudaError_t e, const char *what, const char *file, int line) {

@@ -31,6 +31,7 @@ void ck_fail(cudaError_t e, const char *what, const char *file, int line);
 
 // every kernel launch is followed by this check, which also counts the launch
 void count_launch();
+void add_launches(long long n);
 long long launch_count();
 #define NAIR_LAUNCH_CHECK()        \
   do {                             \

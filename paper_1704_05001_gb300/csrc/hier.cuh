@@ -39,10 +39,21 @@ struct Level {
   T *f = nullptr, *x = nullptr, *x2 = nullptr;
 };
 
+// The V-cycle replayed as one CUDA graph: it reads its input from and writes its
+// output to the two device pointers in dptr (set before each launch), so one
+// instantiated graph serves every Krylov vector.
+struct VGraph {
+  cudaGraphExec_t exec = nullptr;
+  void **dptr = nullptr;  // device: [0] input (double*), [1] output (double*)
+  void **hptr = nullptr;  // pinned host staging of the two pointers
+  long long nodes = 0;    // kernels per replay
+};
+
 template <typename T>
 struct Hier {
   int b = 0, nlev = 0;
   std::vector<Level<T>> lev;
+  mutable VGraph graph;
   double setup_ms = 0.0;
   double op_complexity = 0.0, cycle_complexity = 0.0;
 };
@@ -65,6 +76,9 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
 // V-cycle with zero initial guess on level 0: x = M^{-1} f (device vectors of T)
 template <typename T>
 void vcycle(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s);
+
+// release the V-cycle graph of a hierarchy
+void release_graph(VGraph &g);
 
 // diagonal-block inverses in FP64 of the blocks at positions pos[] (or 0..nblk-1)
 template <typename TI>

@@ -1,0 +1,131 @@
+// Block-row kernels of the solve phase (a10-a14): SpMV, residual, block
+// Jacobi sweep (optionally reading its input through the one-point
+// interpolation, which fuses x = P x_c into the first sweep) and restriction.
+//
+// A team of G x b threads owns one block row: thread (g, r) accumulates output
+// component r over the row's blocks p = start + g, start + g + G, ...; the G
+// partial sums are then added in fixed order g = 0..G-1.  b is a template
+// parameter for the common DG block sizes so that the b loads of a block row
+// and of x_j are issued back to back (no exposed latency per scalar), with a
+// runtime-b fallback.  G > 1 is used on coarse levels, whose rows are long and
+// few, to shorten the serial chain per thread.
+#pragma once
+
+#include "common.cuh"
+
+namespace nair {
+
+enum RowOp { OP_SPMV = 0, OP_RESID = 1, OP_JACOBI = 2, OP_RESTRICT = 3 };
+
+template <typename T>
+struct RowArgs {
+  int nrows, b, G, tpc;
+  const int *rp, *ci;
+  const T *v;
+  const T *x;            // input vector; read as x[ipc[j]] (or 0) when ipc is set
+  const int *ipc;
+  const T *f;            // right-hand side (RESID, JACOBI) or fine vector (RESTRICT)
+  const int *c2f;        // RESTRICT: coarse row -> fine element of its identity part
+  const T *dinv;         // JACOBI: inverse diagonal blocks
+  const signed char *cf; // JACOBI: row class
+  int which;             // JACOBI: update rows with cf == which
+  T *out;
+};
+
+template <typename T, int B>
+__device__ __forceinline__ T xval(const T *__restrict__ x, const int *__restrict__ ipc, int j, int c, int b) {
+  const int bt = B > 0 ? B : b;
+  if (ipc) {
+    const int J = ipc[j];
+    return J >= 0 ? x[(size_t)J * bt + c] : (T)0;
+  }
+  return x[(size_t)j * bt + c];
+}
+
+template <typename T, int B>
+__device__ __forceinline__ T row_partial(const RowArgs<T> &a, int i, int g, int r) {
+  const int b = B > 0 ? B : a.b;
+  const int bb = b * b;
+  T acc = 0;
+  const int p1 = a.rp[i + 1];
+  for (int p = a.rp[i] + g; p < p1; p += a.G) {
+    const int j = a.ci[p];
+    const T *av = a.v + (size_t)p * bb + r * b;
+    if constexpr (B > 0) {
+      T va[B], vx[B];
+      if (a.ipc) {
+        const int J = a.ipc[j];
+        if (J < 0) continue;
+        const T *xj = a.x + (size_t)J * B;
+#pragma unroll
+        for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
+      } else {
+        const T *xj = a.x + (size_t)j * B;
+#pragma unroll
+        for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
+      }
+#pragma unroll
+      for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
+    } else {
+#pragma unroll 4
+      for (int c = 0; c < b; ++c) acc = fma(av[c], xval<T, 0>(a.x, a.ipc, j, c, b), acc);
+    }
+  }
+  return acc;
+}
+
+template <typename T, int B, int OP>
+__global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
+  extern __shared__ unsigned char smraw[];
+  T *red = reinterpret_cast<T *>(smraw);             // [tpc][G][b]
+  const int b = B > 0 ? B : a.b;
+  const int tsz = a.G * b;
+  T *sres = red + (size_t)a.tpc * tsz;               // [tpc][b]
+  const int team = threadIdx.x / tsz, lt = threadIdx.x - team * tsz;
+  const int g = lt / b, r = lt - g * b;
+  const int i = blockIdx.x * a.tpc + team;
+  const bool active = team < a.tpc && i < a.nrows;
+  bool upd = active;
+  if (OP == OP_JACOBI && active) upd = a.cf[i] == a.which;
+  T acc = 0;
+  if (upd) acc = row_partial<T, B>(a, i, g, r);
+  if (a.G > 1) {
+    if (team < a.tpc) red[(size_t)team * tsz + lt] = acc;
+    __syncthreads();
+    if (g == 0 && upd) {
+      for (int gg = 1; gg < a.G; ++gg) acc += red[(size_t)team * tsz + gg * b + r];
+    }
+  }
+  if (OP == OP_SPMV) {
+    if (active && g == 0) a.out[(size_t)i * b + r] = acc;
+  } else if (OP == OP_RESID) {
+    if (active && g == 0) a.out[(size_t)i * b + r] = a.f[(size_t)i * b + r] - acc;
+  } else if (OP == OP_RESTRICT) {
+    if (active && g == 0) a.out[(size_t)i * b + r] = a.f[(size_t)a.c2f[i] * b + r] + acc;
+  } else {  // OP_JACOBI
+    if (upd && g == 0) sres[(size_t)team * b + r] = a.f[(size_t)i * b + r] - acc;
+    __syncthreads();
+    if (active && g == 0) {
+      T xi = xval<T, B>(a.x, a.ipc, i, r, b);
+      if (upd) {
+        const T *d = a.dinv + (size_t)i * b * b + r * b;
+        const T *sr = sres + (size_t)team * b;
+        T s = 0;
+        if constexpr (B > 0) {
+#pragma unroll
+          for (int c = 0; c < B; ++c) s = fma(d[c], sr[c], s);
+        } else {
+          for (int c = 0; c < b; ++c) s = fma(d[c], sr[c], s);
+        }
+        xi += s;
+      }
+      a.out[(size_t)i * b + r] = xi;
+    }
+  }
+}
+
+// host launcher: picks the team shape from the average row length
+template <typename T, int OP>
+void launch_rowop(RowArgs<T> a, double avg_blocks, cudaStream_t s);
+
+}  // namespace nair

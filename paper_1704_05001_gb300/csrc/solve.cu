@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "rowops.cuh"
 #include "solve.cuh"
 
 namespace nair {
@@ -19,24 +20,8 @@ static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
 // V-cycle kernels
 // ---------------------------------------------------------------------------
 
-// a11: f_c = f_C + R_cf f_F (zero initial guess, so the residual is f)
-template <typename T>
-__global__ void k_restrict(int nC, int b, const int *__restrict__ c2f, const int *__restrict__ rp,
-                           const int *__restrict__ ci, const T *__restrict__ rv,
-                           const T *__restrict__ f, T *__restrict__ fc) {
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)nC * b) return;
-  const int c = (int)(g / b), r = (int)(g - (long long)c * b), bb = b * b;
-  T acc = f[(size_t)c2f[c] * b + r];
-  for (int p = rp[c]; p < rp[c + 1]; ++p) {
-    const T *a = rv + (size_t)p * bb + r * b;
-    const T *ff = f + (size_t)ci[p] * b;
-    for (int t = 0; t < b; ++t) acc += a[t] * ff[t];
-  }
-  fc[g] = acc;
-}
-
-// a12: x = P x_c (C: own coarse value, F: one-point source, or 0)
+// a12: x = P x_c (C: own coarse value, F: one-point source, or 0); used only
+// when no relaxation sweep follows (otherwise the first sweep reads P x_c)
 template <typename T>
 __global__ void k_prolong(int E, int b, const int *__restrict__ ipc, const T *__restrict__ xc,
                           T *__restrict__ x) {
@@ -45,43 +30,6 @@ __global__ void k_prolong(int E, int b, const int *__restrict__ ipc, const T *__
   const int i = (int)(g / b), r = (int)(g - (long long)i * b);
   const int J = ipc[i];
   x[g] = J >= 0 ? xc[(size_t)J * b + r] : (T)0;
-}
-
-// a13/a14: one block-Jacobi sweep on the rows with cf == which:
-// x_i <- x_i + D_ii^{-1} (f - A x)_i, all rows from the sweep's input x
-template <typename T>
-__global__ void k_jacobi(int E, int b, int rpc, const int *__restrict__ rp, const int *__restrict__ ci,
-                         const T *__restrict__ v, const T *__restrict__ dinv,
-                         const signed char *__restrict__ cf, int which, const T *__restrict__ f,
-                         const T *__restrict__ xin, T *__restrict__ xout) {
-  extern __shared__ unsigned char smraw[];
-  T *sres = reinterpret_cast<T *>(smraw);
-  const int lr = threadIdx.x / b, r = threadIdx.x - lr * b, bb = b * b;
-  const int i = blockIdx.x * rpc + lr;
-  const bool active = lr < rpc && i < E;
-  const bool upd = active && cf[i] == which;
-  T res = 0;
-  if (upd) {
-    T acc = f[(size_t)i * b + r];
-    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-      const T *a = v + (size_t)p * bb + r * b;
-      const T *xj = xin + (size_t)ci[p] * b;
-      for (int c = 0; c < b; ++c) acc -= a[c] * xj[c];
-    }
-    res = acc;
-  }
-  if (lr < rpc) sres[lr * b + r] = res;
-  __syncthreads();
-  if (!active) return;
-  const size_t o = (size_t)i * b + r;
-  if (upd) {
-    const T *d = dinv + (size_t)i * bb + r * b;
-    T acc = 0;
-    for (int c = 0; c < b; ++c) acc += d[c] * sres[lr * b + c];
-    xout[o] = xin[o] + acc;
-  } else {
-    xout[o] = xin[o];
-  }
 }
 
 // a9: coarsest level, x = A_c^{-1} f (dense), one warp per row
@@ -96,6 +44,44 @@ __global__ void k_dense_mv(int n, const T *__restrict__ M, const T *__restrict__
   if (lane == 0) x[warp] = acc;
 }
 
+template <typename T, int OP>
+void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
+  const int b = a.b;
+  int G = 1;
+  if (avg > 4.0)
+    while (G * 2 <= avg / 2 && G * 2 * b <= 256 && G < 32) G *= 2;
+  a.G = G;
+  const int tsz = G * b;
+  a.tpc = std::max(1, 256 / tsz);
+  const int threads = a.tpc * tsz;
+  const size_t smem = ((size_t)a.tpc * tsz + (size_t)a.tpc * b) * sizeof(T);
+  const int blocks = std::max(1, cdiv(a.nrows, a.tpc));
+  switch (b) {
+    case 1: k_rowop<T, 1, OP><<<blocks, threads, smem, s>>>(a); break;
+    case 3: k_rowop<T, 3, OP><<<blocks, threads, smem, s>>>(a); break;
+    case 6: k_rowop<T, 6, OP><<<blocks, threads, smem, s>>>(a); break;
+    case 10: k_rowop<T, 10, OP><<<blocks, threads, smem, s>>>(a); break;
+    case 15: k_rowop<T, 15, OP><<<blocks, threads, smem, s>>>(a); break;
+    case 21: k_rowop<T, 21, OP><<<blocks, threads, smem, s>>>(a); break;
+    case 28: k_rowop<T, 28, OP><<<blocks, threads, smem, s>>>(a); break;
+    default: k_rowop<T, 0, OP><<<blocks, threads, smem, s>>>(a); break;
+  }
+  NAIR_LAUNCH_CHECK();
+}
+template void launch_rowop<double, OP_SPMV>(RowArgs<double>, double, cudaStream_t);
+template void launch_rowop<double, OP_RESID>(RowArgs<double>, double, cudaStream_t);
+
+template <typename T>
+static RowArgs<T> row_args(const DBsr<T> &A, int b) {
+  RowArgs<T> a{};
+  a.nrows = A.nrows;
+  a.b = b;
+  a.rp = A.rp;
+  a.ci = A.ci;
+  a.v = A.v;
+  return a;
+}
+
 template <typename T>
 static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, cudaStream_t s) {
   const Level<T> &L = H.lev[l];
@@ -106,25 +92,38 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
     return;
   }
   const Level<T> &N = H.lev[l + 1];
-  k_restrict<T><<<grid((long long)L.nC * b), kThreads, 0, s>>>(L.nC, b, L.c2f, L.R.rp, L.R.ci, L.R.v, f, N.f);
-  NAIR_LAUNCH_CHECK();
+  {  // a11: f_c = f_C + R_cf f_F
+    RowArgs<T> a = row_args(L.R, b);
+    a.nrows = L.nC;
+    a.x = f;
+    a.f = f;
+    a.c2f = L.c2f;
+    a.out = N.f;
+    launch_rowop<T, OP_RESTRICT>(a, L.nC ? (double)L.R.nnzb / L.nC : 0.0, s);
+  }
   vcyc<T>(H, P, l + 1, N.f, N.x, s);
   const int S = P.f_sweeps + P.c_sweeps;
-  T *other = L.x2;
-  T *cur = (S % 2 == 0) ? out : other;
-  T *nxt = (S % 2 == 0) ? other : out;
-  k_prolong<T><<<grid((long long)L.E * b), kThreads, 0, s>>>(L.E, b, L.ipc, N.x, cur);
-  NAIR_LAUNCH_CHECK();
-  const int rpc = std::max(1, kThreads / b);
-  const size_t smem = (size_t)rpc * b * sizeof(T);
-  for (int k = 0; k < S; ++k) {
-    int which = k < P.f_sweeps ? 0 : 1;
-    k_jacobi<T><<<cdiv(L.E, rpc), rpc * b, smem, s>>>(L.E, b, rpc, L.A.rp, L.A.ci, L.A.v, L.dinv, L.cf,
-                                                      which, f, cur, nxt);
+  if (S == 0) {
+    k_prolong<T><<<grid((long long)L.E * b), kThreads, 0, s>>>(L.E, b, L.ipc, N.x, out);
     NAIR_LAUNCH_CHECK();
-    T *t = cur;
-    cur = nxt;
-    nxt = t;
+    return;
+  }
+  // a12-a14: x = P x_c fused into the first sweep, then F sweeps and C sweeps
+  T *bufA = (S % 2 == 1) ? out : L.x2;
+  T *bufB = (S % 2 == 1) ? L.x2 : out;
+  const double avg = (double)L.A.nnzb / L.E;
+  const T *in = N.x;
+  for (int k = 0; k < S; ++k) {
+    RowArgs<T> a = row_args(L.A, b);
+    a.x = in;
+    a.ipc = (k == 0) ? L.ipc : nullptr;
+    a.f = f;
+    a.dinv = L.dinv;
+    a.cf = L.cf;
+    a.which = k < P.f_sweeps ? 0 : 1;
+    a.out = (k % 2 == 0) ? bufA : bufB;
+    launch_rowop<T, OP_JACOBI>(a, avg, s);
+    in = a.out;
   }
 }
 
@@ -138,22 +137,6 @@ template void vcycle<float>(const Hier<float> &, const Params &, const float *, 
 // ---------------------------------------------------------------------------
 // FP64 Krylov kernels
 // ---------------------------------------------------------------------------
-
-// y = A x, or y = b - A x when b is given (a10), one thread per scalar row
-__global__ void k_spmv64(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
-                         const double *__restrict__ v, const double *__restrict__ x,
-                         const double *__restrict__ bvec, double *__restrict__ y) {
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= (long long)E * b) return;
-  const int i = (int)(g / b), r = (int)(g - (long long)i * b), bb = b * b;
-  double acc = 0.0;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    const double *a = v + (size_t)p * bb + r * b;
-    const double *xj = x + (size_t)ci[p] * b;
-    for (int c = 0; c < b; ++c) acc += a[c] * xj[c];
-  }
-  y[g] = bvec ? bvec[g] - acc : acc;
-}
 
 static constexpr int kDotGroup = 8;
 static constexpr int kDotCtas = 304;
@@ -265,8 +248,74 @@ static void multidot(Krylov &K, long long n, int nv, const double *V, const doub
 }
 
 template <typename T>
+__global__ void k_copy_in(long long n, void *const *__restrict__ ptrs, T *__restrict__ dst) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)(static_cast<const double *>(ptrs[0])[i]);
+}
+
+template <typename T>
+__global__ void k_copy_out(long long n, const T *__restrict__ src, void *const *__restrict__ ptrs) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) static_cast<double *>(ptrs[1])[i] = (double)src[i];
+}
+
+void release_graph(VGraph &g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.dptr) cudaFree(g.dptr);
+  if (g.hptr) cudaFreeHost(g.hptr);
+  g = VGraph();
+}
+
+// capture: copy the input into level 0's right-hand side, V-cycle on fixed
+// buffers, copy level 0's solution out (FP64 <-> T casts in mixed precision)
+template <typename T>
+static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
+  VGraph &g = H.graph;
+  NAIR_CK(cudaMalloc(&g.dptr, 2 * sizeof(void *)));
+  NAIR_CK(cudaMallocHost(&g.hptr, 2 * sizeof(void *)));
+  const long long before = launch_count();
+  cudaGraph_t graph;
+  // capture on a private stream (the caller's may be the legacy default stream,
+  // which cannot be captured); the graph is launched on the caller's stream
+  cudaStream_t s;
+  NAIR_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } guard{s};
+  NAIR_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  try {
+    T *f0 = H.lev[0].f, *x0 = H.lev[0].x;
+    k_copy_in<T><<<grid(n), kThreads, 0, s>>>(n, g.dptr, f0);
+    NAIR_LAUNCH_CHECK();
+    vcycle<T>(H, P, f0, x0, s);
+    k_copy_out<T><<<grid(n), kThreads, 0, s>>>(n, x0, g.dptr);
+    NAIR_LAUNCH_CHECK();
+  } catch (...) {
+    cudaStreamEndCapture(s, &graph);
+    throw;
+  }
+  NAIR_CK(cudaStreamEndCapture(s, &graph));
+  g.nodes = launch_count() - before;
+  add_launches(-g.nodes);  // captured, not launched
+  cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  NAIR_CK(e);
+}
+
+template <typename T>
 void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s,
              long long n) {
+  if (P.use_graphs) {
+    VGraph &g = H.graph;
+    if (!g.exec) capture_graph<T>(H, P, n);
+    g.hptr[0] = const_cast<double *>(v);
+    g.hptr[1] = z;
+    NAIR_CK(cudaMemcpyAsync(g.dptr, g.hptr, 2 * sizeof(void *), cudaMemcpyHostToDevice, s));
+    NAIR_CK(cudaGraphLaunch(g.exec, s));
+    add_launches(g.nodes);
+    return;
+  }
   if constexpr (std::is_same<T, double>::value) {
     vcycle<double>(H, P, v, z, s);
   } else {
@@ -281,9 +330,15 @@ void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cuda
 template void precond<double>(const Hier<double> &, const Params &, const double *, double *, cudaStream_t, long long);
 template void precond<float>(const Hier<float> &, const Params &, const double *, double *, cudaStream_t, long long);
 
+// a10: y = A x, or y = b - A x when b is given (FP64, level 0)
 void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s) {
-  k_spmv64<<<grid((long long)A.nrows * b), kThreads, 0, s>>>(A.nrows, b, A.rp, A.ci, A.v, x, bvec, y);
-  NAIR_LAUNCH_CHECK();
+  RowArgs<double> a = row_args(A, b);
+  a.x = x;
+  a.f = bvec;
+  a.out = y;
+  const double avg = (double)A.nnzb / A.nrows;
+  if (bvec) launch_rowop<double, OP_RESID>(a, avg, s);
+  else launch_rowop<double, OP_SPMV>(a, avg, s);
 }
 
 template <typename T>
