@@ -173,6 +173,16 @@ nair_status nair_gradients(int32_t E, int32_t b, const double *M, const double *
  * (a diagnostic counter; every launch site increments it). */
 nair_status nair_kernel_launches(int64_t *count);
 
+/* Per-kernel timing (diagnostic).  nair_profile(1) clears the counters and
+ * starts recording a CUDA event pair around each timed launch site (the
+ * V-cycle then runs launch by launch instead of as a graph); nair_profile(0)
+ * stops.  nair_profile_entry reads entry idx = 0, 1, ... : its name (copied
+ * into name, at most cap bytes with the terminating 0), the number of timed
+ * scopes and their total device time in ms; INVALID_ARG past the last entry.
+ * Reading entry 0 waits for the recorded events. */
+nair_status nair_profile(int32_t enable);
+nair_status nair_profile_entry(int32_t idx, char *name, size_t cap, int64_t *launches, double *total_ms);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *nair_last_error(void);
 

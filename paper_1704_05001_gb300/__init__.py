@@ -61,7 +61,7 @@ _lib = None
 EXPORTS = ["nair_default_params", "nair_setup", "nair_solve", "nair_adjoint_solve", "nair_vcycle",
            "nair_free", "nair_num_levels", "nair_level_sizes", "nair_get_level", "nair_block_inverse",
            "nair_assemble_sigma", "nair_mass_apply", "nair_gradients", "nair_kernel_launches",
-           "nair_last_error"]
+           "nair_profile", "nair_profile_entry", "nair_last_error"]
 
 
 def lib():
@@ -89,6 +89,9 @@ def lib():
     L.nair_mass_apply.argtypes = [I32, I32, P, P, P, P]
     L.nair_gradients.argtypes = [I32, I32, P, P, P, P, P, P]
     L.nair_kernel_launches.argtypes = [ctypes.POINTER(I64)]
+    L.nair_profile.argtypes = [I32]
+    L.nair_profile_entry.argtypes = [I32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(I64),
+                                     ctypes.POINTER(D)]
     L.nair_last_error.argtypes = []
     L.nair_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -122,6 +125,24 @@ def kernel_launches():
     c = ctypes.c_int64(0)
     _check(lib().nair_kernel_launches(ctypes.byref(c)), "nair_kernel_launches")
     return c.value
+
+
+def profile(enable=True):
+    """Turn per-kernel event timing on (clearing it) or off."""
+    _check(lib().nair_profile(int(enable)), "nair_profile")
+
+
+def profile_report():
+    """{name: (timed scopes, total ms)} recorded since profile(True)."""
+    out = {}
+    buf = ctypes.create_string_buffer(256)
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0)
+    idx = 0
+    while lib().nair_profile_entry(idx, buf, 256, ctypes.byref(n), ctypes.byref(ms)) == NAIR_OK:
+        out[buf.value.decode()] = (n.value, ms.value)
+        idx += 1
+    return out
 
 
 def default_params():

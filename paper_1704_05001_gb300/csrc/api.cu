@@ -289,6 +289,31 @@ void nair_default_params(nair_params *p) {
 
 const char *nair_last_error(void) { return g_last_error.c_str(); }
 
+nair_status nair_profile(int32_t enable) {
+  NAIR_API_BEGIN
+  prof_enable(enable != 0);
+  return NAIR_OK;
+  NAIR_API_END
+}
+
+nair_status nair_profile_entry(int32_t idx, char *name, size_t cap, int64_t *launches, double *total_ms) {
+  NAIR_API_BEGIN
+  if (idx == 0) prof_resolve();
+  std::string nm;
+  long long n = 0;
+  double ms = 0.0;
+  if (!prof_entry(idx, nm, n, ms)) return set_error(NAIR_ERR_INVALID_ARG, "no such profile entry");
+  if (name && cap) {
+    size_t k = std::min(cap - 1, nm.size());
+    memcpy(name, nm.data(), k);
+    name[k] = 0;
+  }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return NAIR_OK;
+  NAIR_API_END
+}
+
 nair_status nair_kernel_launches(int64_t *count) {
   if (!count) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
   *count = launch_count();

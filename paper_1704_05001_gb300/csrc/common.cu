@@ -2,6 +2,8 @@
 // per-row counts into block-CSR row pointers.
 #include <atomic>
 #include <cstdio>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -19,6 +21,86 @@ void ck_fail(cudaError_t e, const char *what, const char *file, int line) {
   snprintf(buf, sizeof(buf), "CUDA error %s (%s) in %s at %s:%d", cudaGetErrorName(e),
            cudaGetErrorString(e), what, file, line);
   throw NairError{e == cudaErrorMemoryAllocation ? NAIR_ERR_OOM : NAIR_ERR_CUDA, buf};
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel timing
+// ---------------------------------------------------------------------------
+namespace {
+struct Pending {
+  std::string name;
+  cudaEvent_t e0, e1;
+};
+struct ProfState {
+  std::mutex mu;
+  bool on = false;
+  std::vector<Pending> pending;
+  std::map<std::string, std::pair<long long, double>> stats;
+};
+ProfState &prof() {
+  static ProfState p;
+  return p;
+}
+}  // namespace
+
+bool prof_on() { return prof().on; }
+
+void prof_enable(bool on) {
+  prof_resolve();
+  std::lock_guard<std::mutex> lk(prof().mu);
+  prof().on = on;
+  prof().stats.clear();
+}
+
+void prof_resolve() {
+  std::lock_guard<std::mutex> lk(prof().mu);
+  for (auto &p : prof().pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+      auto &st = prof().stats[p.name];
+      st.first += 1;
+      st.second += ms;
+    }
+    cudaEventDestroy(p.e0);
+    cudaEventDestroy(p.e1);
+  }
+  prof().pending.clear();
+  cudaGetLastError();
+}
+
+int prof_count() {
+  prof_resolve();
+  std::lock_guard<std::mutex> lk(prof().mu);
+  return (int)prof().stats.size();
+}
+
+bool prof_entry(int idx, std::string &name, long long &launches, double &ms) {
+  std::lock_guard<std::mutex> lk(prof().mu);
+  if (idx < 0 || idx >= (int)prof().stats.size()) return false;
+  auto it = prof().stats.begin();
+  std::advance(it, idx);
+  name = it->first;
+  launches = it->second.first;
+  ms = it->second.second;
+  return true;
+}
+
+ProfScope::ProfScope(const char *n, cudaStream_t st, int lvl) : name(n), level(lvl), s(st) {
+  if (!prof().on) return;
+  if (cudaEventCreate(&e0) != cudaSuccess) { e0 = nullptr; return; }
+  cudaEventRecord(e0, s);
+}
+
+void ProfScope::end() {
+  if (!e0) return;
+  cudaEvent_t e1;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); e0 = nullptr; return; }
+  cudaEventRecord(e1, s);
+  std::string nm = name;
+  if (level >= 0) nm += "@L" + std::to_string(level);
+  std::lock_guard<std::mutex> lk(prof().mu);
+  prof().pending.push_back({nm, e0, e1});
+  e0 = nullptr;
 }
 
 void *Mem::raw(size_t bytes) {

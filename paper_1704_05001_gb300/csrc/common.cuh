@@ -87,6 +87,26 @@ __host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
+// ---------------------------------------------------------------------------
+// optional per-kernel timing: when enabled, ProfScope records a CUDA event pair
+// around the launches in its scope; the pairs are resolved into per-name totals
+// ---------------------------------------------------------------------------
+bool prof_on();
+void prof_enable(bool on);
+void prof_resolve();
+int prof_count();
+bool prof_entry(int idx, std::string &name, long long &launches, double &ms);
+
+struct ProfScope {
+  const char *name;
+  int level;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(const char *name, cudaStream_t s, int level = -1);
+  void end();  // close the scope early (the destructor then does nothing)
+  ~ProfScope() { end(); }
+};
+
 // exclusive scan of n ints into out[0..n]; out[n] = total; returns the total
 // (synchronises the stream to read it back when want_total is set)
 int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, Mem &tmp, bool want_total = true);

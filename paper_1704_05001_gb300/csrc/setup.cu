@@ -636,6 +636,7 @@ static void spgemm(int b, const SpgemmIdx &X, const T *lv, const T *rv, const T 
   out.nrows = nrows;
   out.ncols = ncols;
   out.rp = mem.alloc<int>(nrows + 1);
+  ProfScope ps("spgemm", s);
   k_spgemm_symbolic<false><<<grid(nrows), kThreads, 0, s>>>(X, cursor, cnt, nullptr, nullptr, nullptr);
   NAIR_LAUNCH_CHECK();
   out.nnzb = exclusive_scan(cnt, out.rp, nrows, s, tmp);
@@ -658,6 +659,7 @@ static void spgemm(int b, const SpgemmIdx &X, const T *lv, const T *rv, const T 
 template <typename T>
 static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M) {
   const int nrows = M.nrows;
+  ProfScope ps("filter", s);
   int *newpos = tmp.alloc<int>(M.nnzb);
   int *cnt = tmp.alloc<int>(nrows + 1);
   k_filter_flags<T><<<grid(nrows), kThreads, 0, s>>>(nrows, b, M.rp, M.ci, M.v, tol2, newpos, cnt);
@@ -729,6 +731,8 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   Level<T> &L = H.lev[l];
   const int E = L.E, nnzb = L.A.nnzb;
   // a2: strength
+  ProfScope ps_all("setup_level", s, l);
+  ProfScope ps_str("strength", s, l);
   T *snorm = tmp.alloc<T>(nnzb);
   unsigned char *strong = (P.keep ? mem.alloc<unsigned char>(nnzb) : tmp.alloc<unsigned char>(nnzb));
   k_block_norm2<T><<<grid(nnzb), kThreads, 0, s>>>(nnzb, b, L.A.v, snorm);
@@ -740,6 +744,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   NAIR_CK(cudaMemsetAsync(lam, 0, sizeof(int) * E, s));
   k_lambda<<<grid(nnzb), kThreads, 0, s>>>(nnzb, L.A.ci, strong, lam);
   NAIR_LAUNCH_CHECK();
+  ps_str.end();
   // a3: C/F splitting
   L.cf = mem.alloc<signed char>(E);
   uint64_t *hash = tmp.alloc<uint64_t>(E);
@@ -751,6 +756,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   k_pmis_init<<<grid(E), kThreads, 0, s>>>(E, lam, L.cf, hash, P.seed, mark);
   NAIR_LAUNCH_CHECK();
   int rounds = 0;
+  ProfScope ps_cf("cf_split", s, l);
   for (;;) {
     NAIR_CK(cudaMemsetAsync(remaining, 0, sizeof(int), s));
     k_pmis_mark<<<grid(nnzb), kThreads, 0, s>>>(nnzb, brow, L.A.ci, strong, L.cf, lam, hash, mark, rounds);
@@ -764,6 +770,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     if (rounds > E + 1) fail(NAIR_ERR_CUDA, "C/F splitting did not terminate");
   }
   L.cf_rounds = rounds;
+  ps_cf.end();
   int *isc = tmp.alloc<int>(E);
   int *pre = tmp.alloc<int>(E + 1);
   k_cf_flags<<<grid(E), kThreads, 0, s>>>(E, L.cf, isc);
@@ -787,6 +794,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   NAIR_LAUNCH_CHECK();
 
   // a4: L = -D_ff^{-1} A^S_ff, then Horner T_{t+1} = D^{-1} + L T_t (Eq. neumann)
+  ProfScope ps_neu("neumann", s, l);
   DBsr<T> Lm;
   int *src, *row;
   extract<T>(b, nF, 0, f2f, L, strong, fidx, s, mem, tmp, Lm, &src, &row);
@@ -831,8 +839,10 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   }
   tmp.release(Dg.v);
   tmp.release(Dg.rp);
+  ps_neu.end();
 
   // a5: R_cf = -A_cf Delta over all A_cf blocks
+  ProfScope ps_r("restriction", s, l);
   DBsr<T> Acf;
   extract<T>(b, nC, 1, L.c2f, L, strong, fidx, s, tmp, tmp, Acf, &src, &row);
   tot = (long long)Acf.nnzb * bb;
@@ -851,6 +861,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     NAIR_LAUNCH_CHECK();
   }
   L.R.ncols = E;
+  ps_r.end();
 
   // a6: one-point interpolation
   L.ipc = mem.alloc<int>(E);
@@ -858,6 +869,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   NAIR_LAUNCH_CHECK();
 
   // a7: A P (column merge), then K = (AP)_C + R_cf (AP)_F
+  ProfScope ps_k("galerkin", s, l);
   DBsr<T> AP;
   {
     int *cnt = tmp.alloc<int>(E + 1);
@@ -900,6 +912,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
 template <typename T>
 static void level_dinv(Hier<T> &H, Level<T> &L, cudaStream_t s, Mem &mem, Mem &tmp, int *err) {
   const int b = H.b, E = L.E;
+  ProfScope ps("dinv", s);
   L.diag = mem.alloc<int>(E);
   k_diag_pos<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.diag);
   NAIR_LAUNCH_CHECK();
@@ -935,6 +948,7 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
   }
   L.coarsest = 1;
   L.n = n;
+  ProfScope ps("coarse_inverse", s);
   double *M = tmp.alloc<double>((size_t)n * n);
   NAIR_CK(cudaMemsetAsync(M, 0, sizeof(double) * n * n, s));
   int *brow = tmp.alloc<int>(L.A.nnzb);

@@ -87,12 +87,14 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
   const Level<T> &L = H.lev[l];
   const int b = H.b;
   if (L.coarsest) {
+    ProfScope ps("coarse_solve", s, l);
     k_dense_mv<T><<<cdiv((long long)L.n * 32, kThreads), kThreads, 0, s>>>(L.n, L.ainv, f, out);
     NAIR_LAUNCH_CHECK();
     return;
   }
   const Level<T> &N = H.lev[l + 1];
   {  // a11: f_c = f_C + R_cf f_F
+    ProfScope ps("restrict", s, l);
     RowArgs<T> a = row_args(L.R, b);
     a.nrows = L.nC;
     a.x = f;
@@ -122,6 +124,7 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
     a.cf = L.cf;
     a.which = k < P.f_sweeps ? 0 : 1;
     a.out = (k % 2 == 0) ? bufA : bufB;
+    ProfScope ps(a.which == 0 ? "jacobi_F" : "jacobi_C", s, l);
     launch_rowop<T, OP_JACOBI>(a, avg, s);
     in = a.out;
   }
@@ -241,6 +244,7 @@ Krylov::~Krylov() {
 
 static void multidot(Krylov &K, long long n, int nv, const double *V, const double *w, double *out,
                      cudaStream_t s) {
+  ProfScope ps("multidot", s);
   k_multidot<<<kDotCtas, kThreads, 0, s>>>(n, nv, V, n, w, K.partial);
   NAIR_LAUNCH_CHECK();
   k_reduce_partials<<<nv, 32, 0, s>>>(nv, kDotCtas, K.partial, out);
@@ -306,7 +310,7 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
 template <typename T>
 void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s,
              long long n) {
-  if (P.use_graphs) {
+  if (P.use_graphs && !prof_on()) {
     VGraph &g = H.graph;
     if (!g.exec) capture_graph<T>(H, P, n);
     g.hptr[0] = const_cast<double *>(v);
@@ -337,6 +341,7 @@ void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, d
   a.f = bvec;
   a.out = y;
   const double avg = (double)A.nnzb / A.nrows;
+  ProfScope ps(bvec ? "resid64" : "spmv64", s);
   if (bvec) launch_rowop<double, OP_RESID>(a, avg, s);
   else launch_rowop<double, OP_SPMV>(a, avg, s);
 }
@@ -384,18 +389,30 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
     bool conv = false, brk = false;
     for (j = 0; j < m && it < P.maxiter; ++j) {
       double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
-      precond<T>(H, P, vj, zj, s, n);
+      {
+        ProfScope ps("vcycle", s);
+        precond<T>(H, P, vj, zj, s, n);
+      }
       ++it;
       spmv64(A, b, zj, nullptr, w, s);
       // classical Gram-Schmidt, twice
       multidot(K, n, j + 1, V, w, K.hdev, s);
-      k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev, w);
-      NAIR_LAUNCH_CHECK();
+      {
+        ProfScope ps("axpy_multi", s);
+        k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev, w);
+        NAIR_LAUNCH_CHECK();
+      }
       multidot(K, n, j + 1, V, w, K.hdev + (m + 1), s);
-      k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev + (m + 1), w);
-      NAIR_LAUNCH_CHECK();
+      {
+        ProfScope ps("axpy_multi", s);
+        k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev + (m + 1), w);
+        NAIR_LAUNCH_CHECK();
+      }
       multidot(K, n, 1, w, w, K.hdev + 2 * (m + 1), s);
-      NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+      {
+        ProfScope ps("arnoldi_readback", s);
+        NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+      }
       NAIR_CK(cudaStreamSynchronize(s));
       for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hh[k] + hh[m + 1 + k];
       const double hn = std::sqrt(hh[2 * (m + 1)]);
