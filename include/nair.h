@@ -151,6 +151,24 @@ nair_status nair_get_level(const nair_handle *h, int32_t adjoint, int32_t level,
  * device, nblk*b*b doubles.  Returns SINGULAR_BLOCK if any pivot is zero. */
 nair_status nair_block_inverse(int32_t nblk, int32_t b, const double *A, double *Ainv, void *stream);
 
+/* Same batched inverses as nair_block_inverse, for callers that cannot allocate
+ * device memory (a caching allocator that owns the device, applications that
+ * forbid cudaMalloc after start-up, code that must not synchronise the device
+ * the way cudaMalloc/cudaFree can).  The paper has no counterpart: this is a
+ * deployment variant.  The entry point allocates nothing; its status words live
+ * in a 32 KB array that the library reserves in device memory on every GPU that
+ * loads it, until the process exits.  One call handles at most 8192 thread
+ * blocks of max(1, 256 / b) matrix blocks each (for example 344064 blocks of
+ * size 6, 73728 of size 28); larger calls return INVALID_ARG and launch
+ * nothing.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it, so order
+ * them on one stream.  The call synchronises the stream to read the status.
+ * Returns SINGULAR_BLOCK, naming the range of blocks, if a pivot is zero. */
+nair_status nair_block_inverse_noalloc(int32_t nblk, int32_t b, const double *A, double *Ainv,
+                                       void *stream);
+
 /* Parameter-dependent assembly for the transport problem (Eq. transport):
  * vals = vals0 with diagonal blocks vals0[diag_pos[e]] + sigma[e] * M[e]
  * (sigma_t piecewise constant per element, M the element mass matrices).

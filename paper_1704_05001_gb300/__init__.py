@@ -61,7 +61,7 @@ _lib = None
 EXPORTS = ["nair_default_params", "nair_setup", "nair_solve", "nair_adjoint_solve", "nair_vcycle",
            "nair_free", "nair_num_levels", "nair_level_sizes", "nair_get_level", "nair_block_inverse",
            "nair_assemble_sigma", "nair_mass_apply", "nair_gradients", "nair_kernel_launches",
-           "nair_profile", "nair_profile_entry", "nair_last_error"]
+           "nair_profile", "nair_profile_entry", "nair_block_inverse_noalloc", "nair_last_error"]
 
 
 def lib():
@@ -85,6 +85,7 @@ def lib():
     L.nair_level_sizes.argtypes = [P, I32, I32, P]
     L.nair_get_level.argtypes = [P, I32, I32, I32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.nair_block_inverse.argtypes = [I32, I32, P, P, P]
+    L.nair_block_inverse_noalloc.argtypes = [I32, I32, P, P, P]
     L.nair_assemble_sigma.argtypes = [I32, I32, I64, P, P, P, P, P, P]
     L.nair_mass_apply.argtypes = [I32, I32, P, P, P, P]
     L.nair_gradients.argtypes = [I32, I32, P, P, P, P, P, P]

@@ -39,6 +39,11 @@ static nair_status set_error(nair_status st, const std::string &msg) {
   return st;
 }
 
+namespace nair {
+// error reporting for the allocation-free entry point in noalloc.cu
+nair_status noalloc_error(nair_status st, const char *msg) { return set_error(st, msg ? msg : ""); }
+}  // namespace nair
+
 #define NAIR_API_BEGIN try {
 #define NAIR_API_END                                              \
   }                                                               \
