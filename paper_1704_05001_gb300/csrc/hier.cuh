@@ -24,7 +24,8 @@ struct Level {
   int *diag = nullptr;     // position of the diagonal block of each row
   T *dinv = nullptr;       // E inverse diagonal blocks (computed in FP64)
   signed char *cf = nullptr;  // 1 = C, 0 = F
-  int *c2f = nullptr;      // coarse index -> element
+  int *c2f = nullptr;      // coarse index -> element (the C rows, ascending)
+  int *f2f = nullptr;      // F index -> element (the F rows, ascending)
   int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
   DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
   int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)

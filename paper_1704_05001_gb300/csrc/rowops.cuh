@@ -27,9 +27,13 @@ struct RowArgs {
   const T *f;            // right-hand side (RESID, JACOBI) or fine vector (RESTRICT)
   const int *c2f;        // RESTRICT: coarse row -> fine element of its identity part
   const T *dinv;         // JACOBI: inverse diagonal blocks
-  const signed char *cf; // JACOBI: row class
-  int which;             // JACOBI: update rows with cf == which
+  const int *list;       // rows to process (null: rows 0..nrows-1)
   T *out;
+  // JACOBI copy segment: thread blocks comp_ctas.. copy rows copy_list[0..ncopy)
+  // of the input (through ipc when set) into out and, if set, out2
+  int comp_ctas, ncopy;
+  const int *copy_list;
+  T *out2;
 };
 
 template <typename T, int B>
@@ -76,6 +80,18 @@ __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int i, int g, int 
 
 template <typename T, int B, int OP>
 __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
+  if (OP == OP_JACOBI && (int)blockIdx.x >= a.comp_ctas) {
+    // copy segment: rows of the class this sweep does not update
+    const int bt = B > 0 ? B : a.b;
+    const long long g = (long long)(blockIdx.x - a.comp_ctas) * blockDim.x + threadIdx.x;
+    if (g >= (long long)a.ncopy * bt) return;
+    const int row = (int)(g / bt), r = (int)(g - (long long)row * bt);
+    const int i = a.copy_list[row];
+    const T v = xval<T, B>(a.x, a.ipc, i, r, bt);
+    a.out[(size_t)i * bt + r] = v;
+    if (a.out2) a.out2[(size_t)i * bt + r] = v;
+    return;
+  }
   extern __shared__ unsigned char smraw[];
   T *red = reinterpret_cast<T *>(smraw);             // [tpc][G][b]
   const int b = B > 0 ? B : a.b;
@@ -83,10 +99,10 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
   T *sres = red + (size_t)a.tpc * tsz;               // [tpc][b]
   const int team = threadIdx.x / tsz, lt = threadIdx.x - team * tsz;
   const int g = lt / b, r = lt - g * b;
-  const int i = blockIdx.x * a.tpc + team;
-  const bool active = team < a.tpc && i < a.nrows;
-  bool upd = active;
-  if (OP == OP_JACOBI && active) upd = a.cf[i] == a.which;
+  const int idx = blockIdx.x * a.tpc + team;
+  const bool active = team < a.tpc && idx < a.nrows;
+  const int i = active ? (a.list ? a.list[idx] : idx) : 0;
+  const bool upd = active;
   T acc = 0;
   if (upd) acc = row_partial<T, B>(a, i, g, r);
   if (a.G > 1) {
@@ -124,7 +140,8 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
   }
 }
 
-// host launcher: picks the team shape from the average row length
+// host launcher: picks the team shape from the average row length; for JACOBI,
+// a.nrows / a.list are the rows to update and a.ncopy / a.copy_list the rows to copy
 template <typename T, int OP>
 void launch_rowop(RowArgs<T> a, double avg_blocks, cudaStream_t s);
 

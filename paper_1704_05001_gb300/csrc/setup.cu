@@ -148,6 +148,7 @@ __global__ void k_convert(long long n, const double *__restrict__ in, TO *__rest
 template <typename T>
 __device__ __forceinline__ T block_norm2(const T *__restrict__ x, int bb) {
   T s = 0;
+#pragma unroll 8
   for (int k = 0; k < bb; ++k) s = fma_rn(x[k], x[k], s);
   return s;
 }
@@ -439,19 +440,18 @@ __global__ void k_spgemm_numeric(long long total, int b, SpgemmIdx X, const T *_
 // a8: filtering.  Drop X_ij (j != i) when ||X_ij||^2 <= tol^2 ||X_ii||^2
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_filter_flags(int nrows, int b, const int *__restrict__ rp, const int *__restrict__ ci,
-                               const T *__restrict__ v, T tol2, int *__restrict__ newpos,
+__global__ void k_filter_flags(int nrows, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const T *__restrict__ nrm, T tol2, int *__restrict__ newpos,
                                int *__restrict__ cnt) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nrows) return;
-  const int bb = b * b;
   T dn = 0;
   for (int p = rp[i]; p < rp[i + 1]; ++p)
-    if (ci[p] == i) dn = block_norm2(v + (size_t)p * bb, bb);
+    if (ci[p] == i) dn = nrm[p];
   const T thr = mul_rn(tol2, dn);
   int k = 0;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    bool keep = ci[p] == i || !(block_norm2(v + (size_t)p * bb, bb) <= thr);
+    bool keep = ci[p] == i || !(nrm[p] <= thr);
     newpos[p] = keep ? k++ : -1;
   }
   cnt[i] = k;
@@ -619,6 +619,82 @@ __global__ void __launch_bounds__(kGjThreads) k_dense_gj(int n, double *__restri
   }
 }
 
+// Larger coarsest matrices: one launch per Gauss-Jordan step k, Min -> Mout,
+// the same arithmetic as the in-place single-CTA form.  Every thread block
+// finds the pivot of column k itself (first row with the largest |entry|),
+// reads the pivot row through the row swap k <-> p, scales it once per column
+// into shared memory and updates its tile.
+static constexpr int kGjTileRows = 16, kGjTileCols = 256;
+
+__global__ void __launch_bounds__(256) k_gj_step(int n, int k, const double *__restrict__ Min,
+                                                 double *__restrict__ Mout, int *__restrict__ piv,
+                                                 int *__restrict__ err) {
+  __shared__ double rv[8];
+  __shared__ int ri[8];
+  __shared__ int sp;
+  __shared__ double prow[kGjTileCols];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double best = -1.0;
+  int bi = n;
+  for (int r = k + tid; r < n; r += blockDim.x) {
+    double a = fabs(Min[(size_t)r * n + k]);
+    if (a > best || (a == best && r < bi)) { best = a; bi = r; }
+  }
+  for (int o = 16; o; o >>= 1) {
+    double ob = __shfl_down_sync(0xffffffffu, best, o);
+    int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+  }
+  if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+  __syncthreads();
+  if (tid == 0) {
+    double b0 = rv[0];
+    int i0 = ri[0];
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w)
+      if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
+    sp = i0;
+  }
+  __syncthreads();
+  const int p = sp;
+  const double d = Min[(size_t)p * n + k];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+    piv[k] = p;
+    if (d == 0.0 || d != d) *err = 1;
+  }
+  const int r0 = blockIdx.y * kGjTileRows, c0 = blockIdx.x * kGjTileCols;
+  for (int c = tid; c < kGjTileCols; c += blockDim.x) {
+    const int cc = c0 + c;
+    if (cc < n) prow[c] = __ddiv_rn(cc == k ? 1.0 : Min[(size_t)p * n + cc], d);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kGjTileRows * kGjTileCols; idx += blockDim.x) {
+    const int r = r0 + idx / kGjTileCols, c = c0 + idx % kGjTileCols;
+    if (r >= n || c >= n) continue;
+    if (r == k) {
+      Mout[(size_t)k * n + c] = prow[c - c0];
+      continue;
+    }
+    const int src = (r == p) ? k : r;
+    const double l = Min[(size_t)src * n + k];
+    const double a = (c == k) ? 0.0 : Min[(size_t)src * n + c];
+    Mout[(size_t)r * n + c] = __fma_rn(-l, prow[c - c0], a);
+  }
+}
+
+// undo the row interchanges as column swaps, last step first
+__global__ void __launch_bounds__(1024) k_gj_unscramble(int n, double *__restrict__ M, const int *__restrict__ piv) {
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        double t = M[(size_t)r * n + k];
+        M[(size_t)r * n + k] = M[(size_t)r * n + p];
+        M[(size_t)r * n + p] = t;
+      }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -662,7 +738,12 @@ static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M
   ProfScope ps("filter", s);
   int *newpos = tmp.alloc<int>(M.nnzb);
   int *cnt = tmp.alloc<int>(nrows + 1);
-  k_filter_flags<T><<<grid(nrows), kThreads, 0, s>>>(nrows, b, M.rp, M.ci, M.v, tol2, newpos, cnt);
+  T *nrm = tmp.alloc<T>(M.nnzb);
+  if (M.nnzb) {
+    k_block_norm2<T><<<grid(M.nnzb), kThreads, 0, s>>>(M.nnzb, b, M.v, nrm);
+    NAIR_LAUNCH_CHECK();
+  }
+  k_filter_flags<T><<<grid(nrows), kThreads, 0, s>>>(nrows, M.rp, M.ci, nrm, tol2, newpos, cnt);
   NAIR_LAUNCH_CHECK();
   int *nrp = mem.alloc<int>(nrows + 1);
   int nn = exclusive_scan(cnt, nrp, nrows, s, tmp);
@@ -680,6 +761,7 @@ static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M
   mem.release(M.ci);
   mem.release(M.v);
   tmp.release(src);
+  tmp.release(nrm);
   tmp.release(cnt);
   tmp.release(newpos);
   M.rp = nrp;
@@ -789,7 +871,8 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   }
   int *cidx = tmp.alloc<int>(E), *fidx = tmp.alloc<int>(E);
   L.c2f = mem.alloc<int>(nC);
-  int *f2f = tmp.alloc<int>(nF);
+  L.f2f = mem.alloc<int>(nF);
+  int *f2f = L.f2f;
   k_cf_index<<<grid(E), kThreads, 0, s>>>(E, L.cf, pre, cidx, fidx, L.c2f, f2f);
   NAIR_LAUNCH_CHECK();
 
@@ -960,9 +1043,21 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
     NAIR_LAUNCH_CHECK();
   }
   int *piv = tmp.alloc<int>(n);
-  double *lcol = tmp.alloc<double>(n);
-  k_dense_gj<<<1, kGjThreads, 0, s>>>(n, M, piv, lcol, err);
-  NAIR_LAUNCH_CHECK();
+  if (n <= 256) {
+    double *lcol = tmp.alloc<double>(n);
+    k_dense_gj<<<1, kGjThreads, 0, s>>>(n, M, piv, lcol, err);
+    NAIR_LAUNCH_CHECK();
+  } else {
+    double *M2 = tmp.alloc<double>((size_t)n * n);
+    dim3 g(cdiv(n, kGjTileCols), cdiv(n, kGjTileRows));
+    for (int k = 0; k < n; ++k) {
+      k_gj_step<<<g, 256, 0, s>>>(n, k, M, M2, piv, err);
+      NAIR_LAUNCH_CHECK();
+      std::swap(M, M2);
+    }
+    k_gj_unscramble<<<1, 1024, 0, s>>>(n, M, piv);
+    NAIR_LAUNCH_CHECK();
+  }
   L.ainv = mem.alloc<T>((size_t)n * n);
   tot = (long long)n * n;
   k_convert<T><<<grid(tot), kThreads, 0, s>>>(tot, M, L.ainv);

@@ -55,7 +55,10 @@ void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   a.tpc = std::max(1, 256 / tsz);
   const int threads = a.tpc * tsz;
   const size_t smem = ((size_t)a.tpc * tsz + (size_t)a.tpc * b) * sizeof(T);
-  const int blocks = std::max(1, cdiv(a.nrows, a.tpc));
+  a.comp_ctas = cdiv(a.nrows, a.tpc);
+  int blocks = a.comp_ctas;
+  if (OP == OP_JACOBI && a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
+  if (blocks == 0) return;
   switch (b) {
     case 1: k_rowop<T, 1, OP><<<blocks, threads, smem, s>>>(a); break;
     case 3: k_rowop<T, 3, OP><<<blocks, threads, smem, s>>>(a); break;
@@ -110,24 +113,46 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
     NAIR_LAUNCH_CHECK();
     return;
   }
-  // a12-a14: x = P x_c fused into the first sweep, then F sweeps and C sweeps
-  T *bufA = (S % 2 == 1) ? out : L.x2;
-  T *bufB = (S % 2 == 1) ? L.x2 : out;
-  const double avg = (double)L.A.nnzb / L.E;
+  // a12-a14: x = P x_c fused into the first sweep, then F sweeps and C sweeps.
+  // Each sweep updates one class (F or C) from a compact row list, so no warp
+  // mixes updated and idle rows; rows of the other class are copied into the
+  // output buffer only when that buffer holds an older version of them.
+  T *buf[2] = {(S % 2 == 1) ? out : L.x2, (S % 2 == 1) ? L.x2 : out};
+  const int nrow[2] = {L.nF, L.nC};
+  const int *rows[2] = {L.f2f, L.c2f};
+  int cur_ver[2] = {0, 0};        // version of each class (0 = P x_c)
+  int buf_ver[2][2] = {{-1, -1}, {-1, -1}};
   const T *in = N.x;
+  int in_buf = -1;
   for (int k = 0; k < S; ++k) {
+    const int cls = k < P.f_sweeps ? 0 : 1, oth = 1 - cls, ob = k % 2;
     RowArgs<T> a = row_args(L.A, b);
     a.x = in;
     a.ipc = (k == 0) ? L.ipc : nullptr;
     a.f = f;
     a.dinv = L.dinv;
-    a.cf = L.cf;
-    a.which = k < P.f_sweeps ? 0 : 1;
-    a.out = (k % 2 == 0) ? bufA : bufB;
-    ProfScope ps(a.which == 0 ? "jacobi_F" : "jacobi_C", s, l);
+    a.nrows = nrow[cls];
+    a.list = rows[cls];
+    a.out = buf[ob];
+    if (buf_ver[ob][oth] != cur_ver[oth]) {
+      a.ncopy = nrow[oth];
+      a.copy_list = rows[oth];
+      if (k == 0) a.out2 = buf[1 - ob];  // both buffers then hold P x_c on that class
+    }
+    // average blocks per updated row (F and C rows have similar lengths)
+    const double avg = (double)L.A.nnzb / L.E;
+    ProfScope ps(cls == 0 ? "jacobi_F" : "jacobi_C", s, l);
     launch_rowop<T, OP_JACOBI>(a, avg, s);
-    in = a.out;
+    cur_ver[cls] = k + 1;
+    buf_ver[ob][cls] = k + 1;
+    if (a.ncopy) {
+      buf_ver[ob][oth] = cur_ver[oth];
+      if (a.out2) buf_ver[1 - ob][oth] = cur_ver[oth];
+    }
+    in = buf[ob];
+    in_buf = ob;
   }
+  (void)in_buf;
 }
 
 template <typename T>
@@ -144,37 +169,56 @@ template void vcycle<float>(const Hier<float> &, const Params &, const float *, 
 static constexpr int kDotGroup = 8;
 static constexpr int kDotCtas = 304;
 
-// partial[k * G + cta] = sum over this CTA's elements of V_k . w, k < nv
-__global__ void k_multidot(long long n, int nv, const double *__restrict__ V, long long ldv,
-                           const double *__restrict__ w, double *__restrict__ partial) {
+// partial[k * G + cta] = sum over this CTA's elements of V_k . w, k < nv.
+// Vectors are taken NQ at a time with NQ a compile-time count, so no FP64
+// instruction is issued for a vector that does not exist (on GB300 every
+// warp-wide FP64 instruction is scarce).
+template <int NQ>
+__device__ __forceinline__ void dot_group(long long lo, long long hi, int k0, const double *__restrict__ V,
+                                          long long ldv, const double *__restrict__ w,
+                                          double *__restrict__ partial, double (*red)[kThreads / 32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, G = gridDim.x;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+  for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = fma(V[(k0 + q) * ldv + i], wi, acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double a = acc[q];
+    for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    if (lane == 0) red[q][wid] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double a = 0.0;
+    for (int w2 = 0; w2 < kThreads / 32; ++w2) a += red[threadIdx.x][w2];
+    partial[(size_t)(k0 + threadIdx.x) * G + blockIdx.x] = a;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_multidot(long long n, int nv, const double *__restrict__ V,
+                                                       long long ldv, const double *__restrict__ w,
+                                                       double *__restrict__ partial) {
   __shared__ double red[kDotGroup][kThreads / 32];
   const int G = gridDim.x;
   const long long chunk = (n + G - 1) / G;
   const long long lo = chunk * blockIdx.x, hi = min(n, lo + chunk);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k0 = 0; k0 < nv; k0 += kDotGroup) {
-    double acc[kDotGroup];
-#pragma unroll
-    for (int q = 0; q < kDotGroup; ++q) acc[q] = 0.0;
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int q = 0; q < kDotGroup; ++q)
-        if (k0 + q < nv) acc[q] += V[(k0 + q) * ldv + i] * wi;
-    }
-#pragma unroll
-    for (int q = 0; q < kDotGroup; ++q) {
-      double a = acc[q];
-      for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-      if (lane == 0) red[q][wid] = a;
-    }
-    __syncthreads();
-    if (threadIdx.x < kDotGroup && k0 + (int)threadIdx.x < nv) {
-      double a = 0.0;
-      for (int w2 = 0; w2 < kThreads / 32; ++w2) a += red[threadIdx.x][w2];
-      partial[(size_t)(k0 + threadIdx.x) * G + blockIdx.x] = a;
-    }
-    __syncthreads();
+  int k0 = 0;
+  for (; k0 + kDotGroup <= nv; k0 += kDotGroup) dot_group<kDotGroup>(lo, hi, k0, V, ldv, w, partial, red);
+  switch (nv - k0) {
+    case 1: dot_group<1>(lo, hi, k0, V, ldv, w, partial, red); break;
+    case 2: dot_group<2>(lo, hi, k0, V, ldv, w, partial, red); break;
+    case 3: dot_group<3>(lo, hi, k0, V, ldv, w, partial, red); break;
+    case 4: dot_group<4>(lo, hi, k0, V, ldv, w, partial, red); break;
+    case 5: dot_group<5>(lo, hi, k0, V, ldv, w, partial, red); break;
+    case 6: dot_group<6>(lo, hi, k0, V, ldv, w, partial, red); break;
+    case 7: dot_group<7>(lo, hi, k0, V, ldv, w, partial, red); break;
+    default: break;
   }
 }
 
