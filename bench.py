@@ -143,12 +143,84 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# FP64 pipe of one GB300: 1.25 TFLOP/s dense FP64 (nominal figure of the part; an
+# FMA-throughput probe on the box measured 1.249 TFLOP/s).
+FP64_PEAK_TFLOPS = 1.25
+
+# DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
+# launch, averaged over the sweeps of one V-cycle); None until captured for the
+# current kernel.
+JACOBI_TRAFFIC = None
+
+
+def level_work(S, nlev, b):
+    """Algorithmic FP64 work of every block-Jacobi sweep scope, from the hierarchy.
+
+    A sweep over the rows of one class (F or C) at level l does one FMA per
+    exact nonzero of those rows of A_l and b^2 FMAs per row for D^{-1}; its
+    algorithmic bytes are those nonzeros (8 B), their block column indices
+    (4 B per block), the rows' D^{-1} blocks and right-hand side, and one read
+    and one write of the level vector."""
+    work = {}
+    for l in range(nlev):
+        lev = S.level(l)
+        if lev["coarsest"]:
+            continue
+        rp, vals, cf = lev["row_ptr"], lev["vals"], lev["cf"]
+        nnz_block = np.count_nonzero(vals.reshape(len(vals), -1), axis=1)
+        rows = np.repeat(np.arange(lev["E"]), np.diff(rp))
+        for cls, name in ((0, "jacobi_F"), (1, "jacobi_C")):
+            sel = cf[rows] == cls
+            nrow = int(np.count_nonzero(cf == cls))
+            nnz = int(nnz_block[sel].sum())
+            flops = 2.0 * (nnz + nrow * b * b)
+            byts = 8.0 * nnz + 4.0 * int(sel.sum()) + 8.0 * nrow * b * (b + 1) + 16.0 * lev["E"] * b
+            work[f"{name}@L{l}"] = (flops, byts)
+    return work
+
+
+def roofline(nair, params, rp, ci, v, bvec):
+    """Profiled replay of one step (after the timed region): per-scope CUDA-event
+    durations from the library, combined with the algorithmic work of the
+    dominant kernel, the block-Jacobi sweep (all levels)."""
+    import torch
+    nair.profile(True)
+    S = nair.NairSolver(rp, ci, v, **params)
+    x = torch.zeros_like(bvec)
+    _, rep = S.solve(bvec, x)
+    torch.cuda.synchronize()
+    prof = nair.profile_report()
+    nair.profile(False)
+    work = level_work(S, S.num_levels(), S.b)
+    S.close()
+    fl = by = t = 0.0
+    launches = 0
+    for key, (flops, byts) in work.items():
+        if key in prof:
+            n, ms = prof[key]
+            fl += flops * n
+            by += byts * n
+            t += ms * 1e-3
+            launches += n
+    total_ms = sum(ms for k2, (n, ms) in prof.items() if not k2.startswith(("setup_level", "vcycle")))
+    achieved = fl / t / 1e12 if t else 0.0
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": JACOBI_TRAFFIC,
+            "kernel": "k_rowop block-Jacobi sweep, FP64, all levels",
+            "launches_per_step": launches, "ms_per_step": 1e3 * t,
+            "hbm_achieved_gbs": by / t / 1e9 if t else 0.0,
+            "share_of_profiled_kernel_time": 1e3 * t / total_ms if total_ms else None,
+            "how": "CUDA events around every sweep in a profiled replay of one step after the timed region"}
+
+
 def cpu_baseline(workload):
     """The oracle as it stands, one host thread, on a bounded sample (~10-30 s)."""
     import oracle
     oracle.build()
     cfg = dgtransport.CONFIGS[workload]
-    Ns = max(16, cfg["N"] // 2)
+    # the full workload when it is small enough for ~10-30 s of one host thread
+    Ns = cfg["N"] if cfg["N"] * cfg["N"] * (cfg["p"] + 1) ** 2 <= 256 * 256 * 9 else cfg["N"] // 2
     P = dgtransport.make_problem(workload, N=Ns)
     t0 = time.perf_counter()
     H = oracle.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=P["neumann_degree"])
@@ -287,6 +359,7 @@ def main():
         "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
     }
     if not args.no_extras:
+        line["roofline"] = roofline(nair, params, rp, ci, v, bvec)
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/nair.h"
@@ -106,6 +107,25 @@ struct ProfScope {
   void end();  // close the scope early (the destructor then does nothing)
   ~ProfScope() { end(); }
 };
+
+// launch with programmatic dependent launch allowed: the kernel may start while
+// its predecessor in the stream is still running; it must call griddepcontrol.wait
+// (pdl_wait) before reading anything the predecessor writes
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  NAIR_CK(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 
 // exclusive scan of n ints into out[0..n]; out[n] = total; returns the total
 // (synchronises the stream to read it back when want_total is set)

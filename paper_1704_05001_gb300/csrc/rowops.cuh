@@ -46,31 +46,50 @@ __device__ __forceinline__ T xval(const T *__restrict__ x, const int *__restrict
   return x[(size_t)j * bt + c];
 }
 
+// Programmatic dependent launch: let the next kernel of the stream be
+// scheduled now, and wait for the previous kernel's results before reading them.
+// Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// partial sum of row i over the blocks p = p0, p0 + G, ... < p1; the first
+// block's column, interpolation target and values (va0) were loaded before the
+// dependency wait, because the matrix does not change during a V-cycle
 template <typename T, int B>
-__device__ __forceinline__ T row_partial(const RowArgs<T> &a, int i, int g, int r) {
+__device__ __forceinline__ T row_partial(const RowArgs<T> &a, int p0, int p1, int r, int j0,
+                                         const T *va0) {
   const int b = B > 0 ? B : a.b;
   const int bb = b * b;
   T acc = 0;
-  const int p1 = a.rp[i + 1];
-  for (int p = a.rp[i] + g; p < p1; p += a.G) {
-    const int j = a.ci[p];
-    const T *av = a.v + (size_t)p * bb + r * b;
-    if constexpr (B > 0) {
-      T va[B], vx[B];
+  if constexpr (B > 0) {
+    if (p0 < p1 && j0 >= 0) {
+      const T *xj = a.x + (size_t)j0 * B;
+      T vx[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) vx[c] = xj[c];
+#pragma unroll
+      for (int c = 0; c < B; ++c) acc = fma(va0[c], vx[c], acc);
+    }
+    for (int p = p0 + a.G; p < p1; p += a.G) {
+      int j = a.ci[p];
       if (a.ipc) {
-        const int J = a.ipc[j];
-        if (J < 0) continue;
-        const T *xj = a.x + (size_t)J * B;
-#pragma unroll
-        for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
-      } else {
-        const T *xj = a.x + (size_t)j * B;
-#pragma unroll
-        for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
+        j = a.ipc[j];
+        if (j < 0) continue;
       }
+      const T *av = a.v + (size_t)p * bb + r * B;
+      const T *xj = a.x + (size_t)j * B;
+      T va[B], vx[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
 #pragma unroll
       for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
-    } else {
+    }
+  } else {
+    for (int p = p0; p < p1; p += a.G) {
+      const int j = a.ci[p];
+      const T *av = a.v + (size_t)p * bb + r * b;
 #pragma unroll 4
       for (int c = 0; c < b; ++c) acc = fma(av[c], xval<T, 0>(a.x, a.ipc, j, c, b), acc);
     }
@@ -80,14 +99,18 @@ __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int i, int g, int 
 
 template <typename T, int B, int OP>
 __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
+  pdl_launch_dependents();
   if (OP == OP_JACOBI && (int)blockIdx.x >= a.comp_ctas) {
     // copy segment: rows of the class this sweep does not update
     const int bt = B > 0 ? B : a.b;
     const long long g = (long long)(blockIdx.x - a.comp_ctas) * blockDim.x + threadIdx.x;
-    if (g >= (long long)a.ncopy * bt) return;
-    const int row = (int)(g / bt), r = (int)(g - (long long)row * bt);
-    const int i = a.copy_list[row];
-    const T v = xval<T, B>(a.x, a.ipc, i, r, bt);
+    const bool in = g < (long long)a.ncopy * bt;
+    const int row = in ? (int)(g / bt) : 0, r = in ? (int)(g - (long long)row * bt) : 0;
+    const int i = in ? a.copy_list[row] : 0;
+    const int J = (in && a.ipc) ? a.ipc[i] : i;
+    pdl_wait();
+    if (!in) return;
+    const T v = a.ipc ? (J >= 0 ? a.x[(size_t)J * bt + r] : (T)0) : a.x[(size_t)i * bt + r];
     a.out[(size_t)i * bt + r] = v;
     if (a.out2) a.out2[(size_t)i * bt + r] = v;
     return;
@@ -101,14 +124,37 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
   const int g = lt / b, r = lt - g * b;
   const int idx = blockIdx.x * a.tpc + team;
   const bool active = team < a.tpc && idx < a.nrows;
+  // ---- prologue on data that is constant during the V-cycle
   const int i = active ? (a.list ? a.list[idx] : idx) : 0;
-  const bool upd = active;
+  const int p0 = active ? a.rp[i] + g : 0, p1 = active ? a.rp[i + 1] : 0;
+  int j0 = -1;
+  T va0[B > 0 ? B : 1];
+  T dv[(OP == OP_JACOBI && B > 0) ? B : 1];
+  int ii = 0;
+  if constexpr (B > 0) {
+    if (p0 < p1) {
+      j0 = a.ci[p0];
+      if (a.ipc) j0 = a.ipc[j0];
+      const T *av = a.v + (size_t)p0 * B * B + r * B;
+#pragma unroll
+      for (int c = 0; c < B; ++c) va0[c] = av[c];
+    }
+    if (OP == OP_JACOBI && active && g == 0) {
+      const T *d = a.dinv + (size_t)i * B * B + r * B;
+#pragma unroll
+      for (int c = 0; c < B; ++c) dv[c] = d[c];
+    }
+  }
+  if (OP == OP_JACOBI && active && g == 0) ii = a.ipc ? a.ipc[i] : i;
+  if (OP == OP_RESTRICT && active && g == 0) ii = a.c2f[i];
+  // ---- wait for the producer of x and f
+  pdl_wait();
   T acc = 0;
-  if (upd) acc = row_partial<T, B>(a, i, g, r);
+  if (active) acc = row_partial<T, B>(a, p0, p1, r, j0, va0);
   if (a.G > 1) {
     if (team < a.tpc) red[(size_t)team * tsz + lt] = acc;
     __syncthreads();
-    if (g == 0 && upd) {
+    if (g == 0 && active) {
       for (int gg = 1; gg < a.G; ++gg) acc += red[(size_t)team * tsz + gg * b + r];
     }
   }
@@ -117,25 +163,22 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
   } else if (OP == OP_RESID) {
     if (active && g == 0) a.out[(size_t)i * b + r] = a.f[(size_t)i * b + r] - acc;
   } else if (OP == OP_RESTRICT) {
-    if (active && g == 0) a.out[(size_t)i * b + r] = a.f[(size_t)a.c2f[i] * b + r] + acc;
+    if (active && g == 0) a.out[(size_t)i * b + r] = a.f[(size_t)ii * b + r] + acc;
   } else {  // OP_JACOBI
-    if (upd && g == 0) sres[(size_t)team * b + r] = a.f[(size_t)i * b + r] - acc;
+    if (active && g == 0) sres[(size_t)team * b + r] = a.f[(size_t)i * b + r] - acc;
     __syncthreads();
     if (active && g == 0) {
-      T xi = xval<T, B>(a.x, a.ipc, i, r, b);
-      if (upd) {
-        const T *d = a.dinv + (size_t)i * b * b + r * b;
-        const T *sr = sres + (size_t)team * b;
-        T s = 0;
-        if constexpr (B > 0) {
+      T xi = a.ipc ? (ii >= 0 ? a.x[(size_t)ii * b + r] : (T)0) : a.x[(size_t)i * b + r];
+      const T *sr = sres + (size_t)team * b;
+      T s = 0;
+      if constexpr (B > 0) {
 #pragma unroll
-          for (int c = 0; c < B; ++c) s = fma(d[c], sr[c], s);
-        } else {
-          for (int c = 0; c < b; ++c) s = fma(d[c], sr[c], s);
-        }
-        xi += s;
+        for (int c = 0; c < B; ++c) s = fma(dv[c], sr[c], s);
+      } else {
+        const T *d = a.dinv + (size_t)i * b * b + r * b;
+        for (int c = 0; c < b; ++c) s = fma(d[c], sr[c], s);
       }
-      a.out[(size_t)i * b + r] = xi;
+      a.out[(size_t)i * b + r] = xi + s;
     }
   }
 }

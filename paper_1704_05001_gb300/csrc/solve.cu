@@ -35,6 +35,8 @@ __global__ void k_prolong(int E, int b, const int *__restrict__ ipc, const T *__
 // a9: coarsest level, x = A_c^{-1} f (dense), one warp per row
 template <typename T>
 __global__ void k_dense_mv(int n, const T *__restrict__ M, const T *__restrict__ f, T *__restrict__ x) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const T *row = M + (size_t)warp * n;
@@ -59,15 +61,16 @@ void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   int blocks = a.comp_ctas;
   if (OP == OP_JACOBI && a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
   if (blocks == 0) return;
+  const dim3 gr(blocks), bl(threads);
   switch (b) {
-    case 1: k_rowop<T, 1, OP><<<blocks, threads, smem, s>>>(a); break;
-    case 3: k_rowop<T, 3, OP><<<blocks, threads, smem, s>>>(a); break;
-    case 6: k_rowop<T, 6, OP><<<blocks, threads, smem, s>>>(a); break;
-    case 10: k_rowop<T, 10, OP><<<blocks, threads, smem, s>>>(a); break;
-    case 15: k_rowop<T, 15, OP><<<blocks, threads, smem, s>>>(a); break;
-    case 21: k_rowop<T, 21, OP><<<blocks, threads, smem, s>>>(a); break;
-    case 28: k_rowop<T, 28, OP><<<blocks, threads, smem, s>>>(a); break;
-    default: k_rowop<T, 0, OP><<<blocks, threads, smem, s>>>(a); break;
+    case 1: launch_pdl(k_rowop<T, 1, OP>, gr, bl, smem, s, a); break;
+    case 3: launch_pdl(k_rowop<T, 3, OP>, gr, bl, smem, s, a); break;
+    case 6: launch_pdl(k_rowop<T, 6, OP>, gr, bl, smem, s, a); break;
+    case 10: launch_pdl(k_rowop<T, 10, OP>, gr, bl, smem, s, a); break;
+    case 15: launch_pdl(k_rowop<T, 15, OP>, gr, bl, smem, s, a); break;
+    case 21: launch_pdl(k_rowop<T, 21, OP>, gr, bl, smem, s, a); break;
+    case 28: launch_pdl(k_rowop<T, 28, OP>, gr, bl, smem, s, a); break;
+    default: launch_pdl(k_rowop<T, 0, OP>, gr, bl, smem, s, a); break;
   }
   NAIR_LAUNCH_CHECK();
 }
@@ -91,7 +94,8 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
   const int b = H.b;
   if (L.coarsest) {
     ProfScope ps("coarse_solve", s, l);
-    k_dense_mv<T><<<cdiv((long long)L.n * 32, kThreads), kThreads, 0, s>>>(L.n, L.ainv, f, out);
+    launch_pdl(k_dense_mv<T>, dim3(cdiv((long long)L.n * 32, kThreads)), dim3(kThreads), 0, s, L.n,
+               (const T *)L.ainv, f, out);
     NAIR_LAUNCH_CHECK();
     return;
   }
@@ -297,12 +301,16 @@ static void multidot(Krylov &K, long long n, int nv, const double *V, const doub
 
 template <typename T>
 __global__ void k_copy_in(long long n, void *const *__restrict__ ptrs, T *__restrict__ dst) {
+  pdl_launch_dependents();
+  pdl_wait();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dst[i] = (T)(static_cast<const double *>(ptrs[0])[i]);
 }
 
 template <typename T>
 __global__ void k_copy_out(long long n, const T *__restrict__ src, void *const *__restrict__ ptrs) {
+  pdl_launch_dependents();
+  pdl_wait();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) static_cast<double *>(ptrs[1])[i] = (double)src[i];
 }
@@ -337,7 +345,7 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
     k_copy_in<T><<<grid(n), kThreads, 0, s>>>(n, g.dptr, f0);
     NAIR_LAUNCH_CHECK();
     vcycle<T>(H, P, f0, x0, s);
-    k_copy_out<T><<<grid(n), kThreads, 0, s>>>(n, x0, g.dptr);
+    launch_pdl(k_copy_out<T>, dim3(grid(n)), dim3(kThreads), 0, s, n, (const T *)x0, (void *const *)g.dptr);
     NAIR_LAUNCH_CHECK();
   } catch (...) {
     cudaStreamEndCapture(s, &graph);
