@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--vcycles", type=int, default=0,
+                    help="profiling aid: build the hierarchy (no CUDA graph) and apply this many "
+                         "V-cycles to the right-hand side instead of benchmarking")
     return ap.parse_args()
 
 
@@ -255,6 +258,16 @@ def main():
     P = make_inputs(args.workload)
     k = P["neumann_degree"]
     params = dict(neumann_degree=k, precision=args.precision)
+    if args.vcycles:
+        S = nair.NairSolver(torch.from_numpy(P["row_ptr"]).to(dev), torch.from_numpy(P["col"]).to(dev),
+                            torch.from_numpy(P["vals"]).to(dev), use_graphs=0, **params)
+        f = torch.from_numpy(P["rhs"]).to(dev)
+        for _ in range(args.vcycles):
+            S.vcycle(f)
+        torch.cuda.synchronize()
+        print(json.dumps({"vcycles": args.vcycles, "levels": S.num_levels(),
+                          "elements": [S.sizes(l)["E"] for l in range(S.num_levels())]}))
+        return
     rp = torch.from_numpy(P["row_ptr"]).to(dev)
     ci = torch.from_numpy(P["col"]).to(dev)
     v = torch.from_numpy(P["vals"]).to(dev)
