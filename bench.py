@@ -217,6 +217,71 @@ def roofline(nair, params, rp, ci, v, bvec):
             "how": "CUDA events around every sweep in a profiled replay of one step after the timed region"}
 
 
+def timed_steps(fn, steps, flush, stream):
+    """Device time (CUDA events on the launching stream) of `steps` calls of fn,
+    with an L2 flush before each call outside the timed events."""
+    import torch
+    total = 0.0
+    out = None
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps, out
+
+
+def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps):
+    """The mixed-precision form and the adjoint (forward + A^T solve) timed beside
+    the FP64 solver on the same workload and tolerance."""
+    import torch
+    n = P["n"]
+    w = torch.from_numpy(dgtransport.functional_weights(n)).to(bvec.device)
+    res = {}
+    xref = x64.clone()
+
+    def fwd(prec):
+        def f():
+            S = nair.NairSolver(rp, ci, v, **dict(params, precision=prec))
+            xx, rep = S.solve(bvec)
+            S.close()
+            return xx, rep
+        return f
+
+    def fwd_adj(prec):
+        def f():
+            S = nair.NairSolver(rp, ci, v, **dict(params, precision=prec))
+            xx, rep = S.solve(bvec)
+            lam, repa = S.adjoint_solve(w)
+            S.close()
+            return xx, lam, rep, repa
+        return f
+
+    for prec in ("fp64", "mixed"):
+        fwd(prec)()
+        ms, (xx, rep) = timed_steps(fwd(prec), steps, flush, stream)
+        res[f"forward_{prec}"] = {"ms_per_step": ms, "mdof_s": n / (ms * 1e-3) / 1e6,
+                                 "setup_ms": rep["setup_ms"], "solve_ms": rep["solve_ms"],
+                                 "iterations": rep["iterations"], "rel_res": rep["rel_res"],
+                                 "rel_diff_vs_fp64": float((xx - xref).norm() / xref.norm())}
+    lam_ref = None
+    for prec in ("fp64", "mixed"):
+        fwd_adj(prec)()
+        ms, (xx, lam, rep, repa) = timed_steps(fwd_adj(prec), steps, flush, stream)
+        if lam_ref is None:
+            lam_ref = lam.clone()
+        res[f"forward_adjoint_{prec}"] = {
+            "ms_per_step": ms, "adjoint_setup_ms": repa["setup_ms"], "adjoint_solve_ms": repa["solve_ms"],
+            "adjoint_iterations": repa["iterations"], "adjoint_rel_res": repa["rel_res"],
+            "lambda_rel_diff_vs_fp64": float((lam - lam_ref).norm() / lam_ref.norm())}
+    return res
+
+
 def cpu_baseline(workload):
     """The oracle as it stands, one host thread, on a bounded sample (~10-30 s)."""
     import oracle
@@ -354,6 +419,10 @@ def main():
         e2e = {"value": world * P["n"] / (e2e_ms / args.steps * 1e-3) / 1e6, "unit": "MDOF/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    variants = None
+    if not args.no_extras:
+        variants = measure_variants(nair, params, rp, ci, v, bvec, P, x, flush, stream, args.steps)
+
     if rank != 0:
         return
     last = reps[-1]
@@ -371,6 +440,8 @@ def main():
         "op_complexity": last["op_complexity"], "cycle_complexity": last["cycle_complexity"],
         "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e,
     }
+    if variants:
+        line["variants"] = variants
     if not args.no_extras:
         line["roofline"] = roofline(nair, params, rp, ci, v, bvec)
         line["cpu_baseline"] = cpu_baseline(args.workload)

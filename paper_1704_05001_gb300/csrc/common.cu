@@ -227,10 +227,12 @@ int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, Mem &tmp, boo
 }
 
 int read_int(const int *p, cudaStream_t s) {
-  int v = 0;
-  NAIR_CK(cudaMemcpyAsync(&v, p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  // pinned staging word (one per host thread) keeps the read-back short
+  static thread_local int *stage = nullptr;
+  if (!stage) NAIR_CK(cudaMallocHost(&stage, sizeof(int)));
+  NAIR_CK(cudaMemcpyAsync(stage, p, sizeof(int), cudaMemcpyDeviceToHost, s));
   NAIR_CK(cudaStreamSynchronize(s));
-  return v;
+  return *stage;
 }
 
 }  // namespace nair

@@ -701,12 +701,9 @@ __global__ void __launch_bounds__(1024) k_gj_unscramble(int n, double *__restric
 static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
 
 template <typename T>
-static void spgemm(int b, const SpgemmIdx &X, const T *lv, const T *rv, const T *iv, int negate,
-                   int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out) {
+static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T *rv, const T *iv,
+                   int negate, int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out) {
   const int nrows = X.nrows;
-  int left_nnz = 0;
-  NAIR_CK(cudaMemcpyAsync(&left_nnz, X.lrp + nrows, sizeof(int), cudaMemcpyDeviceToHost, s));
-  NAIR_CK(cudaStreamSynchronize(s));
   int *cursor = tmp.alloc<int>(left_nnz + 1);
   int *cnt = tmp.alloc<int>(nrows + 1);
   out.nrows = nrows;
@@ -839,17 +836,21 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   NAIR_LAUNCH_CHECK();
   int rounds = 0;
   ProfScope ps_cf("cf_split", s, l);
+  // rounds are issued two at a time between read-backs of the undecided count;
+  // a round with no undecided point changes nothing
   for (;;) {
-    NAIR_CK(cudaMemsetAsync(remaining, 0, sizeof(int), s));
-    k_pmis_mark<<<grid(nnzb), kThreads, 0, s>>>(nnzb, brow, L.A.ci, strong, L.cf, lam, hash, mark, rounds);
-    NAIR_LAUNCH_CHECK();
-    k_pmis_select<<<grid(E), kThreads, 0, s>>>(E, L.cf, mark, rounds);
-    NAIR_LAUNCH_CHECK();
-    k_pmis_fmark<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, strong, L.cf, remaining);
-    NAIR_LAUNCH_CHECK();
-    ++rounds;
+    for (int rep = 0; rep < 2; ++rep) {
+      NAIR_CK(cudaMemsetAsync(remaining, 0, sizeof(int), s));
+      k_pmis_mark<<<grid(nnzb), kThreads, 0, s>>>(nnzb, brow, L.A.ci, strong, L.cf, lam, hash, mark, rounds);
+      NAIR_LAUNCH_CHECK();
+      k_pmis_select<<<grid(E), kThreads, 0, s>>>(E, L.cf, mark, rounds);
+      NAIR_LAUNCH_CHECK();
+      k_pmis_fmark<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, strong, L.cf, remaining);
+      NAIR_LAUNCH_CHECK();
+      ++rounds;
+    }
     if (read_int(remaining, s) == 0) break;
-    if (rounds > E + 1) fail(NAIR_ERR_CUDA, "C/F splitting did not terminate");
+    if (rounds > E + 2) fail(NAIR_ERR_CUDA, "C/F splitting did not terminate");
   }
   L.cf_rounds = rounds;
   ps_cf.end();
@@ -915,7 +916,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   for (int t = 0; t < P.k; ++t) {
     SpgemmIdx X{nF, Lm.rp, Lm.ci, nullptr, Tk.rp, Tk.ci, Dg.rp, Dg.rp, nullptr};
     DBsr<T> Tn;
-    spgemm<T>(b, X, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn);
+    spgemm<T>(b, X, Lm.nnzb, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn);
     if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn);
     release_bsr(mem, Tk);
     Tk = Tn;
@@ -935,7 +936,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   }
   {
     SpgemmIdx X{nC, Acf.rp, Acf.ci, nullptr, Tk.rp, Tk.ci, nullptr, nullptr, nullptr};
-    spgemm<T>(b, X, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R);
+    spgemm<T>(b, X, Acf.nnzb, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R);
   }
   L.R_ci_f = L.R.ci;
   L.R.ci = mem.alloc<int>(L.R.nnzb);
@@ -976,7 +977,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   Level<T> nx;
   {
     SpgemmIdx X{nC, L.R.rp, L.R.ci, nullptr, AP.rp, AP.ci, AP.rp, AP.ci, L.c2f};
-    spgemm<T>(b, X, L.R.v, AP.v, AP.v, 0, nC, s, mem, tmp, nx.A);
+    spgemm<T>(b, X, L.R.nnzb, L.R.v, AP.v, AP.v, 0, nC, s, mem, tmp, nx.A);
     if (P.filter_targets & 2) filter<T>(b, tol2, s, mem, tmp, nx.A);
   }
   nx.E = nC;
