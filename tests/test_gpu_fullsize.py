@@ -100,7 +100,7 @@ def test_c5_full_forward_adjoint_mixed_vs_fp64(nair):
     w = dev(D.functional_weights(n))
     out = {}
     for prec in ("fp64", "mixed"):
-        S = nair.NairSolver(*args, neumann_degree=1, precision=prec)
+        S = nair.NairSolver(*args, neumann_degree=P["neumann_degree"], precision=prec)
         x, rep = S.solve(dev(P["rhs"]))
         lam, repa = S.adjoint_solve(w)
         gs, gq = nair.gradients(dev(P["mass"]), lam, x)
