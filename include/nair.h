@@ -75,6 +75,7 @@ typedef struct {
   void *stream;           /* cudaStream_t for all work; NULL */
   int32_t keep_setup_data;/* keep strength, L and Delta for nair_get_level; 0 */
   int32_t use_graphs;     /* replay the V-cycle as a CUDA graph; 1 */
+  int32_t sweep_timing;   /* stamp every block-Jacobi sweep with the device clock; 0 */
 } nair_params;
 
 /* Solve report.  history is an optional host buffer owned by the caller. */
@@ -190,6 +191,16 @@ nair_status nair_gradients(int32_t E, int32_t b, const double *M, const double *
 /* Total number of kernels this library has launched in the process so far
  * (a diagnostic counter; every launch site increments it). */
 nair_status nair_kernel_launches(int64_t *count);
+
+/* Device time of the block-Jacobi sweeps of the forward hierarchy, recorded
+ * when the handle was set up with sweep_timing = 1: for level `level` and class
+ * `cls` (0 = F sweeps, 1 = C sweeps), the number of sweeps run so far and their
+ * summed duration in ms, each sweep timed from its first thread block passing
+ * the dependency wait to its last thread block finishing (%globaltimer).  The
+ * stamps ride inside the kernels, so the CUDA graph and the overlap of
+ * consecutive launches are kept. */
+nair_status nair_sweep_timing(const nair_handle *h, int32_t level, int32_t cls, int64_t *sweeps,
+                              double *total_ms);
 
 /* Per-kernel timing (diagnostic).  nair_profile(1) clears the counters and
  * starts recording a CUDA event pair around each timed launch site (the

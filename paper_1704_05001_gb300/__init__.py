@@ -44,7 +44,8 @@ class _Params(ctypes.Structure):
                 ("max_dense", ctypes.c_int32), ("cf_seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
                 ("maxiter", ctypes.c_int32), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
-                ("keep_setup_data", ctypes.c_int32), ("use_graphs", ctypes.c_int32)]
+                ("keep_setup_data", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
+                ("sweep_timing", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -61,7 +62,8 @@ _lib = None
 EXPORTS = ["nair_default_params", "nair_setup", "nair_solve", "nair_adjoint_solve", "nair_vcycle",
            "nair_free", "nair_num_levels", "nair_level_sizes", "nair_get_level", "nair_block_inverse",
            "nair_assemble_sigma", "nair_mass_apply", "nair_gradients", "nair_kernel_launches",
-           "nair_profile", "nair_profile_entry", "nair_block_inverse_noalloc", "nair_last_error"]
+           "nair_profile", "nair_profile_entry", "nair_block_inverse_noalloc", "nair_sweep_timing",
+           "nair_last_error"]
 
 
 def lib():
@@ -91,6 +93,7 @@ def lib():
     L.nair_gradients.argtypes = [I32, I32, P, P, P, P, P, P]
     L.nair_kernel_launches.argtypes = [ctypes.POINTER(I64)]
     L.nair_profile.argtypes = [I32]
+    L.nair_sweep_timing.argtypes = [P, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(D)]
     L.nair_profile_entry.argtypes = [I32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(I64),
                                      ctypes.POINTER(D)]
     L.nair_last_error.argtypes = []
@@ -251,6 +254,19 @@ class NairSolver:
                                         out.ctypes.data_as(ctypes.c_void_p), need.value,
                                         ctypes.byref(need)), "nair_get_level")
         return out.reshape(shape) if shape is not None else out
+
+    def sweep_timing(self):
+        """{(level, "F"|"C"): (sweeps, total ms)} stamped on the device (sweep_timing=1)."""
+        out = {}
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0)
+        for l in range(self.num_levels()):
+            for cls, nm in ((0, "F"), (1, "C")):
+                _check(lib().nair_sweep_timing(self._h, l, cls, ctypes.byref(n), ctypes.byref(ms)),
+                       "nair_sweep_timing")
+                if n.value:
+                    out[(l, nm)] = (n.value, ms.value)
+        return out
 
     def level(self, l, adjoint=False):
         """Host copies of the arrays of level l (values as float64)."""

@@ -76,6 +76,7 @@ Params resolve_params(const nair_params *p, int b) {
   P.tol = p->tol;
   P.keep = p->keep_setup_data;
   P.use_graphs = p->use_graphs;
+  P.sweep_timing = p->sweep_timing;
   return P;
 }
 }  // namespace nair
@@ -294,6 +295,24 @@ void nair_default_params(nair_params *p) {
 
 const char *nair_last_error(void) { return g_last_error.c_str(); }
 
+nair_status nair_sweep_timing(const nair_handle *h, int32_t level, int32_t cls, int64_t *sweeps,
+                              double *total_ms) {
+  NAIR_API_BEGIN
+  if (!h || !sweeps || !total_ms || cls < 0 || cls > 1) return set_error(NAIR_ERR_INVALID_ARG, "bad arguments");
+  const SweepClock &c = h->mixed ? h->h32.clock : h->h64.clock;
+  const int nl = h->mixed ? h->h32.nlev : h->h64.nlev;
+  if (level < 0 || level >= nl) return set_error(NAIR_ERR_INVALID_ARG, "level out of range");
+  if (!c.dev) {
+    *sweeps = 0;
+    *total_ms = 0.0;
+    return NAIR_OK;
+  }
+  *sweeps = c.count[2 * level + cls];
+  *total_ms = c.ms[2 * level + cls];
+  return NAIR_OK;
+  NAIR_API_END
+}
+
 nair_status nair_profile(int32_t enable) {
   NAIR_API_BEGIN
   prof_enable(enable != 0);
@@ -466,6 +485,8 @@ void nair_free(nair_handle *h) {
   cudaStreamSynchronize(h->s);
   release_graph(h->h64.graph);
   release_graph(h->h32.graph);
+  release_clock(h->h64.clock);
+  release_clock(h->h32.clock);
   h->K.mem.release_all();
   h->mem.release_all();
   cudaStreamSynchronize(h->s);

@@ -50,11 +50,22 @@ struct VGraph {
   long long nodes = 0;    // kernels per replay
 };
 
+// device-clock stamps of the block-Jacobi sweeps: slot s holds the earliest
+// start and the latest end of the sweep with site index s = level * S + k
+struct SweepClock {
+  unsigned long long *dev = nullptr;   // [2 * nsites]: starts, then ends
+  unsigned long long *host = nullptr;  // pinned copy
+  int nsites = 0, S = 0;
+  std::vector<long long> count;        // per (level, class)
+  std::vector<double> ms;
+};
+
 template <typename T>
 struct Hier {
   int b = 0, nlev = 0;
   std::vector<Level<T>> lev;
   mutable VGraph graph;
+  mutable SweepClock clock;
   double setup_ms = 0.0;
   double op_complexity = 0.0, cycle_complexity = 0.0;
 };
@@ -65,7 +76,7 @@ struct Params {
   uint64_t seed;
   int precision, restart, maxiter;
   double tol;
-  int keep, use_graphs;
+  int keep, use_graphs, sweep_timing;
 };
 
 Params resolve_params(const nair_params *p, int b);
@@ -80,6 +91,7 @@ void vcycle(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s)
 
 // release the V-cycle graph of a hierarchy
 void release_graph(VGraph &g);
+void release_clock(SweepClock &c);
 
 // diagonal-block inverses in FP64 of the blocks at positions pos[] (or 0..nblk-1)
 template <typename TI>

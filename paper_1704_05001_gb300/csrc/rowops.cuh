@@ -34,7 +34,15 @@ struct RowArgs {
   int comp_ctas, ncopy;
   const int *copy_list;
   T *out2;
+  unsigned long long *stamp;  // optional: [0] earliest start, [ns] latest end (device clock)
+  int ns;
 };
+
+__device__ __forceinline__ unsigned long long global_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 template <typename T, int B>
 __device__ __forceinline__ T xval(const T *__restrict__ x, const int *__restrict__ ipc, int j, int c, int b) {
@@ -109,10 +117,16 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
     const int i = in ? a.copy_list[row] : 0;
     const int J = (in && a.ipc) ? a.ipc[i] : i;
     pdl_wait();
-    if (!in) return;
-    const T v = a.ipc ? (J >= 0 ? a.x[(size_t)J * bt + r] : (T)0) : a.x[(size_t)i * bt + r];
-    a.out[(size_t)i * bt + r] = v;
-    if (a.out2) a.out2[(size_t)i * bt + r] = v;
+    if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
+    if (in) {
+      const T v = a.ipc ? (J >= 0 ? a.x[(size_t)J * bt + r] : (T)0) : a.x[(size_t)i * bt + r];
+      a.out[(size_t)i * bt + r] = v;
+      if (a.out2) a.out2[(size_t)i * bt + r] = v;
+    }
+    if (a.stamp) {
+      __syncthreads();
+      if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
+    }
     return;
   }
   extern __shared__ unsigned char smraw[];
@@ -149,6 +163,7 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
   if (OP == OP_RESTRICT && active && g == 0) ii = a.c2f[i];
   // ---- wait for the producer of x and f
   pdl_wait();
+  if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
   T acc = 0;
   if (active) acc = row_partial<T, B>(a, p0, p1, r, j0, va0);
   if (a.G > 1) {
@@ -180,6 +195,10 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
       }
       a.out[(size_t)i * b + r] = xi + s;
     }
+  }
+  if (a.stamp) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
   }
 }
 

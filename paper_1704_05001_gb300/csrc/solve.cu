@@ -143,6 +143,10 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
       a.copy_list = rows[oth];
       if (k == 0) a.out2 = buf[1 - ob];  // both buffers then hold P x_c on that class
     }
+    if (H.clock.dev) {
+      a.stamp = H.clock.dev + (size_t)l * S + k;
+      a.ns = H.clock.nsites;
+    }
     // average blocks per updated row (F and C rows have similar lengths)
     const double avg = (double)L.A.nnzb / L.E;
     ProfScope ps(cls == 0 ? "jacobi_F" : "jacobi_C", s, l);
@@ -315,6 +319,48 @@ __global__ void k_copy_out(long long n, const T *__restrict__ src, void *const *
   if (i < n) static_cast<double *>(ptrs[1])[i] = (double)src[i];
 }
 
+void release_clock(SweepClock &c) {
+  if (c.dev) cudaFree(c.dev);
+  if (c.host) cudaFreeHost(c.host);
+  c = SweepClock();
+}
+
+// reset all sweep stamps (starts to the maximum, ends to zero) on the stream
+static void clock_reset(const SweepClock &c, cudaStream_t s) {
+  NAIR_CK(cudaMemsetAsync(c.dev, 0xff, sizeof(unsigned long long) * c.nsites, s));
+  NAIR_CK(cudaMemsetAsync(c.dev + c.nsites, 0, sizeof(unsigned long long) * c.nsites, s));
+}
+
+template <typename T>
+static void clock_init(const Hier<T> &H, const Params &P) {
+  SweepClock &c = H.clock;
+  if (!P.sweep_timing || c.dev) return;
+  c.S = P.f_sweeps + P.c_sweeps;
+  c.nsites = std::max(1, H.nlev * c.S);
+  NAIR_CK(cudaMalloc(&c.dev, sizeof(unsigned long long) * 2 * c.nsites));
+  NAIR_CK(cudaMallocHost(&c.host, sizeof(unsigned long long) * 2 * c.nsites));
+  c.count.assign(2 * H.nlev, 0);
+  c.ms.assign(2 * H.nlev, 0.0);
+}
+
+// after the stream has been synchronised: add the stamped sweep durations
+template <typename T>
+static void clock_collect(const Hier<T> &H, const Params &P, cudaStream_t s) {
+  SweepClock &c = H.clock;
+  if (!c.dev) return;
+  NAIR_CK(cudaMemcpyAsync(c.host, c.dev, sizeof(unsigned long long) * 2 * c.nsites, cudaMemcpyDeviceToHost, s));
+  NAIR_CK(cudaStreamSynchronize(s));
+  for (int l = 0; l < H.nlev; ++l)
+    for (int k = 0; k < c.S; ++k) {
+      const int site = l * c.S + k;
+      const unsigned long long t0 = c.host[site], t1 = c.host[c.nsites + site];
+      if (t1 == 0 || t0 == ~0ULL || t1 < t0) continue;
+      const int cls = k < P.f_sweeps ? 0 : 1;
+      c.count[2 * l + cls] += 1;
+      c.ms[2 * l + cls] += (double)(t1 - t0) * 1e-6;
+    }
+}
+
 void release_graph(VGraph &g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
   if (g.dptr) cudaFree(g.dptr);
@@ -342,6 +388,7 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
   NAIR_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   try {
     T *f0 = H.lev[0].f, *x0 = H.lev[0].x;
+    if (H.clock.dev) clock_reset(H.clock, s);
     k_copy_in<T><<<grid(n), kThreads, 0, s>>>(n, g.dptr, f0);
     NAIR_LAUNCH_CHECK();
     vcycle<T>(H, P, f0, x0, s);
@@ -362,6 +409,7 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
 template <typename T>
 void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s,
              long long n) {
+  clock_init(H, P);
   if (P.use_graphs && !prof_on()) {
     VGraph &g = H.graph;
     if (!g.exec) capture_graph<T>(H, P, n);
@@ -372,6 +420,7 @@ void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cuda
     add_launches(g.nodes);
     return;
   }
+  if (H.clock.dev) clock_reset(H.clock, s);
   if constexpr (std::is_same<T, double>::value) {
     vcycle<double>(H, P, v, z, s);
   } else {
@@ -466,6 +515,7 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
         NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
       }
       NAIR_CK(cudaStreamSynchronize(s));
+      clock_collect(H, P, s);
       for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hh[k] + hh[m + 1 + k];
       const double hn = std::sqrt(hh[2 * (m + 1)]);
       if (!std::isfinite(hn)) return NAIR_ERR_BREAKDOWN;
