@@ -151,9 +151,9 @@ def run_reference(args, rank, world):
 FP64_PEAK_TFLOPS = 1.25
 
 # DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
-# launch, averaged over the sweeps of one V-cycle); None until captured for the
-# current kernel.
-JACOBI_TRAFFIC = None
+# launch, averaged over the 40 sweeps of one C2 V-cycle: dram__bytes_read.sum +
+# dram__bytes_write.sum); set to None whenever the kernel changes until recaptured.
+JACOBI_TRAFFIC = 23.63e6
 
 
 def level_work(S, nlev, b):

@@ -436,6 +436,109 @@ __global__ void k_spgemm_numeric(long long total, int b, SpgemmIdx X, const T *_
   ov[g] = negate ? -acc : acc;
 }
 
+// Warp-per-row form of the same product.  The lanes own the row's left entries
+// (32 per chunk, at most kMergeChunks chunks) and keep one cursor each into the
+// sorted right row it selects; every step the warp takes the smallest head
+// column (the next output column), records which entries meet it -- in
+// ascending left-entry order, the order of the canonical sum -- and advances
+// them.  COUNT gives the output and product counts of each row; FILL writes the
+// output columns, each output's slice of (left entry, right entry) pairs, and
+// the position of its start value in the init row (or -1).  A row with more
+// left entries than the warp holds raises `overflow` (the caller then uses the
+// thread-per-row kernels above).
+static constexpr int kMergeChunks = 8;
+
+template <bool FILL>
+__global__ void k_spgemm_warp(SpgemmIdx X, int *__restrict__ cnt, int *__restrict__ pcnt,
+                              const int *__restrict__ orp, const int *__restrict__ prp,
+                              int *__restrict__ oci, int *__restrict__ orow, int *__restrict__ pbeg,
+                              int2 *__restrict__ pairs, int *__restrict__ iq, int *__restrict__ overflow) {
+  const int lane = threadIdx.x & 31;
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= X.nrows) return;  // uniform across the warp
+  const int l0 = X.lrp[i], l1 = X.lrp[i + 1];
+  if (l1 - l0 > 32 * kMergeChunks) {
+    if (lane == 0) {
+      atomicOr(overflow, 1);
+      if (!FILL) { cnt[i] = 0; pcnt[i] = 0; }
+    }
+    return;
+  }
+  int cur[kMergeChunks], end[kMergeChunks];
+#pragma unroll
+  for (int c = 0; c < kMergeChunks; ++c) {
+    const int p = l0 + c * 32 + lane;
+    cur[c] = end[c] = 0;
+    if (p < l1) {
+      const int m = X.rmap ? X.rmap[X.lci[p]] : X.lci[p];
+      cur[c] = X.rrp[m];
+      end[c] = X.rrp[m + 1];
+    }
+  }
+  int icur = 0, iend = 0;
+  if (X.irp && lane == 0) {
+    const int ii = X.imap ? X.imap[i] : i;
+    icur = X.irp[ii];
+    iend = X.irp[ii + 1];
+  }
+  int nout = 0, pw = FILL ? prp[i] : 0, w = FILL ? orp[i] : 0;
+  for (;;) {
+    int h = INT_MAX;
+#pragma unroll
+    for (int c = 0; c < kMergeChunks; ++c)
+      if (cur[c] < end[c]) h = min(h, X.rci[cur[c]]);
+    if (icur < iend) h = min(h, X.ici[icur]);
+    const int jmin = __reduce_min_sync(0xffffffffu, h);
+    if (jmin == INT_MAX) break;
+    const int im = (icur < iend && X.ici[icur] == jmin) ? icur : -1;
+    if (FILL && lane == 0) {
+      oci[w] = jmin;
+      orow[w] = i;
+      pbeg[w] = pw;
+      iq[w] = im;
+    }
+#pragma unroll
+    for (int c = 0; c < kMergeChunks; ++c) {
+      const bool mt = cur[c] < end[c] && X.rci[cur[c]] == jmin;
+      const unsigned ball = __ballot_sync(0xffffffffu, mt);
+      if (FILL && mt) pairs[pw + __popc(ball & ((1u << lane) - 1u))] = make_int2(l0 + c * 32 + lane, cur[c]);
+      pw += __popc(ball);
+      if (mt) ++cur[c];
+    }
+    if (im >= 0) ++icur;
+    ++w;
+    ++nout;
+  }
+  if (!FILL && lane == 0) {
+    cnt[i] = nout;
+    pcnt[i] = pw;
+  }
+}
+
+// numeric phase over the recorded pairs: the start value, then one fma chain over
+// the pairs in order (left entry ascending) and t ascending
+template <typename T>
+__global__ void k_spgemm_pairs(long long total, int b, const int *__restrict__ pbeg,
+                               const int2 *__restrict__ pairs, const int *__restrict__ iq,
+                               const T *__restrict__ lv, const T *__restrict__ rv,
+                               const T *__restrict__ iv, int negate, T *__restrict__ ov) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long blk = g / bb;
+  const int rc = (int)(g - blk * bb), r = rc / b, c = rc - r * b;
+  const int q0 = iq[blk];
+  T acc = q0 >= 0 ? iv[(size_t)q0 * bb + rc] : (T)0;
+  const int k1 = pbeg[blk + 1];
+  for (int k = pbeg[blk]; k < k1; ++k) {
+    const int2 pq = pairs[k];
+    const T *a = lv + (size_t)pq.x * bb + r * b;
+    const T *bv = rv + (size_t)pq.y * bb + c;
+    for (int t = 0; t < b; ++t) acc = fma_rn(a[t], bv[t * b], acc);
+  }
+  ov[g] = negate ? -acc : acc;
+}
+
 // ---------------------------------------------------------------------------
 // a8: filtering.  Drop X_ij (j != i) when ||X_ij||^2 <= tol^2 ||X_ii||^2
 // ---------------------------------------------------------------------------
@@ -547,8 +650,10 @@ __global__ void k_dense_fill(long long total, int b, int n, const int *__restric
 
 static constexpr int kGjThreads = 1024;
 
-__global__ void __launch_bounds__(kGjThreads) k_dense_gj(int n, double *__restrict__ M, int *__restrict__ piv,
-                                                         double *__restrict__ lcol, int *__restrict__ err) {
+// in-place Gauss-Jordan with partial pivoting on an n x n matrix held by one
+// thread block (in shared or global memory); same arithmetic as the block inverse
+__device__ void dense_gj_cta(int n, double *__restrict__ M, int *__restrict__ piv,
+                             double *__restrict__ lcol, int *__restrict__ err) {
   __shared__ double rv[kGjThreads / 32];
   __shared__ int ri[kGjThreads / 32];
   __shared__ int pk;
@@ -617,6 +722,22 @@ __global__ void __launch_bounds__(kGjThreads) k_dense_gj(int n, double *__restri
       }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kGjThreads) k_dense_gj(int n, double *__restrict__ M, int *__restrict__ piv,
+                                                         double *__restrict__ lcol, int *__restrict__ err) {
+  dense_gj_cta(n, M, piv, lcol, err);
+}
+
+// the same, with the matrix staged in shared memory (small coarsest levels)
+__global__ void __launch_bounds__(kGjThreads) k_dense_gj_smem(int n, double *__restrict__ Mg, int *__restrict__ err) {
+  extern __shared__ double sm[];
+  double *M = sm, *lcol = sm + (size_t)n * n;
+  int *piv = reinterpret_cast<int *>(lcol + n);
+  for (long long g = threadIdx.x; g < (long long)n * n; g += blockDim.x) M[g] = Mg[g];
+  __syncthreads();
+  dense_gj_cta(n, M, piv, lcol, err);
+  for (long long g = threadIdx.x; g < (long long)n * n; g += blockDim.x) Mg[g] = M[g];
 }
 
 // Larger coarsest matrices: one launch per Gauss-Jordan step k, Min -> Mout,
@@ -701,15 +822,15 @@ __global__ void __launch_bounds__(1024) k_gj_unscramble(int n, double *__restric
 static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
 
 template <typename T>
-static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T *rv, const T *iv,
-                   int negate, int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out) {
+static void spgemm_rowwise(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T *rv,
+                           const T *iv, int negate, int ncols, cudaStream_t s, Mem &mem, Mem &tmp,
+                           DBsr<T> &out) {
   const int nrows = X.nrows;
   int *cursor = tmp.alloc<int>(left_nnz + 1);
   int *cnt = tmp.alloc<int>(nrows + 1);
   out.nrows = nrows;
   out.ncols = ncols;
   out.rp = mem.alloc<int>(nrows + 1);
-  ProfScope ps("spgemm", s);
   k_spgemm_symbolic<false><<<grid(nrows), kThreads, 0, s>>>(X, cursor, cnt, nullptr, nullptr, nullptr);
   NAIR_LAUNCH_CHECK();
   out.nnzb = exclusive_scan(cnt, out.rp, nrows, s, tmp);
@@ -727,6 +848,71 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
   tmp.release(orow);
   tmp.release(cnt);
   tmp.release(cursor);
+}
+
+template <typename T>
+static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T *rv, const T *iv,
+                   int negate, int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out) {
+  ProfScope ps("spgemm", s);
+  const int nrows = X.nrows;
+  int *cnt = tmp.alloc<int>(nrows + 1), *pcnt = tmp.alloc<int>(nrows + 1);
+  int *prp = tmp.alloc<int>(nrows + 1), *flags = tmp.alloc<int>(4);
+  NAIR_CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
+  const int wblocks = std::max(1, cdiv((long long)nrows * 32, kThreads));
+  k_spgemm_warp<false><<<wblocks, kThreads, 0, s>>>(X, cnt, pcnt, nullptr, nullptr, nullptr, nullptr,
+                                                    nullptr, nullptr, nullptr, flags);
+  NAIR_LAUNCH_CHECK();
+  out.nrows = nrows;
+  out.ncols = ncols;
+  out.rp = mem.alloc<int>(nrows + 1);
+  exclusive_scan(cnt, out.rp, nrows, s, tmp, false);
+  exclusive_scan(pcnt, prp, nrows, s, tmp, false);
+  // one read-back: output blocks, products, overflow flag
+  NAIR_CK(cudaMemcpyAsync(flags + 1, out.rp + nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  NAIR_CK(cudaMemcpyAsync(flags + 2, prp + nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  int h[3];
+  {
+    static thread_local int *stage = nullptr;
+    if (!stage) NAIR_CK(cudaMallocHost(&stage, 4 * sizeof(int)));
+    NAIR_CK(cudaMemcpyAsync(stage, flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    NAIR_CK(cudaStreamSynchronize(s));
+    h[0] = stage[0];
+    h[1] = stage[1];
+    h[2] = stage[2];
+  }
+  if (h[0]) {  // a row longer than the warp merge holds: thread-per-row kernels
+    mem.release(out.rp);
+    tmp.release(flags);
+    tmp.release(prp);
+    tmp.release(pcnt);
+    tmp.release(cnt);
+    spgemm_rowwise<T>(b, X, left_nnz, lv, rv, iv, negate, ncols, s, mem, tmp, out);
+    return;
+  }
+  out.nnzb = h[1];
+  const int nprod = h[2];
+  out.ci = mem.alloc<int>(out.nnzb);
+  int *orow = tmp.alloc<int>(out.nnzb), *pbeg = tmp.alloc<int>(out.nnzb + 1), *iq = tmp.alloc<int>(out.nnzb);
+  int2 *pairs = tmp.alloc<int2>(nprod);
+  k_spgemm_warp<true><<<wblocks, kThreads, 0, s>>>(X, nullptr, nullptr, out.rp, prp, out.ci, orow, pbeg,
+                                                   pairs, iq, flags);
+  NAIR_LAUNCH_CHECK();
+  NAIR_CK(cudaMemcpyAsync(pbeg + out.nnzb, prp + nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  out.v = mem.alloc<T>((size_t)out.nnzb * b * b);
+  const long long total = (long long)out.nnzb * b * b;
+  if (total) {
+    k_spgemm_pairs<T><<<grid(total), kThreads, 0, s>>>(total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    NAIR_LAUNCH_CHECK();
+  }
+  tmp.release(pairs);
+  tmp.release(iq);
+  tmp.release(pbeg);
+  tmp.release(orow);
+  tmp.release(flags);
+  tmp.release(prp);
+  tmp.release(pcnt);
+  tmp.release(cnt);
+  (void)left_nnz;
 }
 
 template <typename T>
@@ -1044,7 +1230,12 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
     NAIR_LAUNCH_CHECK();
   }
   int *piv = tmp.alloc<int>(n);
-  if (n <= 256) {
+  const size_t gj_smem = (size_t)n * n * sizeof(double) + (size_t)n * (sizeof(double) + sizeof(int));
+  if (gj_smem <= 200 * 1024) {
+    NAIR_CK(cudaFuncSetAttribute(k_dense_gj_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem));
+    k_dense_gj_smem<<<1, kGjThreads, gj_smem, s>>>(n, M, err);
+    NAIR_LAUNCH_CHECK();
+  } else if (n <= 256) {
     double *lcol = tmp.alloc<double>(n);
     k_dense_gj<<<1, kGjThreads, 0, s>>>(n, M, piv, lcol, err);
     NAIR_LAUNCH_CHECK();
