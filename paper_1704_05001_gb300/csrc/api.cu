@@ -29,6 +29,7 @@ struct nair_handle {
   bool mixed = false;
   Hier<double> h64;
   Hier<float> h32;
+  L0Comp<double> l0c64;  // level-0 compression of the FP64 matrix (mixed precision)
   Krylov K;
   nair_handle *adj = nullptr;
   double setup_ms = 0.0;
@@ -256,6 +257,7 @@ static void setup_impl(nair_handle *h, const int *rp, const int *ci, const doubl
     NAIR_LAUNCH_CHECK();
     h->h32.b = b;
     build_hierarchy<float>(F, h->P, s, mem, h->h32);
+    if (!h->h32.lev[0].coarsest) build_l0comp<double>(A, h->h32.lev[0].diag, b, s, mem, h->l0c64);
   } else {
     h->h64.b = b;
     build_hierarchy<double>(A, h->P, s, mem, h->h64);
@@ -405,8 +407,8 @@ nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *in
   std::vector<double> hist;
   int iters = 0;
   double relres = 0.0;
-  nair_status st = h->mixed ? fgmres<float>(h->A64, h->h32, h->P, h->K, b, x, hist, &iters, &relres, h->s)
-                            : fgmres<double>(h->A64, h->h64, h->P, h->K, b, x, hist, &iters, &relres, h->s);
+  nair_status st = h->mixed ? fgmres<float>(h->A64, h->h32, h->P, h->K, b, x, hist, &iters, &relres, h->s, &h->l0c64)
+                            : fgmres<double>(h->A64, h->h64, h->P, h->K, b, x, hist, &iters, &relres, h->s, &h->h64.l0c);
   NAIR_CK(cudaEventRecord(e1, h->s));
   NAIR_CK(cudaEventSynchronize(e1));
   float ms = 0.f;

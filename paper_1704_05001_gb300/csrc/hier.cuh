@@ -26,6 +26,7 @@ struct Level {
   signed char *cf = nullptr;  // 1 = C, 0 = F
   int *c2f = nullptr;      // coarse index -> element (the C rows, ascending)
   int *f2f = nullptr;      // F index -> element (the F rows, ascending)
+  int *fsweep = nullptr, *csweep = nullptr;  // F / C rows ordered by row length (sweep work lists)
   int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
   DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
   int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)
@@ -39,6 +40,22 @@ struct Level {
   // V-cycle vectors
   T *f = nullptr, *x = nullptr, *x2 = nullptr;
 };
+
+// Level-0 off-diagonal blocks restricted to their nonzero columns.  An upwind
+// DG coupling block is nonzero only in the columns of the p + 1 face nodes of
+// the neighbour, so each off-diagonal block keeps W <= b columns (the largest
+// count over all blocks, padded with zero columns): off block q of row i is
+// q = p - i - (p > diag(i)) for its BSR position p.
+template <typename T>
+struct L0Comp {
+  int W = 0;                         // 0: not built (kernels use the BSR blocks)
+  int *oci = nullptr;                // block column of each off-diagonal block
+  unsigned long long *ocols = nullptr;  // W local column indices, 8 bits each
+  T *ov = nullptr;                   // (nnzb - E) x b x W values
+};
+
+template <typename T>
+void build_l0comp(const DBsr<T> &A, const int *diag, int b, cudaStream_t s, Mem &mem, L0Comp<T> &C);
 
 // The V-cycle replayed as one CUDA graph: it reads its input from and writes its
 // output to the two device pointers in dptr (set before each launch), so one
@@ -66,6 +83,7 @@ struct Hier {
   std::vector<Level<T>> lev;
   mutable VGraph graph;
   mutable SweepClock clock;
+  L0Comp<T> l0c;
   double setup_ms = 0.0;
   double op_complexity = 0.0, cycle_complexity = 0.0;
 };

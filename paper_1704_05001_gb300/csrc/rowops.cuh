@@ -36,6 +36,10 @@ struct RowArgs {
   T *out2;
   unsigned long long *stamp;  // optional: [0] earliest start, [ns] latest end (device clock)
   int ns;
+  // level-0 column-compressed off-diagonal blocks (k_rowop_l0)
+  const int *diag, *oci;
+  const unsigned long long *ocols;
+  const T *ov;
 };
 
 __device__ __forceinline__ unsigned long long global_clock() {
@@ -201,6 +205,123 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
     if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
   }
 }
+
+// Level-0 form of the row kernel: the diagonal block from the BSR values, the
+// off-diagonal blocks from their W nonzero columns (one team of B threads per
+// row).  Same operations as k_rowop for OP_SPMV, OP_RESID and OP_JACOBI.
+template <typename T, int B, int W, int OP>
+__global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
+  pdl_launch_dependents();
+  if (OP == OP_JACOBI && (int)blockIdx.x >= a.comp_ctas) {
+    const long long g = (long long)(blockIdx.x - a.comp_ctas) * blockDim.x + threadIdx.x;
+    const bool in = g < (long long)a.ncopy * B;
+    const int row = in ? (int)(g / B) : 0, r = in ? (int)(g - (long long)row * B) : 0;
+    const int i = in ? a.copy_list[row] : 0;
+    const int J = (in && a.ipc) ? a.ipc[i] : i;
+    pdl_wait();
+    if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
+    if (in) {
+      const T v = a.ipc ? (J >= 0 ? a.x[(size_t)J * B + r] : (T)0) : a.x[(size_t)i * B + r];
+      a.out[(size_t)i * B + r] = v;
+      if (a.out2) a.out2[(size_t)i * B + r] = v;
+    }
+    if (a.stamp) {
+      __syncthreads();
+      if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
+    }
+    return;
+  }
+  __shared__ T sres[256];
+  const int team = threadIdx.x / B, r = threadIdx.x - team * B;
+  const int idx = blockIdx.x * a.tpc + team;
+  const bool active = team < a.tpc && idx < a.nrows;
+  // ---- prologue on data that is constant during the V-cycle
+  const int i = active ? (a.list ? a.list[idx] : idx) : 0;
+  const int q0 = active ? a.rp[i] - i : 0, q1 = active ? a.rp[i + 1] - i - 1 : 0;
+  T dv[B], drow[OP == OP_JACOBI ? B : 1], ov0[W];
+  int j0 = -1;
+  unsigned long long cols0 = 0;
+  int ii = i;
+  if (active) {
+    const T *dp = a.v + (size_t)a.diag[i] * B * B + r * B;
+#pragma unroll
+    for (int c = 0; c < B; ++c) dv[c] = dp[c];
+    if (OP == OP_JACOBI) {
+      const T *dd = a.dinv + (size_t)i * B * B + r * B;
+#pragma unroll
+      for (int c = 0; c < B; ++c) drow[c] = dd[c];
+    }
+    if (q0 < q1) {
+      j0 = a.oci[q0];
+      if (a.ipc) j0 = a.ipc[j0];
+      cols0 = a.ocols[q0];
+      const T *o = a.ov + (size_t)q0 * B * W + r * W;
+#pragma unroll
+      for (int w = 0; w < W; ++w) ov0[w] = o[w];
+    }
+    if (a.ipc) ii = a.ipc[i];
+  }
+  // ---- wait for the producer of x and f
+  pdl_wait();
+  if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
+  T acc = 0, xr = 0;
+  if (active) {
+    T xv[B];
+    if (ii >= 0) {
+      const T *xi = a.x + (size_t)ii * B;
+#pragma unroll
+      for (int c = 0; c < B; ++c) xv[c] = xi[c];
+      xr = xi[r];
+    } else {
+#pragma unroll
+      for (int c = 0; c < B; ++c) xv[c] = 0;
+    }
+#pragma unroll
+    for (int c = 0; c < B; ++c) acc = fma(dv[c], xv[c], acc);
+    if (q0 < q1 && j0 >= 0) {
+      const T *xj = a.x + (size_t)j0 * B;
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc = fma(ov0[w], xj[(cols0 >> (8 * w)) & 255u], acc);
+    }
+    for (int q = q0 + 1; q < q1; ++q) {
+      int j = a.oci[q];
+      if (a.ipc) {
+        j = a.ipc[j];
+        if (j < 0) continue;
+      }
+      const unsigned long long cols = a.ocols[q];
+      const T *o = a.ov + (size_t)q * B * W + r * W;
+      const T *xj = a.x + (size_t)j * B;
+      T ovq[W], xq[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) { ovq[w] = o[w]; xq[w] = xj[(cols >> (8 * w)) & 255u]; }
+#pragma unroll
+      for (int w = 0; w < W; ++w) acc = fma(ovq[w], xq[w], acc);
+    }
+  }
+  if (OP == OP_SPMV) {
+    if (active) a.out[(size_t)i * B + r] = acc;
+  } else if (OP == OP_RESID) {
+    if (active) a.out[(size_t)i * B + r] = a.f[(size_t)i * B + r] - acc;
+  } else {
+    if (active) sres[team * B + r] = a.f[(size_t)i * B + r] - acc;
+    __syncthreads();
+    if (active) {
+      T s2 = 0;
+#pragma unroll
+      for (int c = 0; c < B; ++c) s2 = fma(drow[c], sres[team * B + c], s2);
+      a.out[(size_t)i * B + r] = xr + s2;
+    }
+  }
+  if (a.stamp) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
+  }
+}
+
+// host launcher of the level-0 form (b must have a compressed width W)
+template <typename T, int OP>
+void launch_rowop_l0(RowArgs<T> a, int W, cudaStream_t s);
 
 // host launcher: picks the team shape from the average row length; for JACOBI,
 // a.nrows / a.list are the rows to update and a.ncopy / a.copy_list the rows to copy

@@ -252,6 +252,47 @@ __global__ void k_cf_index(int E, const signed char *__restrict__ cf, const int 
 }
 
 // ---------------------------------------------------------------------------
+// sweep work lists: the rows of one class ordered by decreasing row length, so
+// that rows sharing a warp have similar trip counts (any order gives the same
+// sweep result: every row is computed independently)
+// ---------------------------------------------------------------------------
+static constexpr int kLenBuckets = 64;
+
+__global__ void k_len_count(int n, const int *__restrict__ list, const int *__restrict__ rp,
+                            int *__restrict__ counts) {
+  __shared__ int h[kLenBuckets];
+  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x) h[k] = 0;
+  __syncthreads();
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    const int i = list[t];
+    atomicAdd(&h[min(rp[i + 1] - rp[i], kLenBuckets - 1)], 1);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x)
+    if (h[k]) atomicAdd(&counts[k], h[k]);
+}
+
+// offsets of the buckets, longest rows first
+__global__ void k_len_offsets(int *__restrict__ counts) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int run = 0;
+  for (int k = kLenBuckets - 1; k >= 0; --k) {
+    const int c = counts[k];
+    counts[k] = run;
+    run += c;
+  }
+}
+
+__global__ void k_len_scatter(int n, const int *__restrict__ list, const int *__restrict__ rp,
+                              int *__restrict__ offs, int *__restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = list[t];
+  out[atomicAdd(&offs[min(rp[i + 1] - rp[i], kLenBuckets - 1)], 1)] = i;
+}
+
+// ---------------------------------------------------------------------------
 // a6: one-point interpolation: strongest strong C neighbour, first on ties
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -705,10 +746,15 @@ __device__ void dense_gj_cta(int n, double *__restrict__ M, int *__restrict__ pi
       if (r != k) M[(size_t)r * n + k] = 0.0;
     }
     __syncthreads();
-    for (long long g = tid; g < (long long)n * n; g += blockDim.x) {
-      int r = (int)(g / n), c = (int)(g - (long long)r * n);
-      if (r == k) continue;
-      M[g] = __fma_rn(-lcol[r], M[(size_t)k * n + c], M[g]);
+    {
+      const int lane32 = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+      for (int r = warp; r < n; r += nw) {
+        if (r == k) continue;
+        const double l = lcol[r];
+        double *row = M + (size_t)r * n;
+        const double *prw = M + (size_t)k * n;
+        for (int c = lane32; c < n; c += 32) row[c] = __fma_rn(-l, prw[c], row[c]);
+      }
     }
     __syncthreads();
   }
@@ -815,6 +861,86 @@ __global__ void __launch_bounds__(1024) k_gj_unscramble(int n, double *__restric
     __syncthreads();
   }
 }
+
+// ---------------------------------------------------------------------------
+// level-0 column compression of the off-diagonal blocks
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_colmask(int nnzb, int b, const int *__restrict__ brow, const int *__restrict__ diag,
+                          const T *__restrict__ v, unsigned *__restrict__ mask, int *__restrict__ wmax) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnzb) return;
+  if (diag[brow[p]] == p) { mask[p] = 0; return; }
+  const T *x = v + (size_t)p * b * b;
+  unsigned m = 0;
+  for (int r = 0; r < b; ++r)
+    for (int c = 0; c < b; ++c)
+      if (x[r * b + c] != (T)0) m |= 1u << c;
+  mask[p] = m;
+  atomicMax(wmax, __popc(m));
+}
+
+template <typename T>
+__global__ void k_comp_fill(int nnzb, int b, int W, const int *__restrict__ brow, const int *__restrict__ diag,
+                            const int *__restrict__ ci, const T *__restrict__ v, const unsigned *__restrict__ mask,
+                            int *__restrict__ oci, unsigned long long *__restrict__ ocols, T *__restrict__ ov) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnzb) return;
+  const int i = brow[p], d = diag[i];
+  if (p == d) return;
+  const int q = p - i - (p > d ? 1 : 0);
+  unsigned m = mask[p];
+  int cols[32];
+  int w = 0;
+  for (int c = 0; c < b && w < W; ++c)
+    if (m & (1u << c)) cols[w++] = c;
+  for (int c = 0; c < b && w < W; ++c)  // pad with columns that are zero in this block
+    if (!(m & (1u << c))) cols[w++] = c;
+  unsigned long long packed = 0;
+  for (int k = 0; k < W; ++k) packed |= (unsigned long long)cols[k] << (8 * k);
+  oci[q] = ci[p];
+  ocols[q] = packed;
+  const T *x = v + (size_t)p * b * b;
+  T *o = ov + (size_t)q * b * W;
+  for (int r = 0; r < b; ++r)
+    for (int k = 0; k < W; ++k) o[r * W + k] = x[r * b + cols[k]];
+}
+
+static inline int grid1d(long long n) { return std::max(1, cdiv(n, kThreads)); }
+
+static bool l0_supported(int b, int W) {
+  return (b == 3 && W == 2) || (b == 6 && W == 3) || (b == 10 && W == 4) || (b == 15 && W == 5) ||
+         (b == 21 && W == 6) || (b == 28 && W == 7);
+}
+
+template <typename T>
+void build_l0comp(const DBsr<T> &A, const int *diag, int b, cudaStream_t s, Mem &mem, L0Comp<T> &C) {
+  C = L0Comp<T>();
+  const int E = A.nrows, nnzb = A.nnzb, noff = nnzb - E;
+  if (noff <= 0) return;
+  Mem tmp;
+  tmp.s = s;
+  int *brow = tmp.alloc<int>(nnzb), *wmax = tmp.alloc<int>(1);
+  unsigned *mask = tmp.alloc<unsigned>(nnzb);
+  NAIR_CK(cudaMemsetAsync(wmax, 0, sizeof(int), s));
+  k_block_rows<<<grid1d(E), kThreads, 0, s>>>(E, A.rp, brow);
+  NAIR_LAUNCH_CHECK();
+  k_colmask<T><<<grid1d(nnzb), kThreads, 0, s>>>(nnzb, b, brow, diag, A.v, mask, wmax);
+  NAIR_LAUNCH_CHECK();
+  int W = read_int(wmax, s);
+  if (W == 0) W = 1;
+  for (int w = W; w < b; ++w)
+    if (l0_supported(b, w)) { W = w; break; }
+  if (!l0_supported(b, W)) return;
+  C.W = W;
+  C.oci = mem.alloc<int>(noff);
+  C.ocols = mem.alloc<unsigned long long>(noff);
+  C.ov = mem.alloc<T>((size_t)noff * b * W);
+  k_comp_fill<T><<<grid1d(nnzb), kThreads, 0, s>>>(nnzb, b, W, brow, diag, A.ci, A.v, mask, C.oci, C.ocols, C.ov);
+  NAIR_LAUNCH_CHECK();
+}
+template void build_l0comp<double>(const DBsr<double> &, const int *, int, cudaStream_t, Mem &, L0Comp<double> &);
+template void build_l0comp<float>(const DBsr<float> &, const int *, int, cudaStream_t, Mem &, L0Comp<float> &);
 
 // ---------------------------------------------------------------------------
 // host orchestration
@@ -966,6 +1092,24 @@ static void check_flag(int *flag, cudaStream_t s, nair_status st, const char *ms
   if (v) fail(st, msg);
 }
 
+static int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem, Mem &tmp) {
+  int *out = mem.alloc<int>(n);
+  int *counts = tmp.alloc<int>(kLenBuckets);
+  NAIR_CK(cudaMemsetAsync(counts, 0, sizeof(int) * kLenBuckets, s));
+  if (n) {
+    k_len_count<<<grid(n), kThreads, 0, s>>>(n, list, rp, counts);
+    NAIR_LAUNCH_CHECK();
+  }
+  k_len_offsets<<<1, 32, 0, s>>>(counts);
+  NAIR_LAUNCH_CHECK();
+  if (n) {
+    k_len_scatter<<<grid(n), kThreads, 0, s>>>(n, list, rp, counts, out);
+    NAIR_LAUNCH_CHECK();
+  }
+  tmp.release(counts);
+  return out;
+}
+
 // extract rows `rowmap` (nrows of them) of A with the chosen column test
 template <typename T>
 static void extract(int b, int nrows, int mode, const int *rowmap, const Level<T> &L,
@@ -1062,6 +1206,8 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   int *f2f = L.f2f;
   k_cf_index<<<grid(E), kThreads, 0, s>>>(E, L.cf, pre, cidx, fidx, L.c2f, f2f);
   NAIR_LAUNCH_CHECK();
+  L.fsweep = sweep_list(nF, f2f, L.A.rp, s, mem, tmp);
+  L.csweep = sweep_list(nC, L.c2f, L.A.rp, s, mem, tmp);
 
   // a4: L = -D_ff^{-1} A^S_ff, then Horner T_{t+1} = D^{-1} + L T_t (Eq. neumann)
   ProfScope ps_neu("neumann", s, l);
@@ -1287,6 +1433,7 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     }
   }
   H.nlev = (int)H.lev.size();
+  if (!H.lev[0].coarsest) build_l0comp<T>(H.lev[0].A, H.lev[0].diag, H.b, s, mem, H.l0c);
   // V-cycle vectors and complexities (Sec. 6: OC and CC in work units)
   const int b = H.b;
   double nnz0 = (double)H.lev[0].A.nnzb, oc = 0.0, cc = 0.0;

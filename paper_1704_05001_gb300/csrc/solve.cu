@@ -74,6 +74,27 @@ void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   }
   NAIR_LAUNCH_CHECK();
 }
+template <typename T, int OP>
+void launch_rowop_l0(RowArgs<T> a, int W, cudaStream_t s) {
+  const int b = a.b;
+  a.G = 1;
+  a.tpc = std::max(1, 256 / b);
+  const int threads = a.tpc * b;
+  a.comp_ctas = cdiv(a.nrows, a.tpc);
+  int blocks = a.comp_ctas;
+  if (OP == OP_JACOBI && a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
+  if (blocks == 0) return;
+  const dim3 gr(blocks), bl(threads);
+  if (b == 3 && W == 2) launch_pdl(k_rowop_l0<T, 3, 2, OP>, gr, bl, 0, s, a);
+  else if (b == 6 && W == 3) launch_pdl(k_rowop_l0<T, 6, 3, OP>, gr, bl, 0, s, a);
+  else if (b == 10 && W == 4) launch_pdl(k_rowop_l0<T, 10, 4, OP>, gr, bl, 0, s, a);
+  else if (b == 15 && W == 5) launch_pdl(k_rowop_l0<T, 15, 5, OP>, gr, bl, 0, s, a);
+  else if (b == 21 && W == 6) launch_pdl(k_rowop_l0<T, 21, 6, OP>, gr, bl, 0, s, a);
+  else if (b == 28 && W == 7) launch_pdl(k_rowop_l0<T, 28, 7, OP>, gr, bl, 0, s, a);
+  else fail(NAIR_ERR_UNSUPPORTED, "no level-0 kernel for this block size and width");
+  NAIR_LAUNCH_CHECK();
+}
+
 template void launch_rowop<double, OP_SPMV>(RowArgs<double>, double, cudaStream_t);
 template void launch_rowop<double, OP_RESID>(RowArgs<double>, double, cudaStream_t);
 
@@ -123,7 +144,7 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
   // output buffer only when that buffer holds an older version of them.
   T *buf[2] = {(S % 2 == 1) ? out : L.x2, (S % 2 == 1) ? L.x2 : out};
   const int nrow[2] = {L.nF, L.nC};
-  const int *rows[2] = {L.f2f, L.c2f};
+  const int *rows[2] = {L.fsweep, L.csweep};
   int cur_ver[2] = {0, 0};        // version of each class (0 = P x_c)
   int buf_ver[2][2] = {{-1, -1}, {-1, -1}};
   const T *in = N.x;
@@ -150,7 +171,15 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
     // average blocks per updated row (F and C rows have similar lengths)
     const double avg = (double)L.A.nnzb / L.E;
     ProfScope ps(cls == 0 ? "jacobi_F" : "jacobi_C", s, l);
-    launch_rowop<T, OP_JACOBI>(a, avg, s);
+    if (l == 0 && H.l0c.W > 0) {
+      a.diag = L.diag;
+      a.oci = H.l0c.oci;
+      a.ocols = H.l0c.ocols;
+      a.ov = H.l0c.ov;
+      launch_rowop_l0<T, OP_JACOBI>(a, H.l0c.W, s);
+    } else {
+      launch_rowop<T, OP_JACOBI>(a, avg, s);
+    }
     cur_ver[cls] = k + 1;
     buf_ver[ob][cls] = k + 1;
     if (a.ncopy) {
@@ -436,13 +465,23 @@ template void precond<double>(const Hier<double> &, const Params &, const double
 template void precond<float>(const Hier<float> &, const Params &, const double *, double *, cudaStream_t, long long);
 
 // a10: y = A x, or y = b - A x when b is given (FP64, level 0)
-void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s) {
+void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s,
+            const L0Comp<double> *C, const int *diag) {
   RowArgs<double> a = row_args(A, b);
   a.x = x;
   a.f = bvec;
   a.out = y;
   const double avg = (double)A.nnzb / A.nrows;
   ProfScope ps(bvec ? "resid64" : "spmv64", s);
+  if (C && C->W > 0 && diag) {
+    a.diag = diag;
+    a.oci = C->oci;
+    a.ocols = C->ocols;
+    a.ov = C->ov;
+    if (bvec) launch_rowop_l0<double, OP_RESID>(a, C->W, s);
+    else launch_rowop_l0<double, OP_SPMV>(a, C->W, s);
+    return;
+  }
   if (bvec) launch_rowop<double, OP_RESID>(a, avg, s);
   else launch_rowop<double, OP_SPMV>(a, avg, s);
 }
@@ -450,7 +489,8 @@ void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, d
 template <typename T>
 nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
                    const double *bvec, double *x, std::vector<double> &hist, int *iters,
-                   double *relres, cudaStream_t s) {
+                   double *relres, cudaStream_t s, const L0Comp<double> *C) {
+  const int *diag0 = H.lev[0].diag;
   const int b = H.b, m = P.restart;
   const long long n = (long long)A.nrows * b;
   K.ensure(n, m, s);
@@ -472,7 +512,7 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
   }
   double *V = K.V, *Z = K.Z, *w = K.w;
   for (;;) {
-    spmv64(A, b, x, bvec, w, s);
+    spmv64(A, b, x, bvec, w, s, C, diag0);
     multidot(K, n, 1, w, w, K.hdev, s);
     NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
     NAIR_CK(cudaStreamSynchronize(s));
@@ -495,7 +535,7 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
         precond<T>(H, P, vj, zj, s, n);
       }
       ++it;
-      spmv64(A, b, zj, nullptr, w, s);
+      spmv64(A, b, zj, nullptr, w, s, C, diag0);
       // classical Gram-Schmidt, twice
       multidot(K, n, j + 1, V, w, K.hdev, s);
       {
@@ -555,7 +595,7 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
     if (conv || brk) { status = NAIR_OK; break; }
     if (it >= P.maxiter) break;
   }
-  spmv64(A, b, x, bvec, w, s);
+  spmv64(A, b, x, bvec, w, s, C, diag0);
   multidot(K, n, 1, w, w, K.hdev, s);
   NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double), cudaMemcpyDeviceToHost, s));
   NAIR_CK(cudaStreamSynchronize(s));
@@ -568,9 +608,9 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
 
 template nair_status fgmres<double>(const DBsr<double> &, const Hier<double> &, const Params &, Krylov &,
                                     const double *, double *, std::vector<double> &, int *, double *,
-                                    cudaStream_t);
+                                    cudaStream_t, const L0Comp<double> *);
 template nair_status fgmres<float>(const DBsr<double> &, const Hier<float> &, const Params &, Krylov &,
                                    const double *, double *, std::vector<double> &, int *, double *,
-                                   cudaStream_t);
+                                   cudaStream_t, const L0Comp<double> *);
 
 }  // namespace nair

@@ -20,7 +20,8 @@ struct Krylov {
   ~Krylov();
 };
 
-void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s);
+void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s,
+            const L0Comp<double> *C = nullptr, const int *diag = nullptr);
 
 template <typename T>
 void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s, long long n);
@@ -28,6 +29,6 @@ void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cuda
 template <typename T>
 nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
                    const double *bvec, double *x, std::vector<double> &hist, int *iters,
-                   double *relres, cudaStream_t s);
+                   double *relres, cudaStream_t s, const L0Comp<double> *C);
 
 }  // namespace nair
