@@ -223,11 +223,39 @@ __device__ __forceinline__ void dot_group(long long lo, long long hi, int k0, co
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = fma(V[(k0 + q) * ldv + i], wi, acc[q]);
   }
+  if constexpr (NQ == 8) {
+    // butterfly reduce-scatter: after it, lanes 4k hold the warp's sum of
+    // accumulator k (9 additions per lane instead of 8 full reductions)
+    double u[4], t[2];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    double a = acc[q];
-    for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    if (lane == 0) red[q][wid] = a;
+    for (int q = 0; q < 4; ++q) {
+      const bool hi = lane & 16;
+      const double snd = hi ? acc[q] : acc[q + 4];
+      const double rcv = __shfl_xor_sync(0xffffffffu, snd, 16);
+      u[q] = (hi ? acc[q + 4] : acc[q]) + rcv;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const bool hi = lane & 8;
+      const double snd = hi ? u[q] : u[q + 2];
+      const double rcv = __shfl_xor_sync(0xffffffffu, snd, 8);
+      t[q] = (hi ? u[q + 2] : u[q]) + rcv;
+    }
+    const bool hi4 = lane & 4;
+    double z = (hi4 ? t[1] : t[0]) + __shfl_xor_sync(0xffffffffu, hi4 ? t[0] : t[1], 4);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    if ((lane & 3) == 0) {
+      const int k = ((lane >> 2) & 1) | (((lane >> 3) & 1) << 1) | (((lane >> 4) & 1) << 2);
+      red[k][wid] = z;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double a = acc[q];
+      for (int o = 16; o; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      if (lane == 0) red[q][wid] = a;
+    }
   }
   __syncthreads();
   if (threadIdx.x < NQ) {
