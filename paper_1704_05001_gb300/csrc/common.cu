@@ -165,6 +165,8 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int *warp_sums, int *to
   return inc - v + warp_sums[wid];
 }
 
+// writes the exclusive prefix of each tile, the tile sums, and (single-tile
+// case) the total into out[n]
 __global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, int n,
                              int *__restrict__ tile_sums) {
   __shared__ int warp_sums[kScanThreads / 32];
@@ -185,43 +187,51 @@ __global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, 
     if (i < n) out[i] = pre;
     pre += v[k];
   }
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+  if (threadIdx.x == 0) {
+    if (tile_sums) tile_sums[blockIdx.x] = total;
+    else out[n] = total;  // one tile: the total follows the prefixes
+  }
 }
 
-__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ tile_off) {
+// adds the scanned tile offsets; offs[tiles] is the total, copied to out[n]
+__global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ tile_off, int tiles) {
   const long long base = (long long)blockIdx.x * kScanTile;
   const int add = tile_off[blockIdx.x];
   for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
     long long i = base + k;
     if (i < n) out[i] += add;
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_off[tiles];
 }
 
-__global__ void k_scan_total(int *out, int n, const int *in, const int *tile_total) {
-  // out[n] = out[n-1] + in[n-1] (or the single tile total when n fits one tile)
-  if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = (n > 0) ? out[n - 1] + in[n - 1] : 0;
-  (void)tile_total;
-}
+__global__ void k_scan_zero(int *out) { out[0] = 0; }
 
+// out[0..n) = exclusive prefix of in, out[n] = total
 static void scan_rec(const int *in, int *out, int n, cudaStream_t s, Mem &tmp) {
-  int tiles = cdiv(n, kScanTile);
+  const int tiles = cdiv(n, kScanTile);
+  if (tiles <= 1) {
+    k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    NAIR_LAUNCH_CHECK();
+    return;
+  }
   int *sums = tmp.alloc<int>(tiles + 1);
   k_scan_tiles<<<tiles, kScanThreads, 0, s>>>(in, out, n, sums);
   NAIR_LAUNCH_CHECK();
-  if (tiles > 1) {
-    int *offs = tmp.alloc<int>(tiles + 1);
-    scan_rec(sums, offs, tiles, s, tmp);
-    k_scan_add<<<tiles, kScanThreads, 0, s>>>(out, n, offs);
-    NAIR_LAUNCH_CHECK();
-    tmp.release(offs);
-  }
+  int *offs = tmp.alloc<int>(tiles + 1);
+  scan_rec(sums, offs, tiles, s, tmp);
+  k_scan_add<<<tiles, kScanThreads, 0, s>>>(out, n, offs, tiles);
+  NAIR_LAUNCH_CHECK();
+  tmp.release(offs);
   tmp.release(sums);
 }
 
 int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, Mem &tmp, bool want_total) {
-  if (n > 0) scan_rec(in, out, n, s, tmp);
-  k_scan_total<<<1, 32, 0, s>>>(out, n, in, nullptr);
-  NAIR_LAUNCH_CHECK();
+  if (n > 0) {
+    scan_rec(in, out, n, s, tmp);
+  } else {
+    k_scan_zero<<<1, 1, 0, s>>>(out);
+    NAIR_LAUNCH_CHECK();
+  }
   if (!want_total) return -1;
   return read_int(out + n, s);
 }

@@ -84,6 +84,7 @@ __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int p0, int p1, in
 #pragma unroll
       for (int c = 0; c < B; ++c) acc = fma(va0[c], vx[c], acc);
     }
+#pragma unroll 2
     for (int p = p0 + a.G; p < p1; p += a.G) {
       int j = a.ci[p];
       if (a.ipc) {

@@ -1347,7 +1347,7 @@ static void level_dinv(Hier<T> &H, Level<T> &L, cudaStream_t s, Mem &mem, Mem &t
     NAIR_LAUNCH_CHECK();
     tmp.release(d64);
   }
-  check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular diagonal block");
+  // the singular-block flag is read once, at the end of the hierarchy build
 }
 
 template <typename T>
@@ -1356,6 +1356,8 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
   const int b = H.b;
   const int n = L.E * b;
   if (n > P.max_dense) {
+    // a singular diagonal block upstream explains a stalled coarsening first
+    check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular diagonal block");
     char buf[200];
     snprintf(buf, sizeof(buf),
              "coarsest level has %d unknowns, above max_dense = %d (coarsening stalled)", n,
@@ -1400,7 +1402,7 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
   tot = (long long)n * n;
   k_convert<T><<<grid(tot), kThreads, 0, s>>>(tot, M, L.ainv);
   NAIR_LAUNCH_CHECK();
-  check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular coarsest-level matrix");
+  // the flag is read at the end of the hierarchy build
   tmp.release_all();
 }
 
@@ -1433,6 +1435,7 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     }
   }
   H.nlev = (int)H.lev.size();
+  check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular diagonal block or coarsest-level matrix");
   if (!H.lev[0].coarsest) build_l0comp<T>(H.lev[0].A, H.lev[0].diag, H.b, s, mem, H.l0c);
   // V-cycle vectors and complexities (Sec. 6: OC and CC in work units)
   const int b = H.b;

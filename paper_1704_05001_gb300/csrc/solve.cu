@@ -49,6 +49,8 @@ __global__ void k_dense_mv(int n, const T *__restrict__ M, const T *__restrict__
 template <typename T, int OP>
 void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   const int b = a.b;
+  // threads per row: enough block groups that each thread handles about two
+  // blocks of a long (coarse-level) row, keeping the serial chain short
   int G = 1;
   if (avg > 4.0)
     while (G * 2 <= avg / 2 && G * 2 * b <= 256 && G < 32) G *= 2;
