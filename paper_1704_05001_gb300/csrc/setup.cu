@@ -1355,6 +1355,14 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
                           Mem &tmp, int *err) {
   const int b = H.b;
   const int n = L.E * b;
+  if (L.A.nnzb == L.E) {
+    // block-diagonal coarsest matrix (coarsening stopped on isolated elements):
+    // its exact inverse is the diagonal-block inverse already computed
+    L.coarsest = 1;
+    L.n = n;
+    L.ainv = nullptr;
+    return;
+  }
   if (n > P.max_dense) {
     // a singular diagonal block upstream explains a stalled coarsening first
     check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular diagonal block");
@@ -1449,7 +1457,7 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     double a = (double)L.A.nnzb / nnz0;
     oc += a;
     if (L.coarsest) {
-      cc += (double)L.n * L.n / (nnz0 * b * b);
+      cc += L.ainv ? (double)L.n * L.n / (nnz0 * b * b) : a;
     } else {
       // restriction + (f + c) sweeps over the selected rows, counted as full SpMVs
       cc += a * (P.f_sweeps + P.c_sweeps) + (double)L.R.nnzb / nnz0;

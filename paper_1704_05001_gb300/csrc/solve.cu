@@ -46,6 +46,22 @@ __global__ void k_dense_mv(int n, const T *__restrict__ M, const T *__restrict__
   if (lane == 0) x[warp] = acc;
 }
 
+// x_i = D_ii^{-1} f_i for a block-diagonal coarsest level
+template <typename T>
+__global__ void k_bdiag_apply(int E, int b, const T *__restrict__ dinv, const T *__restrict__ f,
+                              T *__restrict__ x) {
+  pdl_launch_dependents();
+  pdl_wait();
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)E * b) return;
+  const int i = (int)(g / b), r = (int)(g - (long long)i * b);
+  const T *d = dinv + (size_t)i * b * b + r * b;
+  const T *fi = f + (size_t)i * b;
+  T acc = 0;
+  for (int c = 0; c < b; ++c) acc = fma(d[c], fi[c], acc);
+  x[g] = acc;
+}
+
 template <typename T, int OP>
 void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   const int b = a.b;
@@ -117,8 +133,13 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
   const int b = H.b;
   if (L.coarsest) {
     ProfScope ps("coarse_solve", s, l);
-    launch_pdl(k_dense_mv<T>, dim3(cdiv((long long)L.n * 32, kThreads)), dim3(kThreads), 0, s, L.n,
-               (const T *)L.ainv, f, out);
+    if (L.ainv) {
+      launch_pdl(k_dense_mv<T>, dim3(cdiv((long long)L.n * 32, kThreads)), dim3(kThreads), 0, s, L.n,
+                 (const T *)L.ainv, f, out);
+    } else {  // block-diagonal coarsest matrix: x_i = D_ii^{-1} f_i
+      launch_pdl(k_bdiag_apply<T>, dim3(grid((long long)L.E * b)), dim3(kThreads), 0, s, L.E, b,
+                 (const T *)L.dinv, f, out);
+    }
     NAIR_LAUNCH_CHECK();
     return;
   }
