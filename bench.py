@@ -215,6 +215,17 @@ def roofline(nair, params, rp, ci, v, sweep_ms):
                    "thread block done) on every sweep inside the timed steps"}
 
 
+def aggregate_ranks(total_ms, steps, dofs, world, device):
+    """Whole-job throughput of replicated solves: the slowest rank's time (max over
+    ranks) for `steps` steps, and MDOF/s = world * dofs / time per step."""
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(t.item()) / steps
+    return ms, world * dofs / (ms * 1e-3) / 1e6
+
+
 def timed_steps(fn, steps, flush, stream):
     """Device time (CUDA events on the launching stream) of `steps` calls of fn,
     with an L2 flush before each call outside the timed events."""
@@ -384,12 +395,7 @@ def main():
     clocks = sampler.stop()
     timed["on"] = False
     launches = (nair.kernel_launches() - launches0) // max(1, args.steps)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms = float(t.item())
-    ms = total_ms / args.steps
-    value = world * P["n"] / (ms * 1e-3) / 1e6
+    ms, value = aggregate_ranks(total_ms, args.steps, P["n"], world, dev)
 
     # end to end through the public API from pinned host buffers
     e2e = None

@@ -1166,10 +1166,10 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   NAIR_LAUNCH_CHECK();
   int rounds = 0;
   ProfScope ps_cf("cf_split", s, l);
-  // rounds are issued two at a time between read-backs of the undecided count;
-  // a round with no undecided point changes nothing
-  for (;;) {
-    for (int rep = 0; rep < 2; ++rep) {
+  // rounds are issued in batches (four, then two at a time) between read-backs
+  // of the undecided count; a round with no undecided point changes nothing
+  for (int batch = 4;; batch = 2) {
+    for (int rep = 0; rep < batch; ++rep) {
       NAIR_CK(cudaMemsetAsync(remaining, 0, sizeof(int), s));
       k_pmis_mark<<<grid(nnzb), kThreads, 0, s>>>(nnzb, brow, L.A.ci, strong, L.cf, lam, hash, mark, rounds);
       NAIR_LAUNCH_CHECK();
