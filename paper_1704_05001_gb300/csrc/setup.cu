@@ -356,11 +356,13 @@ __global__ void k_sub_fill(int nrows, int mode, const int *__restrict__ rowmap,
 template <typename T>
 __global__ void k_L_values(long long total, int b, const int *__restrict__ orow,
                            const int *__restrict__ osrc, const int *__restrict__ rowmap,
-                           const T *__restrict__ dinv, const T *__restrict__ Av, T *__restrict__ out) {
+                           const T *__restrict__ dinv, const T *__restrict__ Av, T *__restrict__ out,
+                           const int *__restrict__ nblk) {
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
   const long long blk = g / bb;
+  if (nblk && blk >= *nblk) return;  // grid sized by an upper bound
   const int rc = (int)(g - blk * bb), r = rc / b, c = rc - r * b;
   const T *d = dinv + (size_t)rowmap[orow[blk]] * bb + r * b;
   const T *a = Av + (size_t)osrc[blk] * bb + c;
@@ -371,11 +373,13 @@ __global__ void k_L_values(long long total, int b, const int *__restrict__ orow,
 
 template <typename T>
 __global__ void k_copy_blocks(long long total, int b, const int *__restrict__ src,
-                              const T *__restrict__ in, T *__restrict__ out) {
+                              const T *__restrict__ in, T *__restrict__ out,
+                              const int *__restrict__ nblk = nullptr) {
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
   const long long blk = g / bb;
+  if (nblk && blk >= *nblk) return;  // grid sized by an upper bound
   const int rc = (int)(g - blk * bb);
   out[g] = in[(size_t)src[blk] * bb + rc];
 }
@@ -656,11 +660,12 @@ template <typename T>
 __global__ void k_ap_values(long long total, int b, const int *__restrict__ orow,
                             const int *__restrict__ oci, const int *__restrict__ rp,
                             const int *__restrict__ ci, const int *__restrict__ ipc,
-                            const T *__restrict__ Av, T *__restrict__ out) {
+                            const T *__restrict__ Av, T *__restrict__ out, const int *__restrict__ nblk) {
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
   const long long blk = g / bb;
+  if (blk >= *nblk) return;  // grid sized by an upper bound
   const int rc = (int)(g - blk * bb);
   const int r = orow[blk], J = oci[blk];
   T acc = 0;
@@ -1041,29 +1046,33 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
   (void)left_nnz;
 }
 
+// With defer, the kept count stays on the device (M.nnzb = -1, the buffers sized
+// by the unfiltered count): no host round trip.
 template <typename T>
-static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M) {
+static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M, bool defer = false) {
   const int nrows = M.nrows;
   ProfScope ps("filter", s);
-  int *newpos = tmp.alloc<int>(M.nnzb);
+  const int ub = M.nnzb;
+  int *newpos = tmp.alloc<int>(ub);
   int *cnt = tmp.alloc<int>(nrows + 1);
-  T *nrm = tmp.alloc<T>(M.nnzb);
-  if (M.nnzb) {
-    k_block_norm2<T><<<grid(M.nnzb), kThreads, 0, s>>>(M.nnzb, b, M.v, nrm);
+  T *nrm = tmp.alloc<T>(ub);
+  if (ub) {
+    k_block_norm2<T><<<grid(ub), kThreads, 0, s>>>(ub, b, M.v, nrm);
     NAIR_LAUNCH_CHECK();
   }
   k_filter_flags<T><<<grid(nrows), kThreads, 0, s>>>(nrows, M.rp, M.ci, nrm, tol2, newpos, cnt);
   NAIR_LAUNCH_CHECK();
   int *nrp = mem.alloc<int>(nrows + 1);
-  int nn = exclusive_scan(cnt, nrp, nrows, s, tmp);
-  int *nci = mem.alloc<int>(nn);
-  int *src = tmp.alloc<int>(nn);
+  const int nn = exclusive_scan(cnt, nrp, nrows, s, tmp, !defer);
+  const int cap = defer ? ub : nn;
+  int *nci = mem.alloc<int>(cap);
+  int *src = tmp.alloc<int>(cap);
   k_filter_compact<<<grid(nrows), kThreads, 0, s>>>(nrows, M.rp, M.ci, newpos, nrp, nci, src);
   NAIR_LAUNCH_CHECK();
-  T *nv = mem.alloc<T>((size_t)nn * b * b);
-  long long total = (long long)nn * b * b;
+  T *nv = mem.alloc<T>((size_t)cap * b * b);
+  long long total = (long long)cap * b * b;
   if (total) {
-    k_copy_blocks<T><<<grid(total), kThreads, 0, s>>>(total, b, src, M.v, nv);
+    k_copy_blocks<T><<<grid(total), kThreads, 0, s>>>(total, b, src, M.v, nv, defer ? nrp + nrows : nullptr);
     NAIR_LAUNCH_CHECK();
   }
   mem.release(M.rp);
@@ -1076,7 +1085,7 @@ static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M
   M.rp = nrp;
   M.ci = nci;
   M.v = nv;
-  M.nnzb = nn;
+  M.nnzb = defer ? -1 : nn;
 }
 
 template <typename T>
@@ -1111,23 +1120,27 @@ static int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Me
 }
 
 // extract rows `rowmap` (nrows of them) of A with the chosen column test
+// The output count stays on the device (out.nnzb = -1, buffers sized by the
+// upper bound A.nnzb, returned in *ub): no host round trip.
 template <typename T>
 static void extract(int b, int nrows, int mode, const int *rowmap, const Level<T> &L,
                     const unsigned char *strong, const int *fidx, cudaStream_t s, Mem &mem,
-                    Mem &tmp, DBsr<T> &out, int **src_out, int **row_out) {
+                    Mem &tmp, DBsr<T> &out, int **src_out, int **row_out, int *ub) {
   int *cnt = tmp.alloc<int>(nrows + 1);
   k_sub_count<<<grid(nrows), kThreads, 0, s>>>(nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, cnt);
   NAIR_LAUNCH_CHECK();
   out.nrows = nrows;
   out.rp = mem.alloc<int>(nrows + 1);
-  out.nnzb = exclusive_scan(cnt, out.rp, nrows, s, tmp);
-  out.ci = mem.alloc<int>(out.nnzb);
-  int *src = tmp.alloc<int>(out.nnzb);
-  int *row = tmp.alloc<int>(out.nnzb);
+  exclusive_scan(cnt, out.rp, nrows, s, tmp, false);
+  *ub = L.A.nnzb;
+  out.nnzb = -1;
+  out.ci = mem.alloc<int>(*ub);
+  int *src = tmp.alloc<int>(*ub);
+  int *row = tmp.alloc<int>(*ub);
   k_sub_fill<<<grid(nrows), kThreads, 0, s>>>(nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, fidx,
                                                out.rp, out.ci, src, row);
   NAIR_LAUNCH_CHECK();
-  out.v = mem.alloc<T>((size_t)out.nnzb * b * b);
+  out.v = mem.alloc<T>((size_t)*ub * b * b);
   tmp.release(cnt);
   *src_out = src;
   *row_out = row;
@@ -1213,11 +1226,12 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   ProfScope ps_neu("neumann", s, l);
   DBsr<T> Lm;
   int *src, *row;
-  extract<T>(b, nF, 0, f2f, L, strong, fidx, s, mem, tmp, Lm, &src, &row);
+  int lub = 0;
+  extract<T>(b, nF, 0, f2f, L, strong, fidx, s, mem, tmp, Lm, &src, &row, &lub);
   Lm.ncols = nF;
-  long long tot = (long long)Lm.nnzb * bb;
+  long long tot = (long long)lub * bb;
   if (tot) {
-    k_L_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, row, src, f2f, L.dinv, L.A.v, Lm.v);
+    k_L_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, row, src, f2f, L.dinv, L.A.v, Lm.v, Lm.rp + nF);
     NAIR_LAUNCH_CHECK();
   }
   tmp.release(src);
@@ -1248,8 +1262,8 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   for (int t = 0; t < P.k; ++t) {
     SpgemmIdx X{nF, Lm.rp, Lm.ci, nullptr, Tk.rp, Tk.ci, Dg.rp, Dg.rp, nullptr};
     DBsr<T> Tn;
-    spgemm<T>(b, X, Lm.nnzb, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn);
-    if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn);
+    spgemm<T>(b, X, lub, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn);
+    if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn, true);
     release_bsr(mem, Tk);
     Tk = Tn;
   }
@@ -1260,15 +1274,16 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   // a5: R_cf = -A_cf Delta over all A_cf blocks
   ProfScope ps_r("restriction", s, l);
   DBsr<T> Acf;
-  extract<T>(b, nC, 1, L.c2f, L, strong, fidx, s, tmp, tmp, Acf, &src, &row);
-  tot = (long long)Acf.nnzb * bb;
+  int aub = 0;
+  extract<T>(b, nC, 1, L.c2f, L, strong, fidx, s, tmp, tmp, Acf, &src, &row, &aub);
+  tot = (long long)aub * bb;
   if (tot) {
-    k_copy_blocks<T><<<grid(tot), kThreads, 0, s>>>(tot, b, src, L.A.v, Acf.v);
+    k_copy_blocks<T><<<grid(tot), kThreads, 0, s>>>(tot, b, src, L.A.v, Acf.v, Acf.rp + nC);
     NAIR_LAUNCH_CHECK();
   }
   {
     SpgemmIdx X{nC, Acf.rp, Acf.ci, nullptr, Tk.rp, Tk.ci, nullptr, nullptr, nullptr};
-    spgemm<T>(b, X, Acf.nnzb, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R);
+    spgemm<T>(b, X, aub, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R);
   }
   L.R_ci_f = L.R.ci;
   L.R.ci = mem.alloc<int>(L.R.nnzb);
@@ -1294,15 +1309,17 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     AP.nrows = E;
     AP.ncols = nC;
     AP.rp = tmp.alloc<int>(E + 1);
-    AP.nnzb = exclusive_scan(cnt, AP.rp, E, s, tmp);
-    AP.ci = tmp.alloc<int>(AP.nnzb);
-    int *aprow = tmp.alloc<int>(AP.nnzb);
+    exclusive_scan(cnt, AP.rp, E, s, tmp, false);
+    AP.nnzb = -1;               // at most one block per block of A: sized by nnzb(A)
+    AP.ci = tmp.alloc<int>(nnzb);
+    int *aprow = tmp.alloc<int>(nnzb);
     k_ap_fill<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.ipc, AP.rp, AP.ci, aprow);
     NAIR_LAUNCH_CHECK();
-    AP.v = tmp.alloc<T>((size_t)AP.nnzb * bb);
-    tot = (long long)AP.nnzb * bb;
+    AP.v = tmp.alloc<T>((size_t)nnzb * bb);
+    tot = (long long)nnzb * bb;
     if (tot) {
-      k_ap_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, aprow, AP.ci, L.A.rp, L.A.ci, L.ipc, L.A.v, AP.v);
+      k_ap_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, aprow, AP.ci, L.A.rp, L.A.ci, L.ipc, L.A.v, AP.v,
+                                                   AP.rp + E);
       NAIR_LAUNCH_CHECK();
     }
   }
@@ -1314,6 +1331,8 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   }
   nx.E = nC;
   if (P.keep) {
+    Lm.nnzb = read_int(Lm.rp + nF, s);
+    if (Tk.nnzb < 0) Tk.nnzb = read_int(Tk.rp + nF, s);
     L.L = Lm;
     L.Delta = Tk;
   } else {
