@@ -42,16 +42,18 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
   __syncthreads();
   bool sing = false;
   for (int k = 0; k < b; ++k) {
-    int p = k;
-    if (active) {
+    // pivot search by one thread per block (FP64 compares are FP64-pipe work)
+    if (active && t == 0) {
+      int p = k;
       double best = fabs(M[k * b + k]);
       for (int r = k + 1; r < b; ++r) {
         double a = fabs(M[r * b + k]);
         if (a > best) { best = a; p = r; }
       }
-      if (t == 0) piv[lb * 32 + k] = p;
+      piv[lb * 32 + k] = p;
     }
     __syncthreads();
+    const int p = active ? piv[lb * 32 + k] : k;
     if (active && p != k) {  // thread t swaps column t of rows k and p
       double tmp = M[k * b + t];
       M[k * b + t] = M[p * b + t];
