@@ -85,7 +85,8 @@ static double block_norm2(int b, const double *x) {
 /* ---------------------------------------------------------------------------
  * a1: inverse of one b x b block, in-place Gauss-Jordan with partial pivoting.
  * Pivot = first row (from k down) with the largest |entry| in column k.  The
- * pivot row is divided by the pivot (IEEE division), every other row r gets
+ * pivot row is multiplied by the reciprocal of the pivot (one IEEE division per
+ * step), every other row r gets
  * M[r][c] = fma(-l, M[k][c], M[r][c]) with l = M[r][k]; columns are swapped
  * back at the end.  A zero pivot is a singular block.
  * ------------------------------------------------------------------------- */
@@ -108,8 +109,9 @@ static int gj_inverse(int b, const double *A, double *M) {
       }
     double d = M[k * b + k];
     if (d == 0.0 || d != d) return ORC_ERR_SINGULAR_BLOCK;
+    double rinv = 1.0 / d;
     M[k * b + k] = 1.0;
-    for (int c = 0; c < b; ++c) M[k * b + c] = M[k * b + c] / d;
+    for (int c = 0; c < b; ++c) M[k * b + c] = M[k * b + c] * rinv;
     for (int r = 0; r < b; ++r) {
       if (r == k) continue;
       double l = M[r * b + k];

@@ -41,6 +41,7 @@ __global__ void k_block_inverse_noalloc(int nblk, int b, int bpc, const double *
                                         double *__restrict__ out, int *__restrict__ status) {
   extern __shared__ double sm[];
   int *piv = reinterpret_cast<int *>(sm + (size_t)bpc * b * b);
+  __shared__ double rinv_s[256];
   __shared__ int cta_sing;
   const int lb = threadIdx.x / b, t = threadIdx.x % b;
   const long long blk = (long long)blockIdx.x * bpc + lb;
@@ -72,10 +73,11 @@ __global__ void k_block_inverse_noalloc(int nblk, int b, int bpc, const double *
     __syncthreads();
     const double d = active ? M[k * b + k] : 1.0;
     if (active && (d == 0.0 || d != d)) sing = true;
+    if (active && t == 0) rinv_s[lb] = __ddiv_rn(1.0, d);  // one division per step
     __syncthreads();
     if (active) {
       double v = (t == k) ? 1.0 : M[k * b + t];
-      M[k * b + t] = __ddiv_rn(v, d);
+      M[k * b + t] = __dmul_rn(v, rinv_s[lb]);
     }
     __syncthreads();
     if (active && t != k) {

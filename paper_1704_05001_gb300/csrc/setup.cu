@@ -31,6 +31,7 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
                                 int *__restrict__ err) {
   extern __shared__ double sm[];
   int *piv = reinterpret_cast<int *>(sm + (size_t)bpc * b * b);
+  __shared__ double rinv_s[256];
   const int lb = threadIdx.x / b, t = threadIdx.x % b;
   const long long blk = (long long)blockIdx.x * bpc + lb;
   const bool active = lb < bpc && blk < nblk;
@@ -62,10 +63,11 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
     __syncthreads();
     const double d = active ? M[k * b + k] : 1.0;
     if (active && (d == 0.0 || d != d)) sing = true;
+    if (active && t == 0) rinv_s[lb] = __ddiv_rn(1.0, d);  // one division per step
     __syncthreads();
     if (active) {
       double v = (t == k) ? 1.0 : M[k * b + t];
-      M[k * b + t] = __ddiv_rn(v, d);
+      M[k * b + t] = __dmul_rn(v, rinv_s[lb]);
     }
     __syncthreads();
     if (active && t != k) {
@@ -741,12 +743,13 @@ __device__ void dense_gj_cta(int n, double *__restrict__ M, int *__restrict__ pi
     if (tid == 0) {
       dk = M[(size_t)k * n + k];
       if (dk == 0.0 || dk != dk) *err = 1;
+      dk = __ddiv_rn(1.0, dk);  // reciprocal of the pivot
     }
     __syncthreads();
-    const double d = dk;
+    const double rinv = dk;
     for (int c = tid; c < n; c += blockDim.x) {
       double v = (c == k) ? 1.0 : M[(size_t)k * n + c];
-      M[(size_t)k * n + c] = __ddiv_rn(v, d);
+      M[(size_t)k * n + c] = __dmul_rn(v, rinv);
     }
     for (int r = tid; r < n; r += blockDim.x) {
       lcol[r] = (r == k) ? 0.0 : M[(size_t)r * n + k];
@@ -836,9 +839,10 @@ __global__ void __launch_bounds__(256) k_gj_step(int n, int k, const double *__r
     if (d == 0.0 || d != d) *err = 1;
   }
   const int r0 = blockIdx.y * kGjTileRows, c0 = blockIdx.x * kGjTileCols;
+  const double rinv = __ddiv_rn(1.0, d);
   for (int c = tid; c < kGjTileCols; c += blockDim.x) {
     const int cc = c0 + c;
-    if (cc < n) prow[c] = __ddiv_rn(cc == k ? 1.0 : Min[(size_t)p * n + cc], d);
+    if (cc < n) prow[c] = __dmul_rn(cc == k ? 1.0 : Min[(size_t)p * n + cc], rinv);
   }
   __syncthreads();
   for (int idx = tid; idx < kGjTileRows * kGjTileCols; idx += blockDim.x) {
