@@ -30,15 +30,16 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
                                 const int *__restrict__ pos, double *__restrict__ out,
                                 int *__restrict__ err) {
   extern __shared__ double sm[];
-  int *piv = reinterpret_cast<int *>(sm + (size_t)bpc * b * b);
+  const int ld = b | 1;  // odd row stride: rows of one block fall in distinct banks
+  int *piv = reinterpret_cast<int *>(sm + (size_t)bpc * b * ld);
   __shared__ double rinv_s[256];
   const int lb = threadIdx.x / b, t = threadIdx.x % b;
   const long long blk = (long long)blockIdx.x * bpc + lb;
   const bool active = lb < bpc && blk < nblk;
-  double *M = sm + (size_t)lb * b * b;
+  double *M = sm + (size_t)lb * b * ld;
   if (active) {
     const TI *src = A + (size_t)(pos ? pos[blk] : blk) * b * b;
-    for (int c = 0; c < b; ++c) M[t * b + c] = (double)src[t * b + c];
+    for (int c = 0; c < b; ++c) M[t * ld + c] = (double)src[t * b + c];
   }
   __syncthreads();
   bool sing = false;
@@ -46,9 +47,9 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
     // pivot search by one thread per block (FP64 compares are FP64-pipe work)
     if (active && t == 0) {
       int p = k;
-      double best = fabs(M[k * b + k]);
+      double best = fabs(M[k * ld + k]);
       for (int r = k + 1; r < b; ++r) {
-        double a = fabs(M[r * b + k]);
+        double a = fabs(M[r * ld + k]);
         if (a > best) { best = a; p = r; }
       }
       piv[lb * 32 + k] = p;
@@ -56,24 +57,24 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
     __syncthreads();
     const int p = active ? piv[lb * 32 + k] : k;
     if (active && p != k) {  // thread t swaps column t of rows k and p
-      double tmp = M[k * b + t];
-      M[k * b + t] = M[p * b + t];
-      M[p * b + t] = tmp;
+      double tmp = M[k * ld + t];
+      M[k * ld + t] = M[p * ld + t];
+      M[p * ld + t] = tmp;
     }
     __syncthreads();
-    const double d = active ? M[k * b + k] : 1.0;
+    const double d = active ? M[k * ld + k] : 1.0;
     if (active && (d == 0.0 || d != d)) sing = true;
     if (active && t == 0) rinv_s[lb] = __ddiv_rn(1.0, d);  // one division per step
     __syncthreads();
     if (active) {
-      double v = (t == k) ? 1.0 : M[k * b + t];
-      M[k * b + t] = __dmul_rn(v, rinv_s[lb]);
+      double v = (t == k) ? 1.0 : M[k * ld + t];
+      M[k * ld + t] = __dmul_rn(v, rinv_s[lb]);
     }
     __syncthreads();
     if (active && t != k) {
-      double l = M[t * b + k];
-      M[t * b + k] = 0.0;
-      for (int c = 0; c < b; ++c) M[t * b + c] = __fma_rn(-l, M[k * b + c], M[t * b + c]);
+      double l = M[t * ld + k];
+      M[t * ld + k] = 0.0;
+      for (int c = 0; c < b; ++c) M[t * ld + c] = __fma_rn(-l, M[k * ld + c], M[t * ld + c]);
     }
     __syncthreads();
   }
@@ -81,13 +82,13 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
     for (int k = b - 1; k >= 0; --k) {
       int p = piv[lb * 32 + k];
       if (p != k) {
-        double tmp = M[t * b + k];
-        M[t * b + k] = M[t * b + p];
-        M[t * b + p] = tmp;
+        double tmp = M[t * ld + k];
+        M[t * ld + k] = M[t * ld + p];
+        M[t * ld + p] = tmp;
       }
     }
     double *dst = out + (size_t)blk * b * b;
-    for (int c = 0; c < b; ++c) dst[t * b + c] = M[t * b + c];
+    for (int c = 0; c < b; ++c) dst[t * b + c] = M[t * ld + c];
     if (sing) atomicOr(err, 1);
   }
 }
@@ -97,7 +98,7 @@ void block_inverses(int nblk, int b, const TI *A, const int *pos, double *out, i
                     cudaStream_t s) {
   if (nblk <= 0) return;
   int bpc = std::max(1, kThreads / b);
-  size_t smem = (size_t)bpc * b * b * sizeof(double) + (size_t)bpc * 32 * sizeof(int);
+  size_t smem = (size_t)bpc * b * (b | 1) * sizeof(double) + (size_t)bpc * 32 * sizeof(int);
   if (smem > 48 * 1024) {
     NAIR_CK(cudaFuncSetAttribute(k_block_inverse<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
