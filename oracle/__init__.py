@@ -62,6 +62,31 @@ def _load():
     return _lib
 
 
+class use_library:
+    """Context manager: route the oracle's calls to another build of nair_oracle.c
+    (the mutation tests load deliberately broken copies this way)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self._saved = _lib
+        lib = ctypes.CDLL(self.path)
+        for name in ("orc_setup", "orc_free", "orc_num_levels", "orc_level_sizes", "orc_level_get",
+                     "orc_solve", "orc_vcycle", "orc_block_inverse", "orc_transpose", "orc_gradients"):
+            getattr(lib, name).argtypes = getattr(self._saved, name).argtypes
+            getattr(lib, name).restype = getattr(self._saved, name).restype
+        _lib = lib
+        return lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 

@@ -1,0 +1,75 @@
+"""The oracle pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of nair_oracle.c (a dropped term, a
+wrong sign, a transposed operand, an off-by-one, a wrong comparison), builds
+it, and runs the pins of tests/test_oracle_pins.py against it: at least one pin
+must fail.  The shipped oracle is never modified.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "nair_oracle.c")
+
+# (name, exact text in nair_oracle.c, planted replacement)
+MUTATIONS = [
+    ("inverse: pivot reciprocal dropped", "double rinv = 1.0 / d;", "double rinv = 1.0;"),
+    ("C/F key: measure order reversed", "if (lam[i] != lam[j]) return lam[i] > lam[j];",
+     "if (lam[i] != lam[j]) return lam[i] < lam[j];"),
+    ("strength: threshold ignored", "L->snorm[p] > 0.0 && L->snorm[p] >= thr);", "L->snorm[p] > 0.0);"),
+    ("Neumann: D^-1 term of the Horner step dropped",
+     "memcpy(acc + (size_t)j * bb, init->v + (size_t)p * bb, sizeof(double) * bb);",
+     "memset(acc + (size_t)j * bb, 0, sizeof(double) * bb);"),
+    ("block product: right operand transposed",
+     "for (int t = 0; t < b; ++t) s = fma(a[r * b + t], bv[t * b + cc], s);",
+     "for (int t = 0; t < b; ++t) s = fma(a[r * b + t], bv[cc * b + t], s);"),
+    ("restriction: sign of R_cf lost", "dst[e] = negate ? -src[e] : src[e];", "dst[e] = src[e];"),
+    ("interpolation: weakest instead of strongest C neighbour",
+     "if (best < 0 || L->snorm[p] > bs) { best = j; bs = L->snorm[p]; }",
+     "if (best < 0 || L->snorm[p] < bs) { best = j; bs = L->snorm[p]; }"),
+    ("A P merge: later blocks overwrite instead of add", "c[k] = c[k] + a[k];", "c[k] = a[k];"),
+    ("L: sign of -D^-1 A lost", "o[r * b + c] = -s;", "o[r * b + c] = s;"),
+    ("Jacobi: correction subtracted", "x[(size_t)i * b + r] += s;", "x[(size_t)i * b + r] -= s;"),
+    ("F-relaxation: one sweep short",
+     "for (int s = 0; s < H->f_sweeps; ++s) jacobi(b, L, 0, f, x, tmp);",
+     "for (int s = 1; s < H->f_sweeps; ++s) jacobi(b, L, 0, f, x, tmp);"),
+]
+
+PINS = [
+    lambda o: pins.test_block_inverse_matches_dense_inverse(o, 6),
+    lambda o: pins.test_cf_star_by_hand(o),
+    lambda o: pins.test_cf_measure_priority_by_hand(o),
+    lambda o: pins.test_strength_rule_by_hand(o),
+    lambda o: pins.test_cf_invariants(o, "C2", 8, 2),
+    lambda o: pins.test_neumann_error_identity(o, "C3", 2, 1),
+    lambda o: pins.test_exact_neumann_gives_ideal_restriction_and_schur(o, 1),
+    lambda o: pins.test_galerkin_product_and_wap_identity(o, "C2", 2, 2),
+    lambda o: pins.test_chain_closed_form(o),
+    lambda o: pins.test_exact_settings_one_vcycle_solves(o, 1),
+    lambda o: pins.test_minimal_f_sweeps_two_level(o),
+    lambda o: pins.test_error_propagation_is_strictly_block_lower_triangular(o),
+    lambda o: pins.test_fgmres_matches_dense_solve(o, "C2", 8, 2),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new):
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation target not unique: {old}"
+    src = tmp_path / "mutant.c"
+    src.write_text(text.replace(old, new))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(lib), str(src), "-lm"])
+    caught = []
+    with oracle.use_library(str(lib)):
+        for pin in PINS:
+            try:
+                pin(oracle)
+            except Exception as e:  # a failed assertion or an oracle error status
+                caught.append(type(e).__name__)
+    assert caught, f"no pin caught the planted mistake: {name}"

@@ -129,6 +129,19 @@ def test_cf_star_by_hand(oracle_lib):
     assert lev["ipc"].tolist() == [0, 0, 0, 0, 0]
 
 
+def test_cf_measure_priority_by_hand(oracle_lib):
+    """Classical measure (Sec. 5.1): of two competing undecided points the one more
+    points depend on becomes C.  Point 1 depends on 0; point 2 on 0 and 1:
+    lambda = (2, 1, 0) -> 2 is F at once, 0 beats 1 and becomes C, 1 becomes F."""
+    rp = np.array([0, 1, 3, 6], dtype=np.int32)
+    col = np.array([0, 0, 1, 0, 1, 2], dtype=np.int32)
+    vals = np.array([2.0, -1.0, 2.0, -1.0, -1.0, 2.0]).reshape(-1, 1, 1)
+    H = oracle_lib.Hierarchy(rp, col, vals, max_coarse=1, max_levels=2, filter_targets=0)
+    lev = H.level(0)
+    assert lev["lam"].tolist() == [2, 1, 0]
+    assert lev["cf"].tolist() == [1, 0, 0]
+
+
 def test_strength_rule_by_hand(oracle_lib):
     """Row 2 of a 3-point system: |a_20| = 1, |a_21| = 0.05; theta = 0.1 keeps only 0."""
     rp = np.array([0, 1, 3, 6], dtype=np.int32)
@@ -337,6 +350,25 @@ def test_exact_settings_one_vcycle_solves(oracle_lib, p):
     x = H.vcycle(P["rhs"])
     xs = np.linalg.solve(A, P["rhs"])
     assert np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+def test_minimal_f_sweeps_two_level(oracle_lib):
+    """Two levels, R = R_ideal (theta = 0, no filtering, k >= d_f): after the exact
+    coarse-grid correction the F error is propagated by L, nilpotent of degree
+    d_f + 1, so exactly d_f + 1 Jacobi F sweeps make one cycle exact and d_f do not
+    (Lemma ideal restriction; Sec. 4.1)."""
+    P = tiny("C3", N=6, p=1)   # jittered mesh: the F-F graph has paths (d_f = 2)
+    par = dict(theta=0.0, filter_targets=0, neumann_degree=60, max_levels=2, max_coarse=1,
+               max_dense=100000, c_sweeps=0)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], **par)
+    df = longest_ff_path(H.level(0))
+    assert df >= 2
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    xs = np.linalg.solve(A, P["rhs"])
+    x_ok = H.vcycle(P["rhs"], f_sweeps=df + 1, c_sweeps=0)
+    x_short = H.vcycle(P["rhs"], f_sweeps=df, c_sweeps=0)
+    assert np.linalg.norm(x_ok - xs) <= 1e-12 * np.linalg.norm(xs)
+    assert np.linalg.norm(x_short - xs) >= 1e-8 * np.linalg.norm(xs)
 
 
 def test_error_propagation_is_strictly_block_lower_triangular(oracle_lib):
