@@ -55,6 +55,8 @@ def _load():
             lib.orc_solve.argtypes = [P, P, P, I, I, I, I, D, P, I, ctypes.POINTER(I),
                                       ctypes.POINTER(I), ctypes.POINTER(D)]
             lib.orc_vcycle.argtypes = [P, P, P, I, I]
+            lib.orc_vcycle_t.argtypes = [P, P, P, I, I]
+            lib.orc_solve_t.argtypes = lib.orc_solve.argtypes
             lib.orc_block_inverse.argtypes = [I, P, P]
             lib.orc_transpose.argtypes = [I, I, P, P, P, P, P, P]
             lib.orc_gradients.argtypes = [I, I, P, P, P, P, P]
@@ -75,7 +77,7 @@ class use_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("orc_setup", "orc_free", "orc_num_levels", "orc_level_sizes", "orc_level_get",
-                     "orc_solve", "orc_vcycle", "orc_block_inverse", "orc_transpose", "orc_gradients"):
+                     "orc_solve", "orc_vcycle", "orc_solve_t", "orc_vcycle_t", "orc_block_inverse", "orc_transpose", "orc_gradients"):
             getattr(lib, name).argtypes = getattr(self._saved, name).argtypes
             getattr(lib, name).restype = getattr(self._saved, name).restype
         _lib = lib
@@ -178,7 +180,9 @@ class Hierarchy:
             d["L_v"] = self._get(l, L_V, (s["L_nnzb"], b, b), np.float64)
         return d
 
-    def solve(self, rhs, x0=None, **over):
+    def solve(self, rhs, x0=None, transposed=False, **over):
+        """FGMRES on A x = rhs with the V-cycle, or (transposed=True) on
+        A^T x = rhs with the transposed cycle of the same hierarchy."""
         p = dict(self.params)
         p.update(over)
         rhs = np.ascontiguousarray(rhs, dtype=np.float64)
@@ -188,19 +192,23 @@ class Hierarchy:
         hl = ctypes.c_int(0)
         it = ctypes.c_int(0)
         rr = ctypes.c_double(0)
-        st = _load().orc_solve(self._h, _p(rhs), _p(x), p["f_sweeps"], p["c_sweeps"], p["restart"],
-                               p["maxiter"], p["tol"], _p(hist), cap, ctypes.byref(hl),
-                               ctypes.byref(it), ctypes.byref(rr))
+        fn = _load().orc_solve_t if transposed else _load().orc_solve
+        st = fn(self._h, _p(rhs), _p(x), p["f_sweeps"], p["c_sweeps"], p["restart"],
+                p["maxiter"], p["tol"], _p(hist), cap, ctypes.byref(hl),
+                ctypes.byref(it), ctypes.byref(rr))
         return dict(x=x, status=st, history=hist[:hl.value].copy(), iterations=it.value,
                     relres=rr.value)
 
-    def vcycle(self, f, f_sweeps=None, c_sweeps=None):
+    def vcycle(self, f, f_sweeps=None, c_sweeps=None, transposed=False):
+        """One cycle with zero initial guess: the V-cycle M^{-1} f, or its
+        transpose M^{-T} f (transposed=True)."""
         p = self.params
         f = np.ascontiguousarray(f, dtype=np.float64)
         x = np.zeros_like(f)
-        _load().orc_vcycle(self._h, _p(f), _p(x),
-                           p["f_sweeps"] if f_sweeps is None else f_sweeps,
-                           p["c_sweeps"] if c_sweeps is None else c_sweeps)
+        fn = _load().orc_vcycle_t if transposed else _load().orc_vcycle
+        fn(self._h, _p(f), _p(x),
+           p["f_sweeps"] if f_sweeps is None else f_sweeps,
+           p["c_sweeps"] if c_sweeps is None else c_sweeps)
         return x
 
 

@@ -14,7 +14,9 @@
  *   - block nAIR and filtering, Sec. 5.2;
  *   - V-cycle with no pre-relaxation, F-relaxation with one more sweep than
  *     the Neumann degree, then a C sweep (Sec. 5, Remark on C-relaxation);
- *   - GMRES acceleration (Sec. 6), as flexible GMRES(m) with CGS2.
+ *   - GMRES acceleration (Sec. 6), as flexible GMRES(m) with CGS2;
+ *   - for A^T: the transposed cycle of the same hierarchy (R^T interpolates,
+ *     P^T restricts, pre-relaxation; Corollary on ideal interpolation).
  *
  * Canonical arithmetic (so that the GPU path can be compared bit for bit on
  * C/F splittings and sparsity patterns): every value upstream of a threshold
@@ -65,6 +67,7 @@ typedef struct {
   int b, nlev;
   Level lev[MAXLEV];
   int f_sweeps, c_sweeps;
+  int transposed; /* solve with A^T and the transposed cycle (adjoint) */
 } Hier;
 
 static void bsr_free(Bsr *m) {
@@ -761,6 +764,133 @@ int orc_vcycle(void *h, const double *f, double *x, int f_sweeps, int c_sweeps) 
   return ORC_OK;
 }
 
+/* ---------------------------------------------------------------------------
+ * Adjoint preconditioner from the forward hierarchy.  For A^T the transfer
+ * operators swap roles (Sec. 2, Corollary on ideal interpolation; Remark on
+ * pre-F-relaxation): R^T = [Z^T; I] interpolates, where Z^T = R_cf^T
+ * approximates the ideal interpolation -(A^T)_ff^{-1} (A^T)_fc of A^T, and
+ * P^T = [W^T I] restricts, with coarse operators K^T.  Relaxation comes
+ * before the coarse-grid correction: the C sweeps, then the F sweeps, each a
+ * block-Jacobi sweep on A^T whose blocks (D_ii^{-1})^T are the inverses of the
+ * diagonal blocks of A^T.  As a linear map this cycle is the transpose of the
+ * forward V-cycle (the two error propagators are adjoint to each other).
+ * ------------------------------------------------------------------------- */
+
+/* y = A^T x: y_j = sum over blocks (i, j) of A_ij^T x_i */
+static void spmv_t(int b, const Bsr *A, const double *x, double *y) {
+  size_t bb = (size_t)b * b;
+  memset(y, 0, sizeof(double) * (size_t)A->ncols * b);
+  for (int i = 0; i < A->nrows; ++i)
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      const double *a = A->v + (size_t)p * bb;
+      double *yj = y + (size_t)A->ci[p] * b;
+      const double *xi = x + (size_t)i * b;
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) yj[c] += a[r * b + c] * xi[r];
+    }
+}
+
+/* one block-Jacobi sweep on A^T over the rows with cf == which:
+ * x_i <- x_i + (D_ii^{-1})^T (f - A^T x)_i, every row from the sweep's starting x */
+static void jacobi_t(int b, const Level *L, int which, const double *f, double *x, double *tmp) {
+  size_t bb = (size_t)b * b;
+  spmv_t(b, &L->A, x, tmp);
+  for (int i = 0; i < L->A.nrows; ++i) {
+    if (L->cf[i] != which) continue;
+    double res[32];
+    for (int r = 0; r < b; ++r) res[r] = f[(size_t)i * b + r] - tmp[(size_t)i * b + r];
+    const double *d = L->Dinv + (size_t)i * bb;
+    double *xi = x + (size_t)i * b;
+    for (int r = 0; r < b; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < b; ++c) s += d[c * b + r] * res[c];
+      xi[r] += s;
+    }
+  }
+}
+
+/* x = K^{-T} f from the factors P K = L U of dense_lu: K^T = U^T L^T P, so
+ * solve U^T y = f, then L^T z = y, then undo the row interchanges */
+static void dense_lu_solve_t(int n, const double *a, const int *piv, double *x) {
+  for (int r = 0; r < n; ++r) {
+    double s = x[r];
+    for (int c = 0; c < r; ++c) s -= a[(size_t)c * n + r] * x[c];
+    x[r] = s / a[(size_t)r * n + r];
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = x[r];
+    for (int c = r + 1; c < n; ++c) s -= a[(size_t)c * n + r] * x[c];
+    x[r] = s;
+  }
+  for (int k = n - 1; k >= 0; --k)
+    if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+}
+
+/* transposed cycle with zero initial guess: c_sweeps C sweeps and f_sweeps F
+ * sweeps on A^T, residual, restriction with P^T (each C point takes its own
+ * residual plus those of the F points interpolating from it), recursion on
+ * K^T, interpolation with R^T (x_C += x_c, x_F += R_cf^T x_c) */
+static void vcycle_t(const Hier *H, int l, const double *f, double *x) {
+  int b = H->b;
+  size_t bb = (size_t)b * b;
+  const Level *L = &H->lev[l];
+  size_t n = (size_t)L->A.nrows * b;
+  if (L->coarsest) {
+    memcpy(x, f, sizeof(double) * n);
+    dense_lu_solve_t(L->n, L->lu, L->piv, x);
+    return;
+  }
+  int nC = L->nC;
+  double *rc = (double *)calloc((size_t)nC * b + 8, sizeof(double));
+  double *xc = (double *)malloc(sizeof(double) * (size_t)nC * b + 8);
+  double *tmp = (double *)malloc(sizeof(double) * n + 8);
+  memset(x, 0, sizeof(double) * n);
+  for (int s = 0; s < H->c_sweeps; ++s) jacobi_t(b, L, 1, f, x, tmp);
+  for (int s = 0; s < H->f_sweeps; ++s) jacobi_t(b, L, 0, f, x, tmp);
+  spmv_t(b, &L->A, x, tmp);
+  for (size_t k = 0; k < n; ++k) tmp[k] = f[k] - tmp[k];
+  for (int i = 0; i < L->A.nrows; ++i) {
+    int J = L->ipc[i];
+    if (J < 0) continue;
+    for (int r = 0; r < b; ++r) rc[(size_t)J * b + r] += tmp[(size_t)i * b + r];
+  }
+  vcycle_t(H, l + 1, rc, xc);
+  for (int c = 0; c < nC; ++c) {
+    const double *xcc = xc + (size_t)c * b;
+    double *xi = x + (size_t)L->c2f[c] * b;
+    for (int r = 0; r < b; ++r) xi[r] += xcc[r];
+    for (int p = L->Rcf.rp[c]; p < L->Rcf.rp[c + 1]; ++p) {
+      const double *rv = L->Rcf.v + (size_t)p * bb;
+      double *xf = x + (size_t)L->f2f[L->Rcf.ci[p]] * b;
+      for (int r = 0; r < b; ++r)
+        for (int t = 0; t < b; ++t) xf[r] += rv[t * b + r] * xcc[t];
+    }
+  }
+  free(rc);
+  free(xc);
+  free(tmp);
+}
+
+int orc_vcycle_t(void *h, const double *f, double *x, int f_sweeps, int c_sweeps) {
+  Hier *H = (Hier *)h;
+  H->f_sweeps = f_sweeps;
+  H->c_sweeps = c_sweeps;
+  vcycle_t(H, 0, f, x);
+  return ORC_OK;
+}
+
+/* the operator and preconditioner of the Krylov solve: A and the V-cycle, or
+ * A^T and the transposed cycle */
+static void op_apply(const Hier *H, const double *x, double *y) {
+  if (H->transposed) spmv_t(H->b, &H->lev[0].A, x, y);
+  else spmv(H->b, &H->lev[0].A, x, y);
+}
+
+static void precond_apply(const Hier *H, const double *v, double *z) {
+  if (H->transposed) vcycle_t(H, 0, v, z);
+  else vcycle(H, 0, v, z);
+}
+
 static double dot(size_t n, const double *a, const double *b) {
   double s = 0.0;
   for (size_t i = 0; i < n; ++i) s += a[i] * b[i];
@@ -778,8 +908,7 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
   H->f_sweeps = f_sweeps;
   H->c_sweeps = c_sweeps;
   int b = H->b;
-  const Bsr *A = &H->lev[0].A;
-  size_t n = (size_t)A->nrows * b;
+  size_t n = (size_t)H->lev[0].A.nrows * b;
   int m = restart;
   double *V = (double *)malloc(sizeof(double) * n * (m + 1));
   double *Z = (double *)malloc(sizeof(double) * n * m);
@@ -797,7 +926,7 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
     goto done;
   }
   for (;;) {
-    spmv(b, A, x, w);
+    op_apply(H, x, w);
     for (size_t i = 0; i < n; ++i) w[i] = bvec[i] - w[i];
     double beta = sqrt(dot(n, w, w));
     if (nh == 0 && nh < hist_cap) hist[nh++] = beta / bnorm;
@@ -809,9 +938,9 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
     int j, conv = 0, brk = 0;
     for (j = 0; j < m && it < maxiter; ++j) {
       double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
-      vcycle(H, 0, vj, zj);
+      precond_apply(H, vj, zj);
       ++it;
-      spmv(b, A, zj, w);
+      op_apply(H, zj, w);
       for (int k = 0; k <= j; ++k) hc[k] = 0.0;
       for (int pass = 0; pass < 2; ++pass) {
         for (int k = 0; k <= j; ++k) {
@@ -862,7 +991,7 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
     if (conv || brk) { status = ORC_OK; break; }
     if (it >= maxiter) break;
   }
-  spmv(b, A, x, w);
+  op_apply(H, x, w);
   for (size_t i = 0; i < n; ++i) w[i] = bvec[i] - w[i];
   *relres = sqrt(dot(n, w, w)) / bnorm;
   *iters = it;
@@ -871,6 +1000,19 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
 done:
   free(V); free(Z); free(w); free(Hm); free(cs); free(sn); free(g); free(y); free(hc);
   return status;
+}
+
+/* Solve A^T lambda = w with the same flexible GMRES, preconditioned by the
+ * transposed cycle of the forward hierarchy (no second setup). */
+int orc_solve_t(void *h, const double *w, double *lam, int f_sweeps, int c_sweeps, int restart,
+                int maxiter, double tol, double *hist, int hist_cap, int *hist_len, int *iters,
+                double *relres) {
+  Hier *H = (Hier *)h;
+  H->transposed = 1;
+  int st = orc_solve(h, w, lam, f_sweeps, c_sweeps, restart, maxiter, tol, hist, hist_cap, hist_len,
+                     iters, relres);
+  H->transposed = 0;
+  return st;
 }
 
 /* ---------------------------------------------------------------------------

@@ -37,6 +37,18 @@ MUTATIONS = [
     ("F-relaxation: one sweep short",
      "for (int s = 0; s < H->f_sweeps; ++s) jacobi(b, L, 0, f, x, tmp);",
      "for (int s = 1; s < H->f_sweeps; ++s) jacobi(b, L, 0, f, x, tmp);"),
+    ("transposed cycle: F sweeps before C sweeps",
+     "  for (int s = 0; s < H->c_sweeps; ++s) jacobi_t(b, L, 1, f, x, tmp);\n"
+     "  for (int s = 0; s < H->f_sweeps; ++s) jacobi_t(b, L, 0, f, x, tmp);",
+     "  for (int s = 0; s < H->f_sweeps; ++s) jacobi_t(b, L, 0, f, x, tmp);\n"
+     "  for (int s = 0; s < H->c_sweeps; ++s) jacobi_t(b, L, 1, f, x, tmp);"),
+    ("transposed Jacobi: D^-1 not transposed", "s += d[c * b + r] * res[c];", "s += d[r * b + c] * res[c];"),
+    ("transposed interpolation: R_cf block not transposed", "xf[r] += rv[t * b + r] * xcc[t];",
+     "xf[r] += rv[r * b + t] * xcc[t];"),
+    ("P^T restriction: F residuals dropped", "    if (J < 0) continue;\n    for (int r = 0; r < b; ++r) rc",
+     "    if (J < 0 || !L->cf[i]) continue;\n    for (int r = 0; r < b; ++r) rc"),
+    ("transposed coarse solve: K^-1 instead of K^-T", "dense_lu_solve_t(L->n, L->lu, L->piv, x);",
+     "dense_lu_solve(L->n, L->lu, L->piv, x);"),
 ]
 
 PINS = [
@@ -53,6 +65,8 @@ PINS = [
     lambda o: pins.test_minimal_f_sweeps_two_level(o),
     lambda o: pins.test_error_propagation_is_strictly_block_lower_triangular(o),
     lambda o: pins.test_fgmres_matches_dense_solve(o, "C2", 8, 2),
+    lambda o: pins.test_transposed_cycle_is_adjoint_of_vcycle(o, "C2", 4, 2, 2, 2, 1),
+    lambda o: pins.test_transposed_cycle_exact_under_ideal_interpolation(o, 1),
 ]
 
 

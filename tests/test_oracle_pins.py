@@ -421,6 +421,64 @@ def test_fgmres_matches_dense_solve(oracle_lib, name, N, p):
 # a16: adjoint
 # -----------------------------------------------------------------------------
 
+def dense_cycle(H, n, **kw):
+    """The cycle with zero initial guess as a dense matrix (columns = images of e_k)."""
+    return np.stack([H.vcycle(e, **kw) for e in np.eye(n)], axis=1)
+
+
+@pytest.mark.parametrize("name,N,p,k", [("C1", 4, 1, 1), ("C2", 4, 2, 2), ("C3", 4, 2, 1)])
+@pytest.mark.parametrize("fs,cs", [(2, 1), (3, 0), (1, 2), (0, 0)])
+def test_transposed_cycle_is_adjoint_of_vcycle(oracle_lib, name, N, p, k, fs, cs):
+    """The transposed cycle (R^T interpolation, P^T restriction, C then F
+    pre-sweeps with the transposed diagonal-block inverses, K^T coarse solve) is
+    the transpose of the V-cycle as a linear map: M_T = M^T.  Compared on
+    unit vectors against the dense forward cycle."""
+    P = tiny(name, N=N, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=k, max_coarse=2)
+    assert H.nlev >= 3
+    n = P["n"]
+    M = dense_cycle(H, n, f_sweeps=fs, c_sweeps=cs)
+    MT = dense_cycle(H, n, f_sweeps=fs, c_sweeps=cs, transposed=True)
+    scale = np.abs(M).max()
+    assert np.abs(MT - M.T).max() <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_transposed_cycle_exact_under_ideal_interpolation(oracle_lib, p):
+    """Corollary (ideal interpolation): for A^T, R^T with exact Neumann R is the
+    ideal interpolation -(A^T)_ff^{-1} (A^T)_fc; an exact F solve before the
+    coarse-grid correction (enough Jacobi F sweeps on the nilpotent F block)
+    makes every level exact, so one transposed cycle solves A^T y = w."""
+    P = tiny("C1", N=6, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], theta=0.0, filter_targets=0,
+                             neumann_degree=80, max_coarse=2, f_sweeps=80, c_sweeps=1)
+    assert H.nlev >= 3
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    w = D.functional_weights(P["n"])
+    y = H.vcycle(w, transposed=True)
+    ys = np.linalg.solve(A.T, w)
+    assert np.linalg.norm(y - ys) <= 1e-11 * np.linalg.norm(ys)
+    # too few F sweeps: the pre-relaxation is no longer an exact F solve
+    H2 = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], theta=0.0, filter_targets=0,
+                              neumann_degree=80, max_coarse=2, f_sweeps=1, c_sweeps=1)
+    y2 = H2.vcycle(w, transposed=True)
+    assert np.linalg.norm(y2 - ys) >= 1e-6 * np.linalg.norm(ys)
+
+
+@pytest.mark.parametrize("name,N,p", [("C2", 8, 2), ("C3", 6, 3)])
+def test_transposed_solve_matches_dense_solve(oracle_lib, name, N, p):
+    """FGMRES on A^T with the transposed cycle of the forward hierarchy."""
+    P = tiny(name, N=N, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=2, max_coarse=4)
+    w = D.functional_weights(P["n"])
+    r = H.solve(w, transposed=True, restart=5)
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    ys = np.linalg.solve(A.T, w)
+    assert r["status"] == 0 and r["relres"] <= 1e-10
+    assert np.linalg.norm(r["x"] - ys) <= 1e-8 * np.linalg.norm(ys)
+    assert np.all(np.diff(r["history"]) <= 1e-14)
+
+
 def test_transpose_and_adjoint_gradients(oracle_lib):
     """A^T lambda = w by nAIR on A^T; gradients of J = w . x against central
     finite differences of dense solves."""
@@ -434,6 +492,8 @@ def test_transpose_and_adjoint_gradients(oracle_lib):
     Ht = oracle_lib.Hierarchy(trp, tci, tv, neumann_degree=2, max_coarse=4)
     x = Hf.solve(P["rhs"], tol=1e-13)["x"]
     lam = Ht.solve(w, tol=1e-13)["x"]
+    lam_t = Hf.solve(w, tol=1e-13, transposed=True)["x"]
+    assert np.linalg.norm(lam_t - lam) <= 1e-10 * np.linalg.norm(lam)
     gs, gq = oracle_lib.gradients(P["mass"], lam, x)
 
     def J(sig, q):
