@@ -46,6 +46,16 @@ typedef enum {
 
 typedef enum { NAIR_FP64 = 0, NAIR_MIXED = 1 } nair_precision;
 
+/* How nair_adjoint_solve preconditions A^T.
+ *   NAIR_ADJOINT_TRANSPOSED: the transpose of the forward V-cycle, from the
+ *     forward hierarchy (R^T interpolates, P^T restricts, C then F block-Jacobi
+ *     sweeps on A^T before the coarse-grid correction; Sec. 2, Corollary on
+ *     ideal interpolation, and the Remark on pre-F-relaxation).  The first
+ *     call only transposes the stored level operators.
+ *   NAIR_ADJOINT_REBUILD: a second nAIR hierarchy built for A^T with the same
+ *     parameters (its levels are exported with adjoint = 1). */
+typedef enum { NAIR_ADJOINT_TRANSPOSED = 0, NAIR_ADJOINT_REBUILD = 1 } nair_adjoint_mode;
+
 /* A block-CSR matrix in device memory (caller-owned, read-only during a call). */
 typedef struct {
   int32_t nb_rows;        /* number of block rows = number of elements E */
@@ -76,6 +86,7 @@ typedef struct {
   int32_t keep_setup_data;/* keep strength, L and Delta for nair_get_level; 0 */
   int32_t use_graphs;     /* replay the V-cycle as a CUDA graph; 1 */
   int32_t sweep_timing;   /* stamp every block-Jacobi sweep with the device clock; 0 */
+  int32_t adjoint_mode;   /* nair_adjoint_mode; NAIR_ADJOINT_TRANSPOSED */
 } nair_params;
 
 /* Solve report.  history is an optional host buffer owned by the caller. */
@@ -113,18 +124,30 @@ nair_status nair_setup(const nair_bsr *A, const nair_params *p, nair_handle **ou
  * within maxiter (x then holds the last iterate). */
 nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *info);
 
-/* Solve A^T lambda = w.  On the first call the library forms A^T (block
- * transpose, on the device) and builds a second nAIR hierarchy for it with the
- * same parameters; later calls reuse it.  w, lambda: device, n doubles. */
+/* Solve A^T lambda = w (the adjoint of nair_solve) with FGMRES on A^T.  The
+ * preconditioner follows adjoint_mode: the transposed V-cycle of the forward
+ * hierarchy (the first call forms A_l^T, R_cf^T, the P^T lists and the
+ * transposed diagonal and coarsest inverses, on the device), or a second
+ * hierarchy built for A^T on the first call.  Later calls reuse what the
+ * first built.  info->setup_ms reports that build.  w, lambda: device, n
+ * doubles; lambda holds the initial guess on entry.  Errors as nair_solve. */
 nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lambda, nair_info *info);
 
 /* Apply one V-cycle to f with zero initial guess: x = M^{-1} f (device, n doubles). */
 nair_status nair_vcycle(nair_handle *h, const double *f, double *x);
 
+/* Apply the transposed cycle of the forward hierarchy to f with zero initial
+ * guess: x = M^{-T} f, the preconditioner of NAIR_ADJOINT_TRANSPOSED (device,
+ * n doubles).  Forms the transposed operators on first use, whatever
+ * adjoint_mode says.  Synchronises the stream. */
+nair_status nair_adjoint_vcycle(nair_handle *h, const double *f, double *x);
+
 /* Release every device allocation of the handle (NULL is ignored). */
 void nair_free(nair_handle *h);
 
-/* Number of levels of the hierarchy (forward hierarchy when adjoint == 0). */
+/* Number of levels of the hierarchy: the forward hierarchy when adjoint == 0,
+ * the A^T hierarchy of NAIR_ADJOINT_REBUILD when adjoint == 1 (INVALID_ARG
+ * before the first adjoint solve or in NAIR_ADJOINT_TRANSPOSED mode). */
 nair_status nair_num_levels(const nair_handle *h, int32_t adjoint, int32_t *levels);
 
 /* Sizes of one level, 10 int64 values:

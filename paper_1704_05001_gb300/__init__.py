@@ -19,6 +19,7 @@ NAIR_OK = 0
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "SINGULAR_BLOCK", 3: "NOT_CONVERGED", 4: "BREAKDOWN",
           5: "OOM", 6: "CUDA", 7: "UNSUPPORTED"}
 FP64, MIXED = 0, 1
+ADJOINT_TRANSPOSED, ADJOINT_REBUILD = 0, 1
 
 # nair_level_array
 (A_ROWPTR, A_COL, A_VALS, DINV, CF, P_MAP, DELTA_ROWPTR, DELTA_COL, DELTA_VALS, R_ROWPTR, R_COL,
@@ -45,7 +46,7 @@ class _Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
                 ("maxiter", ctypes.c_int32), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("keep_setup_data", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("sweep_timing", ctypes.c_int32)]
+                ("sweep_timing", ctypes.c_int32), ("adjoint_mode", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -60,6 +61,7 @@ _lib = None
 
 # every entry point of include/nair.h
 EXPORTS = ["nair_default_params", "nair_setup", "nair_solve", "nair_adjoint_solve", "nair_vcycle",
+           "nair_adjoint_vcycle",
            "nair_free", "nair_num_levels", "nair_level_sizes", "nair_get_level", "nair_block_inverse",
            "nair_assemble_sigma", "nair_mass_apply", "nair_gradients", "nair_kernel_launches",
            "nair_profile", "nair_profile_entry", "nair_block_inverse_noalloc", "nair_sweep_timing",
@@ -81,6 +83,7 @@ def lib():
     L.nair_solve.argtypes = [P, P, P, ctypes.POINTER(_Info)]
     L.nair_adjoint_solve.argtypes = [P, P, P, ctypes.POINTER(_Info)]
     L.nair_vcycle.argtypes = [P, P, P]
+    L.nair_adjoint_vcycle.argtypes = [P, P, P]
     L.nair_free.argtypes = [P]
     L.nair_free.restype = None
     L.nair_num_levels.argtypes = [P, I32, ctypes.POINTER(I32)]
@@ -161,7 +164,8 @@ class NairSolver:
     row_ptr, col: int32 CUDA tensors; vals: float64 CUDA tensor (nnzb, b, b).
     Keyword arguments set fields of nair_params (strength_theta, filter_tol,
     neumann_degree, f_sweeps, c_sweeps, max_coarse, precision ("fp64" or
-    "mixed"), gmres_restart, maxiter, tol, keep_setup_data, ...).
+    "mixed"), gmres_restart, maxiter, tol, keep_setup_data, adjoint_mode
+    ("transposed" or "rebuild"), ...).
     """
 
     def __init__(self, row_ptr, col, vals, **params):
@@ -170,6 +174,8 @@ class NairSolver:
         for k, v in params.items():
             if k == "precision" and isinstance(v, str):
                 v = {"fp64": FP64, "mixed": MIXED}[v]
+            if k == "adjoint_mode" and isinstance(v, str):
+                v = {"transposed": ADJOINT_TRANSPOSED, "rebuild": ADJOINT_REBUILD}[v]
             if not hasattr(p, k):
                 raise TypeError(f"unknown parameter {k}")
             setattr(p, k, v)
@@ -219,7 +225,8 @@ class NairSolver:
         return x, self._report(info, hist, st)
 
     def adjoint_solve(self, w, lam=None, check=True):
-        """Solve A^T lambda = w; builds the A^T hierarchy on first use."""
+        """Solve A^T lambda = w; the first call forms the transposed operators
+        (adjoint_mode "transposed") or the A^T hierarchy ("rebuild")."""
         lam = torch.zeros_like(w) if lam is None else lam
         info, hist = self._info(self.params.maxiter + self.params.maxiter // max(1, self.params.gmres_restart) + 4)
         st = lib().nair_adjoint_solve(self._h, _ptr(w), _ptr(lam), ctypes.byref(info))
@@ -230,6 +237,12 @@ class NairSolver:
     def vcycle(self, f):
         x = torch.empty_like(f)
         _check(lib().nair_vcycle(self._h, _ptr(f), _ptr(x)), "nair_vcycle")
+        return x
+
+    def adjoint_vcycle(self, f):
+        """The transposed cycle of the forward hierarchy: M^{-T} f."""
+        x = torch.empty_like(f)
+        _check(lib().nair_adjoint_vcycle(self._h, _ptr(f), _ptr(x)), "nair_adjoint_vcycle")
         return x
 
     def num_levels(self, adjoint=False):
@@ -331,7 +344,8 @@ def gradients(mass, lam, x):
 class NairSolve(torch.autograd.Function):
     """x = A(sigma)^{-1} M q for the DG transport operator, with A(sigma)'s
     diagonal blocks A0_ee + sigma_e M_e.  Backward solves A^T lambda = dJ/dx
-    with nAIR on A^T and returns dJ/dq = M^T lambda, dJ/dsigma_e = -lambda_e^T M_e x_e.
+    (by default with the transposed cycle of the forward hierarchy) and
+    returns dJ/dq = M^T lambda, dJ/dsigma_e = -lambda_e^T M_e x_e.
     """
 
     @staticmethod

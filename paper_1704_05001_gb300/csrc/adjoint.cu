@@ -1,0 +1,197 @@
+// Adjoint operators on the GPU: block transposes of block-CSR matrices and the
+// transposed form of a finished hierarchy.  For A^T the transfer operators of
+// the forward hierarchy swap roles (Sec. 2, Corollary on ideal interpolation):
+// R^T = [R_cf^T; I] interpolates -- R_cf^T approximates the ideal
+// interpolation -(A^T)_ff^{-1} (A^T)_fc of A^T -- and P^T = [W^T I] restricts,
+// with coarse operators K^T.  An F solve must then come before the coarse-grid
+// correction (Remark on pre-F-relaxation), so the block-Jacobi sweeps move in
+// front of it.  The result, the transpose of the V-cycle, preconditions A^T
+// without a second setup.
+#include <algorithm>
+
+#include "hier.cuh"
+
+namespace nair {
+
+static constexpr int kThreads = 256;
+static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
+
+// ---------------------------------------------------------------------------
+// block-CSR transpose: counts per column, scan, scatter, per-row sort
+// ---------------------------------------------------------------------------
+__global__ void k_t_count(int nnzb, const int *__restrict__ ci, int *__restrict__ cnt) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nnzb) atomicAdd(&cnt[ci[p]], 1);
+}
+
+__global__ void k_t_fill(int nr, const int *__restrict__ rp, const int *__restrict__ ci,
+                         const int *__restrict__ trp, int *__restrict__ fill, int *__restrict__ tci,
+                         int *__restrict__ tsrc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    const int j = ci[p];
+    const int q = trp[j] + atomicAdd(&fill[j], 1);
+    tci[q] = i;
+    tsrc[q] = p;
+  }
+}
+
+// sort each row by column, carrying a companion index when given (insertion
+// sort: the rows of a transposed DG operator are short)
+__global__ void k_sort_rows(int n, const int *__restrict__ rp, int *__restrict__ ci, int *__restrict__ comp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = rp[i] + 1; a < rp[i + 1]; ++a) {
+    const int c = ci[a], s = comp ? comp[a] : 0;
+    int q = a - 1;
+    while (q >= rp[i] && ci[q] > c) {
+      ci[q + 1] = ci[q];
+      if (comp) comp[q + 1] = comp[q];
+      --q;
+    }
+    ci[q + 1] = c;
+    if (comp) comp[q + 1] = s;
+  }
+}
+
+// out block q = (in block tsrc[q])^T
+template <typename T>
+__global__ void k_t_vals(long long total, int b, const int *__restrict__ tsrc, const T *__restrict__ v,
+                         T *__restrict__ tv) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long q = g / bb;
+  const int rc = (int)(g - q * bb), r = rc / b, c = rc - r * b;
+  tv[g] = v[(size_t)tsrc[q] * bb + c * b + r];
+}
+
+// every b x b block transposed in place of position
+template <typename T>
+__global__ void k_block_transpose(long long total, int b, const T *__restrict__ in, T *__restrict__ out) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bb = b * b;
+  const long long q = g / bb;
+  const int rc = (int)(g - q * bb), r = rc / b, c = rc - r * b;
+  out[g] = in[(size_t)q * bb + c * b + r];
+}
+
+// C elements: own coarse index; F elements: -1
+__global__ void k_cself(int E, const signed char *__restrict__ cf, const int *__restrict__ ipc,
+                        int *__restrict__ cself) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < E) cself[i] = cf[i] ? ipc[i] : -1;
+}
+
+// P^T lists: F elements that interpolate from coarse point J
+__global__ void k_pt_count(int E, const signed char *__restrict__ cf, const int *__restrict__ ipc,
+                           int *__restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < E && !cf[i] && ipc[i] >= 0) atomicAdd(&cnt[ipc[i]], 1);
+}
+
+__global__ void k_pt_fill(int E, const signed char *__restrict__ cf, const int *__restrict__ ipc,
+                          const int *__restrict__ prp, int *__restrict__ fill, int *__restrict__ pci) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E || cf[i] || ipc[i] < 0) return;
+  const int J = ipc[i];
+  pci[prp[J] + atomicAdd(&fill[J], 1)] = i;
+}
+
+template <typename T>
+void bsr_transpose(const DBsr<T> &A, int b, DBsr<T> &out, cudaStream_t s, Mem &mem) {
+  const int nr = A.nrows, nc = A.ncols, nnzb = A.nnzb;
+  out.nrows = nc;
+  out.ncols = nr;
+  out.nnzb = nnzb;
+  out.rp = mem.alloc<int>(nc + 1);
+  out.ci = mem.alloc<int>(nnzb);
+  out.v = mem.alloc<T>((size_t)nnzb * b * b);
+  Mem tmp;
+  tmp.s = s;
+  int *cnt = tmp.alloc<int>(nc + 1), *fill = tmp.alloc<int>(nc + 1), *tsrc = tmp.alloc<int>(nnzb);
+  NAIR_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * (nc + 1), s));
+  NAIR_CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nc + 1), s));
+  if (nnzb) {
+    k_t_count<<<grid(nnzb), kThreads, 0, s>>>(nnzb, A.ci, cnt);
+    NAIR_LAUNCH_CHECK();
+  }
+  exclusive_scan(cnt, out.rp, nc, s, tmp, false);
+  if (nnzb) {
+    k_t_fill<<<grid(nr), kThreads, 0, s>>>(nr, A.rp, A.ci, out.rp, fill, out.ci, tsrc);
+    NAIR_LAUNCH_CHECK();
+    k_sort_rows<<<grid(nc), kThreads, 0, s>>>(nc, out.rp, out.ci, tsrc);
+    NAIR_LAUNCH_CHECK();
+    const long long tot = (long long)nnzb * b * b;
+    k_t_vals<T><<<grid(tot), kThreads, 0, s>>>(tot, b, tsrc, A.v, out.v);
+    NAIR_LAUNCH_CHECK();
+  }
+}
+template void bsr_transpose<double>(const DBsr<double> &, int, DBsr<double> &, cudaStream_t, Mem &);
+template void bsr_transpose<float>(const DBsr<float> &, int, DBsr<float> &, cudaStream_t, Mem &);
+
+template <typename T>
+void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem) {
+  ProfScope ps("transpose_hierarchy", s);
+  const int b = H.b;
+  H.tlev.assign(H.nlev, TLevel<T>());
+  Mem tmp;
+  tmp.s = s;
+  for (int l = 0; l < H.nlev; ++l) {
+    const Level<T> &L = H.lev[l];
+    TLevel<T> &TL = H.tlev[l];
+    const int E = L.E;
+    const long long tb = (long long)E * b * b;
+    TL.dinvT = mem.alloc<T>((size_t)tb);
+    k_block_transpose<T><<<grid(tb), kThreads, 0, s>>>(tb, b, L.dinv, TL.dinvT);
+    NAIR_LAUNCH_CHECK();
+    if (l == 0 || !L.coarsest) {
+      // A_l^T: level 0's is also the operator of the outer Krylov solve
+      bsr_transpose<T>(L.A, b, TL.At, s, mem);
+      TL.diag = mem.alloc<int>(E);
+      diag_positions(E, TL.At.rp, TL.At.ci, TL.diag, s);
+    }
+    if (L.coarsest) {
+      if (L.ainv) {
+        const long long nn = (long long)L.n * L.n;
+        TL.ainvT = mem.alloc<T>((size_t)nn);
+        k_block_transpose<T><<<grid(nn), kThreads, 0, s>>>(nn, L.n, L.ainv, TL.ainvT);
+        NAIR_LAUNCH_CHECK();
+      }
+      continue;
+    }
+    const int nC = L.nC, nF = L.nF;
+    TL.fsweep = sweep_list(nF, L.f2f, TL.At.rp, s, mem, tmp);
+    TL.csweep = sweep_list(nC, L.c2f, TL.At.rp, s, mem, tmp);
+    // R_cf (nC rows, element columns) -> R_cf^T (element rows, nC columns)
+    DBsr<T> R = L.R;
+    R.nrows = nC;
+    R.ncols = E;
+    bsr_transpose<T>(R, b, TL.Rt, s, mem);
+    TL.cself = mem.alloc<int>(E);
+    k_cself<<<grid(E), kThreads, 0, s>>>(E, L.cf, L.ipc, TL.cself);
+    NAIR_LAUNCH_CHECK();
+    // P^T: for each coarse point the F elements interpolating from it
+    int *cnt = tmp.alloc<int>(nC + 1), *fill = tmp.alloc<int>(nC + 1);
+    NAIR_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * (nC + 1), s));
+    NAIR_CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nC + 1), s));
+    k_pt_count<<<grid(E), kThreads, 0, s>>>(E, L.cf, L.ipc, cnt);
+    NAIR_LAUNCH_CHECK();
+    TL.pt_rp = mem.alloc<int>(nC + 1);
+    exclusive_scan(cnt, TL.pt_rp, nC, s, tmp, false);
+    TL.pt_ci = mem.alloc<int>(nF);  // at most one entry per F element
+    k_pt_fill<<<grid(E), kThreads, 0, s>>>(E, L.cf, L.ipc, TL.pt_rp, fill, TL.pt_ci);
+    NAIR_LAUNCH_CHECK();
+    k_sort_rows<<<grid(nC), kThreads, 0, s>>>(nC, TL.pt_rp, TL.pt_ci, nullptr);
+    NAIR_LAUNCH_CHECK();
+    TL.r = mem.alloc<T>((size_t)E * b);
+  }
+  if (!H.lev[0].coarsest) build_l0comp<T>(H.tlev[0].At, H.tlev[0].diag, b, s, mem, H.tl0c);
+  NAIR_CK(cudaStreamSynchronize(s));
+}
+template void build_transposed<double>(Hier<double> &, cudaStream_t, Mem &);
+template void build_transposed<float>(Hier<float> &, cudaStream_t, Mem &);
+
+}  // namespace nair

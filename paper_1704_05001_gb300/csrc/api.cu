@@ -31,8 +31,13 @@ struct nair_handle {
   Hier<float> h32;
   L0Comp<double> l0c64;  // level-0 compression of the FP64 matrix (mixed precision)
   Krylov K;
-  nair_handle *adj = nullptr;
+  nair_handle *adj = nullptr;  // NAIR_ADJOINT_REBUILD: the hierarchy of A^T
   double setup_ms = 0.0;
+  // transposed form of the forward hierarchy (adjoint solves)
+  bool tbuilt = false;
+  DBsr<double> At64;       // A^T in FP64, the operator of the adjoint Krylov solve
+  L0Comp<double> tl0c64;   // its level-0 compression (mixed precision)
+  double tsetup_ms = 0.0;
 };
 
 static nair_status set_error(nair_status st, const std::string &msg) {
@@ -89,50 +94,6 @@ template <typename A, typename B>
 __global__ void k_cast_api(long long n, const A *__restrict__ in, B *__restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (B)in[i];
-}
-
-__global__ void k_t_count(int nnzb, const int *__restrict__ ci, int *__restrict__ cnt) {
-  int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < nnzb) atomicAdd(&cnt[ci[p]], 1);
-}
-
-__global__ void k_t_fill(int E, const int *__restrict__ rp, const int *__restrict__ ci,
-                         const int *__restrict__ trp, int *__restrict__ fill, int *__restrict__ tci,
-                         int *__restrict__ tsrc) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= E) return;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    int j = ci[p];
-    int q = trp[j] + atomicAdd(&fill[j], 1);
-    tci[q] = i;
-    tsrc[q] = p;
-  }
-}
-
-// sort each transposed row by column (insertion sort: rows are short)
-__global__ void k_t_sort(int E, const int *__restrict__ trp, int *__restrict__ tci, int *__restrict__ tsrc) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= E) return;
-  for (int a = trp[i] + 1; a < trp[i + 1]; ++a) {
-    int c = tci[a], s = tsrc[a], q = a - 1;
-    while (q >= trp[i] && tci[q] > c) {
-      tci[q + 1] = tci[q];
-      tsrc[q + 1] = tsrc[q];
-      --q;
-    }
-    tci[q + 1] = c;
-    tsrc[q + 1] = s;
-  }
-}
-
-__global__ void k_t_vals(long long total, int b, const int *__restrict__ tsrc, const double *__restrict__ v,
-                         double *__restrict__ tv) {
-  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= total) return;
-  const int bb = b * b;
-  const long long q = g / bb;
-  const int rc = (int)(g - q * bb), r = rc / b, c = rc - r * b;
-  tv[g] = v[(size_t)tsrc[q] * bb + c * b + r];
 }
 
 __global__ void k_assemble_sigma(int E, int b, const int *__restrict__ dpos, const double *__restrict__ v0,
@@ -209,6 +170,8 @@ static void check_params(const nair_params *p, int b) {
   if (p->gmres_restart < 1 || p->gmres_restart > 1000) fail(NAIR_ERR_INVALID_ARG, "gmres_restart must lie in 1..1000");
   if (p->maxiter < 0) fail(NAIR_ERR_INVALID_ARG, "maxiter must be >= 0");
   if (!(p->tol >= 0.0)) fail(NAIR_ERR_INVALID_ARG, "tol must be >= 0");
+  if (p->adjoint_mode != NAIR_ADJOINT_TRANSPOSED && p->adjoint_mode != NAIR_ADJOINT_REBUILD)
+    fail(NAIR_ERR_INVALID_ARG, "unknown adjoint_mode");
 }
 
 static void setup_impl(nair_handle *h, const int *rp, const int *ci, const double *v, int E, int b,
@@ -293,6 +256,8 @@ void nair_default_params(nair_params *p) {
   p->stream = nullptr;
   p->keep_setup_data = 0;
   p->use_graphs = 1;
+  p->sweep_timing = 0;
+  p->adjoint_mode = NAIR_ADJOINT_TRANSPOSED;
 }
 
 const char *nair_last_error(void) { return g_last_error.c_str(); }
@@ -376,12 +341,12 @@ nair_status nair_setup(const nair_bsr *A, const nair_params *p, nair_handle **ou
 }
 
 static void fill_info(nair_handle *h, nair_info *info, int iters, double relres, double ms,
-                      const std::vector<double> &hist) {
+                      const std::vector<double> &hist, bool transposed) {
   if (!info) return;
   info->iterations = iters;
   info->rel_res = relres;
   info->solve_ms = ms;
-  info->setup_ms = h->setup_ms;
+  info->setup_ms = transposed ? h->tsetup_ms : h->setup_ms;
   if (h->mixed) {
     info->levels = h->h32.nlev;
     info->op_complexity = h->h32.op_complexity;
@@ -397,9 +362,8 @@ static void fill_info(nair_handle *h, nair_info *info, int iters, double relres,
     for (int k = 0; k < std::min(nh, info->history_cap); ++k) info->history[k] = hist[k];
 }
 
-nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *info) {
-  NAIR_API_BEGIN
-  if (!h || !b || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+// FGMRES on A (or on A^T with the transposed cycle)
+static nair_status solve_impl(nair_handle *h, const double *b, double *x, nair_info *info, bool transposed) {
   cudaEvent_t e0, e1;
   NAIR_CK(cudaEventCreate(&e0));
   NAIR_CK(cudaEventCreate(&e1));
@@ -407,19 +371,27 @@ nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *in
   std::vector<double> hist;
   int iters = 0;
   double relres = 0.0;
-  nair_status st = h->mixed ? fgmres<float>(h->A64, h->h32, h->P, h->K, b, x, hist, &iters, &relres, h->s, &h->l0c64)
-                            : fgmres<double>(h->A64, h->h64, h->P, h->K, b, x, hist, &iters, &relres, h->s, &h->h64.l0c);
+  const DBsr<double> &A = transposed ? h->At64 : h->A64;
+  const L0Comp<double> *C = h->mixed ? (transposed ? &h->tl0c64 : &h->l0c64) : (transposed ? &h->h64.tl0c : &h->h64.l0c);
+  nair_status st = h->mixed ? fgmres<float>(A, h->h32, h->P, h->K, b, x, hist, &iters, &relres, h->s, C, transposed)
+                            : fgmres<double>(A, h->h64, h->P, h->K, b, x, hist, &iters, &relres, h->s, C, transposed);
   NAIR_CK(cudaEventRecord(e1, h->s));
   NAIR_CK(cudaEventSynchronize(e1));
   float ms = 0.f;
   NAIR_CK(cudaEventElapsedTime(&ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  fill_info(h, info, iters, relres, ms, hist);
+  fill_info(h, info, iters, relres, ms, hist, transposed);
   if (st == NAIR_ERR_NOT_CONVERGED) return set_error(st, "GMRES did not reach the tolerance within maxiter");
   if (st == NAIR_ERR_BREAKDOWN) return set_error(st, "non-finite value in the Krylov iteration");
   if (st == NAIR_OK) g_last_error.clear();
   return st;
+}
+
+nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *info) {
+  NAIR_API_BEGIN
+  if (!h || !b || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  return solve_impl(h, b, x, info, false);
   NAIR_API_END
 }
 
@@ -433,6 +405,31 @@ nair_status nair_vcycle(nair_handle *h, const double *f, double *x) {
   NAIR_API_END
 }
 
+// the transposed form of the forward hierarchy, and A^T in FP64
+static void build_transposed_handle(nair_handle *h) {
+  cudaStream_t s = h->s;
+  cudaEvent_t e0, e1;
+  NAIR_CK(cudaEventCreate(&e0));
+  NAIR_CK(cudaEventCreate(&e1));
+  NAIR_CK(cudaEventRecord(e0, s));
+  if (h->mixed) {
+    build_transposed<float>(h->h32, s, h->mem);
+    bsr_transpose<double>(h->A64, h->b, h->At64, s, h->mem);
+    if (h->h32.tl0c.W > 0) build_l0comp<double>(h->At64, h->h32.tlev[0].diag, h->b, s, h->mem, h->tl0c64);
+  } else {
+    build_transposed<double>(h->h64, s, h->mem);
+    h->At64 = h->h64.tlev[0].At;
+  }
+  NAIR_CK(cudaEventRecord(e1, s));
+  NAIR_CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  NAIR_CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tsetup_ms = ms;
+  h->tbuilt = true;
+}
+
 static void build_adjoint(nair_handle *h) {
   cudaStream_t s = h->s;
   nair_handle *a = new nair_handle();
@@ -443,28 +440,7 @@ static void build_adjoint(nair_handle *h) {
   a->mem.s = s;
   try {
     const int E = h->E, b = h->b, nnzb = h->A64.nnzb;
-    const DBsr<double> &A = h->A64;
-    DBsr<double> &T = a->A64;
-    T.nrows = T.ncols = E;
-    T.nnzb = nnzb;
-    T.rp = a->mem.alloc<int>(E + 1);
-    T.ci = a->mem.alloc<int>(nnzb);
-    T.v = a->mem.alloc<double>((size_t)nnzb * b * b);
-    Mem tmp;
-    tmp.s = s;
-    int *cnt = tmp.alloc<int>(E + 1), *fill = tmp.alloc<int>(E + 1), *tsrc = tmp.alloc<int>(nnzb);
-    NAIR_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * (E + 1), s));
-    NAIR_CK(cudaMemsetAsync(fill, 0, sizeof(int) * (E + 1), s));
-    k_t_count<<<grid(nnzb), kThreads, 0, s>>>(nnzb, A.ci, cnt);
-    NAIR_LAUNCH_CHECK();
-    exclusive_scan(cnt, T.rp, E, s, tmp, false);
-    k_t_fill<<<grid(E), kThreads, 0, s>>>(E, A.rp, A.ci, T.rp, fill, T.ci, tsrc);
-    NAIR_LAUNCH_CHECK();
-    k_t_sort<<<grid(E), kThreads, 0, s>>>(E, T.rp, T.ci, tsrc);
-    NAIR_LAUNCH_CHECK();
-    long long tot = (long long)nnzb * b * b;
-    k_t_vals<<<grid(tot), kThreads, 0, s>>>(tot, b, tsrc, A.v, T.v);
-    NAIR_LAUNCH_CHECK();
+    bsr_transpose<double>(h->A64, b, a->A64, s, a->mem);
     setup_impl(a, nullptr, nullptr, nullptr, E, b, nnzb, true);
   } catch (...) {
     nair_free(a);
@@ -476,8 +452,23 @@ static void build_adjoint(nair_handle *h) {
 nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lam, nair_info *info) {
   NAIR_API_BEGIN
   if (!h || !w || !lam) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
-  if (!h->adj) build_adjoint(h);
-  return nair_solve(h->adj, w, lam, info);
+  if (h->raw.adjoint_mode == NAIR_ADJOINT_REBUILD) {
+    if (!h->adj) build_adjoint(h);
+    return nair_solve(h->adj, w, lam, info);
+  }
+  if (!h->tbuilt) build_transposed_handle(h);
+  return solve_impl(h, w, lam, info, true);
+  NAIR_API_END
+}
+
+nair_status nair_adjoint_vcycle(nair_handle *h, const double *f, double *x) {
+  NAIR_API_BEGIN
+  if (!h || !f || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (!h->tbuilt) build_transposed_handle(h);
+  if (h->mixed) precond<float>(h->h32, h->P, f, x, h->s, h->n, true);
+  else precond<double>(h->h64, h->P, f, x, h->s, h->n, true);
+  NAIR_CK(cudaStreamSynchronize(h->s));
+  return NAIR_OK;
   NAIR_API_END
 }
 
@@ -487,6 +478,8 @@ void nair_free(nair_handle *h) {
   cudaStreamSynchronize(h->s);
   release_graph(h->h64.graph);
   release_graph(h->h32.graph);
+  release_graph(h->h64.tgraph);
+  release_graph(h->h32.tgraph);
   release_clock(h->h64.clock);
   release_clock(h->h32.clock);
   h->K.mem.release_all();

@@ -77,6 +77,23 @@ struct SweepClock {
   std::vector<double> ms;
 };
 
+// One level of the transposed hierarchy, which preconditions A^T with the
+// transpose of the V-cycle: R^T = [R_cf^T; I] interpolates, P^T = [W^T I]
+// restricts, and the block-Jacobi sweeps on A_l^T (C sweeps, then F sweeps)
+// come before the coarse-grid correction.  Built from a finished level.
+template <typename T>
+struct TLevel {
+  DBsr<T> At;                  // A_l^T (rows sorted by column)
+  int *diag = nullptr;         // position of the diagonal block of each row of At
+  T *dinvT = nullptr;          // (D_ii^{-1})^T, the inverse diagonal blocks of A_l^T
+  int *fsweep = nullptr, *csweep = nullptr;  // F / C rows ordered by At row length
+  DBsr<T> Rt;                  // R_cf^T: E rows (blocks on F rows only), nC columns
+  int *cself = nullptr;        // element -> its coarse index (C) or -1 (F)
+  int *pt_rp = nullptr, *pt_ci = nullptr;  // P^T: coarse J -> F elements with ip = J, ascending
+  T *r = nullptr;              // residual after the pre-relaxation
+  T *ainvT = nullptr;          // coarsest level: (A_c^{-1})^T
+};
+
 template <typename T>
 struct Hier {
   int b = 0, nlev = 0;
@@ -86,6 +103,10 @@ struct Hier {
   L0Comp<T> l0c;
   double setup_ms = 0.0;
   double op_complexity = 0.0, cycle_complexity = 0.0;
+  // transposed form (empty until build_transposed)
+  std::vector<TLevel<T>> tlev;
+  L0Comp<T> tl0c;
+  mutable VGraph tgraph;
 };
 
 struct Params {
@@ -110,6 +131,24 @@ void vcycle(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s)
 // release the V-cycle graph of a hierarchy
 void release_graph(VGraph &g);
 void release_clock(SweepClock &c);
+
+// transposed cycle with zero initial guess on level 0: x = M^{-T} f
+template <typename T>
+void vcycle_t(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s);
+
+// the transposed form of a built hierarchy (adjoint solves without a second setup)
+template <typename T>
+void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem);
+
+// block transpose of a block-CSR matrix (each block transposed, rows sorted)
+template <typename T>
+void bsr_transpose(const DBsr<T> &A, int b, DBsr<T> &out, cudaStream_t s, Mem &mem);
+
+// rows of one class ordered by decreasing row length (sweep work list)
+int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem, Mem &tmp);
+
+// position of the diagonal block of every row
+void diag_positions(int E, const int *rp, const int *ci, int *out, cudaStream_t s);
 
 // diagonal-block inverses in FP64 of the blocks at positions pos[] (or 0..nblk-1)
 template <typename TI>

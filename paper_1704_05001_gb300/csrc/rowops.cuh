@@ -15,7 +15,9 @@
 
 namespace nair {
 
-enum RowOp { OP_SPMV = 0, OP_RESID = 1, OP_JACOBI = 2, OP_RESTRICT = 3 };
+// OP_INTERP_T: out_i = f_i + sum_j v_ij x_j + (c2f[i] >= 0 ? x[c2f[i]] : 0), the
+// interpolation x_fine += R^T x_c of the transposed cycle (c2f: own coarse index)
+enum RowOp { OP_SPMV = 0, OP_RESID = 1, OP_JACOBI = 2, OP_RESTRICT = 3, OP_INTERP_T = 4 };
 
 template <typename T>
 struct RowArgs {
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
     }
   }
   if (OP == OP_JACOBI && active && g == 0) ii = a.ipc ? a.ipc[i] : i;
-  if (OP == OP_RESTRICT && active && g == 0) ii = a.c2f[i];
+  if ((OP == OP_RESTRICT || OP == OP_INTERP_T) && active && g == 0) ii = a.c2f[i];
   // ---- wait for the producer of x and f
   pdl_wait();
   if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
@@ -184,6 +186,12 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
     if (active && g == 0) a.out[(size_t)i * b + r] = a.f[(size_t)i * b + r] - acc;
   } else if (OP == OP_RESTRICT) {
     if (active && g == 0) a.out[(size_t)i * b + r] = a.f[(size_t)ii * b + r] + acc;
+  } else if (OP == OP_INTERP_T) {
+    if (active && g == 0) {
+      T v = a.f[(size_t)i * b + r] + acc;
+      if (ii >= 0) v += a.x[(size_t)ii * b + r];
+      a.out[(size_t)i * b + r] = v;
+    }
   } else {  // OP_JACOBI
     if (active && g == 0) sres[(size_t)team * b + r] = a.f[(size_t)i * b + r] - acc;
     __syncthreads();

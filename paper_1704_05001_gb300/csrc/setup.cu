@@ -93,10 +93,152 @@ __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__
   }
 }
 
+// The same Gauss-Jordan inverse with one block per segment of SEG lanes (SEG the
+// power of two >= B) and row r of the block in the registers of lane r, for
+// the DG block sizes.  Every FP64 instruction occupies the scarce FP64 pipe
+// whatever the number of active lanes, so everything that is not arithmetic
+// on values runs on the integer pipe or through shuffles:
+//   - the pivot search compares |x| as integers: for IEEE doubles with the sign
+//     cleared, the bit patterns order like the values; a NaN below the
+//     diagonal ranks lowest (a comparison with it is false), a NaN on the
+//     diagonal highest (nothing compares greater than it);
+//   - rows are exchanged logically: each lane tracks the index of the row it
+//     holds, so a swap moves two integers, not two rows;
+//   - the pivot row is scaled once, one element per lane, through shared memory.
+// The values computed (reciprocal, products, fma chains, column order) are
+// those of k_block_inverse, so both give identical bits.
+template <int B>
+struct SegShape {
+  static constexpr int SEG = B <= 4 ? 4 : B <= 8 ? 8 : B <= 16 ? 16 : 32;
+  static constexpr int NSEG = kThreads / SEG;  // blocks per CTA
+  static constexpr int LD = B | 1;
+  // shared memory per segment: staging (B x LD doubles), scaled pivot row (B
+  // doubles), pivot rows (B ints) and the column order (2 B ints), rounded up
+  // to 16 bytes so that every segment's doubles stay aligned
+  static constexpr size_t BYTES = (sizeof(double) * (B * LD + B) + sizeof(int) * 3 * B + 15) / 16 * 16;
+};
+
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+template <int B, typename TI>
+__global__ void __launch_bounds__(kThreads) k_block_inverse_seg(int nblk, const TI *__restrict__ A,
+                                                                const int *__restrict__ pos,
+                                                                double *__restrict__ out, int *__restrict__ err) {
+  using S = SegShape<B>;
+  constexpr int SEG = S::SEG, LD = S::LD;
+  extern __shared__ double smb[];
+  const int seg = threadIdx.x / SEG, r = threadIdx.x % SEG;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned segmask = (SEG == 32) ? 0xffffffffu : (((1u << SEG) - 1u) << (lane & ~(unsigned)(SEG - 1)));
+  unsigned char *base = reinterpret_cast<unsigned char *>(smb) + (size_t)seg * S::BYTES;
+  double *stage = reinterpret_cast<double *>(base);
+  double *prow = stage + B * LD;
+  int *pk = reinterpret_cast<int *>(prow + B);
+  int *content = pk + B, *inv = content + B;
+  const long long blk = (long long)blockIdx.x * S::NSEG + seg;
+  const bool have = blk < nblk;
+  const bool active = have && r < B;
+  // coalesced load of the block into the staging area, then row r to registers
+  if (have) {
+    const TI *src = A + (size_t)(pos ? pos[blk] : blk) * B * B;
+    for (int e = r; e < B * B; e += SEG) stage[(e / B) * LD + e % B] = (double)src[e];
+  }
+  __syncwarp();
+  double M[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) M[c] = active ? stage[r * LD + c] : 0.0;
+  int li = r;  // index of the row this lane holds
+  bool sing = false;
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    // pivot: first row (in the current order) of largest |M[.][k]| among rows >= k
+    const unsigned long long a = abs_key(M[k]);
+    const bool nan = a > 0x7FF0000000000000ull;
+    unsigned long long key = (!active || li < k) ? 0ull : nan ? (li == k ? ~0ull : 1ull) : a + 1ull;
+    int bli = li;
+#pragma unroll
+    for (int o = SEG / 2; o; o >>= 1) {
+      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o, SEG);
+      const int l2 = __shfl_xor_sync(0xffffffffu, bli, o, SEG);
+      if (k2 > key || (k2 == key && l2 < bli)) { key = k2; bli = l2; }
+    }
+    const int p = bli;
+    if (r == 0) pk[k] = p;
+    if (li == p) li = k;
+    else if (li == k) li = p;
+    const bool piv = active && li == k;
+    const unsigned pmask = __ballot_sync(0xffffffffu, piv) & segmask;
+    const int plane = pmask ? __ffs(pmask) - 1 : (int)(lane & ~(unsigned)(SEG - 1));
+    const double d = __shfl_sync(0xffffffffu, M[k], plane);
+    const unsigned long long dk = abs_key(d);
+    if (active && (dk == 0ull || dk > 0x7FF0000000000000ull)) sing = true;
+    const double rinv = __drcp_rn(d);
+    if (piv) {
+#pragma unroll
+      for (int c = 0; c < B; ++c) prow[c] = M[c];
+    }
+    __syncwarp();
+    if (r < B && have) prow[r] = __dmul_rn(r == k ? 1.0 : prow[r], rinv);
+    __syncwarp();
+    const double l = M[k];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const double pc = prow[c];
+      const double nv = __fma_rn(-l, pc, c == k ? 0.0 : M[c]);
+      M[c] = piv ? pc : nv;
+    }
+    __syncwarp();
+  }
+  // column order after undoing the row exchanges in reverse (Gauss-Jordan unscramble)
+  if (r == 0 && have) {
+    for (int c = 0; c < B; ++c) content[c] = c;
+    for (int k = B - 1; k >= 0; --k) {
+      const int p = pk[k];
+      const int t = content[k];
+      content[k] = content[p];
+      content[p] = t;
+    }
+    for (int c = 0; c < B; ++c) inv[content[c]] = c;
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < B; ++c) stage[li * LD + inv[c]] = M[c];
+  }
+  __syncwarp();
+  if (have) {
+    double *dst = out + (size_t)blk * B * B;
+    for (int e = r; e < B * B; e += SEG) dst[e] = stage[(e / B) * LD + e % B];
+  }
+  const bool any = __any_sync(0xffffffffu, sing);
+  if (any && r == 0 && have) atomicOr(err, 1);
+}
+
+template <int B, typename TI>
+static void launch_inverse_seg(int nblk, const TI *A, const int *pos, double *out, int *err, cudaStream_t s) {
+  using S = SegShape<B>;
+  const size_t smem = (size_t)S::NSEG * S::BYTES;
+  if (smem > 48 * 1024)
+    NAIR_CK(cudaFuncSetAttribute(k_block_inverse_seg<B, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_block_inverse_seg<B, TI><<<cdiv(nblk, S::NSEG), kThreads, smem, s>>>(nblk, A, pos, out, err);
+  NAIR_LAUNCH_CHECK();
+}
+
 template <typename TI>
 void block_inverses(int nblk, int b, const TI *A, const int *pos, double *out, int *err,
                     cudaStream_t s) {
   if (nblk <= 0) return;
+  switch (b) {
+    case 3: launch_inverse_seg<3, TI>(nblk, A, pos, out, err, s); return;
+    case 6: launch_inverse_seg<6, TI>(nblk, A, pos, out, err, s); return;
+    case 10: launch_inverse_seg<10, TI>(nblk, A, pos, out, err, s); return;
+    case 15: launch_inverse_seg<15, TI>(nblk, A, pos, out, err, s); return;
+    case 21: launch_inverse_seg<21, TI>(nblk, A, pos, out, err, s); return;
+    case 28: launch_inverse_seg<28, TI>(nblk, A, pos, out, err, s); return;
+    default: break;
+  }
   int bpc = std::max(1, kThreads / b);
   size_t smem = (size_t)bpc * b * (b | 1) * sizeof(double) + (size_t)bpc * 32 * sizeof(int);
   if (smem > 48 * 1024) {
@@ -1108,7 +1250,7 @@ static void check_flag(int *flag, cudaStream_t s, nair_status st, const char *ms
   if (v) fail(st, msg);
 }
 
-static int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem, Mem &tmp) {
+int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem, Mem &tmp) {
   int *out = mem.alloc<int>(n);
   int *counts = tmp.alloc<int>(kLenBuckets);
   NAIR_CK(cudaMemsetAsync(counts, 0, sizeof(int) * kLenBuckets, s));
@@ -1349,6 +1491,11 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   tmp.release_all();
   H.lev.push_back(nx);
   return true;
+}
+
+void diag_positions(int E, const int *rp, const int *ci, int *out, cudaStream_t s) {
+  k_diag_pos<<<grid(E), kThreads, 0, s>>>(E, rp, ci, out);
+  NAIR_LAUNCH_CHECK();
 }
 
 template <typename T>

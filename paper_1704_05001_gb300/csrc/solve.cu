@@ -223,6 +223,169 @@ template void vcycle<double>(const Hier<double> &, const Params &, const double 
 template void vcycle<float>(const Hier<float> &, const Params &, const float *, float *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// transposed cycle (preconditioner of A^T): from a zero iterate, C sweeps then
+// F sweeps of block Jacobi on A_l^T, the residual, restriction with P^T,
+// recursion on K^T, interpolation with R^T = [R_cf^T; I]
+// ---------------------------------------------------------------------------
+
+// first sweep from a zero iterate: rows of `list` get (D_ii^{-1})^T f_i, rows
+// of `zlist` are zeroed in out and out2
+template <typename T>
+__global__ void k_first_sweep_t(int nrows, int b, const int *__restrict__ list, const T *__restrict__ dinvT,
+                                const T *__restrict__ f, int nzero, const int *__restrict__ zlist,
+                                T *__restrict__ out, T *__restrict__ out2) {
+  pdl_launch_dependents();
+  pdl_wait();
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long na = (long long)nrows * b;
+  if (g < na) {
+    const int k = (int)(g / b), r = (int)(g - (long long)k * b);
+    const int i = list[k];
+    const T *d = dinvT + (size_t)i * b * b + r * b;
+    const T *fi = f + (size_t)i * b;
+    T acc = 0;
+    for (int c = 0; c < b; ++c) acc = fma(d[c], fi[c], acc);
+    out[(size_t)i * b + r] = acc;
+    return;
+  }
+  g -= na;
+  if (g < (long long)nzero * b) {
+    const int k = (int)(g / b), r = (int)(g - (long long)k * b);
+    const size_t o = (size_t)zlist[k] * b + r;
+    out[o] = (T)0;
+    if (out2) out2[o] = (T)0;
+  }
+}
+
+// P^T restriction: f_c[J] = r[c2f[J]] + the sum of r over the F elements with ip = J
+template <typename T>
+__global__ void k_restrict_pt(int nC, int b, const int *__restrict__ c2f, const int *__restrict__ prp,
+                              const int *__restrict__ pci, const T *__restrict__ r, T *__restrict__ fc) {
+  pdl_launch_dependents();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = g < (long long)nC * b;
+  const int J = in ? (int)(g / b) : 0, c = in ? (int)(g - (long long)J * b) : 0;
+  const int self = in ? c2f[J] : 0, q0 = in ? prp[J] : 0, q1 = in ? prp[J + 1] : 0;
+  pdl_wait();
+  if (!in) return;
+  T acc = r[(size_t)self * b + c];
+  for (int q = q0; q < q1; ++q) acc += r[(size_t)pci[q] * b + c];
+  fc[g] = acc;
+}
+
+template <typename T>
+static void l0_args(RowArgs<T> &a, const TLevel<T> &TL, const L0Comp<T> &C) {
+  a.diag = TL.diag;
+  a.oci = C.oci;
+  a.ocols = C.ocols;
+  a.ov = C.ov;
+}
+
+template <typename T>
+static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out, cudaStream_t s) {
+  const Level<T> &L = H.lev[l];
+  const TLevel<T> &TL = H.tlev[l];
+  const int b = H.b;
+  if (L.coarsest) {
+    ProfScope ps("coarse_solve_t", s, l);
+    if (TL.ainvT) {
+      launch_pdl(k_dense_mv<T>, dim3(cdiv((long long)L.n * 32, kThreads)), dim3(kThreads), 0, s, L.n,
+                 (const T *)TL.ainvT, f, out);
+    } else {
+      launch_pdl(k_bdiag_apply<T>, dim3(grid((long long)L.E * b)), dim3(kThreads), 0, s, L.E, b,
+                 (const T *)TL.dinvT, f, out);
+    }
+    NAIR_LAUNCH_CHECK();
+    return;
+  }
+  const Level<T> &N = H.lev[l + 1];
+  const int S = P.c_sweeps + P.f_sweeps;
+  const bool comp = l == 0 && H.tl0c.W > 0;
+  const double avg = (double)TL.At.nnzb / L.E;
+  const T *r = f;  // residual after the pre-relaxation (f itself without one)
+  if (S == 0) {
+    NAIR_CK(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)L.E * b, s));
+  } else {
+    // the sweeps alternate between two buffers and end in out
+    T *buf[2] = {(S % 2 == 1) ? out : L.x2, (S % 2 == 1) ? L.x2 : out};
+    const int nrow[2] = {L.nF, L.nC};
+    const int *rows[2] = {TL.fsweep, TL.csweep};
+    int cur_ver[2] = {0, 0};  // version of each class (0 = the zero start)
+    int buf_ver[2][2] = {{-1, -1}, {-1, -1}};
+    for (int k = 0; k < S; ++k) {
+      const int cls = k < P.c_sweeps ? 1 : 0, oth = 1 - cls, ob = k % 2;
+      ProfScope ps(cls == 0 ? "jacobi_tF" : "jacobi_tC", s, l);
+      if (k == 0) {
+        const long long tot = (long long)(nrow[cls] + nrow[oth]) * b;
+        launch_pdl(k_first_sweep_t<T>, dim3(grid(tot)), dim3(kThreads), 0, s, nrow[cls], b, rows[cls],
+                   (const T *)TL.dinvT, f, nrow[oth], rows[oth], buf[0], buf[1]);
+        NAIR_LAUNCH_CHECK();
+        cur_ver[cls] = 1;
+        buf_ver[0][cls] = 1;
+        buf_ver[0][oth] = buf_ver[1][oth] = 0;
+        continue;
+      }
+      RowArgs<T> a = row_args(TL.At, b);
+      a.x = buf[1 - ob];
+      a.f = f;
+      a.dinv = TL.dinvT;
+      a.nrows = nrow[cls];
+      a.list = rows[cls];
+      a.out = buf[ob];
+      if (buf_ver[ob][oth] != cur_ver[oth]) {
+        a.ncopy = nrow[oth];
+        a.copy_list = rows[oth];
+      }
+      if (comp) {
+        l0_args(a, TL, H.tl0c);
+        launch_rowop_l0<T, OP_JACOBI>(a, H.tl0c.W, s);
+      } else {
+        launch_rowop<T, OP_JACOBI>(a, avg, s);
+      }
+      cur_ver[cls] = k + 1;
+      buf_ver[ob][cls] = k + 1;
+      if (a.ncopy) buf_ver[ob][oth] = cur_ver[oth];
+    }
+    ProfScope ps("resid_t", s, l);
+    RowArgs<T> a = row_args(TL.At, b);
+    a.x = out;
+    a.f = f;
+    a.out = TL.r;
+    if (comp) {
+      l0_args(a, TL, H.tl0c);
+      launch_rowop_l0<T, OP_RESID>(a, H.tl0c.W, s);
+    } else {
+      launch_rowop<T, OP_RESID>(a, avg, s);
+    }
+    r = TL.r;
+  }
+  {
+    ProfScope ps("restrict_t", s, l);
+    launch_pdl(k_restrict_pt<T>, dim3(grid((long long)L.nC * b)), dim3(kThreads), 0, s, L.nC, b,
+               (const int *)L.c2f, (const int *)TL.pt_rp, (const int *)TL.pt_ci, r, N.f);
+    NAIR_LAUNCH_CHECK();
+  }
+  vcyc_t<T>(H, P, l + 1, N.f, N.x, s);
+  {  // x += R^T x_c: F rows through R_cf^T, C rows take their own coarse value
+    ProfScope ps("interp_t", s, l);
+    RowArgs<T> a = row_args(TL.Rt, b);
+    a.x = N.x;
+    a.f = out;
+    a.c2f = TL.cself;
+    a.out = out;
+    launch_rowop<T, OP_INTERP_T>(a, (double)TL.Rt.nnzb / L.E, s);
+  }
+}
+
+template <typename T>
+void vcycle_t(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s) {
+  if ((int)H.tlev.size() != H.nlev) fail(NAIR_ERR_INVALID_ARG, "transposed hierarchy not built");
+  vcyc_t<T>(H, P, 0, f, x, s);
+}
+template void vcycle_t<double>(const Hier<double> &, const Params &, const double *, double *, cudaStream_t);
+template void vcycle_t<float>(const Hier<float> &, const Params &, const float *, float *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // FP64 Krylov kernels
 // ---------------------------------------------------------------------------
 
@@ -451,8 +614,8 @@ void release_graph(VGraph &g) {
 // capture: copy the input into level 0's right-hand side, V-cycle on fixed
 // buffers, copy level 0's solution out (FP64 <-> T casts in mixed precision)
 template <typename T>
-static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
-  VGraph &g = H.graph;
+static void capture_graph(const Hier<T> &H, const Params &P, long long n, bool transposed) {
+  VGraph &g = transposed ? H.tgraph : H.graph;
   NAIR_CK(cudaMalloc(&g.dptr, 2 * sizeof(void *)));
   NAIR_CK(cudaMallocHost(&g.hptr, 2 * sizeof(void *)));
   const long long before = launch_count();
@@ -468,10 +631,11 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
   NAIR_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   try {
     T *f0 = H.lev[0].f, *x0 = H.lev[0].x;
-    if (H.clock.dev) clock_reset(H.clock, s);
+    if (H.clock.dev && !transposed) clock_reset(H.clock, s);
     k_copy_in<T><<<grid(n), kThreads, 0, s>>>(n, g.dptr, f0);
     NAIR_LAUNCH_CHECK();
-    vcycle<T>(H, P, f0, x0, s);
+    if (transposed) vcycle_t<T>(H, P, f0, x0, s);
+    else vcycle<T>(H, P, f0, x0, s);
     launch_pdl(k_copy_out<T>, dim3(grid(n)), dim3(kThreads), 0, s, n, (const T *)x0, (void *const *)g.dptr);
     NAIR_LAUNCH_CHECK();
   } catch (...) {
@@ -488,11 +652,11 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n) {
 
 template <typename T>
 void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s,
-             long long n) {
-  clock_init(H, P);
+             long long n, bool transposed) {
+  if (!transposed) clock_init(H, P);
   if (P.use_graphs && !prof_on()) {
-    VGraph &g = H.graph;
-    if (!g.exec) capture_graph<T>(H, P, n);
+    VGraph &g = transposed ? H.tgraph : H.graph;
+    if (!g.exec) capture_graph<T>(H, P, n, transposed);
     g.hptr[0] = const_cast<double *>(v);
     g.hptr[1] = z;
     NAIR_CK(cudaMemcpyAsync(g.dptr, g.hptr, 2 * sizeof(void *), cudaMemcpyHostToDevice, s));
@@ -500,20 +664,24 @@ void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cuda
     add_launches(g.nodes);
     return;
   }
-  if (H.clock.dev) clock_reset(H.clock, s);
+  if (H.clock.dev && !transposed) clock_reset(H.clock, s);
   if constexpr (std::is_same<T, double>::value) {
-    vcycle<double>(H, P, v, z, s);
+    if (transposed) vcycle_t<double>(H, P, v, z, s);
+    else vcycle<double>(H, P, v, z, s);
   } else {
     T *f0 = H.lev[0].f, *x0 = H.lev[0].x;
     k_cast<double, T><<<grid(n), kThreads, 0, s>>>(n, v, f0);
     NAIR_LAUNCH_CHECK();
-    vcycle<T>(H, P, f0, x0, s);
+    if (transposed) vcycle_t<T>(H, P, f0, x0, s);
+    else vcycle<T>(H, P, f0, x0, s);
     k_cast<T, double><<<grid(n), kThreads, 0, s>>>(n, x0, z);
     NAIR_LAUNCH_CHECK();
   }
 }
-template void precond<double>(const Hier<double> &, const Params &, const double *, double *, cudaStream_t, long long);
-template void precond<float>(const Hier<float> &, const Params &, const double *, double *, cudaStream_t, long long);
+template void precond<double>(const Hier<double> &, const Params &, const double *, double *, cudaStream_t, long long,
+                              bool);
+template void precond<float>(const Hier<float> &, const Params &, const double *, double *, cudaStream_t, long long,
+                             bool);
 
 // a10: y = A x, or y = b - A x when b is given (FP64, level 0)
 void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s,
@@ -540,8 +708,9 @@ void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, d
 template <typename T>
 nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
                    const double *bvec, double *x, std::vector<double> &hist, int *iters,
-                   double *relres, cudaStream_t s, const L0Comp<double> *C) {
-  const int *diag0 = H.lev[0].diag;
+                   double *relres, cudaStream_t s, const L0Comp<double> *C, bool transposed) {
+  // transposed: A is A^T and the preconditioner the transposed cycle
+  const int *diag0 = transposed ? H.tlev[0].diag : H.lev[0].diag;
   const int b = H.b, m = P.restart;
   const long long n = (long long)A.nrows * b;
   K.ensure(n, m, s);
@@ -583,7 +752,7 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
       double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
       {
         ProfScope ps("vcycle", s);
-        precond<T>(H, P, vj, zj, s, n);
+        precond<T>(H, P, vj, zj, s, n, transposed);
       }
       ++it;
       spmv64(A, b, zj, nullptr, w, s, C, diag0);
@@ -606,7 +775,7 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
         NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
       }
       NAIR_CK(cudaStreamSynchronize(s));
-      clock_collect(H, P, s);
+      if (!transposed) clock_collect(H, P, s);
       for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hh[k] + hh[m + 1 + k];
       const double hn = std::sqrt(hh[2 * (m + 1)]);
       if (!std::isfinite(hn)) return NAIR_ERR_BREAKDOWN;
@@ -659,9 +828,9 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
 
 template nair_status fgmres<double>(const DBsr<double> &, const Hier<double> &, const Params &, Krylov &,
                                     const double *, double *, std::vector<double> &, int *, double *,
-                                    cudaStream_t, const L0Comp<double> *);
+                                    cudaStream_t, const L0Comp<double> *, bool);
 template nair_status fgmres<float>(const DBsr<double> &, const Hier<float> &, const Params &, Krylov &,
                                    const double *, double *, std::vector<double> &, int *, double *,
-                                   cudaStream_t, const L0Comp<double> *);
+                                   cudaStream_t, const L0Comp<double> *, bool);
 
 }  // namespace nair

@@ -24,11 +24,12 @@ void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, d
             const L0Comp<double> *C = nullptr, const int *diag = nullptr);
 
 template <typename T>
-void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s, long long n);
+void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s, long long n,
+             bool transposed = false);
 
 template <typename T>
 nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
                    const double *bvec, double *x, std::vector<double> &hist, int *iters,
-                   double *relres, cudaStream_t s, const L0Comp<double> *C);
+                   double *relres, cudaStream_t s, const L0Comp<double> *C, bool transposed = false);
 
 }  // namespace nair

@@ -5,9 +5,10 @@ and the residual history against the FP64 oracle run to completion.
 C3 (917,504 unknowns, b = 28): hierarchy against the oracle, mixed precision
 against FP64.  C5 (5,242,880 unknowns): too large for the oracle in a test, so
 it is checked by properties that hold at any size: the FP64 residual of the
-returned solution recomputed independently on the host (scipy BSR product), and
-the mixed-precision forward and adjoint solutions and gradients against the
-all-FP64 GPU solve.
+returned forward and adjoint solutions recomputed independently on the host
+(scipy BSR products), and the mixed-precision forward and adjoint solutions and
+gradients against the all-FP64 GPU solve.  The adjoint solves use the
+transposed cycle of the forward hierarchy (C2: against the oracle's).
 """
 import numpy as np
 import pytest
@@ -39,10 +40,13 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def host_residual(P, x):
+def host_residual(P, x, w=None):
+    """||rhs - A x|| / ||rhs||, or ||w - A^T x|| / ||w|| when w is given."""
     sp = pytest.importorskip("scipy.sparse")
     b = P["b"]
     A = sp.bsr_matrix((P["vals"], P["col"], P["row_ptr"]), shape=(P["n"], P["n"]), blocksize=(b, b))
+    if w is not None:
+        return np.linalg.norm(w - A.T @ x) / np.linalg.norm(w)
     r = P["rhs"] - A @ x
     return np.linalg.norm(r) / np.linalg.norm(P["rhs"])
 
@@ -74,6 +78,13 @@ def test_c2_full_hierarchy_and_history(nair, oracle_mod):
     xs = x.cpu().numpy()
     assert host_residual(P, xs) <= 1e-10
     assert np.linalg.norm(xs - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    # C4: the adjoint through the transposed cycle of the same hierarchy
+    w = D.functional_weights(P["n"])
+    lam, repa = S.adjoint_solve(dev(w))
+    refa = H.solve(w, transposed=True)
+    assert repa["iterations"] == refa["iterations"]
+    assert np.max(np.abs(repa["history"] - refa["history"])) <= 1e-12
+    assert host_residual(P, lam.cpu().numpy(), w) <= 1e-10
 
 
 def test_c3_full_hierarchy_and_mixed(nair, oracle_mod):
@@ -105,6 +116,7 @@ def test_c5_full_forward_adjoint_mixed_vs_fp64(nair):
         lam, repa = S.adjoint_solve(w)
         gs, gq = nair.gradients(dev(P["mass"]), lam, x)
         assert rep["rel_res"] <= 1e-10 and repa["rel_res"] <= 1e-10
+        assert host_residual(P, lam.cpu().numpy(), w.cpu().numpy()) <= 1e-10
         out[prec] = (x.cpu().numpy(), gs.cpu().numpy(), gq.cpu().numpy())
         S.close()
     x64, gs64, gq64 = out["fp64"]

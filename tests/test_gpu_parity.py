@@ -79,7 +79,7 @@ def compare_hierarchies(S, H, b, check_setup_data=True):
             assert rel_rows(g["L_v"], o["L_v"]) <= 1e-12, f"level {l} L values"
 
 
-@pytest.mark.parametrize("b", [1, 3, 6, 10, 28, 32])
+@pytest.mark.parametrize("b", [1, 3, 6, 10, 15, 21, 28, 32])
 def test_block_inverse_bitwise(nair, oracle_mod, b):
     r = np.random.default_rng(100 + b)
     nblk = 333
@@ -89,8 +89,30 @@ def test_block_inverse_bitwise(nair, oracle_mod, b):
         assert np.array_equal(X[k], oracle_mod.block_inverse(A[k]))
 
 
-def test_block_inverse_singular(nair):
-    A = np.ones((4, 3, 3))
+@pytest.mark.parametrize("b", [3, 6, 10, 15, 21, 28])
+def test_block_inverse_pivot_ties_bitwise(nair, oracle_mod, b):
+    """Small-integer blocks: equal |entries| in a pivot column are common, zero
+    diagonals force row exchanges, and -0.0 meets +0.0; the first row of largest
+    magnitude must win exactly as in the oracle."""
+    r = np.random.default_rng(200 + b)
+    blocks = []
+    while len(blocks) < 200:
+        A = r.integers(-2, 3, size=(b, b)).astype(np.float64)
+        A[r.random((b, b)) < 0.2] = -0.0
+        try:
+            X = oracle_mod.block_inverse(A)
+        except oracle_mod.OracleError:
+            continue
+        blocks.append((A, X))
+    A = np.stack([a for a, _ in blocks])
+    X = nair.block_inverse(dev(A)).cpu().numpy()
+    for k, (_, Xo) in enumerate(blocks):
+        assert np.array_equal(X[k].view(np.uint64), Xo.view(np.uint64))
+
+
+@pytest.mark.parametrize("b", [3, 6, 28, 32])
+def test_block_inverse_singular(nair, b):
+    A = np.ones((40, b, b))
     with pytest.raises(nair.NairError) as e:
         nair.block_inverse(dev(A))
     assert e.value.status == 2
@@ -221,10 +243,12 @@ def test_zero_rhs_and_maxiter(nair):
 
 
 def test_adjoint_parity_and_gradients(nair, oracle_mod):
+    """Adjoint by a second hierarchy built for A^T (adjoint_mode "rebuild")."""
     P = D.make_problem("C2", N=12, keep_parts=True)
     b, E, n = P["b"], P["E"], P["n"]
     params = dict(neumann_degree=2, max_coarse=4)
-    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), keep_setup_data=1, **params)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), keep_setup_data=1,
+                        adjoint_mode="rebuild", **params)
     w = D.functional_weights(n)
     lam, rep = S.adjoint_solve(dev(w))
     trp, tci, tv = oracle_mod.transpose(P["row_ptr"], P["col"], P["vals"])
@@ -240,6 +264,70 @@ def test_adjoint_parity_and_gradients(nair, oracle_mod):
     ogs, ogq = oracle_mod.gradients(P["mass"], lam.cpu().numpy(), x.cpu().numpy())
     assert np.allclose(gs.cpu().numpy(), ogs, rtol=1e-12, atol=1e-15 * np.abs(ogs).max())
     assert np.allclose(gq.cpu().numpy(), ogq, rtol=1e-12, atol=1e-15 * np.abs(ogq).max())
+
+
+@pytest.mark.parametrize("name,N,p,k", CASES)
+@pytest.mark.parametrize("fs,cs,graphs", [(0, 1, 1), (3, 0, 1), (1, 2, 0), (0, 1, 0)])
+def test_transposed_cycle_parity(nair, oracle_mod, name, N, p, k, fs, cs, graphs):
+    """The transposed cycle of the forward hierarchy (R^T interpolation, P^T
+    restriction, C then F pre-sweeps on A^T) against the oracle's, on a seeded
+    vector; fs = 0 means k + 1 F sweeps.  Graph replay and direct launches."""
+    P = D.make_problem(name, N=N, p=p)
+    params = dict(neumann_degree=k, max_coarse=4, c_sweeps=cs)
+    if fs:
+        params["f_sweeps"] = fs
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), use_graphs=graphs, **params)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params)
+    f = D.rng.uniform(11, P["n"]) - 0.5
+    for rep in range(2):  # the second call replays what the first built
+        z = S.adjoint_vcycle(dev(f)).cpu().numpy()
+        zr = H.vcycle(f, transposed=True)
+        assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    # the forward cycle is unchanged by the transposed form living beside it
+    zf = S.vcycle(dev(f)).cpu().numpy()
+    assert np.linalg.norm(zf - H.vcycle(f)) <= 1e-12 * np.linalg.norm(zf)
+    S.close()
+
+
+@pytest.mark.parametrize("name,N,p,k", CASES)
+def test_transposed_adjoint_solve_parity(nair, oracle_mod, name, N, p, k):
+    """FGMRES on A^T preconditioned by the transposed cycle: same iteration
+    count and residual history (1e-12) as the oracle, and the solution."""
+    P = D.make_problem(name, N=N, p=p)
+    params = dict(neumann_degree=k, max_coarse=4)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), **params)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params)
+    w = D.functional_weights(P["n"])
+    lam, rep = S.adjoint_solve(dev(w))
+    ref = H.solve(w, transposed=True)
+    assert ref["status"] == 0
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    assert rep["rel_res"] <= 1e-10
+    ls = lam.cpu().numpy()
+    assert np.linalg.norm(ls - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    # a second adjoint solve reuses the transposed form
+    lam2, rep2 = S.adjoint_solve(dev(w))
+    assert rep2["iterations"] == rep["iterations"]
+    assert float((lam2 - lam).abs().max()) <= 1e-13 * float(lam.abs().max())
+    S.close()
+
+
+def test_transposed_adjoint_gradients_match_rebuild(nair):
+    """Both adjoint modes solve the same A^T lambda = w: gradients agree."""
+    P = D.make_problem("C2", N=12, keep_parts=True)
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    w = dev(D.functional_weights(P["n"]))
+    out = {}
+    for mode in ("transposed", "rebuild"):
+        S = nair.NairSolver(*args, neumann_degree=2, max_coarse=4, tol=1e-13, adjoint_mode=mode)
+        x, _ = S.solve(dev(P["rhs"]))
+        lam, rep = S.adjoint_solve(w)
+        assert rep["rel_res"] <= 1e-12
+        out[mode] = nair.gradients(dev(P["mass"]), lam, x)
+        S.close()
+    for a, b in zip(out["transposed"], out["rebuild"]):
+        assert float((a - b).norm() / b.norm()) <= 1e-10
 
 
 def test_autograd_against_finite_differences(nair):
@@ -290,3 +378,9 @@ def test_mixed_precision_accuracy(nair, name, N, p, k):
     assert r64["rel_res"] <= 1e-10 and r32["rel_res"] <= 1e-10
     err = float((x32 - x64).norm() / x64.norm())
     assert err <= 1e-8, err
+    # the transposed cycle in FP32 inside FP64 FGMRES on A^T
+    w = dev(D.functional_weights(P["n"]))
+    l64, a64 = S64.adjoint_solve(w)
+    l32, a32 = S32.adjoint_solve(w)
+    assert a64["rel_res"] <= 1e-10 and a32["rel_res"] <= 1e-10
+    assert float((l32 - l64).norm() / l64.norm()) <= 1e-8
