@@ -4,11 +4,11 @@
 //
 // A team of G x b threads owns one block row: thread (g, r) accumulates output
 // component r over the row's blocks p = start + g, start + g + G, ...; the G
-// partial sums are then added in fixed order g = 0..G-1.  b is a template
+// partial sums are then added by a fixed pairwise tree.  b is a template
 // parameter for the common DG block sizes so that the b loads of a block row
 // and of x_j are issued back to back (no exposed latency per scalar), with a
 // runtime-b fallback.  G > 1 is used on coarse levels, whose rows are long and
-// few, to shorten the serial chain per thread.
+// few, to shorten the serial chain per thread and to fill the GPU.
 #pragma once
 
 #include "common.cuh"
@@ -173,12 +173,15 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
   if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
   T acc = 0;
   if (active) acc = row_partial<T, B>(a, p0, p1, r, j0, va0);
-  if (a.G > 1) {
-    if (team < a.tpc) red[(size_t)team * tsz + lt] = acc;
+  if (a.G > 1) {  // pairwise tree over the G partial sums (G is a power of two)
+    T *tr = red + (size_t)team * tsz;
+    if (team < a.tpc) tr[lt] = acc;
     __syncthreads();
-    if (g == 0 && active) {
-      for (int gg = 1; gg < a.G; ++gg) acc += red[(size_t)team * tsz + gg * b + r];
+    for (int h = a.G / 2; h > 0; h >>= 1) {
+      if (team < a.tpc && g < h) tr[lt] += tr[lt + h * b];
+      __syncthreads();
     }
+    if (g == 0 && active) acc = tr[r];
   }
   if (OP == OP_SPMV) {
     if (active && g == 0) a.out[(size_t)i * b + r] = acc;

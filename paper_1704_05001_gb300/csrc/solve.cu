@@ -62,14 +62,29 @@ __global__ void k_bdiag_apply(int E, int b, const T *__restrict__ dinv, const T 
   x[g] = acc;
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    NAIR_CK(cudaGetDevice(&dev));
+    NAIR_CK(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return n;
+}
+
 template <typename T, int OP>
 void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   const int b = a.b;
   // threads per row: enough block groups that each thread handles about two
-  // blocks of a long (coarse-level) row, keeping the serial chain short
+  // blocks of a long (coarse-level) row, keeping the serial chain short; on
+  // small levels more, until the rows fill about one wave of the GPU (those
+  // sweeps are bound by each thread's chain of dependent loads, not by
+  // throughput), up to about one group per block of an average row
   int G = 1;
   if (avg > 4.0)
     while (G * 2 <= avg / 2 && G * 2 * b <= 256 && G < 32) G *= 2;
+  const long long wave = (long long)sm_count() * 1536;
+  while (G < 32 && G * 2 * b <= 256 && G * 2 <= 2 * avg && (long long)a.nrows * b * G * 2 <= wave) G *= 2;
   a.G = G;
   const int tsz = G * b;
   a.tpc = std::max(1, 256 / tsz);
