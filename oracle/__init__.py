@@ -56,6 +56,7 @@ def _load():
                                       ctypes.POINTER(I), ctypes.POINTER(D)]
             lib.orc_vcycle.argtypes = [P, P, P, I, I]
             lib.orc_vcycle_t.argtypes = [P, P, P, I, I]
+            lib.orc_set_cycle.argtypes = [P, I]
             lib.orc_solve_t.argtypes = lib.orc_solve.argtypes
             lib.orc_block_inverse.argtypes = [I, P, P]
             lib.orc_transpose.argtypes = [I, I, P, P, P, P, P, P]
@@ -77,7 +78,7 @@ class use_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("orc_setup", "orc_free", "orc_num_levels", "orc_level_sizes", "orc_level_get",
-                     "orc_solve", "orc_vcycle", "orc_solve_t", "orc_vcycle_t", "orc_block_inverse", "orc_transpose", "orc_gradients"):
+                     "orc_solve", "orc_vcycle", "orc_solve_t", "orc_vcycle_t", "orc_set_cycle", "orc_block_inverse", "orc_transpose", "orc_gradients"):
             getattr(lib, name).argtypes = getattr(self._saved, name).argtypes
             getattr(lib, name).restype = getattr(self._saved, name).restype
         _lib = lib
@@ -101,7 +102,7 @@ class OracleError(RuntimeError):
 
 DEFAULTS = dict(theta=0.1, filter_tol=1e-4, filter_targets=3, neumann_degree=1, max_levels=25,
                 max_coarse=None, max_dense=4096, seed=0, f_sweeps=None, c_sweeps=1,
-                restart=50, maxiter=500, tol=1e-10)
+                restart=50, maxiter=500, tol=1e-10, cycle="V")
 
 
 def default_max_coarse(b):
@@ -134,6 +135,14 @@ class Hierarchy:
         if not self._h:
             raise OracleError(st.value, "setup")
         self.nlev = lib.orc_num_levels(self._h)
+        self.set_cycle(p["cycle"])
+
+    def set_cycle(self, cycle):
+        """Preconditioner cycle of the forward solve: "V" or "F"."""
+        st = _load().orc_set_cycle(self._h, {"V": 0, "F": 1}[cycle])
+        if st:
+            raise OracleError(st, "set_cycle")
+        self.params["cycle"] = cycle
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -200,8 +209,8 @@ class Hierarchy:
                     relres=rr.value)
 
     def vcycle(self, f, f_sweeps=None, c_sweeps=None, transposed=False):
-        """One cycle with zero initial guess: the V-cycle M^{-1} f, or its
-        transpose M^{-T} f (transposed=True)."""
+        """One cycle with zero initial guess: M^{-1} f with the hierarchy's cycle
+        (V or F), or the transposed V-cycle M^{-T} f (transposed=True)."""
         p = self.params
         f = np.ascontiguousarray(f, dtype=np.float64)
         x = np.zeros_like(f)

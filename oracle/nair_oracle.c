@@ -14,6 +14,7 @@
  *   - block nAIR and filtering, Sec. 5.2;
  *   - V-cycle with no pre-relaxation, F-relaxation with one more sweep than
  *     the Neumann degree, then a C sweep (Sec. 5, Remark on C-relaxation);
+ *     optionally the F-cycle of the scaling study (Sec. 6);
  *   - GMRES acceleration (Sec. 6), as flexible GMRES(m) with CGS2;
  *   - for A^T: the transposed cycle of the same hierarchy (R^T interpolates,
  *     P^T restricts, pre-relaxation; Corollary on ideal interpolation).
@@ -68,6 +69,7 @@ typedef struct {
   Level lev[MAXLEV];
   int f_sweeps, c_sweeps;
   int transposed; /* solve with A^T and the transposed cycle (adjoint) */
+  int cycle_type; /* 0: V-cycle, 1: F-cycle (forward preconditioner) */
 } Hier;
 
 static void bsr_free(Bsr *m) {
@@ -716,10 +718,14 @@ static void jacobi(int b, const Level *L, int which, const double *f, double *x,
   }
 }
 
-/* V-cycle with zero initial guess and no pre-relaxation (Sec. 5): restrict the
- * right-hand side with R = [R_cf I], recurse, interpolate with P, then
- * f_sweeps F-Jacobi sweeps and c_sweeps C-Jacobi sweeps. */
-static void vcycle(const Hier *H, int l, const double *f, double *x) {
+/* One cycle on level l for A_l x = f, with no pre-relaxation (Sec. 5):
+ * restrict the residual with R = [R_cf I] (the right-hand side itself when x
+ * enters as zero), solve the coarse problem approximately, add P x_c, then
+ * f_sweeps F-Jacobi sweeps and c_sweeps C-Jacobi sweeps.  The coarse problem
+ * gets one V-cycle from zero (type 0, V-cycle), or one F-cycle from zero
+ * followed by one V-cycle from its result (type 1, F-cycle; Sec. 6 scaling
+ * study).  The coarsest level is solved exactly. */
+static void cycle(const Hier *H, int l, int type, const double *f, double *x, int zero) {
   int b = H->b;
   size_t bb = (size_t)b * b;
   const Level *L = &H->lev[l];
@@ -731,36 +737,54 @@ static void vcycle(const Hier *H, int l, const double *f, double *x) {
   }
   int nC = L->nC;
   double *fc = (double *)malloc(sizeof(double) * (size_t)nC * b + 8);
-  double *xc = (double *)malloc(sizeof(double) * (size_t)nC * b + 8);
+  double *xc = (double *)calloc((size_t)nC * b + 8, sizeof(double));
   double *tmp = (double *)malloc(sizeof(double) * n + 8);
+  double *r = (double *)malloc(sizeof(double) * n + 8);
+  if (zero) {
+    memcpy(r, f, sizeof(double) * n);
+  } else {
+    spmv(b, &L->A, x, r);
+    for (size_t k = 0; k < n; ++k) r[k] = f[k] - r[k];
+  }
   for (int c = 0; c < nC; ++c) {
     int i = L->c2f[c];
-    for (int r = 0; r < b; ++r) {
-      double s = f[(size_t)i * b + r];
+    for (int rr = 0; rr < b; ++rr) {
+      double s = r[(size_t)i * b + rr];
       for (int p = L->Rcf.rp[c]; p < L->Rcf.rp[c + 1]; ++p) {
-        const double *rv = L->Rcf.v + (size_t)p * bb + r * b;
-        const double *ff = f + (size_t)L->f2f[L->Rcf.ci[p]] * b;
+        const double *rv = L->Rcf.v + (size_t)p * bb + rr * b;
+        const double *ff = r + (size_t)L->f2f[L->Rcf.ci[p]] * b;
         for (int t = 0; t < b; ++t) s += rv[t] * ff[t];
       }
-      fc[(size_t)c * b + r] = s;
+      fc[(size_t)c * b + rr] = s;
     }
   }
-  vcycle(H, l + 1, fc, xc);
+  cycle(H, l + 1, type, fc, xc, 1);
+  if (type == 1) cycle(H, l + 1, 0, fc, xc, 0);
   for (int i = 0; i < L->A.nrows; ++i)
-    for (int r = 0; r < b; ++r)
-      x[(size_t)i * b + r] = L->ipc[i] >= 0 ? xc[(size_t)L->ipc[i] * b + r] : 0.0;
+    for (int rr = 0; rr < b; ++rr) {
+      double v = L->ipc[i] >= 0 ? xc[(size_t)L->ipc[i] * b + rr] : 0.0;
+      x[(size_t)i * b + rr] = zero ? v : x[(size_t)i * b + rr] + v;
+    }
   for (int s = 0; s < H->f_sweeps; ++s) jacobi(b, L, 0, f, x, tmp);
   for (int s = 0; s < H->c_sweeps; ++s) jacobi(b, L, 1, f, x, tmp);
   free(fc);
   free(xc);
   free(tmp);
+  free(r);
 }
 
 int orc_vcycle(void *h, const double *f, double *x, int f_sweeps, int c_sweeps) {
   Hier *H = (Hier *)h;
   H->f_sweeps = f_sweeps;
   H->c_sweeps = c_sweeps;
-  vcycle(H, 0, f, x);
+  cycle(H, 0, H->cycle_type, f, x, 1);
+  return ORC_OK;
+}
+
+/* cycle of the preconditioner: 0 = V-cycle, 1 = F-cycle */
+int orc_set_cycle(void *h, int type) {
+  if (type != 0 && type != 1) return ORC_ERR_INVALID_ARG;
+  ((Hier *)h)->cycle_type = type;
   return ORC_OK;
 }
 
@@ -888,7 +912,7 @@ static void op_apply(const Hier *H, const double *x, double *y) {
 
 static void precond_apply(const Hier *H, const double *v, double *z) {
   if (H->transposed) vcycle_t(H, 0, v, z);
-  else vcycle(H, 0, v, z);
+  else cycle(H, 0, H->cycle_type, v, z, 1);
 }
 
 static double dot(size_t n, const double *a, const double *b) {

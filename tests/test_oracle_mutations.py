@@ -49,6 +49,15 @@ MUTATIONS = [
      "    if (J < 0 || !L->cf[i]) continue;\n    for (int r = 0; r < b; ++r) rc"),
     ("transposed coarse solve: K^-1 instead of K^-T", "dense_lu_solve_t(L->n, L->lu, L->piv, x);",
      "dense_lu_solve(L->n, L->lu, L->piv, x);"),
+    ("F-cycle: V-cycle correction skipped", "if (type == 1) cycle(H, l + 1, 0, fc, xc, 0);", ";"),
+    ("F-cycle: V-cycle correction from zero", "if (type == 1) cycle(H, l + 1, 0, fc, xc, 0);",
+     "if (type == 1) cycle(H, l + 1, 0, fc, xc, 1);"),
+    ("F-cycle: V-cycles below the first coarse level", "cycle(H, l + 1, type, fc, xc, 1);",
+     "cycle(H, l + 1, 0, fc, xc, 1);"),
+    ("nonzero guess: residual not formed", "for (size_t k = 0; k < n; ++k) r[k] = f[k] - r[k];",
+     "for (size_t k = 0; k < n; ++k) r[k] = f[k];"),
+    ("nonzero guess: interpolation replaces x",
+     "x[(size_t)i * b + rr] = zero ? v : x[(size_t)i * b + rr] + v;", "x[(size_t)i * b + rr] = v;"),
 ]
 
 PINS = [
@@ -67,6 +76,8 @@ PINS = [
     lambda o: pins.test_fgmres_matches_dense_solve(o, "C2", 8, 2),
     lambda o: pins.test_transposed_cycle_is_adjoint_of_vcycle(o, "C2", 4, 2, 2, 2, 1),
     lambda o: pins.test_transposed_cycle_exact_under_ideal_interpolation(o, 1),
+    lambda o: pins.test_cycles_match_composed_error_propagation(o, "V", "C2", 4, 2, 2, 3, 1),
+    lambda o: pins.test_cycles_match_composed_error_propagation(o, "F", "C2", 4, 2, 2, 3, 1),
 ]
 
 
