@@ -262,9 +262,9 @@ def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps
             return xx, rep
         return f
 
-    def fwd_adj(prec):
+    def fwd_adj(prec, mode="transposed"):
         def f():
-            S = nair.NairSolver(rp, ci, v, **dict(params, precision=prec))
+            S = nair.NairSolver(rp, ci, v, **dict(params, precision=prec, adjoint_mode=mode))
             xx, rep = S.solve(bvec)
             lam, repa = S.adjoint_solve(w)
             S.close()
@@ -278,13 +278,32 @@ def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps
                                  "setup_ms": rep["setup_ms"], "solve_ms": rep["solve_ms"],
                                  "iterations": rep["iterations"], "rel_res": rep["rel_res"],
                                  "rel_diff_vs_fp64": float((xx - xref).norm() / xref.norm())}
+    # the F-cycle and Neumann degree 3 of the scaling study (Sec. 6)
+    for label, extra in (("forward_vcycle_k3_fp64", dict(neumann_degree=3)),
+                         ("forward_fcycle_k3_fp64", dict(neumann_degree=3, cycle_type="F")),
+                         ("forward_fcycle_k3_mixed", dict(neumann_degree=3, cycle_type="F", precision="mixed"))):
+        def fk(extra=extra):
+            S = nair.NairSolver(rp, ci, v, **dict(params, **extra))
+            xx, rep = S.solve(bvec)
+            S.close()
+            return xx, rep
+        fk()
+        ms, (xx, rep) = timed_steps(fk, steps, flush, stream)
+        res[label] = {"ms_per_step": ms, "mdof_s": n / (ms * 1e-3) / 1e6, "setup_ms": rep["setup_ms"],
+                      "solve_ms": rep["solve_ms"], "iterations": rep["iterations"], "rel_res": rep["rel_res"],
+                      "cycle_complexity": rep["cycle_complexity"], "op_complexity": rep["op_complexity"],
+                      "rel_diff_vs_fp64": float((xx - xref).norm() / xref.norm())}
     lam_ref = None
-    for prec in ("fp64", "mixed"):
-        fwd_adj(prec)()
-        ms, (xx, lam, rep, repa) = timed_steps(fwd_adj(prec), steps, flush, stream)
+    # the adjoint through the transposed forward hierarchy (default), and by a
+    # second hierarchy built on A^T
+    for prec, mode, label in (("fp64", "transposed", "forward_adjoint_fp64"),
+                              ("mixed", "transposed", "forward_adjoint_mixed"),
+                              ("fp64", "rebuild", "forward_adjoint_rebuild_fp64")):
+        fwd_adj(prec, mode)()
+        ms, (xx, lam, rep, repa) = timed_steps(fwd_adj(prec, mode), steps, flush, stream)
         if lam_ref is None:
             lam_ref = lam.clone()
-        res[f"forward_adjoint_{prec}"] = {
+        res[label] = {
             "ms_per_step": ms, "adjoint_setup_ms": repa["setup_ms"], "adjoint_solve_ms": repa["solve_ms"],
             "adjoint_iterations": repa["iterations"], "adjoint_rel_res": repa["rel_res"],
             "lambda_rel_diff_vs_fp64": float((lam - lam_ref).norm() / lam_ref.norm())}

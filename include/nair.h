@@ -56,6 +56,13 @@ typedef enum { NAIR_FP64 = 0, NAIR_MIXED = 1 } nair_precision;
  *     parameters (its levels are exported with adjoint = 1). */
 typedef enum { NAIR_ADJOINT_TRANSPOSED = 0, NAIR_ADJOINT_REBUILD = 1 } nair_adjoint_mode;
 
+/* Cycle of the forward preconditioner (Sec. 5; the F-cycle of the scaling
+ * study of Sec. 6).  Both have no pre-relaxation and the same post-relaxation.
+ *   NAIR_CYCLE_V: the coarse problem gets one V-cycle from zero.
+ *   NAIR_CYCLE_F: the coarse problem gets one F-cycle from zero, then one
+ *     V-cycle from that result (which restricts the coarse residual). */
+typedef enum { NAIR_CYCLE_V = 0, NAIR_CYCLE_F = 1 } nair_cycle;
+
 /* A block-CSR matrix in device memory (caller-owned, read-only during a call). */
 typedef struct {
   int32_t nb_rows;        /* number of block rows = number of elements E */
@@ -87,6 +94,8 @@ typedef struct {
   int32_t use_graphs;     /* replay the V-cycle as a CUDA graph; 1 */
   int32_t sweep_timing;   /* stamp every block-Jacobi sweep with the device clock; 0 */
   int32_t adjoint_mode;   /* nair_adjoint_mode; NAIR_ADJOINT_TRANSPOSED */
+  int32_t cycle_type;     /* nair_cycle of nair_solve and nair_vcycle; NAIR_CYCLE_V.  The
+                             transposed adjoint always uses the transposed V-cycle. */
 } nair_params;
 
 /* Solve report.  history is an optional host buffer owned by the caller. */
@@ -133,7 +142,8 @@ nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *in
  * doubles; lambda holds the initial guess on entry.  Errors as nair_solve. */
 nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lambda, nair_info *info);
 
-/* Apply one V-cycle to f with zero initial guess: x = M^{-1} f (device, n doubles). */
+/* Apply one cycle (cycle_type) to f with zero initial guess: x = M^{-1} f
+ * (device, n doubles). */
 nair_status nair_vcycle(nair_handle *h, const double *f, double *x);
 
 /* Apply the transposed cycle of the forward hierarchy to f with zero initial

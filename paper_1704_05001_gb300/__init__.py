@@ -20,6 +20,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "SINGULAR_BLOCK", 3: "NOT_CONVERGED", 4:
           5: "OOM", 6: "CUDA", 7: "UNSUPPORTED"}
 FP64, MIXED = 0, 1
 ADJOINT_TRANSPOSED, ADJOINT_REBUILD = 0, 1
+CYCLE_V, CYCLE_F = 0, 1
 
 # nair_level_array
 (A_ROWPTR, A_COL, A_VALS, DINV, CF, P_MAP, DELTA_ROWPTR, DELTA_COL, DELTA_VALS, R_ROWPTR, R_COL,
@@ -46,7 +47,8 @@ class _Params(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("gmres_restart", ctypes.c_int32),
                 ("maxiter", ctypes.c_int32), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("keep_setup_data", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
-                ("sweep_timing", ctypes.c_int32), ("adjoint_mode", ctypes.c_int32)]
+                ("sweep_timing", ctypes.c_int32), ("adjoint_mode", ctypes.c_int32),
+                ("cycle_type", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -165,7 +167,7 @@ class NairSolver:
     Keyword arguments set fields of nair_params (strength_theta, filter_tol,
     neumann_degree, f_sweeps, c_sweeps, max_coarse, precision ("fp64" or
     "mixed"), gmres_restart, maxiter, tol, keep_setup_data, adjoint_mode
-    ("transposed" or "rebuild"), ...).
+    ("transposed" or "rebuild"), cycle_type ("V" or "F"), ...).
     """
 
     def __init__(self, row_ptr, col, vals, **params):
@@ -176,6 +178,8 @@ class NairSolver:
                 v = {"fp64": FP64, "mixed": MIXED}[v]
             if k == "adjoint_mode" and isinstance(v, str):
                 v = {"transposed": ADJOINT_TRANSPOSED, "rebuild": ADJOINT_REBUILD}[v]
+            if k == "cycle_type" and isinstance(v, str):
+                v = {"V": CYCLE_V, "F": CYCLE_F}[v]
             if not hasattr(p, k):
                 raise TypeError(f"unknown parameter {k}")
             setattr(p, k, v)

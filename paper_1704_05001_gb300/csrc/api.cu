@@ -83,6 +83,7 @@ Params resolve_params(const nair_params *p, int b) {
   P.keep = p->keep_setup_data;
   P.use_graphs = p->use_graphs;
   P.sweep_timing = p->sweep_timing;
+  P.cycle = p->cycle_type;
   return P;
 }
 }  // namespace nair
@@ -172,6 +173,7 @@ static void check_params(const nair_params *p, int b) {
   if (!(p->tol >= 0.0)) fail(NAIR_ERR_INVALID_ARG, "tol must be >= 0");
   if (p->adjoint_mode != NAIR_ADJOINT_TRANSPOSED && p->adjoint_mode != NAIR_ADJOINT_REBUILD)
     fail(NAIR_ERR_INVALID_ARG, "unknown adjoint_mode");
+  if (p->cycle_type != NAIR_CYCLE_V && p->cycle_type != NAIR_CYCLE_F) fail(NAIR_ERR_INVALID_ARG, "unknown cycle_type");
 }
 
 static void setup_impl(nair_handle *h, const int *rp, const int *ci, const double *v, int E, int b,
@@ -258,6 +260,7 @@ void nair_default_params(nair_params *p) {
   p->use_graphs = 1;
   p->sweep_timing = 0;
   p->adjoint_mode = NAIR_ADJOINT_TRANSPOSED;
+  p->cycle_type = NAIR_CYCLE_V;
 }
 
 const char *nair_last_error(void) { return g_last_error.c_str(); }

@@ -37,8 +37,8 @@ struct Level {
   // coarsest level: dense inverse
   int n = 0;
   T *ainv = nullptr;
-  // V-cycle vectors
-  T *f = nullptr, *x = nullptr, *x2 = nullptr;
+  // cycle vectors: right-hand side, iterate, second sweep buffer, residual
+  T *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr;
 };
 
 // Level-0 off-diagonal blocks restricted to their nonzero columns.  An upwind
@@ -116,6 +116,7 @@ struct Params {
   int precision, restart, maxiter;
   double tol;
   int keep, use_graphs, sweep_timing;
+  int cycle;  // 0: V-cycle, 1: F-cycle
 };
 
 Params resolve_params(const nair_params *p, int b);
@@ -124,7 +125,7 @@ Params resolve_params(const nair_params *p, int b);
 template <typename T>
 void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &mem, Hier<T> &H);
 
-// V-cycle with zero initial guess on level 0: x = M^{-1} f (device vectors of T)
+// one cycle (P.cycle) with zero initial guess on level 0: x = M^{-1} f (device vectors of T)
 template <typename T>
 void vcycle(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s);
 

@@ -1627,13 +1627,17 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     L.f = mem.alloc<T>(n);
     L.x = mem.alloc<T>(n);
     L.x2 = mem.alloc<T>(n);
+    L.r = mem.alloc<T>(n);
     double a = (double)L.A.nnzb / nnz0;
     oc += a;
+    // visits of level l per cycle: 1 in a V-cycle; 1 + l in an F-cycle (one
+    // F-type visit, and l V-type visits from a nonzero guess, each adding a residual)
+    const double visits = P.cycle == 1 ? 1.0 + l : 1.0, resid = P.cycle == 1 ? (double)l : 0.0;
     if (L.coarsest) {
-      cc += L.ainv ? (double)L.n * L.n / (nnz0 * b * b) : a;
+      cc += visits * (L.ainv ? (double)L.n * L.n / (nnz0 * b * b) : a);
     } else {
       // restriction + (f + c) sweeps over the selected rows, counted as full SpMVs
-      cc += a * (P.f_sweeps + P.c_sweeps) + (double)L.R.nnzb / nnz0;
+      cc += visits * (a * (P.f_sweeps + P.c_sweeps) + (double)L.R.nnzb / nnz0) + resid * a;
     }
   }
   H.op_complexity = oc;

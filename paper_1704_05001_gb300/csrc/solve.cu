@@ -142,11 +142,33 @@ static RowArgs<T> row_args(const DBsr<T> &A, int b) {
   return a;
 }
 
+// a12 from a nonzero iterate: dst = x + P x_c (dst may be x itself)
 template <typename T>
-static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, cudaStream_t s) {
+__global__ void k_prolong_add(int E, int b, const int *__restrict__ ipc, const T *__restrict__ xc, const T *x,
+                              T *dst) {
+  pdl_launch_dependents();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = g < (long long)E * b;
+  const int i = in ? (int)(g / b) : 0, r = in ? (int)(g - (long long)i * b) : 0;
+  const int J = in ? ipc[i] : -1;
+  pdl_wait();
+  if (!in) return;
+  dst[g] = x[g] + (J >= 0 ? xc[(size_t)J * b + r] : (T)0);
+}
+
+// One cycle on level l for A_l x = f (Sec. 5: no pre-relaxation).  zero: x
+// enters as zero, so the right-hand side itself is restricted and the first
+// sweep reads x = P x_c through the interpolation map; otherwise the residual
+// is restricted and x + P x_c is formed first.  The coarse problem gets a
+// V-cycle (type 0), or an F-cycle and then a V-cycle from its result (type 1).
+template <typename T>
+static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f, T *out, bool zero,
+                 cudaStream_t s) {
   const Level<T> &L = H.lev[l];
   const int b = H.b;
-  if (L.coarsest) {
+  const bool comp = l == 0 && H.l0c.W > 0;
+  const double avg = (double)L.A.nnzb / L.E;  // blocks per row (F and C rows have similar lengths)
+  if (L.coarsest) {  // exact: the initial guess does not matter
     ProfScope ps("coarse_solve", s, l);
     if (L.ainv) {
       launch_pdl(k_dense_mv<T>, dim3(cdiv((long long)L.n * 32, kThreads)), dim3(kThreads), 0, s, L.n,
@@ -159,39 +181,81 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
     return;
   }
   const Level<T> &N = H.lev[l + 1];
-  {  // a11: f_c = f_C + R_cf f_F
+  const T *rhs = f;
+  if (!zero) {  // residual of the incoming iterate
+    ProfScope ps("resid", s, l);
+    RowArgs<T> a = row_args(L.A, b);
+    a.x = out;
+    a.f = f;
+    a.out = L.r;
+    if (comp) {
+      a.diag = L.diag;
+      a.oci = H.l0c.oci;
+      a.ocols = H.l0c.ocols;
+      a.ov = H.l0c.ov;
+      launch_rowop_l0<T, OP_RESID>(a, H.l0c.W, s);
+    } else {
+      launch_rowop<T, OP_RESID>(a, avg, s);
+    }
+    rhs = L.r;
+  }
+  {  // a11: f_c = r_C + R_cf r_F
     ProfScope ps("restrict", s, l);
     RowArgs<T> a = row_args(L.R, b);
     a.nrows = L.nC;
-    a.x = f;
-    a.f = f;
+    a.x = rhs;
+    a.f = rhs;
     a.c2f = L.c2f;
     a.out = N.f;
     launch_rowop<T, OP_RESTRICT>(a, L.nC ? (double)L.R.nnzb / L.nC : 0.0, s);
   }
-  vcyc<T>(H, P, l + 1, N.f, N.x, s);
+  vcyc<T>(H, P, l + 1, type, N.f, N.x, true, s);
+  if (type == 1) vcyc<T>(H, P, l + 1, 0, N.f, N.x, false, s);
   const int S = P.f_sweeps + P.c_sweeps;
-  if (S == 0) {
-    k_prolong<T><<<grid((long long)L.E * b), kThreads, 0, s>>>(L.E, b, L.ipc, N.x, out);
-    NAIR_LAUNCH_CHECK();
-    return;
+  // a12-a14: x = P x_c (or x + P x_c), then F sweeps and C sweeps.  Each sweep
+  // updates one class (F or C) from a compact row list, so no warp mixes
+  // updated and idle rows; rows of the other class are copied into the output
+  // buffer only when that buffer holds an older version of them.  The sweeps
+  // alternate between two buffers and end in out.
+  T *buf[2];
+  int buf_ver[2][2] = {{-1, -1}, {-1, -1}};
+  const T *in;
+  const int *ipc0;
+  if (zero) {
+    if (S == 0) {
+      k_prolong<T><<<grid((long long)L.E * b), kThreads, 0, s>>>(L.E, b, L.ipc, N.x, out);
+      NAIR_LAUNCH_CHECK();
+      return;
+    }
+    buf[0] = (S % 2 == 1) ? out : L.x2;
+    buf[1] = (S % 2 == 1) ? L.x2 : out;
+    in = N.x;  // read through ipc by the first sweep
+    ipc0 = L.ipc;
+  } else {
+    T *start = (S % 2 == 1) ? L.x2 : out;
+    {
+      ProfScope ps("prolong_add", s, l);
+      launch_pdl(k_prolong_add<T>, dim3(grid((long long)L.E * b)), dim3(kThreads), 0, s, L.E, b,
+                 (const int *)L.ipc, (const T *)N.x, (const T *)out, start);
+      NAIR_LAUNCH_CHECK();
+    }
+    if (S == 0) return;
+    buf[0] = (start == out) ? L.x2 : out;
+    buf[1] = start;
+    buf_ver[1][0] = buf_ver[1][1] = 0;
+    in = start;
+    ipc0 = nullptr;
   }
-  // a12-a14: x = P x_c fused into the first sweep, then F sweeps and C sweeps.
-  // Each sweep updates one class (F or C) from a compact row list, so no warp
-  // mixes updated and idle rows; rows of the other class are copied into the
-  // output buffer only when that buffer holds an older version of them.
-  T *buf[2] = {(S % 2 == 1) ? out : L.x2, (S % 2 == 1) ? L.x2 : out};
   const int nrow[2] = {L.nF, L.nC};
   const int *rows[2] = {L.fsweep, L.csweep};
-  int cur_ver[2] = {0, 0};        // version of each class (0 = P x_c)
-  int buf_ver[2][2] = {{-1, -1}, {-1, -1}};
-  const T *in = N.x;
-  int in_buf = -1;
+  int cur_ver[2] = {0, 0};  // version of each class (0 = the sweeps' starting iterate)
+  // device-clock stamps only in V-cycles, where every sweep site runs once per cycle
+  const bool stamp = H.clock.dev && P.cycle == 0;
   for (int k = 0; k < S; ++k) {
     const int cls = k < P.f_sweeps ? 0 : 1, oth = 1 - cls, ob = k % 2;
     RowArgs<T> a = row_args(L.A, b);
     a.x = in;
-    a.ipc = (k == 0) ? L.ipc : nullptr;
+    a.ipc = (k == 0) ? ipc0 : nullptr;
     a.f = f;
     a.dinv = L.dinv;
     a.nrows = nrow[cls];
@@ -200,16 +264,14 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
     if (buf_ver[ob][oth] != cur_ver[oth]) {
       a.ncopy = nrow[oth];
       a.copy_list = rows[oth];
-      if (k == 0) a.out2 = buf[1 - ob];  // both buffers then hold P x_c on that class
+      if (k == 0 && zero) a.out2 = buf[1 - ob];  // both buffers then hold P x_c on that class
     }
-    if (H.clock.dev) {
+    if (stamp) {
       a.stamp = H.clock.dev + (size_t)l * S + k;
       a.ns = H.clock.nsites;
     }
-    // average blocks per updated row (F and C rows have similar lengths)
-    const double avg = (double)L.A.nnzb / L.E;
     ProfScope ps(cls == 0 ? "jacobi_F" : "jacobi_C", s, l);
-    if (l == 0 && H.l0c.W > 0) {
+    if (comp) {
       a.diag = L.diag;
       a.oci = H.l0c.oci;
       a.ocols = H.l0c.ocols;
@@ -225,14 +287,12 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, const T *f, T *out, c
       if (a.out2) buf_ver[1 - ob][oth] = cur_ver[oth];
     }
     in = buf[ob];
-    in_buf = ob;
   }
-  (void)in_buf;
 }
 
 template <typename T>
 void vcycle(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t s) {
-  vcyc<T>(H, P, 0, f, x, s);
+  vcyc<T>(H, P, 0, P.cycle, f, x, true, s);
 }
 template void vcycle<double>(const Hier<double> &, const Params &, const double *, double *, cudaStream_t);
 template void vcycle<float>(const Hier<float> &, const Params &, const float *, float *, cudaStream_t);

@@ -87,6 +87,19 @@ def test_c2_full_hierarchy_and_history(nair, oracle_mod):
     assert host_residual(P, lam.cpu().numpy(), w) <= 1e-10
 
 
+def test_c2_full_fcycle_k3(nair):
+    """The F-cycle with Neumann degree 3 (Sec. 6 scaling study) on the full C2
+    problem: FP64 residual recomputed on the host, in both precisions."""
+    P = D.make_problem("C2")
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    for prec in ("fp64", "mixed"):
+        S = nair.NairSolver(*args, neumann_degree=3, cycle_type="F", precision=prec)
+        x, rep = S.solve(dev(P["rhs"]))
+        assert rep["rel_res"] <= 1e-10
+        assert host_residual(P, x.cpu().numpy()) <= 1e-10
+        S.close()
+
+
 def test_c3_full_hierarchy_and_mixed(nair, oracle_mod):
     P = D.make_problem("C3")
     args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))

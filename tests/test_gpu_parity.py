@@ -330,6 +330,42 @@ def test_transposed_adjoint_gradients_match_rebuild(nair):
         assert float((a - b).norm() / b.norm()) <= 1e-10
 
 
+@pytest.mark.parametrize("name,N,p,k", CASES)
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_fcycle_parity(nair, oracle_mod, name, N, p, k, graphs):
+    """The F-cycle (coarse correction by an F-cycle, then a V-cycle from its
+    result, which restricts the coarse residual and adds P x_c to the iterate)
+    against the oracle's: one cycle on a seeded vector, then the FGMRES
+    history.  k = 1 and k = 2 give odd and even sweep counts."""
+    P = D.make_problem(name, N=N, p=p)
+    params = dict(neumann_degree=k, max_coarse=4)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), use_graphs=graphs,
+                        cycle_type="F", **params)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], cycle="F", **params)
+    f = D.rng.uniform(13, P["n"]) - 0.5
+    z = S.vcycle(dev(f)).cpu().numpy()
+    zr = H.vcycle(f)
+    assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    x, rep = S.solve(dev(P["rhs"]))
+    ref = H.solve(P["rhs"])
+    assert ref["status"] == 0
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    assert rep["rel_res"] <= 1e-10
+    S.close()
+
+
+def test_fcycle_mixed_precision(nair):
+    """F-cycle in FP32 inside FP64 FGMRES: FP64 residual and the FP64 solution."""
+    P = D.make_problem("C5", N=24, p=3)
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    rhs = dev(P["rhs"])
+    x64, r64 = nair.NairSolver(*args, neumann_degree=3, cycle_type="F").solve(rhs)
+    x32, r32 = nair.NairSolver(*args, neumann_degree=3, cycle_type="F", precision="mixed").solve(rhs)
+    assert r64["rel_res"] <= 1e-10 and r32["rel_res"] <= 1e-10
+    assert float((x32 - x64).norm() / x64.norm()) <= 1e-8
+
+
 def test_autograd_against_finite_differences(nair):
     """dJ/dq and dJ/dsigma from the adjoint solve vs central differences
     (eps = 1e-6, forward solves to 1e-13) on seeded coordinates."""
