@@ -48,6 +48,8 @@ def _load():
             lib.orc_setup.restype = P
             lib.orc_setup.argtypes = [I, I, P, P, P, D, D, I, I, I, I, I, ctypes.c_ulonglong,
                                       ctypes.POINTER(I)]
+            lib.orc_setup_scalar.restype = P
+            lib.orc_setup_scalar.argtypes = lib.orc_setup.argtypes
             lib.orc_free.argtypes = [P]
             lib.orc_num_levels.argtypes = [P]
             lib.orc_level_sizes.argtypes = [P, I, P]
@@ -77,7 +79,7 @@ class use_library:
         _load()
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
-        for name in ("orc_setup", "orc_free", "orc_num_levels", "orc_level_sizes", "orc_level_get",
+        for name in ("orc_setup", "orc_setup_scalar", "orc_free", "orc_num_levels", "orc_level_sizes", "orc_level_get",
                      "orc_solve", "orc_vcycle", "orc_solve_t", "orc_vcycle_t", "orc_set_cycle", "orc_block_inverse", "orc_transpose", "orc_gradients"):
             getattr(lib, name).argtypes = getattr(self._saved, name).argtypes
             getattr(lib, name).restype = getattr(self._saved, name).restype
@@ -111,16 +113,22 @@ def default_max_coarse(b):
 
 
 class Hierarchy:
-    """An oracle hierarchy built from a block-CSR matrix (host arrays)."""
+    """An oracle hierarchy built from a block-CSR matrix (host arrays).
 
-    def __init__(self, row_ptr, col, vals, **params):
+    scalar=True builds scalar nAIR: the hierarchy (block size 1) of D^{-1} A,
+    with the Krylov solve on A preconditioned by the cycle applied to D^{-1} v.
+    """
+
+    def __init__(self, row_ptr, col, vals, scalar=False, **params):
         lib = _load()
         p = dict(DEFAULTS)
         p.update(params)
         vals = np.ascontiguousarray(vals, dtype=np.float64)
         self.b = vals.shape[-1]
+        self.scalar = bool(scalar)
+        self.level_b = 1 if scalar else self.b  # block size of the hierarchy's levels
         if p["max_coarse"] is None:
-            p["max_coarse"] = default_max_coarse(self.b)
+            p["max_coarse"] = default_max_coarse(self.level_b)
         if p["f_sweeps"] is None:
             p["f_sweeps"] = p["neumann_degree"] + 1
         self.params = p
@@ -128,7 +136,8 @@ class Hierarchy:
         ci = np.ascontiguousarray(col, dtype=np.int32)
         self.E = len(rp) - 1
         st = ctypes.c_int(0)
-        self._h = lib.orc_setup(self.E, self.b, _p(rp), _p(ci), _p(vals), p["theta"],
+        setup = lib.orc_setup_scalar if scalar else lib.orc_setup
+        self._h = setup(self.E, self.b, _p(rp), _p(ci), _p(vals), p["theta"],
                                 p["filter_tol"], p["filter_targets"], p["neumann_degree"],
                                 p["max_levels"], p["max_coarse"], p["max_dense"], p["seed"],
                                 ctypes.byref(st))
@@ -165,7 +174,7 @@ class Hierarchy:
     def level(self, l):
         """All arrays of level l (host copies)."""
         s = self.sizes(l)
-        b = self.b
+        b = self.level_b
         E, nC, nF = s["E"], s["nC"], s["nF"]
         d = dict(s)
         d["row_ptr"] = self._get(l, A_RP, E + 1, np.int32)

@@ -70,6 +70,11 @@ typedef struct {
   int f_sweeps, c_sweeps;
   int transposed; /* solve with A^T and the transposed cycle (adjoint) */
   int cycle_type; /* 0: V-cycle, 1: F-cycle (forward preconditioner) */
+  /* scalar nAIR: the hierarchy (b = 1) is built for D^{-1} A; the Krylov solve
+   * keeps the block matrix A (block size bo) and D^{-1} */
+  int scalar, bo;
+  Bsr Ao;
+  double *Do;
 } Hier;
 
 static void bsr_free(Bsr *m) {
@@ -462,6 +467,8 @@ void orc_free(void *h) {
   Hier *H = (Hier *)h;
   if (!H) return;
   for (int l = 0; l < H->nlev; ++l) level_free(&H->lev[l]);
+  bsr_free(&H->Ao);
+  free(H->Do);
   free(H);
 }
 
@@ -675,6 +682,99 @@ void *orc_setup(int E, int b, const int *rp, const int *ci, const double *v, dou
 }
 
 /* ---------------------------------------------------------------------------
+ * Scalar nAIR (Sec. 5.2: the default form): scale A by its block-diagonal
+ * inverse, so that every diagonal block becomes the identity, and coarsen the
+ * scaled matrix degree of freedom by degree of freedom (block size 1, with the
+ * same strength, splitting, Neumann, interpolation and filtering rules).  The
+ * diagonal blocks are set to I exactly; an off-diagonal block D_ii^{-1} A_ij is
+ * a block product in the canonical order; exact zeros are not stored.  The
+ * Krylov solve keeps A, preconditioned by the scalar cycle applied to D^{-1} v.
+ * ------------------------------------------------------------------------- */
+void *orc_setup_scalar(int E, int b, const int *rp, const int *ci, const double *v, double theta,
+                       double filter_tol, int filter_targets, int neumann_degree, int max_levels,
+                       int max_coarse, int max_dense, unsigned long long seed, int *status) {
+  *status = ORC_OK;
+  if (E <= 0 || b <= 0 || b > 32) {
+    *status = ORC_ERR_INVALID_ARG;
+    return NULL;
+  }
+  size_t bb = (size_t)b * b;
+  int nnzb = rp[E];
+  double *D = (double *)malloc(sizeof(double) * bb * E);
+  for (int i = 0; i < E; ++i) {
+    int dp = -1;
+    for (int p = rp[i]; p < rp[i + 1]; ++p)
+      if (ci[p] == i) dp = p;
+    int st = dp < 0 ? ORC_ERR_INVALID_ARG : gj_inverse(b, v + (size_t)dp * bb, D + (size_t)i * bb);
+    if (st) { free(D); *status = st; return NULL; }
+  }
+  /* scaled scalar rows: (i, r) -> the identity entry and the nonzeros of row r
+   * of D_ii^{-1} A_ij, j != i, in ascending column order */
+  int n = E * b;
+  int *srp = (int *)malloc(sizeof(int) * (n + 1));
+  int *sci = (int *)malloc(sizeof(int) * ((size_t)nnzb * bb + n + 1));
+  double *sv = (double *)malloc(sizeof(double) * ((size_t)nnzb * bb + n + 1));
+  double *blk = (double *)malloc(sizeof(double) * bb);
+  int w = 0;
+  srp[0] = 0;
+  for (int i = 0; i < E; ++i) {
+    const double *Di = D + (size_t)i * bb;
+    for (int r = 0; r < b; ++r) {
+      for (int p = rp[i]; p < rp[i + 1]; ++p) {
+        int j = ci[p];
+        if (j == i) {
+          sci[w] = i * b + r;
+          sv[w++] = 1.0;
+          continue;
+        }
+        const double *a = v + (size_t)p * bb;
+        for (int c = 0; c < b; ++c) {
+          double acc = 0.0;
+          for (int t = 0; t < b; ++t) acc = fma(Di[r * b + t], a[t * b + c], acc);
+          blk[c] = acc;
+        }
+        for (int c = 0; c < b; ++c)
+          if (blk[c] != 0.0) {
+            sci[w] = j * b + c;
+            sv[w++] = blk[c];
+          }
+      }
+      srp[i * b + r + 1] = w;
+    }
+  }
+  free(blk);
+  Hier *H = (Hier *)orc_setup(n, 1, srp, sci, sv, theta, filter_tol, filter_targets, neumann_degree,
+                              max_levels, max_coarse, max_dense, seed, status);
+  free(srp);
+  free(sci);
+  free(sv);
+  if (!H) { free(D); return NULL; }
+  H->scalar = 1;
+  H->bo = b;
+  H->Do = D;
+  H->Ao.nrows = H->Ao.ncols = E;
+  H->Ao.rp = (int *)malloc(sizeof(int) * (E + 1));
+  H->Ao.ci = (int *)malloc(sizeof(int) * (nnzb ? nnzb : 1));
+  H->Ao.v = (double *)malloc(sizeof(double) * bb * (nnzb ? nnzb : 1));
+  memcpy(H->Ao.rp, rp, sizeof(int) * (E + 1));
+  memcpy(H->Ao.ci, ci, sizeof(int) * nnzb);
+  memcpy(H->Ao.v, v, sizeof(double) * bb * nnzb);
+  return H;
+}
+
+/* y_i = D_i^{-1} x_i, or (D_i^{-1})^T x_i when transposed, for E blocks of size b */
+static void block_diag_apply(int E, int b, const double *D, const double *x, double *y, int transposed) {
+  size_t bb = (size_t)b * b;
+  for (int i = 0; i < E; ++i)
+    for (int r = 0; r < b; ++r) {
+      double s = 0.0;
+      for (int c = 0; c < b; ++c)
+        s += (transposed ? D[(size_t)i * bb + c * b + r] : D[(size_t)i * bb + r * b + c]) * x[(size_t)i * b + c];
+      y[(size_t)i * b + r] = s;
+    }
+}
+
+/* ---------------------------------------------------------------------------
  * Solve phase
  * ------------------------------------------------------------------------- */
 static void spmv(int b, const Bsr *A, const double *x, double *y) {
@@ -773,11 +873,14 @@ static void cycle(const Hier *H, int l, int type, const double *f, double *x, in
   free(r);
 }
 
+static void precond_apply(const Hier *H, const double *v, double *z);
+
 int orc_vcycle(void *h, const double *f, double *x, int f_sweeps, int c_sweeps) {
   Hier *H = (Hier *)h;
   H->f_sweeps = f_sweeps;
   H->c_sweeps = c_sweeps;
-  cycle(H, 0, H->cycle_type, f, x, 1);
+  H->transposed = 0;
+  precond_apply(H, f, x);
   return ORC_OK;
 }
 
@@ -899,20 +1002,40 @@ int orc_vcycle_t(void *h, const double *f, double *x, int f_sweeps, int c_sweeps
   Hier *H = (Hier *)h;
   H->f_sweeps = f_sweeps;
   H->c_sweeps = c_sweeps;
-  vcycle_t(H, 0, f, x);
+  H->transposed = 1;
+  precond_apply(H, f, x);
+  H->transposed = 0;
   return ORC_OK;
 }
 
 /* the operator and preconditioner of the Krylov solve: A and the V-cycle, or
  * A^T and the transposed cycle */
 static void op_apply(const Hier *H, const double *x, double *y) {
-  if (H->transposed) spmv_t(H->b, &H->lev[0].A, x, y);
-  else spmv(H->b, &H->lev[0].A, x, y);
+  const Bsr *A = H->scalar ? &H->Ao : &H->lev[0].A;
+  int b = H->scalar ? H->bo : H->b;
+  if (H->transposed) spmv_t(b, A, x, y);
+  else spmv(b, A, x, y);
 }
 
+/* the preconditioner: the cycle, or its transpose; for scalar nAIR the cycle of
+ * D^{-1} A applied to D^{-1} v (transposed: D^{-T} applied after the cycle) */
 static void precond_apply(const Hier *H, const double *v, double *z) {
-  if (H->transposed) vcycle_t(H, 0, v, z);
-  else cycle(H, 0, H->cycle_type, v, z, 1);
+  if (!H->scalar) {
+    if (H->transposed) vcycle_t(H, 0, v, z);
+    else cycle(H, 0, H->cycle_type, v, z, 1);
+    return;
+  }
+  size_t n = (size_t)H->lev[0].A.nrows;
+  double *t = (double *)malloc(sizeof(double) * n + 8);
+  int E = (int)(n / H->bo);
+  if (H->transposed) {
+    vcycle_t(H, 0, v, t);
+    block_diag_apply(E, H->bo, H->Do, t, z, 1);
+  } else {
+    block_diag_apply(E, H->bo, H->Do, v, t, 0);
+    cycle(H, 0, H->cycle_type, t, z, 1);
+  }
+  free(t);
 }
 
 static double dot(size_t n, const double *a, const double *b) {

@@ -58,6 +58,13 @@ MUTATIONS = [
      "for (size_t k = 0; k < n; ++k) r[k] = f[k];"),
     ("nonzero guess: interpolation replaces x",
      "x[(size_t)i * b + rr] = zero ? v : x[(size_t)i * b + rr] + v;", "x[(size_t)i * b + rr] = v;"),
+    ("scalar: blocks not scaled by D^-1", "for (int t = 0; t < b; ++t) acc = fma(Di[r * b + t], a[t * b + c], acc);",
+     "acc = a[r * b + c];"),
+    ("scalar: explicit zeros stored", "if (blk[c] != 0.0) {", "if (1) {"),
+    ("scalar: D^-1 not applied before the cycle", "block_diag_apply(E, H->bo, H->Do, v, t, 0);",
+     "memcpy(t, v, sizeof(double) * n);"),
+    ("scalar adjoint: D^-1 not transposed", "block_diag_apply(E, H->bo, H->Do, t, z, 1);",
+     "block_diag_apply(E, H->bo, H->Do, t, z, 0);"),
 ]
 
 PINS = [
@@ -78,6 +85,9 @@ PINS = [
     lambda o: pins.test_transposed_cycle_exact_under_ideal_interpolation(o, 1),
     lambda o: pins.test_cycles_match_composed_error_propagation(o, "V", "C2", 4, 2, 2, 3, 1),
     lambda o: pins.test_cycles_match_composed_error_propagation(o, "F", "C2", 4, 2, 2, 3, 1),
+    lambda o: pins.test_scalar_scaled_matrix(o, "C2", 4, 2),
+    lambda o: pins.test_scalar_exact_under_ideal_settings(o, 1),
+    lambda o: pins.test_scalar_preconditioner_composition(o, "C2", 4, 2, 2),
 ]
 
 

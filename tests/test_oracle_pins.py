@@ -513,6 +513,93 @@ def test_fgmres_matches_dense_solve(oracle_lib, name, N, p):
 
 
 # -----------------------------------------------------------------------------
+# scalar nAIR (block-diagonal scaling, then coarsening by degree of freedom)
+# -----------------------------------------------------------------------------
+
+def scaled_dense(P):
+    """D^{-1} A with D the block diagonal of A (numpy inverses)."""
+    b, E = P["b"], P["E"]
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    Dinv = np.zeros_like(A)
+    for i in range(E):
+        sl = slice(i * b, (i + 1) * b)
+        Dinv[sl, sl] = np.linalg.inv(A[sl, sl])
+    return A, Dinv, Dinv @ A
+
+
+@pytest.mark.parametrize("name,N,p", [("C1", 4, 1), ("C2", 4, 2), ("C3", 3, 3)])
+def test_scalar_scaled_matrix(oracle_lib, name, N, p):
+    """Level 0 of scalar nAIR is D^{-1} A stored by degree of freedom: unit
+    diagonal, no coupling inside an element (D_ii^{-1} A_ii = I exactly), the
+    structural zeros of the face couplings not stored, sorted columns."""
+    P = tiny(name, N=N, p=p)
+    b = P["b"]
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], scalar=True)
+    lev = H.level(0)
+    assert lev["E"] == P["n"] and lev["vals"].shape[1:] == (1, 1)
+    S = bsr_dense(lev["row_ptr"], lev["col"], lev["vals"])
+    A, Dinv, DA = scaled_dense(P)
+    for i in range(P["E"]):
+        sl = slice(i * b, (i + 1) * b)
+        DA[sl, sl] = np.eye(b)
+    assert np.array_equal(S != 0, DA != 0)
+    assert np.abs(S - DA).max() <= 1e-13 * np.abs(DA).max()
+    assert np.all(np.diag(S) == 1.0)
+    assert np.all(lev["vals"] != 0.0)
+    for i in range(lev["E"]):
+        c = lev["col"][lev["row_ptr"][i]:lev["row_ptr"][i + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_scalar_exact_under_ideal_settings(oracle_lib, p):
+    """Scalar nAIR under ideal settings (theta = 0, no filtering, exact Neumann,
+    enough F sweeps): the cycle solves (D^{-1} A) y = D^{-1} f exactly, so the
+    preconditioner applied to f is A^{-1} f (Lemma ideal restriction)."""
+    P = tiny("C1", N=5, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], scalar=True, theta=0.0, filter_targets=0,
+                             neumann_degree=80, max_coarse=2, f_sweeps=80, c_sweeps=1)
+    assert H.nlev >= 3
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    xs = np.linalg.solve(A, P["rhs"])
+    x = H.vcycle(P["rhs"])
+    assert np.linalg.norm(x - xs) <= 1e-11 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("name,N,p", [("C2", 8, 2), ("C3", 6, 3)])
+def test_scalar_solve_matches_dense(oracle_lib, name, N, p):
+    P = tiny(name, N=N, p=p)
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], scalar=True, neumann_degree=2)
+    r = H.solve(P["rhs"], restart=10)
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    xs = np.linalg.solve(A, P["rhs"])
+    assert r["status"] == 0 and r["relres"] <= 1e-10
+    assert np.linalg.norm(r["x"] - xs) <= 1e-8 * np.linalg.norm(xs)
+    w = D.functional_weights(P["n"])
+    ra = H.solve(w, transposed=True, restart=10)
+    assert ra["status"] == 0
+    assert np.linalg.norm(ra["x"] - np.linalg.solve(A.T, w)) <= 1e-8 * np.linalg.norm(ra["x"])
+
+
+@pytest.mark.parametrize("name,N,p,k", [("C2", 4, 2, 2), ("C3", 3, 2, 1)])
+def test_scalar_preconditioner_composition(oracle_lib, name, N, p, k):
+    """The scalar preconditioner is M_s D^{-1} (M_s the cycle of the scaled
+    matrix, pinned by the composition test on its own hierarchy) and the
+    transposed one is its transpose D^{-T} M_s^T."""
+    P = tiny(name, N=N, p=p)
+    n = P["n"]
+    H = oracle_lib.Hierarchy(P["row_ptr"], P["col"], P["vals"], scalar=True, neumann_degree=k,
+                             max_coarse=4, filter_targets=0)
+    assert H.nlev >= 3
+    _, Dinv, _ = scaled_dense(P)
+    M = np.stack([H.vcycle(e) for e in np.eye(n)], axis=1)
+    Ms = composed_cycle(H, 0, "V", k + 1, 1, 1)
+    assert np.abs(M - Ms @ Dinv).max() <= 1e-11 * np.abs(M).max()
+    MT = np.stack([H.vcycle(e, transposed=True) for e in np.eye(n)], axis=1)
+    assert np.abs(MT - M.T).max() <= 1e-12 * np.abs(M).max()
+
+
+# -----------------------------------------------------------------------------
 # a16: adjoint
 # -----------------------------------------------------------------------------
 
