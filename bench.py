@@ -278,10 +278,13 @@ def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps
                                  "setup_ms": rep["setup_ms"], "solve_ms": rep["solve_ms"],
                                  "iterations": rep["iterations"], "rel_res": rep["rel_res"],
                                  "rel_diff_vs_fp64": float((xx - xref).norm() / xref.norm())}
-    # the F-cycle and Neumann degree 3 of the scaling study (Sec. 6)
+    # the F-cycle and Neumann degree 3 of the scaling study (Sec. 6), and scalar nAIR
     for label, extra in (("forward_vcycle_k3_fp64", dict(neumann_degree=3)),
                          ("forward_fcycle_k3_fp64", dict(neumann_degree=3, cycle_type="F")),
-                         ("forward_fcycle_k3_mixed", dict(neumann_degree=3, cycle_type="F", precision="mixed"))):
+                         ("forward_fcycle_k3_mixed", dict(neumann_degree=3, cycle_type="F", precision="mixed")),
+                         # scalar nAIR (block-diagonal scaling, coarsening by degree of freedom)
+                         ("forward_scalar_fp64", dict(scalar=1)),
+                         ("forward_scalar_mixed", dict(scalar=1, precision="mixed"))):
         def fk(extra=extra):
             S = nair.NairSolver(rp, ci, v, **dict(params, **extra))
             xx, rep = S.solve(bvec)

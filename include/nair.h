@@ -96,6 +96,12 @@ typedef struct {
   int32_t adjoint_mode;   /* nair_adjoint_mode; NAIR_ADJOINT_TRANSPOSED */
   int32_t cycle_type;     /* nair_cycle of nair_solve and nair_vcycle; NAIR_CYCLE_V.  The
                              transposed adjoint always uses the transposed V-cycle. */
+  int32_t scalar;         /* 0: block nAIR (element blocks on every level); 1: scalar nAIR
+                             (Sec. 5.2, the paper's default): the hierarchy is built, degree of
+                             freedom by degree of freedom, for D^{-1} A (D the block diagonal,
+                             D_ii^{-1} A_ii set to I, zeros not stored) and the preconditioner is
+                             the cycle applied to D^{-1} v; GMRES still solves A x = b.  The
+                             exported levels then have block size 1.  0 */
 } nair_params;
 
 /* Solve report.  history is an optional host buffer owned by the caller. */

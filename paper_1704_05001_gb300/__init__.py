@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
                 ("maxiter", ctypes.c_int32), ("tol", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("keep_setup_data", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("sweep_timing", ctypes.c_int32), ("adjoint_mode", ctypes.c_int32),
-                ("cycle_type", ctypes.c_int32)]
+                ("cycle_type", ctypes.c_int32), ("scalar", ctypes.c_int32)]
 
 
 class _Info(ctypes.Structure):
@@ -167,7 +167,7 @@ class NairSolver:
     Keyword arguments set fields of nair_params (strength_theta, filter_tol,
     neumann_degree, f_sweeps, c_sweeps, max_coarse, precision ("fp64" or
     "mixed"), gmres_restart, maxiter, tol, keep_setup_data, adjoint_mode
-    ("transposed" or "rebuild"), cycle_type ("V" or "F"), ...).
+    ("transposed" or "rebuild"), cycle_type ("V" or "F"), scalar (0 or 1), ...).
     """
 
     def __init__(self, row_ptr, col, vals, **params):
@@ -186,6 +186,7 @@ class NairSolver:
         p.stream = _stream()
         self.params = p
         self.b = int(vals.shape[-1])
+        self.level_b = 1 if p.scalar else self.b  # block size of the hierarchy's levels
         self.E = int(row_ptr.shape[0] - 1)
         self.n = self.E * self.b
         A = _Bsr(self.E, self.b, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(vals))
@@ -288,7 +289,7 @@ class NairSolver:
     def level(self, l, adjoint=False):
         """Host copies of the arrays of level l (values as float64)."""
         s = self.sizes(l, adjoint)
-        b = self.b
+        b = self.level_b
         d = dict(s)
         d["row_ptr"] = self._array(l, A_ROWPTR, np.int32, None, adjoint)
         d["col"] = self._array(l, A_COL, np.int32, None, adjoint)

@@ -26,17 +26,14 @@ struct nair_handle {
   Mem mem;
   DBsr<double> A64;
   DBsr<float> A32;
-  bool mixed = false;
+  bool mixed = false, scalar = false;
   Hier<double> h64;
   Hier<float> h32;
-  L0Comp<double> l0c64;  // level-0 compression of the FP64 matrix (mixed precision)
+  Outer fwd, bwd;  // FP64 operators of the forward (A) and adjoint (A^T) Krylov solves
   Krylov K;
   nair_handle *adj = nullptr;  // NAIR_ADJOINT_REBUILD: the hierarchy of A^T
   double setup_ms = 0.0;
-  // transposed form of the forward hierarchy (adjoint solves)
-  bool tbuilt = false;
-  DBsr<double> At64;       // A^T in FP64, the operator of the adjoint Krylov solve
-  L0Comp<double> tl0c64;   // its level-0 compression (mixed precision)
+  bool tbuilt = false;  // transposed form of the forward hierarchy (adjoint solves)
   double tsetup_ms = 0.0;
 };
 
@@ -84,6 +81,7 @@ Params resolve_params(const nair_params *p, int b) {
   P.use_graphs = p->use_graphs;
   P.sweep_timing = p->sweep_timing;
   P.cycle = p->cycle_type;
+  P.scalar = p->scalar;
   return P;
 }
 }  // namespace nair
@@ -174,6 +172,7 @@ static void check_params(const nair_params *p, int b) {
   if (p->adjoint_mode != NAIR_ADJOINT_TRANSPOSED && p->adjoint_mode != NAIR_ADJOINT_REBUILD)
     fail(NAIR_ERR_INVALID_ARG, "unknown adjoint_mode");
   if (p->cycle_type != NAIR_CYCLE_V && p->cycle_type != NAIR_CYCLE_F) fail(NAIR_ERR_INVALID_ARG, "unknown cycle_type");
+  if (p->scalar != 0 && p->scalar != 1) fail(NAIR_ERR_INVALID_ARG, "scalar must be 0 or 1");
 }
 
 static void setup_impl(nair_handle *h, const int *rp, const int *ci, const double *v, int E, int b,
@@ -210,22 +209,63 @@ static void setup_impl(nair_handle *h, const int *rp, const int *ci, const doubl
     validate_bsr(E, E, A.rp, A.ci, (int)nnzb, s, tmp);
   }
   h->mixed = h->P.precision == NAIR_MIXED;
+  h->scalar = h->P.scalar != 0;
+  h->fwd.A = A;
+  h->fwd.b = b;
+  // the matrix the hierarchy is built for: A, or for scalar nAIR D^{-1} A by
+  // degree of freedom (block size 1)
+  DBsr<double> M = A;
+  int bm = b;
+  double *Dsc = nullptr;
+  if (h->scalar) {
+    Mem tmp;
+    tmp.s = s;
+    int *diagA = mem.alloc<int>(E), *err = tmp.alloc<int>(1);
+    NAIR_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
+    diag_positions(E, A.rp, A.ci, diagA, s);
+    Dsc = mem.alloc<double>((size_t)E * b * b);
+    block_inverses<double>(E, b, A.v, diagA, Dsc, err, s);
+    if (read_int(err, s)) fail(NAIR_ERR_SINGULAR_BLOCK, "singular diagonal block");
+    scalar_matrix(A, b, Dsc, diagA, M, s, mem);
+    bm = 1;
+    h->fwd.diag = diagA;
+    build_l0comp<double>(A, diagA, b, s, mem, h->fwd.C);
+  }
   if (h->mixed) {
     DBsr<float> &F = h->A32;
-    F.nrows = F.ncols = E;
-    F.nnzb = A.nnzb;
-    F.rp = A.rp;
-    F.ci = A.ci;
-    F.v = mem.alloc<float>((size_t)nnzb * b * b);
-    long long tot = nnzb * b * b;
-    k_cast_api<double, float><<<grid(tot), kThreads, 0, s>>>(tot, A.v, F.v);
+    F.nrows = F.ncols = M.nrows;
+    F.nnzb = M.nnzb;
+    F.rp = M.rp;
+    F.ci = M.ci;
+    F.v = mem.alloc<float>((size_t)M.nnzb * bm * bm);
+    long long tot = (long long)M.nnzb * bm * bm;
+    k_cast_api<double, float><<<grid(tot), kThreads, 0, s>>>(tot, M.v, F.v);
     NAIR_LAUNCH_CHECK();
-    h->h32.b = b;
+    h->h32.b = bm;
     build_hierarchy<float>(F, h->P, s, mem, h->h32);
-    if (!h->h32.lev[0].coarsest) build_l0comp<double>(A, h->h32.lev[0].diag, b, s, mem, h->l0c64);
+    if (h->scalar) {
+      const long long nd = (long long)E * b * b;
+      float *d32 = mem.alloc<float>((size_t)nd);
+      k_cast_api<double, float><<<grid(nd), kThreads, 0, s>>>(nd, Dsc, d32);
+      NAIR_LAUNCH_CHECK();
+      h->h32.pre_dinv = d32;
+      h->h32.pre_b = b;
+      h->h32.pre_E = E;
+    } else {
+      h->fwd.diag = h->h32.lev[0].diag;
+      if (!h->h32.lev[0].coarsest) build_l0comp<double>(A, h->fwd.diag, b, s, mem, h->fwd.C);
+    }
   } else {
-    h->h64.b = b;
-    build_hierarchy<double>(A, h->P, s, mem, h->h64);
+    h->h64.b = bm;
+    build_hierarchy<double>(M, h->P, s, mem, h->h64);
+    if (h->scalar) {
+      h->h64.pre_dinv = Dsc;
+      h->h64.pre_b = b;
+      h->h64.pre_E = E;
+    } else {
+      h->fwd.diag = h->h64.lev[0].diag;
+      h->fwd.C = h->h64.l0c;
+    }
   }
   NAIR_CK(cudaEventRecord(e1, s));
   NAIR_CK(cudaEventSynchronize(e1));
@@ -261,6 +301,7 @@ void nair_default_params(nair_params *p) {
   p->sweep_timing = 0;
   p->adjoint_mode = NAIR_ADJOINT_TRANSPOSED;
   p->cycle_type = NAIR_CYCLE_V;
+  p->scalar = 0;
 }
 
 const char *nair_last_error(void) { return g_last_error.c_str(); }
@@ -328,7 +369,7 @@ nair_status nair_setup(const nair_bsr *A, const nair_params *p, nair_handle **ou
   init_pool_once();
   nair_handle *h = new nair_handle();
   h->raw = *p;
-  h->P = resolve_params(p, b);
+  h->P = resolve_params(p, p->scalar ? 1 : b);
   h->s = (cudaStream_t)p->stream;
   h->K.mem.s = h->s;
   try {
@@ -374,10 +415,9 @@ static nair_status solve_impl(nair_handle *h, const double *b, double *x, nair_i
   std::vector<double> hist;
   int iters = 0;
   double relres = 0.0;
-  const DBsr<double> &A = transposed ? h->At64 : h->A64;
-  const L0Comp<double> *C = h->mixed ? (transposed ? &h->tl0c64 : &h->l0c64) : (transposed ? &h->h64.tl0c : &h->h64.l0c);
-  nair_status st = h->mixed ? fgmres<float>(A, h->h32, h->P, h->K, b, x, hist, &iters, &relres, h->s, C, transposed)
-                            : fgmres<double>(A, h->h64, h->P, h->K, b, x, hist, &iters, &relres, h->s, C, transposed);
+  const Outer &op = transposed ? h->bwd : h->fwd;
+  nair_status st = h->mixed ? fgmres<float>(op, h->h32, h->P, h->K, b, x, hist, &iters, &relres, h->s, transposed)
+                            : fgmres<double>(op, h->h64, h->P, h->K, b, x, hist, &iters, &relres, h->s, transposed);
   NAIR_CK(cudaEventRecord(e1, h->s));
   NAIR_CK(cudaEventSynchronize(e1));
   float ms = 0.f;
@@ -415,13 +455,19 @@ static void build_transposed_handle(nair_handle *h) {
   NAIR_CK(cudaEventCreate(&e0));
   NAIR_CK(cudaEventCreate(&e1));
   NAIR_CK(cudaEventRecord(e0, s));
-  if (h->mixed) {
-    build_transposed<float>(h->h32, s, h->mem);
-    bsr_transpose<double>(h->A64, h->b, h->At64, s, h->mem);
-    if (h->h32.tl0c.W > 0) build_l0comp<double>(h->At64, h->h32.tlev[0].diag, h->b, s, h->mem, h->tl0c64);
+  if (h->mixed) build_transposed<float>(h->h32, s, h->mem);
+  else build_transposed<double>(h->h64, s, h->mem);
+  h->bwd.b = h->b;
+  if (!h->mixed && !h->scalar) {  // level 0 of the transposed hierarchy is A^T itself
+    h->bwd.A = h->h64.tlev[0].At;
+    h->bwd.diag = h->h64.tlev[0].diag;
+    h->bwd.C = h->h64.tl0c;
   } else {
-    build_transposed<double>(h->h64, s, h->mem);
-    h->At64 = h->h64.tlev[0].At;
+    bsr_transpose<double>(h->A64, h->b, h->bwd.A, s, h->mem);
+    int *diag = h->mem.alloc<int>(h->E);
+    diag_positions(h->E, h->bwd.A.rp, h->bwd.A.ci, diag, s);
+    h->bwd.diag = diag;
+    build_l0comp<double>(h->bwd.A, diag, h->b, s, h->mem, h->bwd.C);
   }
   NAIR_CK(cudaEventRecord(e1, s));
   NAIR_CK(cudaEventSynchronize(e1));

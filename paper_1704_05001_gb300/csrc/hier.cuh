@@ -107,6 +107,11 @@ struct Hier {
   std::vector<TLevel<T>> tlev;
   L0Comp<T> tl0c;
   mutable VGraph tgraph;
+  // scalar nAIR: the hierarchy is built for D^{-1} A; the preconditioner applies
+  // the pre_E blocks of D^{-1} (size pre_b) before the cycle (after the
+  // transposed cycle, transposed)
+  const T *pre_dinv = nullptr;
+  int pre_b = 0, pre_E = 0;
 };
 
 struct Params {
@@ -116,7 +121,8 @@ struct Params {
   int precision, restart, maxiter;
   double tol;
   int keep, use_graphs, sweep_timing;
-  int cycle;  // 0: V-cycle, 1: F-cycle
+  int cycle;   // 0: V-cycle, 1: F-cycle
+  int scalar;  // 1: scalar nAIR (hierarchy of D^{-1} A by degree of freedom)
 };
 
 Params resolve_params(const nair_params *p, int b);
@@ -144,6 +150,11 @@ void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem);
 // block transpose of a block-CSR matrix (each block transposed, rows sorted)
 template <typename T>
 void bsr_transpose(const DBsr<T> &A, int b, DBsr<T> &out, cudaStream_t s, Mem &mem);
+
+// scalar form of a block matrix: D^{-1} A (Dinv: the inverse diagonal blocks,
+// diag: their positions) by degree of freedom, identity diagonal, no zeros stored
+void scalar_matrix(const DBsr<double> &A, int b, const double *Dinv, const int *diag, DBsr<double> &out,
+                   cudaStream_t s, Mem &mem);
 
 // rows of one class ordered by decreasing row length (sweep work list)
 int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem, Mem &tmp);

@@ -46,19 +46,21 @@ __global__ void k_dense_mv(int n, const T *__restrict__ M, const T *__restrict__
   if (lane == 0) x[warp] = acc;
 }
 
-// x_i = D_ii^{-1} f_i for a block-diagonal coarsest level
+// x_i = D_ii^{-1} f_i (trans: (D_ii^{-1})^T f_i) for E blocks: a block-diagonal
+// coarsest level, or the scaling of scalar nAIR
 template <typename T>
 __global__ void k_bdiag_apply(int E, int b, const T *__restrict__ dinv, const T *__restrict__ f,
-                              T *__restrict__ x) {
+                              T *__restrict__ x, int trans) {
   pdl_launch_dependents();
   pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)E * b) return;
   const int i = (int)(g / b), r = (int)(g - (long long)i * b);
-  const T *d = dinv + (size_t)i * b * b + r * b;
+  const T *d = dinv + (size_t)i * b * b + (trans ? r : r * b);
+  const int step = trans ? b : 1;
   const T *fi = f + (size_t)i * b;
   T acc = 0;
-  for (int c = 0; c < b; ++c) acc = fma(d[c], fi[c], acc);
+  for (int c = 0; c < b; ++c) acc = fma(d[(size_t)c * step], fi[c], acc);
   x[g] = acc;
 }
 
@@ -175,7 +177,7 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
                  (const T *)L.ainv, f, out);
     } else {  // block-diagonal coarsest matrix: x_i = D_ii^{-1} f_i
       launch_pdl(k_bdiag_apply<T>, dim3(grid((long long)L.E * b)), dim3(kThreads), 0, s, L.E, b,
-                 (const T *)L.dinv, f, out);
+                 (const T *)L.dinv, f, out, 0);
     }
     NAIR_LAUNCH_CHECK();
     return;
@@ -368,7 +370,7 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
                  (const T *)TL.ainvT, f, out);
     } else {
       launch_pdl(k_bdiag_apply<T>, dim3(grid((long long)L.E * b)), dim3(kThreads), 0, s, L.E, b,
-                 (const T *)TL.dinvT, f, out);
+                 (const T *)TL.dinvT, f, out, 0);
     }
     NAIR_LAUNCH_CHECK();
     return;
@@ -686,6 +688,34 @@ void release_graph(VGraph &g) {
   g = VGraph();
 }
 
+// the preconditioner on level-0 vectors: the cycle (or the transposed cycle);
+// for scalar nAIR with the block scaling D^{-1} before it (D^{-T} after the
+// transposed cycle), through level 0's residual vector, which a cycle from a
+// zero guess does not use on level 0
+template <typename T>
+static void cycle_apply(const Hier<T> &H, const Params &P, const T *f, T *x, bool transposed, cudaStream_t s) {
+  if (!H.pre_dinv) {
+    if (transposed) vcycle_t<T>(H, P, f, x, s);
+    else vcycle<T>(H, P, f, x, s);
+    return;
+  }
+  T *tmp = H.lev[0].r;
+  const dim3 g(grid((long long)H.pre_E * H.pre_b));
+  if (transposed) {
+    vcycle_t<T>(H, P, f, tmp, s);
+    ProfScope ps("scaling", s);
+    launch_pdl(k_bdiag_apply<T>, g, dim3(kThreads), 0, s, H.pre_E, H.pre_b, H.pre_dinv, (const T *)tmp, x, 1);
+    NAIR_LAUNCH_CHECK();
+  } else {
+    {
+      ProfScope ps("scaling", s);
+      launch_pdl(k_bdiag_apply<T>, g, dim3(kThreads), 0, s, H.pre_E, H.pre_b, H.pre_dinv, f, tmp, 0);
+      NAIR_LAUNCH_CHECK();
+    }
+    vcycle<T>(H, P, (const T *)tmp, x, s);
+  }
+}
+
 // capture: copy the input into level 0's right-hand side, V-cycle on fixed
 // buffers, copy level 0's solution out (FP64 <-> T casts in mixed precision)
 template <typename T>
@@ -709,8 +739,7 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n, bool t
     if (H.clock.dev && !transposed) clock_reset(H.clock, s);
     k_copy_in<T><<<grid(n), kThreads, 0, s>>>(n, g.dptr, f0);
     NAIR_LAUNCH_CHECK();
-    if (transposed) vcycle_t<T>(H, P, f0, x0, s);
-    else vcycle<T>(H, P, f0, x0, s);
+    cycle_apply<T>(H, P, f0, x0, transposed, s);
     launch_pdl(k_copy_out<T>, dim3(grid(n)), dim3(kThreads), 0, s, n, (const T *)x0, (void *const *)g.dptr);
     NAIR_LAUNCH_CHECK();
   } catch (...) {
@@ -741,14 +770,12 @@ void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cuda
   }
   if (H.clock.dev && !transposed) clock_reset(H.clock, s);
   if constexpr (std::is_same<T, double>::value) {
-    if (transposed) vcycle_t<double>(H, P, v, z, s);
-    else vcycle<double>(H, P, v, z, s);
+    cycle_apply<double>(H, P, v, z, transposed, s);
   } else {
     T *f0 = H.lev[0].f, *x0 = H.lev[0].x;
     k_cast<double, T><<<grid(n), kThreads, 0, s>>>(n, v, f0);
     NAIR_LAUNCH_CHECK();
-    if (transposed) vcycle_t<T>(H, P, f0, x0, s);
-    else vcycle<T>(H, P, f0, x0, s);
+    cycle_apply<T>(H, P, f0, x0, transposed, s);
     k_cast<T, double><<<grid(n), kThreads, 0, s>>>(n, x0, z);
     NAIR_LAUNCH_CHECK();
   }
@@ -781,12 +808,14 @@ void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, d
 }
 
 template <typename T>
-nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
-                   const double *bvec, double *x, std::vector<double> &hist, int *iters,
-                   double *relres, cudaStream_t s, const L0Comp<double> *C, bool transposed) {
-  // transposed: A is A^T and the preconditioner the transposed cycle
-  const int *diag0 = transposed ? H.tlev[0].diag : H.lev[0].diag;
-  const int b = H.b, m = P.restart;
+nair_status fgmres(const Outer &op, const Hier<T> &H, const Params &P, Krylov &K, const double *bvec,
+                   double *x, std::vector<double> &hist, int *iters, double *relres, cudaStream_t s,
+                   bool transposed) {
+  // transposed: op is A^T and the preconditioner the transposed cycle
+  const DBsr<double> &A = op.A;
+  const L0Comp<double> *C = &op.C;
+  const int *diag0 = op.diag;
+  const int b = op.b, m = P.restart;
   const long long n = (long long)A.nrows * b;
   K.ensure(n, m, s);
   double *hh = K.hhost;  // [0, m+1): h1, [m+1, 2m+2): h2, [2m+2]: ||w||^2
@@ -901,11 +930,9 @@ nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Kry
   return status;
 }
 
-template nair_status fgmres<double>(const DBsr<double> &, const Hier<double> &, const Params &, Krylov &,
-                                    const double *, double *, std::vector<double> &, int *, double *,
-                                    cudaStream_t, const L0Comp<double> *, bool);
-template nair_status fgmres<float>(const DBsr<double> &, const Hier<float> &, const Params &, Krylov &,
-                                   const double *, double *, std::vector<double> &, int *, double *,
-                                   cudaStream_t, const L0Comp<double> *, bool);
+template nair_status fgmres<double>(const Outer &, const Hier<double> &, const Params &, Krylov &, const double *,
+                                    double *, std::vector<double> &, int *, double *, cudaStream_t, bool);
+template nair_status fgmres<float>(const Outer &, const Hier<float> &, const Params &, Krylov &, const double *,
+                                   double *, std::vector<double> &, int *, double *, cudaStream_t, bool);
 
 }  // namespace nair

@@ -23,13 +23,22 @@ struct Krylov {
 void spmv64(const DBsr<double> &A, int b, const double *x, const double *bvec, double *y, cudaStream_t s,
             const L0Comp<double> *C = nullptr, const int *diag = nullptr);
 
+// the operator of the Krylov solve (A, or A^T for the adjoint) in FP64 with its
+// block size, diagonal-block positions and level-0 column compression
+struct Outer {
+  DBsr<double> A;
+  int b = 0;
+  const int *diag = nullptr;
+  L0Comp<double> C;
+};
+
 template <typename T>
 void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cudaStream_t s, long long n,
              bool transposed = false);
 
 template <typename T>
-nair_status fgmres(const DBsr<double> &A, const Hier<T> &H, const Params &P, Krylov &K,
-                   const double *bvec, double *x, std::vector<double> &hist, int *iters,
-                   double *relres, cudaStream_t s, const L0Comp<double> *C, bool transposed = false);
+nair_status fgmres(const Outer &op, const Hier<T> &H, const Params &P, Krylov &K, const double *bvec,
+                   double *x, std::vector<double> &hist, int *iters, double *relres, cudaStream_t s,
+                   bool transposed = false);
 
 }  // namespace nair

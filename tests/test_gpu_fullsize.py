@@ -100,6 +100,22 @@ def test_c2_full_fcycle_k3(nair):
         S.close()
 
 
+def test_c2_full_scalar(nair):
+    """Scalar nAIR on the full C2 problem: FP64 residual recomputed on the host,
+    forward in both precisions and the adjoint."""
+    P = D.make_problem("C2")
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    w = D.functional_weights(P["n"])
+    for prec in ("fp64", "mixed"):
+        S = nair.NairSolver(*args, neumann_degree=2, scalar=1, precision=prec)
+        x, rep = S.solve(dev(P["rhs"]))
+        assert rep["rel_res"] <= 1e-10
+        assert host_residual(P, x.cpu().numpy()) <= 1e-10
+        lam, repa = S.adjoint_solve(dev(w))
+        assert host_residual(P, lam.cpu().numpy(), w) <= 1e-10
+        S.close()
+
+
 def test_c3_full_hierarchy_and_mixed(nair, oracle_mod):
     P = D.make_problem("C3")
     args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))

@@ -366,6 +366,55 @@ def test_fcycle_mixed_precision(nair):
     assert float((x32 - x64).norm() / x64.norm()) <= 1e-8
 
 
+@pytest.mark.parametrize("name,N,p,k", CASES)
+def test_scalar_hierarchy_and_solve_parity(nair, oracle_mod, name, N, p, k):
+    """Scalar nAIR: the scaled matrix D^{-1} A by degree of freedom and its whole
+    hierarchy bit for bit (patterns, C/F) and in value; the preconditioner
+    (cycle of D^{-1} v) on a seeded vector; forward and adjoint FGMRES
+    histories against the oracle."""
+    P = D.make_problem(name, N=N, p=p)
+    params = dict(neumann_degree=k)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), keep_setup_data=1, scalar=1,
+                        **params)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], scalar=True, **params)
+    compare_hierarchies(S, H, 1)
+    f = D.rng.uniform(17, P["n"]) - 0.5
+    z = S.vcycle(dev(f)).cpu().numpy()
+    zr = H.vcycle(f)
+    assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    x, rep = S.solve(dev(P["rhs"]))
+    ref = H.solve(P["rhs"])
+    assert ref["status"] == 0
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    assert rep["rel_res"] <= 1e-10
+    zt = S.adjoint_vcycle(dev(f)).cpu().numpy()
+    assert np.linalg.norm(zt - H.vcycle(f, transposed=True)) <= 1e-12 * np.linalg.norm(zt)
+    w = D.functional_weights(P["n"])
+    lam, repa = S.adjoint_solve(dev(w))
+    refa = H.solve(w, transposed=True)
+    assert repa["iterations"] == refa["iterations"]
+    assert np.max(np.abs(repa["history"] - refa["history"])) <= 1e-12
+    S.close()
+
+
+def test_scalar_mixed_precision(nair):
+    """Scalar nAIR in FP32 inside FP64 FGMRES, forward and adjoint."""
+    P = D.make_problem("C5", N=24, p=3)
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    rhs, w = dev(P["rhs"]), dev(D.functional_weights(P["n"]))
+    S64 = nair.NairSolver(*args, neumann_degree=2, scalar=1)
+    S32 = nair.NairSolver(*args, neumann_degree=2, scalar=1, precision="mixed")
+    x64, r64 = S64.solve(rhs)
+    x32, r32 = S32.solve(rhs)
+    assert r64["rel_res"] <= 1e-10 and r32["rel_res"] <= 1e-10
+    assert float((x32 - x64).norm() / x64.norm()) <= 1e-8
+    l64, a64 = S64.adjoint_solve(w)
+    l32, a32 = S32.adjoint_solve(w)
+    assert a64["rel_res"] <= 1e-10 and a32["rel_res"] <= 1e-10
+    assert float((l32 - l64).norm() / l64.norm()) <= 1e-8
+
+
 def test_autograd_against_finite_differences(nair):
     """dJ/dq and dJ/dsigma from the adjoint solve vs central differences
     (eps = 1e-6, forward solves to 1e-13) on seeded coordinates."""
