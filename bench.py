@@ -245,6 +245,67 @@ def timed_steps(fn, steps, flush, stream):
     return total / steps, out
 
 
+def conv_factor(rep):
+    """Average convergence factor per iteration from the residual history."""
+    h = rep["history"]
+    return float((h[-1] / h[0]) ** (1.0 / max(1, rep["iterations"]))) if len(h) > 1 else 0.0
+
+
+def measure_second_workload(nair, flush, stream, steps, device):
+    """The paper's non-constant flows b1, b2, b3 (one system each) and the angle
+    sweep: eight constant directions solved one after another and as one
+    concurrent batch (a host thread and a stream per direction)."""
+    import torch
+    res = {}
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    for name in ("F1", "F2", "F3"):
+        Pf = dgtransport.make_problem(name)
+        args = (dev(Pf["row_ptr"]), dev(Pf["col"]), dev(Pf["vals"]))
+        bf = dev(Pf["rhs"])
+
+        def ff(args=args, bf=bf, k=Pf["neumann_degree"]):
+            S = nair.NairSolver(*args, neumann_degree=k)
+            xx, rep = S.solve(bf)
+            S.close()
+            return xx, rep
+        ff()
+        ms, (xx, rep) = timed_steps(ff, steps, flush, stream)
+        res[f"flow_{name}_fp64"] = {"dofs": Pf["n"], "ms_per_step": ms, "mdof_s": Pf["n"] / (ms * 1e-3) / 1e6,
+                                    "setup_ms": rep["setup_ms"], "solve_ms": rep["solve_ms"],
+                                    "iterations": rep["iterations"], "rho": conv_factor(rep),
+                                    "rel_res": rep["rel_res"]}
+    angles = dgtransport.sweep_angles(8)
+    probs = [dgtransport.make_problem("D", theta=t) for t in angles]
+    systems = [(dev(Pd["row_ptr"]), dev(Pd["col"]), dev(Pd["vals"])) for Pd in probs]
+    rhs = [dev(Pd["rhs"]) for Pd in probs]
+    k = probs[0]["neumann_degree"]
+    total = sum(Pd["n"] for Pd in probs)
+
+    def seq():
+        reps = []
+        for sy, r in zip(systems, rhs):
+            S = nair.NairSolver(*sy, neumann_degree=k)
+            reps.append(S.solve(r)[1])
+            S.close()
+        return reps
+
+    def bat():
+        solvers = nair.setup_batch(systems, neumann_degree=k)
+        _, reps = nair.solve_batch(solvers, rhs)
+        for S in solvers:
+            S.close()
+        return reps
+    for label, fn in (("sweep8_sequential_fp64", seq), ("sweep8_batched_fp64", bat)):
+        fn()
+        ms, reps = timed_steps(fn, steps, flush, stream)
+        res[label] = {"directions": len(probs), "dofs_total": total, "ms_per_step": ms,
+                      "mdof_s": total / (ms * 1e-3) / 1e6,
+                      "theta": [round(t, 4) for t in angles],
+                      "iterations": [r["iterations"] for r in reps],
+                      "rho": [round(conv_factor(r), 4) for r in reps]}
+    return res
+
+
 def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps):
     """The mixed-precision form and the adjoint (forward + A^T solve) timed beside
     the FP64 solver on the same workload and tolerance."""
@@ -296,6 +357,7 @@ def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps
                       "solve_ms": rep["solve_ms"], "iterations": rep["iterations"], "rel_res": rep["rel_res"],
                       "cycle_complexity": rep["cycle_complexity"], "op_complexity": rep["op_complexity"],
                       "rel_diff_vs_fp64": float((xx - xref).norm() / xref.norm())}
+    res.update(measure_second_workload(nair, flush, stream, steps, bvec.device))
     lam_ref = None
     # the adjoint through the transposed forward hierarchy (default), and by a
     # second hierarchy built on A^T

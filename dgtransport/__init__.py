@@ -1,8 +1,9 @@
 """Seeded synthetic steady-transport problems (upwind DG on triangle meshes).
 
 The workloads follow the transport problems of Sec. 6.1 of the nAIR paper
-(arXiv 1704.05001): a unit-square domain, constant or rotating flow, element
-absorption sigma_t, source q = 1 and zero inflow.  The paper's own domains
+(arXiv 1704.05001): a unit-square domain, constant, rotating or the paper's
+non-constant flows b1-b3, element absorption sigma_t, source q = 1 and zero
+inflow.  The paper's own domains
 (*inset*, *block-source*) exist only in figures that are not available, so
 these seeded inputs stand in for them.  Nothing in this package computes any
 part of the multigrid method: it is shared input generation for the oracle,
@@ -11,7 +12,7 @@ the GPU library's tests and the benchmark.
 import numpy as np
 
 from . import rng
-from .dg import assemble, constant_flow, rotating_flow, RefElement, face_nodes  # noqa: F401
+from .dg import assemble, constant_flow, paper_flow, rotating_flow, RefElement, face_nodes  # noqa: F401
 
 # name -> (N, p, flow, sigma kind, jitter, order, method parameters)
 CONFIGS = {
@@ -31,7 +32,22 @@ CONFIGS = {
     # stated for this workload: 2 (with degree 1, GMRES(50) stalls near 1e-7)
     "C5": dict(N=512, p=3, flow=("rot",), sigma="lognormal", jitter=0.2,
                order="natural", neumann_degree=2),
+    # second workload: the paper's non-constant flows b1, b2, b3 (Sec. 6.2) on a
+    # P2, 256x256x2 jittered mesh, sigma_t = 1, Neumann degree 1 (paper default),
+    # elements in flow order where the flow graph has none
+    "F1": dict(N=256, p=2, flow=("b1",), sigma="one", jitter=0.2, order="auto", neumann_degree=1),
+    "F2": dict(N=256, p=2, flow=("b2",), sigma="one", jitter=0.2, order="auto", neumann_degree=1),
+    "F3": dict(N=256, p=2, flow=("b3",), sigma="one", jitter=0.2, order="auto", neumann_degree=1),
+    # one direction of the angle sweep (Sec. 6.2): constant b = (cos theta, sin
+    # theta), P2, 128x128x2 jittered; sweep_angles() gives the batch of theta
+    "D": dict(N=128, p=2, flow=("const", 3 * np.pi / 16), sigma="one", jitter=0.2,
+              order="topological", neumann_degree=1),
 }
+
+
+def sweep_angles(count=8):
+    """Directions of the angle sweep: theta_k = (k + 1/2) (pi / 2) / count."""
+    return [(k + 0.5) * 0.5 * np.pi / count for k in range(count)]
 
 JITTER_SEED = 1
 SIGMA_SEED = 2
@@ -48,8 +64,10 @@ def make_problem(name="C1", N=None, p=None, theta=None, keep_parts=False, g=0.0)
         cfg["p"] = p
     if cfg["flow"][0] == "const":
         flow = constant_flow(cfg["flow"][1] if theta is None else theta)
-    else:
+    elif cfg["flow"][0] == "rot":
         flow = rotating_flow
+    else:
+        flow = paper_flow(cfg["flow"][0])
     E = 2 * cfg["N"] * cfg["N"]
     if cfg["sigma"] == "one":
         sigma = 1.0

@@ -183,6 +183,22 @@ def constant_flow(theta):
     return f
 
 
+def paper_flow(kind):
+    """The non-constant flows of the paper's flow study (Sec. 6.2):
+    b1 = (cos^2(pi y), cos^2(pi x)), b2 = (sin^2(pi y), sin^2(pi x)),
+    b3 = (y^4, cos^2(pi x / 2)).  Both components are nonnegative, so the
+    flow has no closed streamlines."""
+    def b1(x, y):
+        return np.cos(np.pi * y) ** 2, np.cos(np.pi * x) ** 2
+
+    def b2(x, y):
+        return np.sin(np.pi * y) ** 2, np.sin(np.pi * x) ** 2
+
+    def b3(x, y):
+        return y ** 4, np.cos(0.5 * np.pi * x) ** 2
+    return {"b1": b1, "b2": b2, "b3": b3}[kind]
+
+
 def rotating_flow(x, y):
     """b = (0.5 - y, x - 0.5) / |.|, and b = 0 where |.| < 1e-14."""
     bx = 0.5 - y
@@ -308,10 +324,12 @@ def assemble(N, p, flow, sigma, q=1.0, g=0.0, jitter=0.0, jitter_seed=0,
     cf_col = hface[twin[inter]]
 
     # ---- ordering
-    if order == "topological":
+    if order in ("topological", "auto"):
         perm = topological_order(E, crow, ccol)
         if perm is None:
-            raise ValueError("flow graph has a cycle: no topological order")
+            if order == "topological":
+                raise ValueError("flow graph has a cycle: no topological order")
+            perm = np.arange(E, dtype=np.int64)
     elif order == "natural":
         perm = np.arange(E, dtype=np.int64)
     else:

@@ -161,6 +161,28 @@ nair_status nair_adjoint_vcycle(nair_handle *h, const double *f, double *x);
 /* Release every device allocation of the handle (NULL is ignored). */
 void nair_free(nair_handle *h);
 
+/* Batches of independent systems (for example the directions of a discrete-
+ * ordinates sweep, one A_k per direction).  Each system's work is issued by
+ * its own host thread on the stream of its own parameters, so give every
+ * system a distinct stream: the launch- and latency-bound parts of the systems
+ * (coarse levels, setup, Krylov read-backs) then overlap on the GPU.  count
+ * lies in 1..256.  Each call returns once every system is done; the status is
+ * NAIR_OK if all succeeded, else the first failing system's status (by index)
+ * with a message naming it.  Results are identical to separate calls.
+ * Profiling (nair_profile) must be off during batch calls. */
+
+/* Set up count systems: A[k] with parameters p[k]; out[k] receives the handles.
+ * On failure every handle of the batch is freed and out[] is all NULL. */
+nair_status nair_setup_batch(const nair_bsr *A, const nair_params *p, int32_t count, nair_handle **out);
+
+/* nair_solve(h[k], b[k], x[k], info + k) for every k (distinct handles); info may be NULL. */
+nair_status nair_solve_batch(nair_handle *const *h, int32_t count, const double *const *b, double *const *x,
+                             nair_info *info);
+
+/* nair_adjoint_solve(h[k], w[k], lambda[k], info + k) for every k (distinct handles). */
+nair_status nair_adjoint_solve_batch(nair_handle *const *h, int32_t count, const double *const *w,
+                                     double *const *lambda, nair_info *info);
+
 /* Number of levels of the hierarchy: the forward hierarchy when adjoint == 0,
  * the A^T hierarchy of NAIR_ADJOINT_REBUILD when adjoint == 1 (INVALID_ARG
  * before the first adjoint solve or in NAIR_ADJOINT_TRANSPOSED mode). */

@@ -67,7 +67,7 @@ EXPORTS = ["nair_default_params", "nair_setup", "nair_solve", "nair_adjoint_solv
            "nair_free", "nair_num_levels", "nair_level_sizes", "nair_get_level", "nair_block_inverse",
            "nair_assemble_sigma", "nair_mass_apply", "nair_gradients", "nair_kernel_launches",
            "nair_profile", "nair_profile_entry", "nair_block_inverse_noalloc", "nair_sweep_timing",
-           "nair_last_error"]
+           "nair_setup_batch", "nair_solve_batch", "nair_adjoint_solve_batch", "nair_last_error"]
 
 
 def lib():
@@ -86,6 +86,10 @@ def lib():
     L.nair_adjoint_solve.argtypes = [P, P, P, ctypes.POINTER(_Info)]
     L.nair_vcycle.argtypes = [P, P, P]
     L.nair_adjoint_vcycle.argtypes = [P, P, P]
+    L.nair_setup_batch.argtypes = [ctypes.POINTER(_Bsr), ctypes.POINTER(_Params), I32, ctypes.POINTER(P)]
+    L.nair_solve_batch.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(P), ctypes.POINTER(P),
+                                   ctypes.POINTER(_Info)]
+    L.nair_adjoint_solve_batch.argtypes = L.nair_solve_batch.argtypes
     L.nair_free.argtypes = [P]
     L.nair_free.restype = None
     L.nair_num_levels.argtypes = [P, I32, ctypes.POINTER(I32)]
@@ -160,40 +164,53 @@ def default_params():
     return p
 
 
+_ENUMS = {"precision": {"fp64": FP64, "mixed": MIXED},
+          "adjoint_mode": {"transposed": ADJOINT_TRANSPOSED, "rebuild": ADJOINT_REBUILD},
+          "cycle_type": {"V": CYCLE_V, "F": CYCLE_F}}
+
+
+def _make_params(params, stream=None):
+    """nair_params from the defaults and keyword overrides; the work goes to
+    ``stream`` (a torch.cuda.Stream) or to the current stream."""
+    p = default_params()
+    for k, v in params.items():
+        if isinstance(v, str) and k in _ENUMS:
+            v = _ENUMS[k][v]
+        if not hasattr(p, k) or k == "stream":
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    p.stream = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _stream()
+    return p
+
+
 class NairSolver:
     """nAIR hierarchy on the current CUDA device (setup at construction).
 
     row_ptr, col: int32 CUDA tensors; vals: float64 CUDA tensor (nnzb, b, b).
-    Keyword arguments set fields of nair_params (strength_theta, filter_tol,
+    ``stream`` (a torch.cuda.Stream, default: the current stream) carries all
+    of the solver's work.  Keyword arguments set fields of nair_params (strength_theta, filter_tol,
     neumann_degree, f_sweeps, c_sweeps, max_coarse, precision ("fp64" or
     "mixed"), gmres_restart, maxiter, tol, keep_setup_data, adjoint_mode
     ("transposed" or "rebuild"), cycle_type ("V" or "F"), scalar (0 or 1), ...).
     """
 
-    def __init__(self, row_ptr, col, vals, **params):
+    def __init__(self, row_ptr, col, vals, stream=None, _handle=None, **params):
         L = lib()
-        p = default_params()
-        for k, v in params.items():
-            if k == "precision" and isinstance(v, str):
-                v = {"fp64": FP64, "mixed": MIXED}[v]
-            if k == "adjoint_mode" and isinstance(v, str):
-                v = {"transposed": ADJOINT_TRANSPOSED, "rebuild": ADJOINT_REBUILD}[v]
-            if k == "cycle_type" and isinstance(v, str):
-                v = {"V": CYCLE_V, "F": CYCLE_F}[v]
-            if not hasattr(p, k):
-                raise TypeError(f"unknown parameter {k}")
-            setattr(p, k, v)
-        p.stream = _stream()
+        p = _make_params(params, stream)
         self.params = p
         self.b = int(vals.shape[-1])
         self.level_b = 1 if p.scalar else self.b  # block size of the hierarchy's levels
         self.E = int(row_ptr.shape[0] - 1)
         self.n = self.E * self.b
+        self.device = vals.device
+        self.stream = stream
+        if _handle is not None:  # adopted from nair_setup_batch
+            self._h = _handle
+            return
         A = _Bsr(self.E, self.b, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(vals))
         h = ctypes.c_void_p()
         _check(L.nair_setup(ctypes.byref(A), ctypes.byref(p), ctypes.byref(h)), "nair_setup")
         self._h = h
-        self.device = vals.device
 
     def close(self):
         if getattr(self, "_h", None):
@@ -220,11 +237,22 @@ class NairSolver:
                     op_complexity=info.op_complexity, cycle_complexity=info.cycle_complexity,
                     history=hist[:min(info.history_len, len(hist))].copy())
 
+    def _enter(self):
+        # the solver's own stream waits for the inputs made on the current stream
+        if self.stream is not None:
+            self.stream.wait_stream(torch.cuda.current_stream())
+
+    def _leave(self):
+        if self.stream is not None:
+            torch.cuda.current_stream().wait_stream(self.stream)
+
     def solve(self, b, x=None, check=True):
         """Solve A x = b (b: float64 CUDA tensor); returns (x, report)."""
         x = torch.zeros_like(b) if x is None else x
         info, hist = self._info(self.params.maxiter + self.params.maxiter // max(1, self.params.gmres_restart) + 4)
+        self._enter()
         st = lib().nair_solve(self._h, _ptr(b), _ptr(x), ctypes.byref(info))
+        self._leave()
         if check:
             _check(st, "nair_solve")
         return x, self._report(info, hist, st)
@@ -234,20 +262,26 @@ class NairSolver:
         (adjoint_mode "transposed") or the A^T hierarchy ("rebuild")."""
         lam = torch.zeros_like(w) if lam is None else lam
         info, hist = self._info(self.params.maxiter + self.params.maxiter // max(1, self.params.gmres_restart) + 4)
+        self._enter()
         st = lib().nair_adjoint_solve(self._h, _ptr(w), _ptr(lam), ctypes.byref(info))
+        self._leave()
         if check:
             _check(st, "nair_adjoint_solve")
         return lam, self._report(info, hist, st)
 
     def vcycle(self, f):
         x = torch.empty_like(f)
+        self._enter()
         _check(lib().nair_vcycle(self._h, _ptr(f), _ptr(x)), "nair_vcycle")
+        self._leave()
         return x
 
     def adjoint_vcycle(self, f):
         """The transposed cycle of the forward hierarchy: M^{-T} f."""
         x = torch.empty_like(f)
+        self._enter()
         _check(lib().nair_adjoint_vcycle(self._h, _ptr(f), _ptr(x)), "nair_adjoint_vcycle")
+        self._leave()
         return x
 
     def num_levels(self, adjoint=False):
@@ -311,6 +345,68 @@ class NairSolver:
                 d["L_ci"] = self._array(l, L_COL, np.int32, None, adjoint)
                 d["L_v"] = self._array(l, L_VALS, np.float64, (-1, b, b), adjoint)
         return d
+
+
+def _ptr_array(ts):
+    return (ctypes.c_void_p * len(ts))(*[_ptr(t).value for t in ts])
+
+
+def setup_batch(systems, streams=None, **params):
+    """Set up independent systems concurrently (nair_setup_batch).
+
+    systems: list of (row_ptr, col, vals) CUDA tensors; each system gets its
+    own stream (new torch.cuda.Stream objects unless ``streams`` is given).
+    Returns the NairSolver objects."""
+    count = len(systems)
+    if streams is None:
+        streams = [torch.cuda.Stream() for _ in range(count)]
+    cur = torch.cuda.current_stream()
+    for st in streams:
+        st.wait_stream(cur)  # the inputs were produced on the current stream
+    A = (_Bsr * count)()
+    P = (_Params * count)()
+    for k, (rp, ci, v) in enumerate(systems):
+        A[k] = _Bsr(int(rp.shape[0] - 1), int(v.shape[-1]), int(ci.shape[0]), _ptr(rp), _ptr(ci), _ptr(v))
+        P[k] = _make_params(params, streams[k])
+    hs = (ctypes.c_void_p * count)()
+    _check(lib().nair_setup_batch(A, P, count, hs), "nair_setup_batch")
+    return [NairSolver(rp, ci, v, stream=streams[k], _handle=ctypes.c_void_p(hs[k]), **params)
+            for k, (rp, ci, v) in enumerate(systems)]
+
+
+def _batch(fn, name, solvers, rhs, check):
+    count = len(solvers)
+    cur = torch.cuda.current_stream()
+    xs = [torch.zeros_like(r) for r in rhs]
+    for S in solvers:
+        if S.stream is not None:
+            S.stream.wait_stream(cur)
+    cap = max(S.params.maxiter + S.params.maxiter // max(1, S.params.gmres_restart) + 4 for S in solvers)
+    infos = (_Info * count)()
+    hists = []
+    for k in range(count):
+        h = np.zeros(cap)
+        hists.append(h)
+        infos[k].history = h.ctypes.data_as(ctypes.c_void_p)
+        infos[k].history_cap = cap
+    hs = (ctypes.c_void_p * count)(*[S._h.value for S in solvers])
+    st = fn(hs, count, _ptr_array(rhs), _ptr_array(xs), infos)
+    if check:
+        _check(st, name)
+    for S in solvers:
+        if S.stream is not None:
+            cur.wait_stream(S.stream)
+    return xs, [NairSolver._report(infos[k], hists[k], st) for k in range(count)]
+
+
+def solve_batch(solvers, rhs, check=True):
+    """Solve solvers[k] x_k = rhs[k] concurrently (nair_solve_batch); returns (xs, reports)."""
+    return _batch(lib().nair_solve_batch, "nair_solve_batch", solvers, rhs, check)
+
+
+def adjoint_solve_batch(solvers, w, check=True):
+    """Solve A_k^T lambda_k = w[k] concurrently (nair_adjoint_solve_batch)."""
+    return _batch(lib().nair_adjoint_solve_batch, "nair_adjoint_solve_batch", solvers, w, check)
 
 
 def block_inverse(A):

@@ -5,7 +5,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <thread>
 
 #include "solve.cuh"
 
@@ -146,16 +149,19 @@ __global__ void k_gradients(int E, int b, const double *__restrict__ M, const do
 // ---------------------------------------------------------------------------
 // handle construction
 // ---------------------------------------------------------------------------
+// keep freed stream-ordered memory in the device's default pool (once per device)
 static void init_pool_once() {
-  static bool done = false;
-  if (done) return;
+  static std::mutex m;
+  static std::set<int> done;
   int dev = 0;
   NAIR_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(m);
+  if (done.count(dev)) return;
   cudaMemPool_t pool;
   NAIR_CK(cudaDeviceGetDefaultMemPool(&pool, dev));
   uint64_t thr = UINT64_MAX;
   NAIR_CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-  done = true;
+  done.insert(dev);
 }
 
 static void check_params(const nair_params *p, int b) {
@@ -518,6 +524,80 @@ nair_status nair_adjoint_vcycle(nair_handle *h, const double *f, double *x) {
   else precond<double>(h->h64, h->P, f, x, h->s, h->n, true);
   NAIR_CK(cudaStreamSynchronize(h->s));
   return NAIR_OK;
+  NAIR_API_END
+}
+
+// ---------------------------------------------------------------------------
+// batches of independent systems: one host thread per system, each issuing its
+// system's work on that system's stream, so that the launch- and latency-bound
+// parts (coarse levels, setup, Krylov read-backs) of the systems overlap
+// ---------------------------------------------------------------------------
+static constexpr int kMaxBatch = 256;
+
+template <typename F>
+static nair_status run_batch(int count, F fn) {
+  int dev = 0;
+  NAIR_CK(cudaGetDevice(&dev));
+  std::vector<nair_status> st(count, NAIR_OK);
+  std::vector<std::string> msg(count);
+  std::vector<std::thread> th;
+  th.reserve(count);
+  for (int k = 0; k < count; ++k)
+    th.emplace_back([&, k] {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        st[k] = NAIR_ERR_CUDA;
+        msg[k] = "cudaSetDevice failed in a batch thread";
+        return;
+      }
+      st[k] = fn(k);
+      if (st[k] != NAIR_OK) msg[k] = g_last_error;
+    });
+  for (auto &t : th) t.join();
+  for (int k = 0; k < count; ++k)
+    if (st[k] != NAIR_OK) return set_error(st[k], "system " + std::to_string(k) + ": " + msg[k]);
+  g_last_error.clear();
+  return NAIR_OK;
+}
+
+nair_status nair_setup_batch(const nair_bsr *A, const nair_params *p, int32_t count, nair_handle **out) {
+  NAIR_API_BEGIN
+  if (!A || !p || !out) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (count < 1 || count > kMaxBatch) return set_error(NAIR_ERR_INVALID_ARG, "count must lie in 1..256");
+  for (int k = 0; k < count; ++k) out[k] = nullptr;
+  init_pool_once();
+  nair_status st = run_batch(count, [&](int k) { return nair_setup(&A[k], &p[k], &out[k]); });
+  if (st != NAIR_OK) {
+    for (int k = 0; k < count; ++k) {
+      nair_free(out[k]);
+      out[k] = nullptr;
+    }
+  }
+  return st;
+  NAIR_API_END
+}
+
+nair_status nair_solve_batch(nair_handle *const *h, int32_t count, const double *const *b, double *const *x,
+                             nair_info *info) {
+  NAIR_API_BEGIN
+  if (!h || !b || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (count < 1 || count > kMaxBatch) return set_error(NAIR_ERR_INVALID_ARG, "count must lie in 1..256");
+  for (int k = 0; k < count; ++k)
+    for (int j = 0; j < k; ++j)
+      if (h[j] == h[k]) return set_error(NAIR_ERR_INVALID_ARG, "a handle appears twice in the batch");
+  return run_batch(count, [&](int k) { return nair_solve(h[k], b[k], x[k], info ? &info[k] : nullptr); });
+  NAIR_API_END
+}
+
+nair_status nair_adjoint_solve_batch(nair_handle *const *h, int32_t count, const double *const *w,
+                                     double *const *lam, nair_info *info) {
+  NAIR_API_BEGIN
+  if (!h || !w || !lam) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (count < 1 || count > kMaxBatch) return set_error(NAIR_ERR_INVALID_ARG, "count must lie in 1..256");
+  for (int k = 0; k < count; ++k)
+    for (int j = 0; j < k; ++j)
+      if (h[j] == h[k]) return set_error(NAIR_ERR_INVALID_ARG, "a handle appears twice in the batch");
+  return run_batch(count,
+                   [&](int k) { return nair_adjoint_solve(h[k], w[k], lam[k], info ? &info[k] : nullptr); });
   NAIR_API_END
 }
 

@@ -12,7 +12,12 @@ namespace nair {
 void fail(nair_status st, const std::string &msg) { throw NairError{st, msg}; }
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;  // launches issued by this host thread
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+long long thread_launch_count() { return t_launches; }
 void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 

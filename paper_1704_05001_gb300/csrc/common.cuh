@@ -34,6 +34,7 @@ void ck_fail(cudaError_t e, const char *what, const char *file, int line);
 void count_launch();
 void add_launches(long long n);
 long long launch_count();
+long long thread_launch_count();  // this host thread's launches (graph capture counts)
 #define NAIR_LAUNCH_CHECK()        \
   do {                             \
     ::nair::count_launch();        \

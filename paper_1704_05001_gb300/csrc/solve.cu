@@ -723,7 +723,7 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n, bool t
   VGraph &g = transposed ? H.tgraph : H.graph;
   NAIR_CK(cudaMalloc(&g.dptr, 2 * sizeof(void *)));
   NAIR_CK(cudaMallocHost(&g.hptr, 2 * sizeof(void *)));
-  const long long before = launch_count();
+  const long long before = thread_launch_count();
   cudaGraph_t graph;
   // capture on a private stream (the caller's may be the legacy default stream,
   // which cannot be captured); the graph is launched on the caller's stream
@@ -747,7 +747,7 @@ static void capture_graph(const Hier<T> &H, const Params &P, long long n, bool t
     throw;
   }
   NAIR_CK(cudaStreamEndCapture(s, &graph));
-  g.nodes = launch_count() - before;
+  g.nodes = thread_launch_count() - before;
   add_launches(-g.nodes);  // captured, not launched
   cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);

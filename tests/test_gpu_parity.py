@@ -415,6 +415,68 @@ def test_scalar_mixed_precision(nair):
     assert float((l32 - l64).norm() / l64.norm()) <= 1e-8
 
 
+@pytest.mark.parametrize("name", ["F1", "F2", "F3"])
+def test_paper_flows_parity(nair, oracle_mod, name):
+    """The flows b1, b2, b3 of the paper's flow study: hierarchy bit for bit and
+    the residual history against the oracle."""
+    P = D.make_problem(name, N=12)
+    params = dict(neumann_degree=1, max_coarse=4)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), keep_setup_data=1, **params)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params)
+    compare_hierarchies(S, H, P["b"])
+    x, rep = S.solve(dev(P["rhs"]))
+    ref = H.solve(P["rhs"])
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    S.close()
+
+
+def test_direction_batch(nair, oracle_mod):
+    """Eight directions of the angle sweep set up and solved concurrently (one
+    host thread and one stream per system): every result equals the separate
+    call bit for bit, and each history matches the oracle."""
+    probs = [D.make_problem("D", N=10, theta=t) for t in D.sweep_angles(8)]
+    systems = [(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"])) for P in probs]
+    rhs = [dev(P["rhs"]) for P in probs]
+    w = [dev(D.functional_weights(P["n"])) for P in probs]
+    params = dict(neumann_degree=1, max_coarse=4)
+    solvers = nair.setup_batch(systems, **params)
+    xs, reps = nair.solve_batch(solvers, rhs)
+    lams, repas = nair.adjoint_solve_batch(solvers, w)
+    for k, P in enumerate(probs):
+        S1 = nair.NairSolver(*systems[k], **params)
+        x1, r1 = S1.solve(rhs[k])
+        l1, a1 = S1.adjoint_solve(w[k])
+        assert torch.equal(xs[k], x1) and torch.equal(lams[k], l1)
+        assert reps[k]["iterations"] == r1["iterations"] and repas[k]["iterations"] == a1["iterations"]
+        ref = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params).solve(P["rhs"])
+        assert reps[k]["iterations"] == ref["iterations"]
+        assert np.max(np.abs(reps[k]["history"] - ref["history"])) <= 1e-12
+        S1.close()
+    for S in solvers:
+        S.close()
+
+
+def test_batch_errors(nair):
+    """A failing system fails the whole batch with its index (a singular
+    diagonal block, made on the host); a handle listed twice is rejected."""
+    probs = [D.make_problem("D", N=6, theta=t) for t in D.sweep_angles(3)]
+    systems = [(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"])) for P in probs]
+    bad = probs[1]["vals"].copy()
+    bad[probs[1]["row_ptr"][4]:probs[1]["row_ptr"][5]] = 0.0  # block row 4, diagonal included
+    systems[1] = (systems[1][0], systems[1][1], dev(bad))
+    with pytest.raises(nair.NairError) as e:
+        nair.setup_batch(systems)
+    assert e.value.status == 2 and "system 1" in str(e.value)
+    good = nair.setup_batch([systems[0], systems[2]])
+    rhs = dev(probs[0]["rhs"])
+    with pytest.raises(nair.NairError) as e:
+        nair.solve_batch([good[0], good[0]], [rhs, rhs])
+    assert e.value.status == 1
+    for S in good:
+        S.close()
+
+
 def test_autograd_against_finite_differences(nair):
     """dJ/dq and dJ/dsigma from the adjoint solve vs central differences
     (eps = 1e-6, forward solves to 1e-13) on seeded coordinates."""
