@@ -791,8 +791,10 @@ static void spmv(int b, const Bsr *A, const double *x, double *y) {
     }
 }
 
-/* one block-Jacobi sweep on the rows with cf == which (Eq. relax):
- * x_i <- x_i + D_ii^{-1} (f - A x)_i, every row from the sweep's starting x */
+/* one block-Jacobi sweep on the rows with cf == which (Eq. relax with M the
+ * block diagonal D): x_i <- x_i + D_ii^{-1} (f - A x)_i, every row from the
+ * sweep's starting x, in its classical form x_i <- D_ii^{-1} (f_i - sum_{j != i}
+ * A_ij x_j) (the same map, since D_ii^{-1} A_ii = I) */
 static void jacobi(int b, const Level *L, int which, const double *f, double *x, double *tmp) {
   size_t bb = (size_t)b * b;
   const Bsr *A = &L->A;
@@ -803,6 +805,7 @@ static void jacobi(int b, const Level *L, int which, const double *f, double *x,
     for (int r = 0; r < b; ++r) {
       double s = f[(size_t)i * b + r];
       for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+        if (A->ci[p] == i) continue;
         const double *a = A->v + (size_t)p * bb + r * b;
         const double *xj = tmp + (size_t)A->ci[p] * b;
         for (int c = 0; c < b; ++c) s -= a[c] * xj[c];
@@ -813,7 +816,7 @@ static void jacobi(int b, const Level *L, int which, const double *f, double *x,
     for (int r = 0; r < b; ++r) {
       double s = 0.0;
       for (int c = 0; c < b; ++c) s += d[r * b + c] * res[c];
-      x[(size_t)i * b + r] += s;
+      x[(size_t)i * b + r] = s;
     }
   }
 }
@@ -917,11 +920,27 @@ static void spmv_t(int b, const Bsr *A, const double *x, double *y) {
     }
 }
 
-/* one block-Jacobi sweep on A^T over the rows with cf == which:
- * x_i <- x_i + (D_ii^{-1})^T (f - A^T x)_i, every row from the sweep's starting x */
+/* y = (A - D)^T x: A^T without its diagonal blocks */
+static void spmv_t_off(int b, const Bsr *A, const double *x, double *y) {
+  size_t bb = (size_t)b * b;
+  memset(y, 0, sizeof(double) * (size_t)A->ncols * b);
+  for (int i = 0; i < A->nrows; ++i)
+    for (int p = A->rp[i]; p < A->rp[i + 1]; ++p) {
+      if (A->ci[p] == i) continue;
+      const double *a = A->v + (size_t)p * bb;
+      double *yj = y + (size_t)A->ci[p] * b;
+      const double *xi = x + (size_t)i * b;
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) yj[c] += a[r * b + c] * xi[r];
+    }
+}
+
+/* one block-Jacobi sweep on A^T over the rows with cf == which, in the same
+ * classical form: x_i <- (D_ii^{-1})^T (f - (A - D)^T x)_i, every row from the
+ * sweep's starting x */
 static void jacobi_t(int b, const Level *L, int which, const double *f, double *x, double *tmp) {
   size_t bb = (size_t)b * b;
-  spmv_t(b, &L->A, x, tmp);
+  spmv_t_off(b, &L->A, x, tmp);
   for (int i = 0; i < L->A.nrows; ++i) {
     if (L->cf[i] != which) continue;
     double res[32];
@@ -931,7 +950,7 @@ static void jacobi_t(int b, const Level *L, int which, const double *f, double *
     for (int r = 0; r < b; ++r) {
       double s = 0.0;
       for (int c = 0; c < b; ++c) s += d[c * b + r] * res[c];
-      xi[r] += s;
+      xi[r] = s;
     }
   }
 }

@@ -33,7 +33,9 @@ MUTATIONS = [
      "if (best < 0 || L->snorm[p] < bs) { best = j; bs = L->snorm[p]; }"),
     ("A P merge: later blocks overwrite instead of add", "c[k] = c[k] + a[k];", "c[k] = a[k];"),
     ("L: sign of -D^-1 A lost", "o[r * b + c] = -s;", "o[r * b + c] = s;"),
-    ("Jacobi: correction subtracted", "x[(size_t)i * b + r] += s;", "x[(size_t)i * b + r] -= s;"),
+    ("Jacobi: off-diagonal coupling added", "for (int c = 0; c < b; ++c) s -= a[c] * xj[c];",
+     "for (int c = 0; c < b; ++c) s += a[c] * xj[c];"),
+    ("Jacobi: old iterate kept", "x[(size_t)i * b + r] = s;", "x[(size_t)i * b + r] += s;"),
     ("F-relaxation: one sweep short",
      "for (int s = 0; s < H->f_sweeps; ++s) jacobi(b, L, 0, f, x, tmp);",
      "for (int s = 1; s < H->f_sweeps; ++s) jacobi(b, L, 0, f, x, tmp);"),
