@@ -153,14 +153,15 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
 # launch, averaged over the 40 sweeps of one C2 V-cycle: dram__bytes_read.sum +
 # dram__bytes_write.sum); set to None whenever the kernel changes until recaptured.
-JACOBI_TRAFFIC = 22.93e6
+JACOBI_TRAFFIC = None
 
 
 def level_work(S, nlev, b):
     """Algorithmic FP64 work of every block-Jacobi sweep scope, from the hierarchy.
 
-    A sweep over the rows of one class (F or C) at level l does one FMA per
-    exact nonzero of those rows of A_l and b^2 FMAs per row for D^{-1}; its
+    A sweep over the rows of one class (F or C) at level l computes
+    x_i = D_ii^{-1} (f_i - sum_{j != i} A_ij x_j): one FMA per exact nonzero of
+    the off-diagonal blocks of those rows and b^2 FMAs per row for D^{-1}; its
     algorithmic bytes are those nonzeros (8 B), their block column indices
     (4 B per block), the rows' D^{-1} blocks and right-hand side, and one read
     and one write of the level vector."""
@@ -169,11 +170,12 @@ def level_work(S, nlev, b):
         lev = S.level(l)
         if lev["coarsest"]:
             continue
-        rp, vals, cf = lev["row_ptr"], lev["vals"], lev["cf"]
+        rp, ci, vals, cf = lev["row_ptr"], lev["col"], lev["vals"], lev["cf"]
         nnz_block = np.count_nonzero(vals.reshape(len(vals), -1), axis=1)
         rows = np.repeat(np.arange(lev["E"]), np.diff(rp))
+        off = ci != rows
         for cls, name in ((0, "jacobi_F"), (1, "jacobi_C")):
-            sel = cf[rows] == cls
+            sel = (cf[rows] == cls) & off
             nrow = int(np.count_nonzero(cf == cls))
             nnz = int(nnz_block[sel].sum())
             flops = 2.0 * (nnz + nrow * b * b)

@@ -73,12 +73,12 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // dependency wait, because the matrix does not change during a V-cycle
 template <typename T, int B>
 __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int p0, int p1, int r, int j0,
-                                         const T *va0) {
+                                         const T *va0, int skip) {
   const int b = B > 0 ? B : a.b;
   const int bb = b * b;
   T acc = 0;
   if constexpr (B > 0) {
-    if (p0 < p1 && j0 >= 0) {
+    if (p0 < p1 && j0 >= 0 && p0 != skip) {
       const T *xj = a.x + (size_t)j0 * B;
       T vx[B];
 #pragma unroll
@@ -88,6 +88,7 @@ __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int p0, int p1, in
     }
 #pragma unroll 2
     for (int p = p0 + a.G; p < p1; p += a.G) {
+      if (p == skip) continue;
       int j = a.ci[p];
       if (a.ipc) {
         j = a.ipc[j];
@@ -103,6 +104,7 @@ __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int p0, int p1, in
     }
   } else {
     for (int p = p0; p < p1; p += a.G) {
+      if (p == skip) continue;
       const int j = a.ci[p];
       const T *av = a.v + (size_t)p * bb + r * b;
 #pragma unroll 4
@@ -166,13 +168,15 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
       for (int c = 0; c < B; ++c) dv[c] = d[c];
     }
   }
-  if (OP == OP_JACOBI && active && g == 0) ii = a.ipc ? a.ipc[i] : i;
+  // JACOBI works in the classical form x_i = D_ii^{-1} (f_i - sum_{j != i} A_ij x_j):
+  // the diagonal block is skipped and x_i is not read
+  const int skip = (OP == OP_JACOBI && active) ? a.diag[i] : -1;
   if ((OP == OP_RESTRICT || OP == OP_INTERP_T) && active && g == 0) ii = a.c2f[i];
   // ---- wait for the producer of x and f
   pdl_wait();
   if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
   T acc = 0;
-  if (active) acc = row_partial<T, B>(a, p0, p1, r, j0, va0);
+  if (active) acc = row_partial<T, B>(a, p0, p1, r, j0, va0, skip);
   if (a.G > 1) {  // pairwise tree over the G partial sums (G is a power of two)
     T *tr = red + (size_t)team * tsz;
     if (team < a.tpc) tr[lt] = acc;
@@ -199,7 +203,6 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
     if (active && g == 0) sres[(size_t)team * b + r] = a.f[(size_t)i * b + r] - acc;
     __syncthreads();
     if (active && g == 0) {
-      T xi = a.ipc ? (ii >= 0 ? a.x[(size_t)ii * b + r] : (T)0) : a.x[(size_t)i * b + r];
       const T *sr = sres + (size_t)team * b;
       T s = 0;
       if constexpr (B > 0) {
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
         const T *d = a.dinv + (size_t)i * b * b + r * b;
         for (int c = 0; c < b; ++c) s = fma(d[c], sr[c], s);
       }
-      a.out[(size_t)i * b + r] = xi + s;
+      a.out[(size_t)i * b + r] = s;
     }
   }
   if (a.stamp) {
@@ -250,14 +253,18 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
   // ---- prologue on data that is constant during the V-cycle
   const int i = active ? (a.list ? a.list[idx] : idx) : 0;
   const int q0 = active ? a.rp[i] - i : 0, q1 = active ? a.rp[i + 1] - i - 1 : 0;
-  T dv[B], drow[OP == OP_JACOBI ? B : 1], ov0[W];
+  // JACOBI: the classical form x_i = D_ii^{-1} (f_i - sum_{j != i} A_ij x_j)
+  // needs neither the diagonal block nor x_i
+  constexpr bool kDiag = OP != OP_JACOBI;
+  T dv[kDiag ? B : 1], drow[OP == OP_JACOBI ? B : 1], ov0[W];
   int j0 = -1;
   unsigned long long cols0 = 0;
-  int ii = i;
   if (active) {
-    const T *dp = a.v + (size_t)a.diag[i] * B * B + r * B;
+    if constexpr (kDiag) {
+      const T *dp = a.v + (size_t)a.diag[i] * B * B + r * B;
 #pragma unroll
-    for (int c = 0; c < B; ++c) dv[c] = dp[c];
+      for (int c = 0; c < B; ++c) dv[c] = dp[c];
+    }
     if (OP == OP_JACOBI) {
       const T *dd = a.dinv + (size_t)i * B * B + r * B;
 #pragma unroll
@@ -271,25 +278,20 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
 #pragma unroll
       for (int w = 0; w < W; ++w) ov0[w] = o[w];
     }
-    if (a.ipc) ii = a.ipc[i];
   }
   // ---- wait for the producer of x and f
   pdl_wait();
   if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
-  T acc = 0, xr = 0;
+  T acc = 0;
   if (active) {
-    T xv[B];
-    if (ii >= 0) {
-      const T *xi = a.x + (size_t)ii * B;
+    if constexpr (kDiag) {  // SPMV / RESID: x is never read through ipc
+      const T *xi = a.x + (size_t)i * B;
+      T xv[B];
 #pragma unroll
       for (int c = 0; c < B; ++c) xv[c] = xi[c];
-      xr = xi[r];
-    } else {
 #pragma unroll
-      for (int c = 0; c < B; ++c) xv[c] = 0;
+      for (int c = 0; c < B; ++c) acc = fma(dv[c], xv[c], acc);
     }
-#pragma unroll
-    for (int c = 0; c < B; ++c) acc = fma(dv[c], xv[c], acc);
     if (q0 < q1 && j0 >= 0) {
       const T *xj = a.x + (size_t)j0 * B;
 #pragma unroll
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
       T s2 = 0;
 #pragma unroll
       for (int c = 0; c < B; ++c) s2 = fma(drow[c], sres[team * B + c], s2);
-      a.out[(size_t)i * B + r] = xr + s2;
+      a.out[(size_t)i * B + r] = s2;
     }
   }
   if (a.stamp) {

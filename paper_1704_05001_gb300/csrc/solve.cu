@@ -260,6 +260,7 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
     a.ipc = (k == 0) ? ipc0 : nullptr;
     a.f = f;
     a.dinv = L.dinv;
+    a.diag = L.diag;
     a.nrows = nrow[cls];
     a.list = rows[cls];
     a.out = buf[ob];
@@ -406,6 +407,7 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
       a.x = buf[1 - ob];
       a.f = f;
       a.dinv = TL.dinvT;
+      a.diag = TL.diag;
       a.nrows = nrow[cls];
       a.list = rows[cls];
       a.out = buf[ob];
