@@ -128,6 +128,14 @@ void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cu
   NAIR_CK(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 
+// Programmatic dependent launch: let the next kernel of the stream be
+// scheduled now, and wait for the previous kernel's results before reading them.
+// Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // exclusive scan of n ints into out[0..n]; out[n] = total; returns the total
 // (synchronises the stream to read it back when want_total is set)
 int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, Mem &tmp, bool want_total = true);

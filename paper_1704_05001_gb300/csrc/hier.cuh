@@ -63,15 +63,14 @@ void build_l0comp(const DBsr<T> &A, const int *diag, int b, cudaStream_t s, Mem 
 struct VGraph {
   cudaGraphExec_t exec = nullptr;
   void **dptr = nullptr;  // device: [0] input (double*), [1] output (double*)
-  void **hptr = nullptr;  // pinned host staging of the two pointers
   long long nodes = 0;    // kernels per replay
 };
 
 // device-clock stamps of the block-Jacobi sweeps: slot s holds the earliest
 // start and the latest end of the sweep with site index s = level * S + k
 struct SweepClock {
-  unsigned long long *dev = nullptr;   // [2 * nsites]: starts, then ends
-  unsigned long long *host = nullptr;  // pinned copy
+  unsigned long long *dev = nullptr;      // [2 * nsites]: starts, then ends
+  unsigned long long *slot[2] = {};       // pinned copies of two consecutive cycles
   int nsites = 0, S = 0;
   std::vector<long long> count;        // per (level, class)
   std::vector<double> ms;

@@ -60,13 +60,6 @@ __device__ __forceinline__ T xval(const T *__restrict__ x, const int *__restrict
   return x[(size_t)j * bt + c];
 }
 
-// Programmatic dependent launch: let the next kernel of the stream be
-// scheduled now, and wait for the previous kernel's results before reading them.
-// Without the launch attribute both are no-ops.
-__device__ __forceinline__ void pdl_launch_dependents() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // partial sum of row i over the blocks p = p0, p0 + G, ... < p1; the first
 // block's column, interpolation target and values (va0) were loaded before the

@@ -845,34 +845,57 @@ static constexpr int kGjThreads = 1024;
 
 // in-place Gauss-Jordan with partial pivoting on an n x n matrix held by one
 // thread block (in shared or global memory); same arithmetic as the block inverse
+// pivot-search key of |x| in row r of pivot column k: IEEE bit patterns of
+// non-negative doubles order like the values, so the search runs on the
+// integer pipe; a NaN ranks lowest below the diagonal (a comparison with it is
+// false) and highest on it (nothing compares greater); 0 marks no candidate
+__device__ __forceinline__ unsigned long long pivot_key(double x, bool diag) {
+  const unsigned long long a = abs_key(x);
+  return a > 0x7FF0000000000000ull ? (diag ? ~0ull : 1ull) : a + 1ull;
+}
+
+// (key, row) pair with the larger key, the smaller row on ties
+__device__ __forceinline__ void pivot_max(unsigned long long &key, int &row, unsigned long long k2, int r2) {
+  if (k2 > key || (k2 == key && r2 < row)) {
+    key = k2;
+    row = r2;
+  }
+}
+
 __device__ void dense_gj_cta(int n, double *__restrict__ M, int *__restrict__ piv,
                              double *__restrict__ lcol, int *__restrict__ err) {
-  __shared__ double rv[kGjThreads / 32];
+  __shared__ unsigned long long rv[kGjThreads / 32];
   __shared__ int ri[kGjThreads / 32];
   __shared__ int pk;
   __shared__ double dk;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   for (int k = 0; k < n; ++k) {
-    double best = -1.0;
+    // pivot: first row of largest |M[r][k]|, r >= k (integer keys, two shuffle levels)
+    unsigned long long key = 0;
     int bi = n;
-    for (int r = k + tid; r < n; r += blockDim.x) {
-      double a = fabs(M[(size_t)r * n + k]);
-      if (a > best || (a == best && r < bi)) { best = a; bi = r; }
-    }
+    for (int r = k + tid; r < n; r += blockDim.x) pivot_max(key, bi, pivot_key(M[(size_t)r * n + k], r == k), r);
     for (int o = 16; o; o >>= 1) {
-      double ob = __shfl_down_sync(0xffffffffu, best, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+      const int r2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      pivot_max(key, bi, k2, r2);
     }
-    if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+    if (lane == 0) {
+      rv[wid] = key;
+      ri[wid] = bi;
+    }
     __syncthreads();
-    if (tid == 0) {
-      double b0 = rv[0];
-      int i0 = ri[0];
-      for (int w = 1; w < (int)(blockDim.x / 32); ++w)
-        if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
-      pk = i0;
-      piv[k] = i0;
+    if (wid == 0) {
+      key = lane < nw ? rv[lane] : 0ull;
+      bi = lane < nw ? ri[lane] : n;
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        const int r2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        pivot_max(key, bi, k2, r2);
+      }
+      if (lane == 0) {
+        pk = bi;
+        piv[k] = bi;
+      }
     }
     __syncthreads();
     const int p = pk;
@@ -923,11 +946,6 @@ __device__ void dense_gj_cta(int n, double *__restrict__ M, int *__restrict__ pi
   }
 }
 
-__global__ void __launch_bounds__(kGjThreads) k_dense_gj(int n, double *__restrict__ M, int *__restrict__ piv,
-                                                         double *__restrict__ lcol, int *__restrict__ err) {
-  dense_gj_cta(n, M, piv, lcol, err);
-}
-
 // the same, with the matrix staged in shared memory (small coarsest levels)
 __global__ void __launch_bounds__(kGjThreads) k_dense_gj_smem(int n, double *__restrict__ Mg, int *__restrict__ err) {
   extern __shared__ double sm[];
@@ -949,29 +967,27 @@ static constexpr int kGjTileRows = 16, kGjTileCols = 256;
 __global__ void __launch_bounds__(256) k_gj_step(int n, int k, const double *__restrict__ Min,
                                                  double *__restrict__ Mout, int *__restrict__ piv,
                                                  int *__restrict__ err) {
-  __shared__ double rv[8];
+  __shared__ unsigned long long rv[8];
   __shared__ int ri[8];
   __shared__ int sp;
   __shared__ double prow[kGjTileCols];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  double best = -1.0;
+  pdl_launch_dependents();
+  pdl_wait();  // Min is the previous step's output, Mout its input
+  unsigned long long key = 0;
   int bi = n;
-  for (int r = k + tid; r < n; r += blockDim.x) {
-    double a = fabs(Min[(size_t)r * n + k]);
-    if (a > best || (a == best && r < bi)) { best = a; bi = r; }
-  }
+  for (int r = k + tid; r < n; r += blockDim.x) pivot_max(key, bi, pivot_key(Min[(size_t)r * n + k], r == k), r);
   for (int o = 16; o; o >>= 1) {
-    double ob = __shfl_down_sync(0xffffffffu, best, o);
-    int oi = __shfl_down_sync(0xffffffffu, bi, o);
-    if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+    const int r2 = __shfl_xor_sync(0xffffffffu, bi, o);
+    pivot_max(key, bi, k2, r2);
   }
-  if (lane == 0) { rv[wid] = best; ri[wid] = bi; }
+  if (lane == 0) { rv[wid] = key; ri[wid] = bi; }
   __syncthreads();
   if (tid == 0) {
-    double b0 = rv[0];
+    unsigned long long k0 = rv[0];
     int i0 = ri[0];
-    for (int w = 1; w < (int)(blockDim.x / 32); ++w)
-      if (rv[w] > b0 || (rv[w] == b0 && ri[w] < i0)) { b0 = rv[w]; i0 = ri[w]; }
+    for (int w = 1; w < (int)(blockDim.x / 32); ++w) pivot_max(k0, i0, rv[w], ri[w]);
     sp = i0;
   }
   __syncthreads();
@@ -1559,20 +1575,19 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
     NAIR_LAUNCH_CHECK();
   }
   int *piv = tmp.alloc<int>(n);
+  // one thread block in shared memory for small matrices; beyond that the
+  // elimination (n^3 FMAs on one SM's FP64 pipe) is spread over thread blocks,
+  // one launch per step, consecutive steps overlapping their launch latency
   const size_t gj_smem = (size_t)n * n * sizeof(double) + (size_t)n * (sizeof(double) + sizeof(int));
-  if (gj_smem <= 200 * 1024) {
+  if (n <= 48) {
     NAIR_CK(cudaFuncSetAttribute(k_dense_gj_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem));
     k_dense_gj_smem<<<1, kGjThreads, gj_smem, s>>>(n, M, err);
-    NAIR_LAUNCH_CHECK();
-  } else if (n <= 256) {
-    double *lcol = tmp.alloc<double>(n);
-    k_dense_gj<<<1, kGjThreads, 0, s>>>(n, M, piv, lcol, err);
     NAIR_LAUNCH_CHECK();
   } else {
     double *M2 = tmp.alloc<double>((size_t)n * n);
     dim3 g(cdiv(n, kGjTileCols), cdiv(n, kGjTileRows));
     for (int k = 0; k < n; ++k) {
-      k_gj_step<<<g, 256, 0, s>>>(n, k, M, M2, piv, err);
+      launch_pdl(k_gj_step, g, dim3(256), 0, s, n, k, (const double *)M, M2, piv, err);
       NAIR_LAUNCH_CHECK();
       std::swap(M, M2);
     }

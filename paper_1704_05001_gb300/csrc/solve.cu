@@ -587,6 +587,17 @@ __global__ void k_div(long long n, const double *__restrict__ w, double d, doubl
   if (i < n) out[i] = w[i] / d;
 }
 
+// out = w / ||w|| from the squared norm on the device (IEEE sqrt and division,
+// the values the host would compute); zero when the norm is zero (breakdown:
+// the host ends the cycle at this column and never uses out)
+__global__ void k_div_norm(long long n, const double *__restrict__ w, const double *__restrict__ nrm2,
+                           double *__restrict__ out) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double d = sqrt(*nrm2);
+  out[i] = d != 0.0 ? w[i] / d : 0.0;
+}
+
 template <typename A, typename B>
 __global__ void k_cast(long long n, const A *__restrict__ in, B *__restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -610,10 +621,19 @@ void Krylov::ensure(long long n_, int m_, cudaStream_t s) {
   ydev = mem.alloc<double>(m + 1);
   if (hhost) cudaFreeHost(hhost);
   NAIR_CK(cudaMallocHost(&hhost, sizeof(double) * (2 * (m + 2) + 2 + m + 1)));
+  for (int q = 0; q < 2; ++q) {
+    if (slot[q]) cudaFreeHost(slot[q]);
+    NAIR_CK(cudaMallocHost(&slot[q], sizeof(double) * (2 * (m + 1) + 1)));
+    if (!ev[q]) NAIR_CK(cudaEventCreateWithFlags(&ev[q], cudaEventDisableTiming));
+  }
 }
 
 Krylov::~Krylov() {
   if (hhost) cudaFreeHost(hhost);
+  for (int q = 0; q < 2; ++q) {
+    if (slot[q]) cudaFreeHost(slot[q]);
+    if (ev[q]) cudaEventDestroy(ev[q]);
+  }
 }
 
 static void multidot(Krylov &K, long long n, int nv, const double *V, const double *w, double *out,
@@ -623,6 +643,11 @@ static void multidot(Krylov &K, long long n, int nv, const double *V, const doub
   NAIR_LAUNCH_CHECK();
   k_reduce_partials<<<nv, 32, 0, s>>>(nv, kDotCtas, K.partial, out);
   NAIR_LAUNCH_CHECK();
+}
+
+__global__ void k_set_ptrs(void **dptr, const double *v, double *z) {
+  dptr[0] = const_cast<double *>(v);
+  dptr[1] = z;
 }
 
 template <typename T>
@@ -643,7 +668,8 @@ __global__ void k_copy_out(long long n, const T *__restrict__ src, void *const *
 
 void release_clock(SweepClock &c) {
   if (c.dev) cudaFree(c.dev);
-  if (c.host) cudaFreeHost(c.host);
+  for (auto sl : c.slot)
+    if (sl) cudaFreeHost(sl);
   c = SweepClock();
 }
 
@@ -660,22 +686,29 @@ static void clock_init(const Hier<T> &H, const Params &P) {
   c.S = P.f_sweeps + P.c_sweeps;
   c.nsites = std::max(1, H.nlev * c.S);
   NAIR_CK(cudaMalloc(&c.dev, sizeof(unsigned long long) * 2 * c.nsites));
-  NAIR_CK(cudaMallocHost(&c.host, sizeof(unsigned long long) * 2 * c.nsites));
+  for (auto &sl : c.slot) NAIR_CK(cudaMallocHost(&sl, sizeof(unsigned long long) * 2 * c.nsites));
   c.count.assign(2 * H.nlev, 0);
   c.ms.assign(2 * H.nlev, 0.0);
 }
 
-// after the stream has been synchronised: add the stamped sweep durations
+// queue a copy of the stamps of the cycle just enqueued into pinned slot q
 template <typename T>
-static void clock_collect(const Hier<T> &H, const Params &P, cudaStream_t s) {
+static void clock_stage(const Hier<T> &H, int q, cudaStream_t s) {
+  const SweepClock &c = H.clock;
+  if (!c.dev) return;
+  NAIR_CK(cudaMemcpyAsync(c.slot[q], c.dev, sizeof(unsigned long long) * 2 * c.nsites, cudaMemcpyDeviceToHost, s));
+}
+
+// once slot q's copy has completed: add the stamped sweep durations
+template <typename T>
+static void clock_collect(const Hier<T> &H, const Params &P, int q) {
   SweepClock &c = H.clock;
   if (!c.dev) return;
-  NAIR_CK(cudaMemcpyAsync(c.host, c.dev, sizeof(unsigned long long) * 2 * c.nsites, cudaMemcpyDeviceToHost, s));
-  NAIR_CK(cudaStreamSynchronize(s));
+  const unsigned long long *h = c.slot[q];
   for (int l = 0; l < H.nlev; ++l)
     for (int k = 0; k < c.S; ++k) {
       const int site = l * c.S + k;
-      const unsigned long long t0 = c.host[site], t1 = c.host[c.nsites + site];
+      const unsigned long long t0 = h[site], t1 = h[c.nsites + site];
       if (t1 == 0 || t0 == ~0ULL || t1 < t0) continue;
       const int cls = k < P.f_sweeps ? 0 : 1;
       c.count[2 * l + cls] += 1;
@@ -686,7 +719,6 @@ static void clock_collect(const Hier<T> &H, const Params &P, cudaStream_t s) {
 void release_graph(VGraph &g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
   if (g.dptr) cudaFree(g.dptr);
-  if (g.hptr) cudaFreeHost(g.hptr);
   g = VGraph();
 }
 
@@ -724,7 +756,6 @@ template <typename T>
 static void capture_graph(const Hier<T> &H, const Params &P, long long n, bool transposed) {
   VGraph &g = transposed ? H.tgraph : H.graph;
   NAIR_CK(cudaMalloc(&g.dptr, 2 * sizeof(void *)));
-  NAIR_CK(cudaMallocHost(&g.hptr, 2 * sizeof(void *)));
   const long long before = thread_launch_count();
   cudaGraph_t graph;
   // capture on a private stream (the caller's may be the legacy default stream,
@@ -763,9 +794,10 @@ void precond(const Hier<T> &H, const Params &P, const double *v, double *z, cuda
   if (P.use_graphs && !prof_on()) {
     VGraph &g = transposed ? H.tgraph : H.graph;
     if (!g.exec) capture_graph<T>(H, P, n, transposed);
-    g.hptr[0] = const_cast<double *>(v);
-    g.hptr[1] = z;
-    NAIR_CK(cudaMemcpyAsync(g.dptr, g.hptr, 2 * sizeof(void *), cudaMemcpyHostToDevice, s));
+    // the pointers travel as kernel arguments (copied at launch), so the host
+    // may queue the next replay before this one has started
+    k_set_ptrs<<<1, 1, 0, s>>>(g.dptr, v, z);
+    NAIR_LAUNCH_CHECK();
     NAIR_CK(cudaGraphLaunch(g.exec, s));
     add_launches(g.nodes);
     return;
@@ -837,6 +869,39 @@ nair_status fgmres(const Outer &op, const Hier<T> &H, const Params &P, Krylov &K
     return NAIR_OK;
   }
   double *V = K.V, *Z = K.Z, *w = K.w;
+  // one Arnoldi step for column j: z_j = M^{-1} v_j, w = A z_j, classical
+  // Gram-Schmidt twice, ||w||^2; the Hessenberg column is copied to pinned slot
+  // j mod 2 (event ev[j mod 2]) and v_{j+1} = w / ||w|| is formed on the device
+  auto arnoldi_step = [&](int j) {
+    const int q = j & 1;
+    double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+    {
+      ProfScope ps("vcycle", s);
+      precond<T>(H, P, vj, zj, s, n, transposed);
+    }
+    if (!transposed) clock_stage(H, q, s);
+    spmv64(A, b, zj, nullptr, w, s, C, diag0);
+    multidot(K, n, j + 1, V, w, K.hdev, s);
+    {
+      ProfScope ps("axpy_multi", s);
+      k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev, w);
+      NAIR_LAUNCH_CHECK();
+    }
+    multidot(K, n, j + 1, V, w, K.hdev + (m + 1), s);
+    {
+      ProfScope ps("axpy_multi", s);
+      k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev + (m + 1), w);
+      NAIR_LAUNCH_CHECK();
+    }
+    multidot(K, n, 1, w, w, K.hdev + 2 * (m + 1), s);
+    {
+      ProfScope ps("arnoldi_readback", s);
+      NAIR_CK(cudaMemcpyAsync(K.slot[q], K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
+      NAIR_CK(cudaEventRecord(K.ev[q], s));
+    }
+    k_div_norm<<<grid(n), kThreads, 0, s>>>(n, w, K.hdev + 2 * (m + 1), V + (size_t)(j + 1) * n);
+    NAIR_LAUNCH_CHECK();
+  };
   for (;;) {
     spmv64(A, b, x, bvec, w, s, C, diag0);
     multidot(K, n, 1, w, w, K.hdev, s);
@@ -853,43 +918,23 @@ nair_status fgmres(const Outer &op, const Hier<T> &H, const Params &P, Krylov &K
     std::fill(Hm.begin(), Hm.end(), 0.0);
     g[0] = beta;
     int j;
-    bool conv = false, brk = false;
+    bool conv = false, brk = false, queued = false;
     for (j = 0; j < m && it < P.maxiter; ++j) {
-      double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
-      {
-        ProfScope ps("vcycle", s);
-        precond<T>(H, P, vj, zj, s, n, transposed);
-      }
+      // column j (if not already in flight), then column j + 1 before column j's
+      // Hessenberg entries are read: the host's read-back and Givens work
+      // overlap the next iteration on the GPU.  A column enqueued past
+      // convergence or breakdown is never used.
+      if (!queued) arnoldi_step(j);
       ++it;
-      spmv64(A, b, zj, nullptr, w, s, C, diag0);
-      // classical Gram-Schmidt, twice
-      multidot(K, n, j + 1, V, w, K.hdev, s);
-      {
-        ProfScope ps("axpy_multi", s);
-        k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev, w);
-        NAIR_LAUNCH_CHECK();
-      }
-      multidot(K, n, j + 1, V, w, K.hdev + (m + 1), s);
-      {
-        ProfScope ps("axpy_multi", s);
-        k_axpy_multi<<<grid(n), kThreads, 0, s>>>(n, j + 1, V, n, K.hdev + (m + 1), w);
-        NAIR_LAUNCH_CHECK();
-      }
-      multidot(K, n, 1, w, w, K.hdev + 2 * (m + 1), s);
-      {
-        ProfScope ps("arnoldi_readback", s);
-        NAIR_CK(cudaMemcpyAsync(hh, K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
-      }
-      NAIR_CK(cudaStreamSynchronize(s));
-      if (!transposed) clock_collect(H, P, s);
-      for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hh[k] + hh[m + 1 + k];
-      const double hn = std::sqrt(hh[2 * (m + 1)]);
+      queued = j + 1 < m && it < P.maxiter;
+      if (queued) arnoldi_step(j + 1);
+      NAIR_CK(cudaEventSynchronize(K.ev[j & 1]));
+      const double *hq = K.slot[j & 1];
+      if (!transposed) clock_collect(H, P, j & 1);
+      for (int k = 0; k <= j; ++k) Hm[(size_t)k * m + j] = hq[k] + hq[m + 1 + k];
+      const double hn = std::sqrt(hq[2 * (m + 1)]);
       if (!std::isfinite(hn)) return NAIR_ERR_BREAKDOWN;
       Hm[(size_t)(j + 1) * m + j] = hn;
-      if (hn != 0.0) {
-        k_div<<<grid(n), kThreads, 0, s>>>(n, w, hn, V + (size_t)(j + 1) * n);
-        NAIR_LAUNCH_CHECK();
-      }
       for (int k = 0; k < j; ++k) {
         double a = Hm[(size_t)k * m + j], c = Hm[(size_t)(k + 1) * m + j];
         Hm[(size_t)k * m + j] = cs[k] * a + sn[k] * c;

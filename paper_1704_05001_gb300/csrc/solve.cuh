@@ -9,13 +9,17 @@
 namespace nair {
 
 // FGMRES(m) workspace: basis V (m + 1 vectors), preconditioned vectors Z (m),
-// one work vector, Arnoldi partial sums and a pinned host staging buffer
+// one work vector, Arnoldi partial sums, a pinned host staging buffer and two
+// pinned read-back slots (with their events) for the Hessenberg columns of
+// two consecutive iterations, which are in flight together
 struct Krylov {
   Mem mem;
   long long n = 0;
   int m = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *partial = nullptr, *hdev = nullptr,
          *ydev = nullptr, *hhost = nullptr;
+  double *slot[2] = {};
+  cudaEvent_t ev[2] = {};
   void ensure(long long n, int m, cudaStream_t s);
   ~Krylov();
 };
