@@ -592,10 +592,9 @@ __global__ void k_div(long long n, const double *__restrict__ w, double d, doubl
 // the host ends the cycle at this column and never uses out)
 __global__ void k_div_norm(long long n, const double *__restrict__ w, const double *__restrict__ nrm2,
                            double *__restrict__ out) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double d = sqrt(*nrm2);
-  out[i] = d != 0.0 ? w[i] / d : 0.0;
+  const double d = sqrt(*nrm2);  // once per thread: a grid-stride loop over the vector
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = d != 0.0 ? w[i] / d : 0.0;
 }
 
 template <typename A, typename B>
@@ -899,7 +898,8 @@ nair_status fgmres(const Outer &op, const Hier<T> &H, const Params &P, Krylov &K
       NAIR_CK(cudaMemcpyAsync(K.slot[q], K.hdev, sizeof(double) * (2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
       NAIR_CK(cudaEventRecord(K.ev[q], s));
     }
-    k_div_norm<<<grid(n), kThreads, 0, s>>>(n, w, K.hdev + 2 * (m + 1), V + (size_t)(j + 1) * n);
+    k_div_norm<<<std::min(grid(n), 4 * kDotCtas), kThreads, 0, s>>>(n, w, K.hdev + 2 * (m + 1),
+                                                                    V + (size_t)(j + 1) * n);
     NAIR_LAUNCH_CHECK();
   };
   for (;;) {
