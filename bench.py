@@ -153,7 +153,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
 # launch, averaged over the 40 sweeps of one C2 V-cycle: dram__bytes_read.sum +
 # dram__bytes_write.sum); set to None whenever the kernel changes until recaptured.
-JACOBI_TRAFFIC = 19.61e6
+JACOBI_TRAFFIC = None
 
 
 def level_work(S, nlev, b):
@@ -164,7 +164,12 @@ def level_work(S, nlev, b):
     the off-diagonal blocks of those rows and b^2 FMAs per row for D^{-1}; its
     algorithmic bytes are those nonzeros (8 B), their block column indices
     (4 B per block), the rows' D^{-1} blocks and right-hand side, and one read
-    and one write of the level vector."""
+    and one write of the level vector.
+
+    Level 0 with column-compressed coupling blocks (W of b columns) sweeps with
+    the couplings scaled in advance, x_i = g_i - sum_j (D_ii^{-1} A_ij) x_j with
+    g = D^{-1} f: b W FMAs per coupling block and no D^{-1} apply; its bytes are
+    the scaled blocks, their column indices, g and the vector."""
     work = {}
     for l in range(nlev):
         lev = S.level(l)
@@ -174,14 +179,34 @@ def level_work(S, nlev, b):
         nnz_block = np.count_nonzero(vals.reshape(len(vals), -1), axis=1)
         rows = np.repeat(np.arange(lev["E"]), np.diff(rp))
         off = ci != rows
+        W = l0_width(vals[off], b) if l == 0 else 0
         for cls, name in ((0, "jacobi_F"), (1, "jacobi_C")):
             sel = (cf[rows] == cls) & off
             nrow = int(np.count_nonzero(cf == cls))
-            nnz = int(nnz_block[sel].sum())
-            flops = 2.0 * (nnz + nrow * b * b)
-            byts = 8.0 * nnz + 4.0 * int(sel.sum()) + 8.0 * nrow * b * (b + 1) + 16.0 * lev["E"] * b
+            nblk = int(sel.sum())
+            if W:
+                flops = 2.0 * nblk * b * W
+                byts = 8.0 * nblk * b * W + 4.0 * nblk + 8.0 * nrow * b + 16.0 * lev["E"] * b
+            else:
+                nnz = int(nnz_block[sel].sum())
+                flops = 2.0 * (nnz + nrow * b * b)
+                byts = 8.0 * nnz + 4.0 * nblk + 8.0 * nrow * b * (b + 1) + 16.0 * lev["E"] * b
             work[f"{name}@L{l}"] = (flops, byts)
     return work
+
+
+# (b, W) pairs with a level-0 column-compressed kernel (P1 to P6 DG blocks)
+L0_WIDTHS = {3: 2, 6: 3, 10: 4, 15: 5, 21: 6, 28: 7}
+
+
+def l0_width(offblocks, b):
+    """W of the level-0 column compression (0 when the library does not compress):
+    the largest number of nonzero columns of an off-diagonal block, raised to
+    the width the kernels provide."""
+    if b not in L0_WIDTHS or len(offblocks) == 0:
+        return 0
+    w = int(np.count_nonzero(np.any(offblocks != 0, axis=1), axis=1).max())
+    return L0_WIDTHS[b] if max(w, 1) <= L0_WIDTHS[b] else 0
 
 
 def roofline(nair, params, rp, ci, v, sweep_ms):

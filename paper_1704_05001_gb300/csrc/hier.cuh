@@ -37,8 +37,9 @@ struct Level {
   // coarsest level: dense inverse
   int n = 0;
   T *ainv = nullptr;
-  // cycle vectors: right-hand side, iterate, second sweep buffer, residual
-  T *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr;
+  // cycle vectors: right-hand side, iterate, second sweep buffer, residual;
+  // level 0 with scaled couplings also g = D^{-1} f
+  T *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr, *g = nullptr;
 };
 
 // Level-0 off-diagonal blocks restricted to their nonzero columns.  An upwind
@@ -52,10 +53,15 @@ struct L0Comp {
   int *oci = nullptr;                // block column of each off-diagonal block
   unsigned long long *ocols = nullptr;  // W local column indices, 8 bits each
   T *ov = nullptr;                   // (nnzb - E) x b x W values
+  T *sv = nullptr;                   // the same blocks scaled, D_ii^{-1} A_ij (forward sweeps)
 };
 
 template <typename T>
 void build_l0comp(const DBsr<T> &A, const int *diag, int b, cudaStream_t s, Mem &mem, L0Comp<T> &C);
+
+// C.sv = D_ii^{-1} A_ij for every compressed off-diagonal block (dinv: E blocks)
+template <typename T>
+void build_l0scaled(const DBsr<T> &A, const T *dinv, int b, cudaStream_t s, Mem &mem, L0Comp<T> &C);
 
 // The V-cycle replayed as one CUDA graph: it reads its input from and writes its
 // output to the two device pointers in dptr (set before each launch), so one

@@ -17,7 +17,10 @@ namespace nair {
 
 // OP_INTERP_T: out_i = f_i + sum_j v_ij x_j + (c2f[i] >= 0 ? x[c2f[i]] : 0), the
 // interpolation x_fine += R^T x_c of the transposed cycle (c2f: own coarse index)
-enum RowOp { OP_SPMV = 0, OP_RESID = 1, OP_JACOBI = 2, OP_RESTRICT = 3, OP_INTERP_T = 4 };
+// OP_JACOBI_S (level-0 form only): the block-Jacobi sweep with the couplings
+// scaled in advance, x_i = g_i - sum_{j != i} (D_ii^{-1} A_ij) x_j, g = D^{-1} f
+// (a.f = g, a.ov = the scaled compressed blocks)
+enum RowOp { OP_SPMV = 0, OP_RESID = 1, OP_JACOBI = 2, OP_RESTRICT = 3, OP_INTERP_T = 4, OP_JACOBI_S = 5 };
 
 template <typename T>
 struct RowArgs {
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
 template <typename T, int B, int W, int OP>
 __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
   pdl_launch_dependents();
-  if (OP == OP_JACOBI && (int)blockIdx.x >= a.comp_ctas) {
+  if ((OP == OP_JACOBI || OP == OP_JACOBI_S) && (int)blockIdx.x >= a.comp_ctas) {
     const long long g = (long long)(blockIdx.x - a.comp_ctas) * blockDim.x + threadIdx.x;
     const bool in = g < (long long)a.ncopy * B;
     const int row = in ? (int)(g / B) : 0, r = in ? (int)(g - (long long)row * B) : 0;
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
   const int q0 = active ? a.rp[i] - i : 0, q1 = active ? a.rp[i + 1] - i - 1 : 0;
   // JACOBI: the classical form x_i = D_ii^{-1} (f_i - sum_{j != i} A_ij x_j)
   // needs neither the diagonal block nor x_i
-  constexpr bool kDiag = OP != OP_JACOBI;
+  constexpr bool kDiag = OP != OP_JACOBI && OP != OP_JACOBI_S;
   T dv[kDiag ? B : 1], drow[OP == OP_JACOBI ? B : 1], ov0[W];
   int j0 = -1;
   unsigned long long cols0 = 0;
@@ -308,7 +311,7 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
   }
   if (OP == OP_SPMV) {
     if (active) a.out[(size_t)i * B + r] = acc;
-  } else if (OP == OP_RESID) {
+  } else if (OP == OP_RESID || OP == OP_JACOBI_S) {
     if (active) a.out[(size_t)i * B + r] = a.f[(size_t)i * B + r] - acc;
   } else {
     if (active) sres[team * B + r] = a.f[(size_t)i * B + r] - acc;

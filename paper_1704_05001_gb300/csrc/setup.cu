@@ -1112,6 +1112,46 @@ void build_l0comp(const DBsr<T> &A, const int *diag, int b, cudaStream_t s, Mem 
 template void build_l0comp<double>(const DBsr<double> &, const int *, int, cudaStream_t, Mem &, L0Comp<double> &);
 template void build_l0comp<float>(const DBsr<float> &, const int *, int, cudaStream_t, Mem &, L0Comp<float> &);
 
+// row of every compressed off-diagonal block: row i owns q in [rp[i] - i, rp[i + 1] - i - 1)
+__global__ void k_l0_qrow(int E, const int *__restrict__ rp, int *__restrict__ qrow) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  for (int q = rp[i] - i; q < rp[i + 1] - i - 1; ++q) qrow[q] = i;
+}
+
+// sv[q][r][w] = sum_t dinv[i][r][t] ov[q][t][w], accumulated in FP64
+template <typename T>
+__global__ void k_l0_scale(long long total, int b, int W, const int *__restrict__ qrow, const T *__restrict__ dinv,
+                           const T *__restrict__ ov, T *__restrict__ sv) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  const int bw = b * W;
+  const long long q = g / bw;
+  const int rw = (int)(g - q * bw), r = rw / W, w = rw - r * W;
+  const T *d = dinv + (size_t)qrow[q] * b * b + (size_t)r * b;
+  const T *o = ov + (size_t)q * bw + w;
+  double acc = 0.0;
+  for (int t = 0; t < b; ++t) acc = fma((double)d[t], (double)o[(size_t)t * W], acc);
+  sv[g] = (T)acc;
+}
+
+template <typename T>
+void build_l0scaled(const DBsr<T> &A, const T *dinv, int b, cudaStream_t s, Mem &mem, L0Comp<T> &C) {
+  if (C.W <= 0) return;
+  const int E = A.nrows, noff = A.nnzb - E;
+  Mem tmp;
+  tmp.s = s;
+  int *qrow = tmp.alloc<int>(noff);
+  k_l0_qrow<<<grid1d(E), kThreads, 0, s>>>(E, A.rp, qrow);
+  NAIR_LAUNCH_CHECK();
+  const long long tot = (long long)noff * b * C.W;
+  C.sv = mem.alloc<T>((size_t)tot);
+  k_l0_scale<T><<<grid1d(tot), kThreads, 0, s>>>(tot, b, C.W, qrow, dinv, C.ov, C.sv);
+  NAIR_LAUNCH_CHECK();
+}
+template void build_l0scaled<double>(const DBsr<double> &, const double *, int, cudaStream_t, Mem &, L0Comp<double> &);
+template void build_l0scaled<float>(const DBsr<float> &, const float *, int, cudaStream_t, Mem &, L0Comp<float> &);
+
 // ---------------------------------------------------------------------------
 // host orchestration
 // ---------------------------------------------------------------------------
@@ -1632,7 +1672,12 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
   }
   H.nlev = (int)H.lev.size();
   check_flag(err, s, NAIR_ERR_SINGULAR_BLOCK, "singular diagonal block or coarsest-level matrix");
-  if (!H.lev[0].coarsest) build_l0comp<T>(H.lev[0].A, H.lev[0].diag, H.b, s, mem, H.l0c);
+  if (!H.lev[0].coarsest) {
+    build_l0comp<T>(H.lev[0].A, H.lev[0].diag, H.b, s, mem, H.l0c);
+    // level-0 sweeps with the couplings scaled in advance (they then skip the
+    // b^2 FMAs per row of the D^{-1} apply)
+    build_l0scaled<T>(H.lev[0].A, H.lev[0].dinv, H.b, s, mem, H.l0c);
+  }
   // V-cycle vectors and complexities (Sec. 6: OC and CC in work units)
   const int b = H.b;
   double nnz0 = (double)H.lev[0].A.nnzb, oc = 0.0, cc = 0.0;
@@ -1643,6 +1688,7 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     L.x = mem.alloc<T>(n);
     L.x2 = mem.alloc<T>(n);
     L.r = mem.alloc<T>(n);
+    if (l == 0 && H.l0c.sv) L.g = mem.alloc<T>(n);
     double a = (double)L.A.nnzb / nnz0;
     oc += a;
     // visits of level l per cycle: 1 in a V-cycle; 1 + l in an F-cycle (one

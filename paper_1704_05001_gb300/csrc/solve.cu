@@ -117,7 +117,7 @@ void launch_rowop_l0(RowArgs<T> a, int W, cudaStream_t s) {
   const int threads = a.tpc * b;
   a.comp_ctas = cdiv(a.nrows, a.tpc);
   int blocks = a.comp_ctas;
-  if (OP == OP_JACOBI && a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
+  if ((OP == OP_JACOBI || OP == OP_JACOBI_S) && a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
   if (blocks == 0) return;
   const dim3 gr(blocks), bl(threads);
   if (b == 3 && W == 2) launch_pdl(k_rowop_l0<T, 3, 2, OP>, gr, bl, 0, s, a);
@@ -251,6 +251,14 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
   const int nrow[2] = {L.nF, L.nC};
   const int *rows[2] = {L.fsweep, L.csweep};
   int cur_ver[2] = {0, 0};  // version of each class (0 = the sweeps' starting iterate)
+  // level 0 with scaled couplings: g = D^{-1} f once, then x_i = g_i - sum_j S_ij x_j
+  const bool scaled = comp && H.l0c.sv && L.g;
+  if (scaled) {
+    ProfScope ps("dinv_f", s, l);
+    launch_pdl(k_bdiag_apply<T>, dim3(grid((long long)L.E * b)), dim3(kThreads), 0, s, L.E, b,
+               (const T *)L.dinv, f, L.g, 0);
+    NAIR_LAUNCH_CHECK();
+  }
   // device-clock stamps only in V-cycles, where every sweep site runs once per cycle
   const bool stamp = H.clock.dev && P.cycle == 0;
   for (int k = 0; k < S; ++k) {
@@ -274,7 +282,14 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       a.ns = H.clock.nsites;
     }
     ProfScope ps(cls == 0 ? "jacobi_F" : "jacobi_C", s, l);
-    if (comp) {
+    if (scaled) {
+      a.f = L.g;
+      a.diag = L.diag;
+      a.oci = H.l0c.oci;
+      a.ocols = H.l0c.ocols;
+      a.ov = H.l0c.sv;
+      launch_rowop_l0<T, OP_JACOBI_S>(a, H.l0c.W, s);
+    } else if (comp) {
       a.diag = L.diag;
       a.oci = H.l0c.oci;
       a.ocols = H.l0c.ocols;
