@@ -153,7 +153,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
 # launch, averaged over the 40 sweeps of one C2 V-cycle: dram__bytes_read.sum +
 # dram__bytes_write.sum); set to None whenever the kernel changes until recaptured.
-JACOBI_TRAFFIC = None
+JACOBI_TRAFFIC = 17.16e6
 
 
 def level_work(S, nlev, b):
