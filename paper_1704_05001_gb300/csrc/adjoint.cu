@@ -20,6 +20,7 @@ static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
 // block-CSR transpose: counts per column, scan, scatter, per-row sort
 // ---------------------------------------------------------------------------
 __global__ void k_t_count(int nnzb, const int *__restrict__ ci, int *__restrict__ cnt) {
+  pdl_wait();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < nnzb) atomicAdd(&cnt[ci[p]], 1);
 }
@@ -27,6 +28,7 @@ __global__ void k_t_count(int nnzb, const int *__restrict__ ci, int *__restrict_
 __global__ void k_t_fill(int nr, const int *__restrict__ rp, const int *__restrict__ ci,
                          const int *__restrict__ trp, int *__restrict__ fill, int *__restrict__ tci,
                          int *__restrict__ tsrc) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nr) return;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
@@ -40,6 +42,7 @@ __global__ void k_t_fill(int nr, const int *__restrict__ rp, const int *__restri
 // sort each row by column, carrying a companion index when given (insertion
 // sort: the rows of a transposed DG operator are short)
 __global__ void k_sort_rows(int n, const int *__restrict__ rp, int *__restrict__ ci, int *__restrict__ comp) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   for (int a = rp[i] + 1; a < rp[i + 1]; ++a) {
@@ -59,6 +62,7 @@ __global__ void k_sort_rows(int n, const int *__restrict__ rp, int *__restrict__
 template <typename T>
 __global__ void k_t_vals(long long total, int b, const int *__restrict__ tsrc, const T *__restrict__ v,
                          T *__restrict__ tv) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -70,6 +74,7 @@ __global__ void k_t_vals(long long total, int b, const int *__restrict__ tsrc, c
 // every b x b block transposed in place of position
 template <typename T>
 __global__ void k_block_transpose(long long total, int b, const T *__restrict__ in, T *__restrict__ out) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -81,6 +86,7 @@ __global__ void k_block_transpose(long long total, int b, const T *__restrict__ 
 // C elements: own coarse index; F elements: -1
 __global__ void k_cself(int E, const signed char *__restrict__ cf, const int *__restrict__ ipc,
                         int *__restrict__ cself) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < E) cself[i] = cf[i] ? ipc[i] : -1;
 }
@@ -88,12 +94,14 @@ __global__ void k_cself(int E, const signed char *__restrict__ cf, const int *__
 // P^T lists: F elements that interpolate from coarse point J
 __global__ void k_pt_count(int E, const signed char *__restrict__ cf, const int *__restrict__ ipc,
                            int *__restrict__ cnt) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < E && !cf[i] && ipc[i] >= 0) atomicAdd(&cnt[ipc[i]], 1);
 }
 
 __global__ void k_pt_fill(int E, const signed char *__restrict__ cf, const int *__restrict__ ipc,
                           const int *__restrict__ prp, int *__restrict__ fill, int *__restrict__ pci) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E || cf[i] || ipc[i] < 0) return;
   const int J = ipc[i];
@@ -115,17 +123,17 @@ void bsr_transpose(const DBsr<T> &A, int b, DBsr<T> &out, cudaStream_t s, Mem &m
   NAIR_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * (nc + 1), s));
   NAIR_CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nc + 1), s));
   if (nnzb) {
-    k_t_count<<<grid(nnzb), kThreads, 0, s>>>(nnzb, A.ci, cnt);
+    launch_pdl(k_t_count, dim3(grid(nnzb)), dim3(kThreads), 0, s, nnzb, A.ci, cnt);
     NAIR_LAUNCH_CHECK();
   }
   exclusive_scan(cnt, out.rp, nc, s, tmp, false);
   if (nnzb) {
-    k_t_fill<<<grid(nr), kThreads, 0, s>>>(nr, A.rp, A.ci, out.rp, fill, out.ci, tsrc);
+    launch_pdl(k_t_fill, dim3(grid(nr)), dim3(kThreads), 0, s, nr, A.rp, A.ci, out.rp, fill, out.ci, tsrc);
     NAIR_LAUNCH_CHECK();
-    k_sort_rows<<<grid(nc), kThreads, 0, s>>>(nc, out.rp, out.ci, tsrc);
+    launch_pdl(k_sort_rows, dim3(grid(nc)), dim3(kThreads), 0, s, nc, out.rp, out.ci, tsrc);
     NAIR_LAUNCH_CHECK();
     const long long tot = (long long)nnzb * b * b;
-    k_t_vals<T><<<grid(tot), kThreads, 0, s>>>(tot, b, tsrc, A.v, out.v);
+    launch_pdl(k_t_vals<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, tsrc, A.v, out.v);
     NAIR_LAUNCH_CHECK();
   }
 }
@@ -145,7 +153,7 @@ void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem) {
     const int E = L.E;
     const long long tb = (long long)E * b * b;
     TL.dinvT = mem.alloc<T>((size_t)tb);
-    k_block_transpose<T><<<grid(tb), kThreads, 0, s>>>(tb, b, L.dinv, TL.dinvT);
+    launch_pdl(k_block_transpose<T>, dim3(grid(tb)), dim3(kThreads), 0, s, tb, b, L.dinv, TL.dinvT);
     NAIR_LAUNCH_CHECK();
     if (l == 0 || !L.coarsest) {
       // A_l^T: level 0's is also the operator of the outer Krylov solve
@@ -157,7 +165,7 @@ void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem) {
       if (L.ainv) {
         const long long nn = (long long)L.n * L.n;
         TL.ainvT = mem.alloc<T>((size_t)nn);
-        k_block_transpose<T><<<grid(nn), kThreads, 0, s>>>(nn, L.n, L.ainv, TL.ainvT);
+        launch_pdl(k_block_transpose<T>, dim3(grid(nn)), dim3(kThreads), 0, s, nn, L.n, L.ainv, TL.ainvT);
         NAIR_LAUNCH_CHECK();
       }
       continue;
@@ -171,20 +179,20 @@ void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem) {
     R.ncols = E;
     bsr_transpose<T>(R, b, TL.Rt, s, mem);
     TL.cself = mem.alloc<int>(E);
-    k_cself<<<grid(E), kThreads, 0, s>>>(E, L.cf, L.ipc, TL.cself);
+    launch_pdl(k_cself, dim3(grid(E)), dim3(kThreads), 0, s, E, L.cf, L.ipc, TL.cself);
     NAIR_LAUNCH_CHECK();
     // P^T: for each coarse point the F elements interpolating from it
     int *cnt = tmp.alloc<int>(nC + 1), *fill = tmp.alloc<int>(nC + 1);
     NAIR_CK(cudaMemsetAsync(cnt, 0, sizeof(int) * (nC + 1), s));
     NAIR_CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nC + 1), s));
-    k_pt_count<<<grid(E), kThreads, 0, s>>>(E, L.cf, L.ipc, cnt);
+    launch_pdl(k_pt_count, dim3(grid(E)), dim3(kThreads), 0, s, E, L.cf, L.ipc, cnt);
     NAIR_LAUNCH_CHECK();
     TL.pt_rp = mem.alloc<int>(nC + 1);
     exclusive_scan(cnt, TL.pt_rp, nC, s, tmp, false);
     TL.pt_ci = mem.alloc<int>(nF);  // at most one entry per F element
-    k_pt_fill<<<grid(E), kThreads, 0, s>>>(E, L.cf, L.ipc, TL.pt_rp, fill, TL.pt_ci);
+    launch_pdl(k_pt_fill, dim3(grid(E)), dim3(kThreads), 0, s, E, L.cf, L.ipc, TL.pt_rp, fill, TL.pt_ci);
     NAIR_LAUNCH_CHECK();
-    k_sort_rows<<<grid(nC), kThreads, 0, s>>>(nC, TL.pt_rp, TL.pt_ci, nullptr);
+    launch_pdl(k_sort_rows, dim3(grid(nC)), dim3(kThreads), 0, s, nC, TL.pt_rp, TL.pt_ci, nullptr);
     NAIR_LAUNCH_CHECK();
     TL.r = mem.alloc<T>((size_t)E * b);
   }

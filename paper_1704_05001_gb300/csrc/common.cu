@@ -174,6 +174,7 @@ __device__ __forceinline__ int cta_exclusive_scan(int v, int *warp_sums, int *to
 // case) the total into out[n]
 __global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, int n,
                              int *__restrict__ tile_sums) {
+  pdl_wait();
   __shared__ int warp_sums[kScanThreads / 32];
   __shared__ int total;
   const long long base = (long long)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
@@ -200,6 +201,7 @@ __global__ void k_scan_tiles(const int *__restrict__ in, int *__restrict__ out, 
 
 // adds the scanned tile offsets; offs[tiles] is the total, copied to out[n]
 __global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__ tile_off, int tiles) {
+  pdl_wait();
   const long long base = (long long)blockIdx.x * kScanTile;
   const int add = tile_off[blockIdx.x];
   for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
@@ -209,22 +211,23 @@ __global__ void k_scan_add(int *__restrict__ out, int n, const int *__restrict__
   if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_off[tiles];
 }
 
-__global__ void k_scan_zero(int *out) { out[0] = 0; }
+__global__ void k_scan_zero(int *out) {
+  pdl_wait(); out[0] = 0; }
 
 // out[0..n) = exclusive prefix of in, out[n] = total
 static void scan_rec(const int *in, int *out, int n, cudaStream_t s, Mem &tmp) {
   const int tiles = cdiv(n, kScanTile);
   if (tiles <= 1) {
-    k_scan_tiles<<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+    launch_pdl(k_scan_tiles, dim3(1), dim3(kScanThreads), 0, s, in, out, n, nullptr);
     NAIR_LAUNCH_CHECK();
     return;
   }
   int *sums = tmp.alloc<int>(tiles + 1);
-  k_scan_tiles<<<tiles, kScanThreads, 0, s>>>(in, out, n, sums);
+  launch_pdl(k_scan_tiles, dim3(tiles), dim3(kScanThreads), 0, s, in, out, n, sums);
   NAIR_LAUNCH_CHECK();
   int *offs = tmp.alloc<int>(tiles + 1);
   scan_rec(sums, offs, tiles, s, tmp);
-  k_scan_add<<<tiles, kScanThreads, 0, s>>>(out, n, offs, tiles);
+  launch_pdl(k_scan_add, dim3(tiles), dim3(kScanThreads), 0, s, out, n, offs, tiles);
   NAIR_LAUNCH_CHECK();
   tmp.release(offs);
   tmp.release(sums);
@@ -234,7 +237,7 @@ int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, Mem &tmp, boo
   if (n > 0) {
     scan_rec(in, out, n, s, tmp);
   } else {
-    k_scan_zero<<<1, 1, 0, s>>>(out);
+    launch_pdl(k_scan_zero, dim3(1), dim3(1), 0, s, out);
     NAIR_LAUNCH_CHECK();
   }
   if (!want_total) return -1;

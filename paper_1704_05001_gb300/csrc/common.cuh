@@ -130,7 +130,11 @@ void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cu
 
 // Programmatic dependent launch: let the next kernel of the stream be
 // scheduled now, and wait for the previous kernel's results before reading them.
-// Without the launch attribute both are no-ops.
+// Without the launch attribute both are no-ops.  The setup kernels call only
+// pdl_wait (their successor is then scheduled as they finish): an early trigger
+// let the successor's waiting thread blocks sit beside long-running kernels of
+// the large-block workloads and slowed them, while the trigger at completion
+// still hides the launch gap between the setup's many short kernels.
 __device__ __forceinline__ void pdl_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }

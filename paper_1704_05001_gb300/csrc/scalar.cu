@@ -16,6 +16,7 @@ static constexpr int kThreads = 256;
 static inline int grid(long long n) { return std::max(1, cdiv(n, kThreads)); }
 
 __global__ void k_row_of_block(int E, const int *__restrict__ rp, int *__restrict__ brow) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   for (int p = rp[i]; p < rp[i + 1]; ++p) brow[p] = i;
@@ -25,6 +26,7 @@ __global__ void k_row_of_block(int E, const int *__restrict__ rp, int *__restric
 __global__ void k_scale_blocks(long long total, int b, const int *__restrict__ brow, const int *__restrict__ diag,
                                const double *__restrict__ Dinv, const double *__restrict__ A,
                                double *__restrict__ S) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -48,6 +50,7 @@ template <bool FILL>
 __global__ void k_scalar_rows(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
                               const double *__restrict__ S, const int *__restrict__ srp, int *__restrict__ cnt,
                               int *__restrict__ sci, double *__restrict__ sv) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)E * b) return;
   const int i = (int)(g / b), r = (int)(g - (long long)i * b);
@@ -79,14 +82,14 @@ void scalar_matrix(const DBsr<double> &A, int b, const double *Dinv, const int *
   Mem tmp;
   tmp.s = s;
   int *brow = tmp.alloc<int>(nnzb);
-  k_row_of_block<<<grid(E), kThreads, 0, s>>>(E, A.rp, brow);
+  launch_pdl(k_row_of_block, dim3(grid(E)), dim3(kThreads), 0, s, E, A.rp, brow);
   NAIR_LAUNCH_CHECK();
   const long long tot = (long long)nnzb * b * b;
   double *S = tmp.alloc<double>((size_t)tot);
-  k_scale_blocks<<<grid(tot), kThreads, 0, s>>>(tot, b, brow, diag, Dinv, A.v, S);
+  launch_pdl(k_scale_blocks, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, brow, diag, Dinv, A.v, S);
   NAIR_LAUNCH_CHECK();
   int *cnt = tmp.alloc<int>(n + 1);
-  k_scalar_rows<false><<<grid(n), kThreads, 0, s>>>(E, b, A.rp, A.ci, S, nullptr, cnt, nullptr, nullptr);
+  launch_pdl(k_scalar_rows<false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, A.rp, A.ci, S, nullptr, cnt, nullptr, nullptr);
   NAIR_LAUNCH_CHECK();
   out.nrows = out.ncols = (int)n;
   out.rp = mem.alloc<int>(n + 1);
@@ -94,7 +97,7 @@ void scalar_matrix(const DBsr<double> &A, int b, const double *Dinv, const int *
   out.nnzb = nnz;
   out.ci = mem.alloc<int>(nnz);
   out.v = mem.alloc<double>(nnz);
-  k_scalar_rows<true><<<grid(n), kThreads, 0, s>>>(E, b, A.rp, A.ci, S, out.rp, nullptr, out.ci, out.v);
+  launch_pdl(k_scalar_rows<true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, A.rp, A.ci, S, out.rp, nullptr, out.ci, out.v);
   NAIR_LAUNCH_CHECK();
 }
 

@@ -29,6 +29,7 @@ template <typename TI>
 __global__ void k_block_inverse(int nblk, int b, int bpc, const TI *__restrict__ A,
                                 const int *__restrict__ pos, double *__restrict__ out,
                                 int *__restrict__ err) {
+  pdl_wait();
   extern __shared__ double sm[];
   const int ld = b | 1;  // odd row stride: rows of one block fall in distinct banks
   int *piv = reinterpret_cast<int *>(sm + (size_t)bpc * b * ld);
@@ -126,6 +127,7 @@ template <int B, typename TI>
 __global__ void __launch_bounds__(kThreads) k_block_inverse_seg(int nblk, const TI *__restrict__ A,
                                                                 const int *__restrict__ pos,
                                                                 double *__restrict__ out, int *__restrict__ err) {
+  pdl_wait();
   using S = SegShape<B>;
   constexpr int SEG = S::SEG, LD = S::LD;
   extern __shared__ double smb[];
@@ -222,7 +224,7 @@ static void launch_inverse_seg(int nblk, const TI *A, const int *pos, double *ou
   const size_t smem = (size_t)S::NSEG * S::BYTES;
   if (smem > 48 * 1024)
     NAIR_CK(cudaFuncSetAttribute(k_block_inverse_seg<B, TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_block_inverse_seg<B, TI><<<cdiv(nblk, S::NSEG), kThreads, smem, s>>>(nblk, A, pos, out, err);
+  launch_pdl(k_block_inverse_seg<B, TI>, dim3(cdiv(nblk, S::NSEG)), dim3(kThreads), smem, s, nblk, A, pos, out, err);
   NAIR_LAUNCH_CHECK();
 }
 
@@ -245,7 +247,7 @@ void block_inverses(int nblk, int b, const TI *A, const int *pos, double *out, i
     NAIR_CK(cudaFuncSetAttribute(k_block_inverse<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   }
-  k_block_inverse<TI><<<cdiv(nblk, bpc), bpc * b, smem, s>>>(nblk, b, bpc, A, pos, out, err);
+  launch_pdl(k_block_inverse<TI>, dim3(cdiv(nblk, bpc)), dim3(bpc * b), smem, s, nblk, b, bpc, A, pos, out, err);
   NAIR_LAUNCH_CHECK();
 }
 template void block_inverses<double>(int, int, const double *, const int *, double *, int *, cudaStream_t);
@@ -256,6 +258,7 @@ template void block_inverses<float>(int, int, const float *, const int *, double
 // ---------------------------------------------------------------------------
 __global__ void k_validate(int E, int ncols, const int *__restrict__ rp, const int *__restrict__ ci,
                            int nnzb, int *__restrict__ err) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   int a = rp[i], e = rp[i + 1];
@@ -273,11 +276,13 @@ __global__ void k_validate(int E, int ncols, const int *__restrict__ rp, const i
 
 __global__ void k_diag_pos(int E, const int *__restrict__ rp, const int *__restrict__ ci,
                            int *__restrict__ dpos) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < E) dpos[i] = find_sorted(ci, rp[i], rp[i + 1], i);
 }
 
 __global__ void k_block_rows(int E, const int *__restrict__ rp, int *__restrict__ brow) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   for (int p = rp[i]; p < rp[i + 1]; ++p) brow[p] = i;
@@ -285,6 +290,7 @@ __global__ void k_block_rows(int E, const int *__restrict__ rp, int *__restrict_
 
 template <typename TO>
 __global__ void k_convert(long long n, const double *__restrict__ in, TO *__restrict__ out) {
+  pdl_wait();
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (TO)in[i];
 }
@@ -302,6 +308,7 @@ __device__ __forceinline__ T block_norm2(const T *__restrict__ x, int bb) {
 
 template <typename T>
 __global__ void k_block_norm2(int nnzb, int b, const T *__restrict__ v, T *__restrict__ s) {
+  pdl_wait();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < nnzb) s[p] = block_norm2(v + (size_t)p * b * b, b * b);
 }
@@ -309,6 +316,7 @@ __global__ void k_block_norm2(int nnzb, int b, const T *__restrict__ v, T *__res
 template <typename T>
 __global__ void k_strength(int E, const int *__restrict__ rp, const int *__restrict__ ci,
                            const T *__restrict__ s, T th2, unsigned char *__restrict__ strong) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   T smax = 0;
@@ -321,6 +329,7 @@ __global__ void k_strength(int E, const int *__restrict__ rp, const int *__restr
 
 __global__ void k_lambda(int nnzb, const int *__restrict__ ci, const unsigned char *__restrict__ strong,
                          int *__restrict__ lam) {
+  pdl_wait();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < nnzb && strong[p]) atomicAdd(&lam[ci[p]], 1);
 }
@@ -331,6 +340,7 @@ __global__ void k_lambda(int nnzb, const int *__restrict__ ci, const unsigned ch
 // ---------------------------------------------------------------------------
 __global__ void k_pmis_init(int E, const int *__restrict__ lam, signed char *__restrict__ st,
                             uint64_t *__restrict__ h, uint64_t seed, int *__restrict__ mark) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   st[i] = lam[i] == 0 ? 0 : -1;
@@ -349,6 +359,7 @@ __global__ void k_pmis_mark(int nnzb, const int *__restrict__ brow, const int *_
                             const unsigned char *__restrict__ strong,
                             const signed char *__restrict__ st, const int *__restrict__ lam,
                             const uint64_t *__restrict__ h, int *__restrict__ mark, int round) {
+  pdl_wait();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnzb || !strong[p]) return;
   int i = brow[p], j = ci[p];
@@ -359,6 +370,7 @@ __global__ void k_pmis_mark(int nnzb, const int *__restrict__ brow, const int *_
 
 __global__ void k_pmis_select(int E, signed char *__restrict__ st, const int *__restrict__ mark,
                               int round) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < E && st[i] == -1 && mark[i] != round) st[i] = 1;
 }
@@ -366,6 +378,7 @@ __global__ void k_pmis_select(int E, signed char *__restrict__ st, const int *__
 __global__ void k_pmis_fmark(int E, const int *__restrict__ rp, const int *__restrict__ ci,
                              const unsigned char *__restrict__ strong, signed char *__restrict__ st,
                              int *__restrict__ remaining) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E || st[i] != -1) return;
   for (int p = rp[i]; p < rp[i + 1]; ++p)
@@ -377,6 +390,7 @@ __global__ void k_pmis_fmark(int E, const int *__restrict__ rp, const int *__res
 }
 
 __global__ void k_cf_flags(int E, const signed char *__restrict__ cf, int *__restrict__ isc) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < E) isc[i] = cf[i] == 1;
 }
@@ -384,6 +398,7 @@ __global__ void k_cf_flags(int E, const signed char *__restrict__ cf, int *__res
 __global__ void k_cf_index(int E, const signed char *__restrict__ cf, const int *__restrict__ pre,
                            int *__restrict__ cidx, int *__restrict__ fidx, int *__restrict__ c2f,
                            int *__restrict__ f2f) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   int c = pre[i];
@@ -407,6 +422,7 @@ static constexpr int kLenBuckets = 64;
 
 __global__ void k_len_count(int n, const int *__restrict__ list, const int *__restrict__ rp,
                             int *__restrict__ counts) {
+  pdl_wait();
   __shared__ int h[kLenBuckets];
   for (int k = threadIdx.x; k < kLenBuckets; k += blockDim.x) h[k] = 0;
   __syncthreads();
@@ -422,6 +438,7 @@ __global__ void k_len_count(int n, const int *__restrict__ list, const int *__re
 
 // offsets of the buckets, longest rows first
 __global__ void k_len_offsets(int *__restrict__ counts) {
+  pdl_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int run = 0;
   for (int k = kLenBuckets - 1; k >= 0; --k) {
@@ -433,6 +450,7 @@ __global__ void k_len_offsets(int *__restrict__ counts) {
 
 __global__ void k_len_scatter(int n, const int *__restrict__ list, const int *__restrict__ rp,
                               int *__restrict__ offs, int *__restrict__ out) {
+  pdl_wait();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int i = list[t];
@@ -447,6 +465,7 @@ __global__ void k_one_point(int E, const int *__restrict__ rp, const int *__rest
                             const unsigned char *__restrict__ strong, const T *__restrict__ s,
                             const signed char *__restrict__ cf, const int *__restrict__ cidx,
                             int *__restrict__ ipc) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   if (cf[i] == 1) { ipc[i] = cidx[i]; return; }
@@ -473,6 +492,7 @@ __global__ void k_sub_count(int nrows, int mode, const int *__restrict__ rowmap,
                             const int *__restrict__ rp, const int *__restrict__ ci,
                             const unsigned char *__restrict__ strong,
                             const signed char *__restrict__ cf, int *__restrict__ cnt) {
+  pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
   int i = rowmap[r], c = 0;
@@ -486,6 +506,7 @@ __global__ void k_sub_fill(int nrows, int mode, const int *__restrict__ rowmap,
                            const signed char *__restrict__ cf, const int *__restrict__ fidx,
                            const int *__restrict__ orp, int *__restrict__ oci,
                            int *__restrict__ osrc, int *__restrict__ orow) {
+  pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrows) return;
   int i = rowmap[r], w = orp[r];
@@ -505,6 +526,7 @@ __global__ void k_L_values(long long total, int b, const int *__restrict__ orow,
                            const int *__restrict__ osrc, const int *__restrict__ rowmap,
                            const T *__restrict__ dinv, const T *__restrict__ Av, T *__restrict__ out,
                            const int *__restrict__ nblk) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -522,6 +544,7 @@ template <typename T>
 __global__ void k_copy_blocks(long long total, int b, const int *__restrict__ src,
                               const T *__restrict__ in, T *__restrict__ out,
                               const int *__restrict__ nblk = nullptr) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -532,12 +555,14 @@ __global__ void k_copy_blocks(long long total, int b, const int *__restrict__ sr
 }
 
 __global__ void k_iota(int n, int *__restrict__ a) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i <= n) a[i] = i;
 }
 
 __global__ void k_map(int n, const int *__restrict__ in, const int *__restrict__ m,
                       int *__restrict__ out) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = m[in[i]];
 }
@@ -558,6 +583,7 @@ template <bool FILL>
 __global__ void k_spgemm_symbolic(SpgemmIdx X, int *__restrict__ cursor, int *__restrict__ cnt,
                                   const int *__restrict__ orp, int *__restrict__ oci,
                                   int *__restrict__ orow) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= X.nrows) return;
   const int l0 = X.lrp[i], l1 = X.lrp[i + 1];
@@ -605,6 +631,7 @@ __global__ void k_spgemm_numeric(long long total, int b, SpgemmIdx X, const T *_
                                  const T *__restrict__ rv, const T *__restrict__ iv,
                                  const int *__restrict__ orow, const int *__restrict__ oci,
                                  int negate, T *__restrict__ ov) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -645,6 +672,7 @@ __global__ void k_spgemm_warp(SpgemmIdx X, int *__restrict__ cnt, int *__restric
                               const int *__restrict__ orp, const int *__restrict__ prp,
                               int *__restrict__ oci, int *__restrict__ orow, int *__restrict__ pbeg,
                               int2 *__restrict__ pairs, int *__restrict__ iq, int *__restrict__ overflow) {
+  pdl_wait();
   const int lane = threadIdx.x & 31;
   const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   if (i >= X.nrows) return;  // uniform across the warp
@@ -714,6 +742,7 @@ __global__ void k_spgemm_pairs(long long total, int b, const int *__restrict__ p
                                const int2 *__restrict__ pairs, const int *__restrict__ iq,
                                const T *__restrict__ lv, const T *__restrict__ rv,
                                const T *__restrict__ iv, int negate, T *__restrict__ ov) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -738,6 +767,7 @@ template <typename T>
 __global__ void k_filter_flags(int nrows, const int *__restrict__ rp, const int *__restrict__ ci,
                                const T *__restrict__ nrm, T tol2, int *__restrict__ newpos,
                                int *__restrict__ cnt) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nrows) return;
   T dn = 0;
@@ -755,6 +785,7 @@ __global__ void k_filter_flags(int nrows, const int *__restrict__ rp, const int 
 __global__ void k_filter_compact(int nrows, const int *__restrict__ rp, const int *__restrict__ ci,
                                  const int *__restrict__ newpos, const int *__restrict__ nrp,
                                  int *__restrict__ nci, int *__restrict__ src) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nrows) return;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
@@ -770,6 +801,7 @@ __global__ void k_filter_compact(int nrows, const int *__restrict__ rp, const in
 // ---------------------------------------------------------------------------
 __global__ void k_ap_count(int E, const int *__restrict__ rp, const int *__restrict__ ci,
                            const int *__restrict__ ipc, int *__restrict__ cnt) {
+  pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= E) return;
   int c = 0;
@@ -786,6 +818,7 @@ __global__ void k_ap_count(int E, const int *__restrict__ rp, const int *__restr
 __global__ void k_ap_fill(int E, const int *__restrict__ rp, const int *__restrict__ ci,
                           const int *__restrict__ ipc, const int *__restrict__ orp,
                           int *__restrict__ oci, int *__restrict__ orow) {
+  pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= E) return;
   int w = orp[r], last = -1;
@@ -808,6 +841,7 @@ __global__ void k_ap_values(long long total, int b, const int *__restrict__ orow
                             const int *__restrict__ oci, const int *__restrict__ rp,
                             const int *__restrict__ ci, const int *__restrict__ ipc,
                             const T *__restrict__ Av, T *__restrict__ out, const int *__restrict__ nblk) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -833,6 +867,7 @@ template <typename T>
 __global__ void k_dense_fill(long long total, int b, int n, const int *__restrict__ brow,
                              const int *__restrict__ ci, const T *__restrict__ v,
                              double *__restrict__ M) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bb = b * b;
@@ -948,6 +983,7 @@ __device__ void dense_gj_cta(int n, double *__restrict__ M, int *__restrict__ pi
 
 // the same, with the matrix staged in shared memory (small coarsest levels)
 __global__ void __launch_bounds__(kGjThreads) k_dense_gj_smem(int n, double *__restrict__ Mg, int *__restrict__ err) {
+  pdl_wait();
   extern __shared__ double sm[];
   double *M = sm, *lcol = sm + (size_t)n * n;
   int *piv = reinterpret_cast<int *>(lcol + n);
@@ -972,7 +1008,6 @@ __global__ void __launch_bounds__(256) k_gj_step(int n, int k, const double *__r
   __shared__ int sp;
   __shared__ double prow[kGjTileCols];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  pdl_launch_dependents();
   pdl_wait();  // Min is the previous step's output, Mout its input
   unsigned long long key = 0;
   int bi = n;
@@ -1020,6 +1055,7 @@ __global__ void __launch_bounds__(256) k_gj_step(int n, int k, const double *__r
 
 // undo the row interchanges as column swaps, last step first
 __global__ void __launch_bounds__(1024) k_gj_unscramble(int n, double *__restrict__ M, const int *__restrict__ piv) {
+  pdl_wait();
   for (int k = n - 1; k >= 0; --k) {
     const int p = piv[k];
     if (p != k)
@@ -1038,6 +1074,7 @@ __global__ void __launch_bounds__(1024) k_gj_unscramble(int n, double *__restric
 template <typename T>
 __global__ void k_colmask(int nnzb, int b, const int *__restrict__ brow, const int *__restrict__ diag,
                           const T *__restrict__ v, unsigned *__restrict__ mask, int *__restrict__ wmax) {
+  pdl_wait();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnzb) return;
   if (diag[brow[p]] == p) { mask[p] = 0; return; }
@@ -1054,6 +1091,7 @@ template <typename T>
 __global__ void k_comp_fill(int nnzb, int b, int W, const int *__restrict__ brow, const int *__restrict__ diag,
                             const int *__restrict__ ci, const T *__restrict__ v, const unsigned *__restrict__ mask,
                             int *__restrict__ oci, unsigned long long *__restrict__ ocols, T *__restrict__ ov) {
+  pdl_wait();
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nnzb) return;
   const int i = brow[p], d = diag[i];
@@ -1093,9 +1131,9 @@ void build_l0comp(const DBsr<T> &A, const int *diag, int b, cudaStream_t s, Mem 
   int *brow = tmp.alloc<int>(nnzb), *wmax = tmp.alloc<int>(1);
   unsigned *mask = tmp.alloc<unsigned>(nnzb);
   NAIR_CK(cudaMemsetAsync(wmax, 0, sizeof(int), s));
-  k_block_rows<<<grid1d(E), kThreads, 0, s>>>(E, A.rp, brow);
+  launch_pdl(k_block_rows, dim3(grid1d(E)), dim3(kThreads), 0, s, E, A.rp, brow);
   NAIR_LAUNCH_CHECK();
-  k_colmask<T><<<grid1d(nnzb), kThreads, 0, s>>>(nnzb, b, brow, diag, A.v, mask, wmax);
+  launch_pdl(k_colmask<T>, dim3(grid1d(nnzb)), dim3(kThreads), 0, s, nnzb, b, brow, diag, A.v, mask, wmax);
   NAIR_LAUNCH_CHECK();
   int W = read_int(wmax, s);
   if (W == 0) W = 1;
@@ -1106,7 +1144,7 @@ void build_l0comp(const DBsr<T> &A, const int *diag, int b, cudaStream_t s, Mem 
   C.oci = mem.alloc<int>(noff);
   C.ocols = mem.alloc<unsigned long long>(noff);
   C.ov = mem.alloc<T>((size_t)noff * b * W);
-  k_comp_fill<T><<<grid1d(nnzb), kThreads, 0, s>>>(nnzb, b, W, brow, diag, A.ci, A.v, mask, C.oci, C.ocols, C.ov);
+  launch_pdl(k_comp_fill<T>, dim3(grid1d(nnzb)), dim3(kThreads), 0, s, nnzb, b, W, brow, diag, A.ci, A.v, mask, C.oci, C.ocols, C.ov);
   NAIR_LAUNCH_CHECK();
 }
 template void build_l0comp<double>(const DBsr<double> &, const int *, int, cudaStream_t, Mem &, L0Comp<double> &);
@@ -1114,6 +1152,7 @@ template void build_l0comp<float>(const DBsr<float> &, const int *, int, cudaStr
 
 // row of every compressed off-diagonal block: row i owns q in [rp[i] - i, rp[i + 1] - i - 1)
 __global__ void k_l0_qrow(int E, const int *__restrict__ rp, int *__restrict__ qrow) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= E) return;
   for (int q = rp[i] - i; q < rp[i + 1] - i - 1; ++q) qrow[q] = i;
@@ -1123,6 +1162,7 @@ __global__ void k_l0_qrow(int E, const int *__restrict__ rp, int *__restrict__ q
 template <typename T>
 __global__ void k_l0_scale(long long total, int b, int W, const int *__restrict__ qrow, const T *__restrict__ dinv,
                            const T *__restrict__ ov, T *__restrict__ sv) {
+  pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
   const int bw = b * W;
@@ -1142,11 +1182,11 @@ void build_l0scaled(const DBsr<T> &A, const T *dinv, int b, cudaStream_t s, Mem 
   Mem tmp;
   tmp.s = s;
   int *qrow = tmp.alloc<int>(noff);
-  k_l0_qrow<<<grid1d(E), kThreads, 0, s>>>(E, A.rp, qrow);
+  launch_pdl(k_l0_qrow, dim3(grid1d(E)), dim3(kThreads), 0, s, E, A.rp, qrow);
   NAIR_LAUNCH_CHECK();
   const long long tot = (long long)noff * b * C.W;
   C.sv = mem.alloc<T>((size_t)tot);
-  k_l0_scale<T><<<grid1d(tot), kThreads, 0, s>>>(tot, b, C.W, qrow, dinv, C.ov, C.sv);
+  launch_pdl(k_l0_scale<T>, dim3(grid1d(tot)), dim3(kThreads), 0, s, tot, b, C.W, qrow, dinv, C.ov, C.sv);
   NAIR_LAUNCH_CHECK();
 }
 template void build_l0scaled<double>(const DBsr<double> &, const double *, int, cudaStream_t, Mem &, L0Comp<double> &);
@@ -1167,17 +1207,17 @@ static void spgemm_rowwise(int b, const SpgemmIdx &X, int left_nnz, const T *lv,
   out.nrows = nrows;
   out.ncols = ncols;
   out.rp = mem.alloc<int>(nrows + 1);
-  k_spgemm_symbolic<false><<<grid(nrows), kThreads, 0, s>>>(X, cursor, cnt, nullptr, nullptr, nullptr);
+  launch_pdl(k_spgemm_symbolic<false>, dim3(grid(nrows)), dim3(kThreads), 0, s, X, cursor, cnt, nullptr, nullptr, nullptr);
   NAIR_LAUNCH_CHECK();
   out.nnzb = exclusive_scan(cnt, out.rp, nrows, s, tmp);
   out.ci = mem.alloc<int>(out.nnzb);
   int *orow = tmp.alloc<int>(out.nnzb);
-  k_spgemm_symbolic<true><<<grid(nrows), kThreads, 0, s>>>(X, cursor, nullptr, out.rp, out.ci, orow);
+  launch_pdl(k_spgemm_symbolic<true>, dim3(grid(nrows)), dim3(kThreads), 0, s, X, cursor, nullptr, out.rp, out.ci, orow);
   NAIR_LAUNCH_CHECK();
   out.v = mem.alloc<T>((size_t)out.nnzb * b * b);
   long long total = (long long)out.nnzb * b * b;
   if (total) {
-    k_spgemm_numeric<T><<<grid(total), kThreads, 0, s>>>(total, b, X, lv, rv, iv, orow, out.ci,
+    launch_pdl(k_spgemm_numeric<T>, dim3(grid(total)), dim3(kThreads), 0, s, total, b, X, lv, rv, iv, orow, out.ci,
                                                         negate, out.v);
     NAIR_LAUNCH_CHECK();
   }
@@ -1195,7 +1235,7 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
   int *prp = tmp.alloc<int>(nrows + 1), *flags = tmp.alloc<int>(4);
   NAIR_CK(cudaMemsetAsync(flags, 0, 4 * sizeof(int), s));
   const int wblocks = std::max(1, cdiv((long long)nrows * 32, kThreads));
-  k_spgemm_warp<false><<<wblocks, kThreads, 0, s>>>(X, cnt, pcnt, nullptr, nullptr, nullptr, nullptr,
+  launch_pdl(k_spgemm_warp<false>, dim3(wblocks), dim3(kThreads), 0, s, X, cnt, pcnt, nullptr, nullptr, nullptr, nullptr,
                                                     nullptr, nullptr, nullptr, flags);
   NAIR_LAUNCH_CHECK();
   out.nrows = nrows;
@@ -1230,14 +1270,14 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
   out.ci = mem.alloc<int>(out.nnzb);
   int *orow = tmp.alloc<int>(out.nnzb), *pbeg = tmp.alloc<int>(out.nnzb + 1), *iq = tmp.alloc<int>(out.nnzb);
   int2 *pairs = tmp.alloc<int2>(nprod);
-  k_spgemm_warp<true><<<wblocks, kThreads, 0, s>>>(X, nullptr, nullptr, out.rp, prp, out.ci, orow, pbeg,
+  launch_pdl(k_spgemm_warp<true>, dim3(wblocks), dim3(kThreads), 0, s, X, nullptr, nullptr, out.rp, prp, out.ci, orow, pbeg,
                                                    pairs, iq, flags);
   NAIR_LAUNCH_CHECK();
   NAIR_CK(cudaMemcpyAsync(pbeg + out.nnzb, prp + nrows, sizeof(int), cudaMemcpyDeviceToDevice, s));
   out.v = mem.alloc<T>((size_t)out.nnzb * b * b);
   const long long total = (long long)out.nnzb * b * b;
   if (total) {
-    k_spgemm_pairs<T><<<grid(total), kThreads, 0, s>>>(total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    launch_pdl(k_spgemm_pairs<T>, dim3(grid(total)), dim3(kThreads), 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     NAIR_LAUNCH_CHECK();
   }
   tmp.release(pairs);
@@ -1262,22 +1302,22 @@ static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M
   int *cnt = tmp.alloc<int>(nrows + 1);
   T *nrm = tmp.alloc<T>(ub);
   if (ub) {
-    k_block_norm2<T><<<grid(ub), kThreads, 0, s>>>(ub, b, M.v, nrm);
+    launch_pdl(k_block_norm2<T>, dim3(grid(ub)), dim3(kThreads), 0, s, ub, b, M.v, nrm);
     NAIR_LAUNCH_CHECK();
   }
-  k_filter_flags<T><<<grid(nrows), kThreads, 0, s>>>(nrows, M.rp, M.ci, nrm, tol2, newpos, cnt);
+  launch_pdl(k_filter_flags<T>, dim3(grid(nrows)), dim3(kThreads), 0, s, nrows, M.rp, M.ci, nrm, tol2, newpos, cnt);
   NAIR_LAUNCH_CHECK();
   int *nrp = mem.alloc<int>(nrows + 1);
   const int nn = exclusive_scan(cnt, nrp, nrows, s, tmp, !defer);
   const int cap = defer ? ub : nn;
   int *nci = mem.alloc<int>(cap);
   int *src = tmp.alloc<int>(cap);
-  k_filter_compact<<<grid(nrows), kThreads, 0, s>>>(nrows, M.rp, M.ci, newpos, nrp, nci, src);
+  launch_pdl(k_filter_compact, dim3(grid(nrows)), dim3(kThreads), 0, s, nrows, M.rp, M.ci, newpos, nrp, nci, src);
   NAIR_LAUNCH_CHECK();
   T *nv = mem.alloc<T>((size_t)cap * b * b);
   long long total = (long long)cap * b * b;
   if (total) {
-    k_copy_blocks<T><<<grid(total), kThreads, 0, s>>>(total, b, src, M.v, nv, defer ? nrp + nrows : nullptr);
+    launch_pdl(k_copy_blocks<T>, dim3(grid(total)), dim3(kThreads), 0, s, total, b, src, M.v, nv, defer ? (const int *)(nrp + nrows) : (const int *)nullptr);
     NAIR_LAUNCH_CHECK();
   }
   mem.release(M.rp);
@@ -1311,13 +1351,13 @@ int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem,
   int *counts = tmp.alloc<int>(kLenBuckets);
   NAIR_CK(cudaMemsetAsync(counts, 0, sizeof(int) * kLenBuckets, s));
   if (n) {
-    k_len_count<<<grid(n), kThreads, 0, s>>>(n, list, rp, counts);
+    launch_pdl(k_len_count, dim3(grid(n)), dim3(kThreads), 0, s, n, list, rp, counts);
     NAIR_LAUNCH_CHECK();
   }
-  k_len_offsets<<<1, 32, 0, s>>>(counts);
+  launch_pdl(k_len_offsets, dim3(1), dim3(32), 0, s, counts);
   NAIR_LAUNCH_CHECK();
   if (n) {
-    k_len_scatter<<<grid(n), kThreads, 0, s>>>(n, list, rp, counts, out);
+    launch_pdl(k_len_scatter, dim3(grid(n)), dim3(kThreads), 0, s, n, list, rp, counts, out);
     NAIR_LAUNCH_CHECK();
   }
   tmp.release(counts);
@@ -1332,7 +1372,7 @@ static void extract(int b, int nrows, int mode, const int *rowmap, const Level<T
                     const unsigned char *strong, const int *fidx, cudaStream_t s, Mem &mem,
                     Mem &tmp, DBsr<T> &out, int **src_out, int **row_out, int *ub) {
   int *cnt = tmp.alloc<int>(nrows + 1);
-  k_sub_count<<<grid(nrows), kThreads, 0, s>>>(nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, cnt);
+  launch_pdl(k_sub_count, dim3(grid(nrows)), dim3(kThreads), 0, s, nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, cnt);
   NAIR_LAUNCH_CHECK();
   out.nrows = nrows;
   out.rp = mem.alloc<int>(nrows + 1);
@@ -1342,7 +1382,7 @@ static void extract(int b, int nrows, int mode, const int *rowmap, const Level<T
   out.ci = mem.alloc<int>(*ub);
   int *src = tmp.alloc<int>(*ub);
   int *row = tmp.alloc<int>(*ub);
-  k_sub_fill<<<grid(nrows), kThreads, 0, s>>>(nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, fidx,
+  launch_pdl(k_sub_fill, dim3(grid(nrows)), dim3(kThreads), 0, s, nrows, mode, rowmap, L.A.rp, L.A.ci, strong, L.cf, fidx,
                                                out.rp, out.ci, src, row);
   NAIR_LAUNCH_CHECK();
   out.v = mem.alloc<T>((size_t)*ub * b * b);
@@ -1362,14 +1402,14 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   ProfScope ps_str("strength", s, l);
   T *snorm = tmp.alloc<T>(nnzb);
   unsigned char *strong = (P.keep ? mem.alloc<unsigned char>(nnzb) : tmp.alloc<unsigned char>(nnzb));
-  k_block_norm2<T><<<grid(nnzb), kThreads, 0, s>>>(nnzb, b, L.A.v, snorm);
+  launch_pdl(k_block_norm2<T>, dim3(grid(nnzb)), dim3(kThreads), 0, s, nnzb, b, L.A.v, snorm);
   NAIR_LAUNCH_CHECK();
   const T th2 = (T)(P.theta * P.theta);
-  k_strength<T><<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, snorm, th2, strong);
+  launch_pdl(k_strength<T>, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, snorm, th2, strong);
   NAIR_LAUNCH_CHECK();
   int *lam = P.keep ? mem.alloc<int>(E) : tmp.alloc<int>(E);
   NAIR_CK(cudaMemsetAsync(lam, 0, sizeof(int) * E, s));
-  k_lambda<<<grid(nnzb), kThreads, 0, s>>>(nnzb, L.A.ci, strong, lam);
+  launch_pdl(k_lambda, dim3(grid(nnzb)), dim3(kThreads), 0, s, nnzb, L.A.ci, strong, lam);
   NAIR_LAUNCH_CHECK();
   ps_str.end();
   // a3: C/F splitting
@@ -1378,9 +1418,9 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   int *mark = tmp.alloc<int>(E);
   int *brow = tmp.alloc<int>(nnzb);
   int *remaining = tmp.alloc<int>(1);
-  k_block_rows<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, brow);
+  launch_pdl(k_block_rows, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, brow);
   NAIR_LAUNCH_CHECK();
-  k_pmis_init<<<grid(E), kThreads, 0, s>>>(E, lam, L.cf, hash, P.seed, mark);
+  launch_pdl(k_pmis_init, dim3(grid(E)), dim3(kThreads), 0, s, E, lam, L.cf, hash, P.seed, mark);
   NAIR_LAUNCH_CHECK();
   int rounds = 0;
   ProfScope ps_cf("cf_split", s, l);
@@ -1389,11 +1429,11 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   for (int batch = 4;; batch = 2) {
     for (int rep = 0; rep < batch; ++rep) {
       NAIR_CK(cudaMemsetAsync(remaining, 0, sizeof(int), s));
-      k_pmis_mark<<<grid(nnzb), kThreads, 0, s>>>(nnzb, brow, L.A.ci, strong, L.cf, lam, hash, mark, rounds);
+      launch_pdl(k_pmis_mark, dim3(grid(nnzb)), dim3(kThreads), 0, s, nnzb, brow, L.A.ci, strong, L.cf, lam, hash, mark, rounds);
       NAIR_LAUNCH_CHECK();
-      k_pmis_select<<<grid(E), kThreads, 0, s>>>(E, L.cf, mark, rounds);
+      launch_pdl(k_pmis_select, dim3(grid(E)), dim3(kThreads), 0, s, E, L.cf, mark, rounds);
       NAIR_LAUNCH_CHECK();
-      k_pmis_fmark<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, strong, L.cf, remaining);
+      launch_pdl(k_pmis_fmark, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, strong, L.cf, remaining);
       NAIR_LAUNCH_CHECK();
       ++rounds;
     }
@@ -1404,7 +1444,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   ps_cf.end();
   int *isc = tmp.alloc<int>(E);
   int *pre = tmp.alloc<int>(E + 1);
-  k_cf_flags<<<grid(E), kThreads, 0, s>>>(E, L.cf, isc);
+  launch_pdl(k_cf_flags, dim3(grid(E)), dim3(kThreads), 0, s, E, L.cf, isc);
   NAIR_LAUNCH_CHECK();
   const int nC = exclusive_scan(isc, pre, E, s, tmp);
   const int nF = E - nC;
@@ -1422,7 +1462,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   L.c2f = mem.alloc<int>(nC);
   L.f2f = mem.alloc<int>(nF);
   int *f2f = L.f2f;
-  k_cf_index<<<grid(E), kThreads, 0, s>>>(E, L.cf, pre, cidx, fidx, L.c2f, f2f);
+  launch_pdl(k_cf_index, dim3(grid(E)), dim3(kThreads), 0, s, E, L.cf, pre, cidx, fidx, L.c2f, f2f);
   NAIR_LAUNCH_CHECK();
   L.fsweep = sweep_list(nF, f2f, L.A.rp, s, mem, tmp);
   L.csweep = sweep_list(nC, L.c2f, L.A.rp, s, mem, tmp);
@@ -1436,7 +1476,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   Lm.ncols = nF;
   long long tot = (long long)lub * bb;
   if (tot) {
-    k_L_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, row, src, f2f, L.dinv, L.A.v, Lm.v, Lm.rp + nF);
+    launch_pdl(k_L_values<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, row, src, f2f, L.dinv, L.A.v, Lm.v, Lm.rp + nF);
     NAIR_LAUNCH_CHECK();
   }
   tmp.release(src);
@@ -1446,11 +1486,11 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   Dg.rp = tmp.alloc<int>(nF + 1);
   Dg.ci = Dg.rp;  // column i of row i: the same iota array
   Dg.v = tmp.alloc<T>((size_t)nF * bb);
-  k_iota<<<grid(nF + 1), kThreads, 0, s>>>(nF, Dg.rp);
+  launch_pdl(k_iota, dim3(grid(nF + 1)), dim3(kThreads), 0, s, nF, Dg.rp);
   NAIR_LAUNCH_CHECK();
   tot = (long long)nF * bb;
   if (tot) {
-    k_copy_blocks<T><<<grid(tot), kThreads, 0, s>>>(tot, b, f2f, L.dinv, Dg.v);
+    launch_pdl(k_copy_blocks<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, f2f, L.dinv, Dg.v, (const int *)nullptr);
     NAIR_LAUNCH_CHECK();
   }
   DBsr<T> Tk;  // T_0 = D^{-1}
@@ -1483,7 +1523,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   extract<T>(b, nC, 1, L.c2f, L, strong, fidx, s, tmp, tmp, Acf, &src, &row, &aub);
   tot = (long long)aub * bb;
   if (tot) {
-    k_copy_blocks<T><<<grid(tot), kThreads, 0, s>>>(tot, b, src, L.A.v, Acf.v, Acf.rp + nC);
+    launch_pdl(k_copy_blocks<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, src, L.A.v, Acf.v, Acf.rp + nC);
     NAIR_LAUNCH_CHECK();
   }
   {
@@ -1493,7 +1533,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   L.R_ci_f = L.R.ci;
   L.R.ci = mem.alloc<int>(L.R.nnzb);
   if (L.R.nnzb) {
-    k_map<<<grid(L.R.nnzb), kThreads, 0, s>>>(L.R.nnzb, L.R_ci_f, f2f, L.R.ci);
+    launch_pdl(k_map, dim3(grid(L.R.nnzb)), dim3(kThreads), 0, s, L.R.nnzb, L.R_ci_f, f2f, L.R.ci);
     NAIR_LAUNCH_CHECK();
   }
   L.R.ncols = E;
@@ -1501,7 +1541,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
 
   // a6: one-point interpolation
   L.ipc = mem.alloc<int>(E);
-  k_one_point<T><<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, strong, snorm, L.cf, cidx, L.ipc);
+  launch_pdl(k_one_point<T>, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, strong, snorm, L.cf, cidx, L.ipc);
   NAIR_LAUNCH_CHECK();
 
   // a7: A P (column merge), then K = (AP)_C + R_cf (AP)_F
@@ -1509,7 +1549,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   DBsr<T> AP;
   {
     int *cnt = tmp.alloc<int>(E + 1);
-    k_ap_count<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.ipc, cnt);
+    launch_pdl(k_ap_count, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, L.ipc, cnt);
     NAIR_LAUNCH_CHECK();
     AP.nrows = E;
     AP.ncols = nC;
@@ -1518,12 +1558,12 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     AP.nnzb = -1;               // at most one block per block of A: sized by nnzb(A)
     AP.ci = tmp.alloc<int>(nnzb);
     int *aprow = tmp.alloc<int>(nnzb);
-    k_ap_fill<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.ipc, AP.rp, AP.ci, aprow);
+    launch_pdl(k_ap_fill, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, L.ipc, AP.rp, AP.ci, aprow);
     NAIR_LAUNCH_CHECK();
     AP.v = tmp.alloc<T>((size_t)nnzb * bb);
     tot = (long long)nnzb * bb;
     if (tot) {
-      k_ap_values<T><<<grid(tot), kThreads, 0, s>>>(tot, b, aprow, AP.ci, L.A.rp, L.A.ci, L.ipc, L.A.v, AP.v,
+      launch_pdl(k_ap_values<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, aprow, AP.ci, L.A.rp, L.A.ci, L.ipc, L.A.v, AP.v,
                                                    AP.rp + E);
       NAIR_LAUNCH_CHECK();
     }
@@ -1550,7 +1590,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
 }
 
 void diag_positions(int E, const int *rp, const int *ci, int *out, cudaStream_t s) {
-  k_diag_pos<<<grid(E), kThreads, 0, s>>>(E, rp, ci, out);
+  launch_pdl(k_diag_pos, dim3(grid(E)), dim3(kThreads), 0, s, E, rp, ci, out);
   NAIR_LAUNCH_CHECK();
 }
 
@@ -1559,7 +1599,7 @@ static void level_dinv(Hier<T> &H, Level<T> &L, cudaStream_t s, Mem &mem, Mem &t
   const int b = H.b, E = L.E;
   ProfScope ps("dinv", s);
   L.diag = mem.alloc<int>(E);
-  k_diag_pos<<<grid(E), kThreads, 0, s>>>(E, L.A.rp, L.A.ci, L.diag);
+  launch_pdl(k_diag_pos, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, L.diag);
   NAIR_LAUNCH_CHECK();
   double *d64;
   if constexpr (std::is_same<T, double>::value) {
@@ -1572,7 +1612,7 @@ static void level_dinv(Hier<T> &H, Level<T> &L, cudaStream_t s, Mem &mem, Mem &t
   if constexpr (!std::is_same<T, double>::value) {
     L.dinv = mem.alloc<T>((size_t)E * b * b);
     long long n = (long long)E * b * b;
-    k_convert<T><<<grid(n), kThreads, 0, s>>>(n, d64, L.dinv);
+    launch_pdl(k_convert<T>, dim3(grid(n)), dim3(kThreads), 0, s, n, d64, L.dinv);
     NAIR_LAUNCH_CHECK();
     tmp.release(d64);
   }
@@ -1607,11 +1647,11 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
   double *M = tmp.alloc<double>((size_t)n * n);
   NAIR_CK(cudaMemsetAsync(M, 0, sizeof(double) * n * n, s));
   int *brow = tmp.alloc<int>(L.A.nnzb);
-  k_block_rows<<<grid(L.E), kThreads, 0, s>>>(L.E, L.A.rp, brow);
+  launch_pdl(k_block_rows, dim3(grid(L.E)), dim3(kThreads), 0, s, L.E, L.A.rp, brow);
   NAIR_LAUNCH_CHECK();
   long long tot = (long long)L.A.nnzb * b * b;
   if (tot) {
-    k_dense_fill<T><<<grid(tot), kThreads, 0, s>>>(tot, b, n, brow, L.A.ci, L.A.v, M);
+    launch_pdl(k_dense_fill<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, n, brow, L.A.ci, L.A.v, M);
     NAIR_LAUNCH_CHECK();
   }
   int *piv = tmp.alloc<int>(n);
@@ -1621,7 +1661,7 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
   const size_t gj_smem = (size_t)n * n * sizeof(double) + (size_t)n * (sizeof(double) + sizeof(int));
   if (n <= 48) {
     NAIR_CK(cudaFuncSetAttribute(k_dense_gj_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gj_smem));
-    k_dense_gj_smem<<<1, kGjThreads, gj_smem, s>>>(n, M, err);
+    launch_pdl(k_dense_gj_smem, dim3(1), dim3(kGjThreads), gj_smem, s, n, M, err);
     NAIR_LAUNCH_CHECK();
   } else {
     double *M2 = tmp.alloc<double>((size_t)n * n);
@@ -1631,12 +1671,12 @@ static void make_coarsest(Hier<T> &H, Level<T> &L, const Params &P, cudaStream_t
       NAIR_LAUNCH_CHECK();
       std::swap(M, M2);
     }
-    k_gj_unscramble<<<1, 1024, 0, s>>>(n, M, piv);
+    launch_pdl(k_gj_unscramble, dim3(1), dim3(1024), 0, s, n, M, piv);
     NAIR_LAUNCH_CHECK();
   }
   L.ainv = mem.alloc<T>((size_t)n * n);
   tot = (long long)n * n;
-  k_convert<T><<<grid(tot), kThreads, 0, s>>>(tot, M, L.ainv);
+  launch_pdl(k_convert<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, M, L.ainv);
   NAIR_LAUNCH_CHECK();
   // the flag is read at the end of the hierarchy build
   tmp.release_all();
@@ -1713,7 +1753,7 @@ template void build_hierarchy<float>(const DBsr<float> &, const Params &, cudaSt
 void validate_bsr(int E, int ncols, const int *rp, const int *ci, int nnzb, cudaStream_t s, Mem &tmp) {
   int *err = tmp.alloc<int>(1);
   NAIR_CK(cudaMemsetAsync(err, 0, sizeof(int), s));
-  k_validate<<<grid(E), kThreads, 0, s>>>(E, ncols, rp, ci, nnzb, err);
+  launch_pdl(k_validate, dim3(grid(E)), dim3(kThreads), 0, s, E, ncols, rp, ci, nnzb, err);
   NAIR_LAUNCH_CHECK();
   int v = read_int(err, s);
   tmp.release(err);
