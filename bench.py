@@ -209,6 +209,17 @@ def l0_width(offblocks, b):
     return L0_WIDTHS[b] if max(w, 1) <= L0_WIDTHS[b] else 0
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json next to
+    this file), else the earlier single measurement used as the fallback."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def roofline(nair, params, rp, ci, v, sweep_ms):
     """Roofline of the dominant kernel, the block-Jacobi sweep (all levels).
 
@@ -230,6 +241,23 @@ def roofline(nair, params, rp, ci, v, sweep_ms):
         t += ms * 1e-3
         launches += n
     achieved = fl / t / 1e12 if t else 0.0
+    hbm_peak, hbm_src = hbm_peak_gbs()
+    by_level = []
+    for l in sorted({l for (l, _c) in sweep_ms}):
+        lf = lb = lt = 0.0
+        ln = 0
+        for cls in ("F", "C"):
+            if (l, cls) in sweep_ms and f"jacobi_{cls}@L{l}" in work:
+                n, ms = sweep_ms[(l, cls)]
+                flops, byts = work[f"jacobi_{cls}@L{l}"]
+                lf += flops * n
+                lb += byts * n
+                lt += ms * 1e-3
+                ln += n
+        if lt:
+            by_level.append({"level": l, "sweeps": ln, "us_per_sweep": round(1e6 * lt / ln, 2),
+                             "tflops": round(lf / lt / 1e12, 4), "frac_fp64": round(lf / lt / 1e12 / FP64_PEAK_TFLOPS, 3),
+                             "gbs": round(lb / lt / 1e9, 1), "frac_hbm": round(lb / lt / 1e9 / hbm_peak, 3)})
     return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": JACOBI_TRAFFIC,
@@ -238,6 +266,8 @@ def roofline(nair, params, rp, ci, v, sweep_ms):
             "launches_per_step": None, "launches_timed": launches,
             "kernel_ms_timed": 1e3 * t,
             "hbm_achieved_gbs": by / t / 1e9 if t else 0.0,
+            "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+            "by_level": by_level,
             "how": "device-clock stamps (first thread block past the dependency wait to last "
                    "thread block done) on every sweep inside the timed steps"}
 
