@@ -151,25 +151,44 @@ def run_reference(args, rank, world):
 FP64_PEAK_TFLOPS = 1.25
 
 # DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
-# launch, averaged over the 40 sweeps of one C2 V-cycle: dram__bytes_read.sum +
-# dram__bytes_write.sum); set to None whenever the kernel changes until recaptured.
-JACOBI_TRAFFIC = 17.16e6
+# launch, averaged over the sweeps of one C2 V-cycle: dram__bytes_read.sum +
+# dram__bytes_write.sum); None whenever the kernel has changed since the capture.
+JACOBI_TRAFFIC = None
 
 
-def level_work(S, nlev, b):
-    """Algorithmic FP64 work of every block-Jacobi sweep scope, from the hierarchy.
+def f_sweep_rows(rows, ci, cf, off, f_sweeps):
+    """Rows updated by each F sweep of a cycle from a zero iterate: all F rows,
+    then only the F rows with an off-diagonal F coupling to a row updated by the
+    previous sweep (the C values do not change during the F sweeps, so any
+    other row would recompute its previous value).  Boolean masks over rows."""
+    F = cf == 0
+    ff = off & F[rows] & F[ci]
+    masks = [F]
+    for _ in range(1, f_sweeps):
+        dep = np.zeros_like(F)
+        np.logical_or.at(dep, rows[ff], masks[-1][ci[ff]])
+        masks.append(dep & F)
+    return masks
 
-    A sweep over the rows of one class (F or C) at level l computes
-    x_i = D_ii^{-1} (f_i - sum_{j != i} A_ij x_j): one FMA per exact nonzero of
-    the off-diagonal blocks of those rows and b^2 FMAs per row for D^{-1}; its
-    algorithmic bytes are those nonzeros (8 B), their block column indices
-    (4 B per block), the rows' D^{-1} blocks and right-hand side, and one read
-    and one write of the level vector.
+
+def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1):
+    """Algorithmic work of every block-Jacobi sweep of a cycle from a zero
+    iterate, {(level, k): (flops, bytes)} for sweep k (F sweeps first).
+
+    A sweep updates rows of one class: x_i = D_ii^{-1} (f_i - sum_{j != i} A_ij x_j),
+    one FMA per exact nonzero of their off-diagonal blocks and b^2 FMAs per row
+    for D^{-1}.  Its bytes: those nonzeros (8 B) and block column indices (4 B),
+    the rows' D^{-1} blocks and right-hand side, one read of each distinct x
+    block the rows reference, the write of the rows, and for every row of the
+    other class that the output buffer lacks, a read and a write.  The first F
+    sweep also writes its rows and copies into the second buffer.  F sweeps
+    after the first update the rows of `f_sweep_rows`; they copy the rows the
+    previous sweep updated that they do not, and the first C sweep copies those
+    of the last F sweep.
 
     Level 0 with column-compressed coupling blocks (W of b columns) sweeps with
     the couplings scaled in advance, x_i = g_i - sum_j (D_ii^{-1} A_ij) x_j with
-    g = D^{-1} f: b W FMAs per coupling block and no D^{-1} apply; its bytes are
-    the scaled blocks, their column indices, g and the vector."""
+    g = D^{-1} f: b W FMAs per coupling block and no D^{-1} apply."""
     work = {}
     for l in range(nlev):
         lev = S.level(l)
@@ -180,18 +199,37 @@ def level_work(S, nlev, b):
         rows = np.repeat(np.arange(lev["E"]), np.diff(rp))
         off = ci != rows
         W = l0_width(vals[off], b) if l == 0 else 0
-        for cls, name in ((0, "jacobi_F"), (1, "jacobi_C")):
-            sel = (cf[rows] == cls) & off
-            nrow = int(np.count_nonzero(cf == cls))
+        short = 2 <= f_sweeps <= 8
+        fm = f_sweep_rows(rows, ci, cf, off, f_sweeps if short else 1)
+        C = cf == 1
+        for k in range(f_sweeps + c_sweeps):
+            dual = 1
+            if k < f_sweeps:
+                upd = fm[k] if short else fm[0]
+                if k == 0:
+                    copy, dual = C, 2 if short else 1
+                else:
+                    copy = (fm[k - 1] & ~fm[k]) if (short and k >= 2) else np.zeros_like(C)
+            else:
+                upd = C
+                if k > f_sweeps:
+                    copy = np.zeros_like(C)
+                else:
+                    copy = fm[f_sweeps - 1] if short else (cf == 0)
+            sel = upd[rows] & off
+            nrow, ncopy = int(upd.sum()), int(copy.sum())
             nblk = int(sel.sum())
+            xcols = len(np.unique(ci[sel]))
             if W:
                 flops = 2.0 * nblk * b * W
-                byts = 8.0 * nblk * b * W + 4.0 * nblk + 8.0 * nrow * b + 16.0 * lev["E"] * b
+                byts = 8.0 * nblk * b * W + 4.0 * nblk + 8.0 * nrow * b
             else:
                 nnz = int(nnz_block[sel].sum())
                 flops = 2.0 * (nnz + nrow * b * b)
-                byts = 8.0 * nnz + 4.0 * nblk + 8.0 * nrow * b * (b + 1) + 16.0 * lev["E"] * b
-            work[f"{name}@L{l}"] = (flops, byts)
+                byts = 8.0 * nnz + 4.0 * nblk + 8.0 * nrow * b * (b + 1)
+            byts += 8.0 * b * xcols + 8.0 * b * (nrow + ncopy) * dual + 8.0 * b * ncopy
+            if nrow or ncopy:
+                work[(l, k)] = (flops, byts)
     return work
 
 
@@ -223,37 +261,33 @@ def hbm_peak_gbs():
 def roofline(nair, params, rp, ci, v, sweep_ms):
     """Roofline of the dominant kernel, the block-Jacobi sweep (all levels).
 
-    sweep_ms maps (level, class) to (sweeps, total ms) stamped on the device
-    inside the timed steps; the algorithmic work per sweep comes from the
-    hierarchy (rebuilt once, untimed, to read its level sizes)."""
+    sweep_ms maps (level, sweep k of the cycle) to (sweeps, total ms) stamped on
+    the device inside the timed steps; the algorithmic work of each sweep comes
+    from the hierarchy (rebuilt once, untimed, to read its level sizes)."""
     S = nair.NairSolver(rp, ci, v, **params)
-    work = level_work(S, S.num_levels(), S.b)
+    work = sweep_work(S, S.num_levels(), S.b, S.f_sweeps, max(S.params.c_sweeps, 0))
     S.close()
     fl = by = t = 0.0
     launches = 0
-    for (l, cls), (n, ms) in sweep_ms.items():
-        key = f"jacobi_{cls}@L{l}"
-        if key not in work:
+    per_level = {}
+    for (l, k), (n, ms) in sweep_ms.items():
+        if (l, k) not in work:
             continue
-        flops, byts = work[key]
+        flops, byts = work[(l, k)]
         fl += flops * n
         by += byts * n
         t += ms * 1e-3
         launches += n
+        a = per_level.setdefault(l, [0.0, 0.0, 0.0, 0])
+        a[0] += flops * n
+        a[1] += byts * n
+        a[2] += ms * 1e-3
+        a[3] += n
     achieved = fl / t / 1e12 if t else 0.0
     hbm_peak, hbm_src = hbm_peak_gbs()
     by_level = []
-    for l in sorted({l for (l, _c) in sweep_ms}):
-        lf = lb = lt = 0.0
-        ln = 0
-        for cls in ("F", "C"):
-            if (l, cls) in sweep_ms and f"jacobi_{cls}@L{l}" in work:
-                n, ms = sweep_ms[(l, cls)]
-                flops, byts = work[f"jacobi_{cls}@L{l}"]
-                lf += flops * n
-                lb += byts * n
-                lt += ms * 1e-3
-                ln += n
+    for l in sorted(per_level):
+        lf, lb, lt, ln = per_level[l]
         if lt:
             by_level.append({"level": l, "sweeps": ln, "us_per_sweep": round(1e6 * lt / ln, 2),
                              "tflops": round(lf / lt / 1e12, 4), "frac_fp64": round(lf / lt / 1e12 / FP64_PEAK_TFLOPS, 3),
@@ -499,7 +533,7 @@ def main():
         x.zero_()
         _, rep = s.solve(bvec, x)
         if timed["on"]:
-            for key, (n, ms) in s.sweep_timing().items():
+            for key, (n, ms) in s.sweep_site_timing().items():
                 c, m = sweep_ms.get(key, (0, 0.0))
                 sweep_ms[key] = (c + n, m + ms)
         s.close()

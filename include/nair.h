@@ -259,7 +259,10 @@ nair_status nair_kernel_launches(int64_t *count);
  * summed duration in ms, each sweep timed from its first thread block passing
  * the dependency wait to its last thread block finishing (%globaltimer).  The
  * stamps ride inside the kernels, so the CUDA graph and the overlap of
- * consecutive launches are kept. */
+ * consecutive launches are kept.  cls = 2 + k selects sweep k of the cycle
+ * alone (k = 0 .. f_sweeps + c_sweeps - 1; the F sweeps come first).  A sweep
+ * with no rows to update or copy is not launched and not counted.
+ * INVALID_ARG for a level or cls out of range. */
 nair_status nair_sweep_timing(const nair_handle *h, int32_t level, int32_t cls, int64_t *sweeps,
                               double *total_ms);
 

@@ -200,6 +200,7 @@ class NairSolver:
         self.params = p
         self.b = int(vals.shape[-1])
         self.level_b = 1 if p.scalar else self.b  # block size of the hierarchy's levels
+        self.f_sweeps = p.f_sweeps if p.f_sweeps > 0 else p.neumann_degree + 1
         self.E = int(row_ptr.shape[0] - 1)
         self.n = self.E * self.b
         self.device = vals.device
@@ -318,6 +319,21 @@ class NairSolver:
                        "nair_sweep_timing")
                 if n.value:
                     out[(l, nm)] = (n.value, ms.value)
+        return out
+
+    def sweep_site_timing(self):
+        """{(level, k): (sweeps, total ms)} for sweep k of the cycle (F sweeps first),
+        stamped on the device (sweep_timing=1)."""
+        out = {}
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0)
+        S = self.f_sweeps + max(self.params.c_sweeps, 0)
+        for l in range(self.num_levels()):
+            for k in range(S):
+                _check(lib().nair_sweep_timing(self._h, l, 2 + k, ctypes.byref(n), ctypes.byref(ms)),
+                       "nair_sweep_timing")
+                if n.value:
+                    out[(l, k)] = (n.value, ms.value)
         return out
 
     def level(self, l, adjoint=False):

@@ -315,13 +315,20 @@ const char *nair_last_error(void) { return g_last_error.c_str(); }
 nair_status nair_sweep_timing(const nair_handle *h, int32_t level, int32_t cls, int64_t *sweeps,
                               double *total_ms) {
   NAIR_API_BEGIN
-  if (!h || !sweeps || !total_ms || cls < 0 || cls > 1) return set_error(NAIR_ERR_INVALID_ARG, "bad arguments");
+  if (!h || !sweeps || !total_ms || cls < 0) return set_error(NAIR_ERR_INVALID_ARG, "bad arguments");
   const SweepClock &c = h->mixed ? h->h32.clock : h->h64.clock;
   const int nl = h->mixed ? h->h32.nlev : h->h64.nlev;
   if (level < 0 || level >= nl) return set_error(NAIR_ERR_INVALID_ARG, "level out of range");
+  const int S = h->P.f_sweeps + h->P.c_sweeps;
+  if (cls > 1 + S) return set_error(NAIR_ERR_INVALID_ARG, "no such sweep");
   if (!c.dev) {
     *sweeps = 0;
     *total_ms = 0.0;
+    return NAIR_OK;
+  }
+  if (cls >= 2) {  // sweep cls - 2 of the cycle
+    *sweeps = c.site_count[(size_t)level * c.S + cls - 2];
+    *total_ms = c.site_ms[(size_t)level * c.S + cls - 2];
     return NAIR_OK;
   }
   *sweeps = c.count[2 * level + cls];

@@ -27,6 +27,17 @@ struct Level {
   int *c2f = nullptr;      // coarse index -> element (the C rows, ascending)
   int *f2f = nullptr;      // F index -> element (the F rows, ascending)
   int *fsweep = nullptr, *csweep = nullptr;  // F / C rows ordered by row length (sweep work lists)
+  // F sweeps after the first in a cycle from a zero iterate.  The C values do
+  // not change during the F sweeps, so an F row whose off-diagonal F couplings
+  // all lead to rows that kept their value in sweep k - 1 would recompute its
+  // previous value from the same inputs: sweep k updates only the rows of
+  // fl[k] (F rows with an F coupling to a row of fl[k - 1]; fl[0] = fsweep),
+  // in the order of fsweep.  fq[k] (k >= 2) holds the rows of fl[k - 1] that
+  // are not in fl[k].  Built for nfl = f_sweeps sweeps (0: not built).
+  static constexpr int kMaxFLists = 8;
+  int nfl = 0;
+  int *fl[kMaxFLists] = {}, *fq[kMaxFLists] = {};
+  int fl_n[kMaxFLists] = {}, fq_n[kMaxFLists] = {};
   int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
   DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
   int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)
@@ -80,6 +91,8 @@ struct SweepClock {
   int nsites = 0, S = 0;
   std::vector<long long> count;        // per (level, class)
   std::vector<double> ms;
+  std::vector<long long> site_count;   // per (level, sweep of the cycle)
+  std::vector<double> site_ms;
 };
 
 // One level of the transposed hierarchy, which preconditions A^T with the

@@ -39,6 +39,7 @@ struct RowArgs {
   int comp_ctas, ncopy;
   const int *copy_list;
   T *out2;
+  T *out2c;              // JACOBI: optional second output of the updated rows
   unsigned long long *stamp;  // optional: [0] earliest start, [ns] latest end (device clock)
   int ns;
   // level-0 column-compressed off-diagonal blocks (k_rowop_l0)
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
         for (int c = 0; c < b; ++c) s = fma(d[c], sr[c], s);
       }
       a.out[(size_t)i * b + r] = s;
+      if (a.out2c) a.out2c[(size_t)i * b + r] = s;
     }
   }
   if (a.stamp) {
@@ -311,8 +313,14 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
   }
   if (OP == OP_SPMV) {
     if (active) a.out[(size_t)i * B + r] = acc;
-  } else if (OP == OP_RESID || OP == OP_JACOBI_S) {
+  } else if (OP == OP_RESID) {
     if (active) a.out[(size_t)i * B + r] = a.f[(size_t)i * B + r] - acc;
+  } else if (OP == OP_JACOBI_S) {
+    if (active) {
+      const T v = a.f[(size_t)i * B + r] - acc;
+      a.out[(size_t)i * B + r] = v;
+      if (a.out2c) a.out2c[(size_t)i * B + r] = v;
+    }
   } else {
     if (active) sres[team * B + r] = a.f[(size_t)i * B + r] - acc;
     __syncthreads();
@@ -321,6 +329,7 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
 #pragma unroll
       for (int c = 0; c < B; ++c) s2 = fma(drow[c], sres[team * B + c], s2);
       a.out[(size_t)i * B + r] = s2;
+      if (a.out2c) a.out2c[(size_t)i * B + r] = s2;
     }
   }
   if (a.stamp) {

@@ -1364,6 +1364,115 @@ int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem,
   return out;
 }
 
+// ---------------------------------------------------------------------------
+// work lists of the F sweeps after the first (cycle from a zero iterate)
+// ---------------------------------------------------------------------------
+// cur[i] = 1 for the F rows with an off-diagonal F coupling to a row changed
+// in the previous sweep (prev = null: the first sweep, which changes every F row)
+__global__ void k_fsweep_dep(int E, const int *__restrict__ rp, const int *__restrict__ ci,
+                             const signed char *__restrict__ cf, const unsigned char *__restrict__ prev,
+                             unsigned char *__restrict__ cur) {
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= E) return;
+  unsigned char c = 0;
+  if (!cf[i]) {
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      const int j = ci[p];
+      if (j != i && !cf[j] && (!prev || prev[j])) {
+        c = 1;
+        break;
+      }
+    }
+  }
+  cur[i] = c;
+}
+
+// membership flags over the positions q of fsweep for m = 2 nf - 3 lists:
+// t < nf - 1: the rows of sweep t + 1; t >= nf - 1: the rows of sweep k - 1 not
+// in sweep k, k = t - nf + 3 (ch: nf rows of E flags, row k for sweep k >= 1)
+__global__ void k_fsweep_flags(int nF, int nf, int E, const int *__restrict__ fsweep,
+                               const unsigned char *__restrict__ ch, int *__restrict__ flag) {
+  pdl_wait();
+  const int m = 2 * nf - 3;
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)m * nF) return;
+  const int t = (int)(g / nF), q = (int)(g - (long long)t * nF), i = fsweep[q];
+  int v;
+  if (t < nf - 1) {
+    v = ch[(size_t)(t + 1) * E + i];
+  } else {
+    const int k = t - nf + 3;
+    v = ch[(size_t)(k - 1) * E + i] && !ch[(size_t)k * E + i];
+  }
+  flag[g] = v;
+}
+
+// stable compaction of each list (list t at out + t nF) and its length
+__global__ void k_fsweep_scatter(int nF, int m, const int *__restrict__ fsweep, const int *__restrict__ flag,
+                                 const int *__restrict__ pre, int *__restrict__ out, int *__restrict__ cnt) {
+  pdl_wait();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < m && cnt) cnt[g] = pre[(size_t)(g + 1) * nF] - pre[(size_t)g * nF];
+  if (g >= (long long)m * nF || !flag[g]) return;
+  const int t = (int)(g / nF), q = (int)(g - (long long)t * nF);
+  out[(size_t)t * nF + pre[g] - pre[(size_t)t * nF]] = fsweep[q];
+}
+
+// the lists of every non-coarsest level, with one read-back of their lengths
+template <typename T>
+static void build_fsweep_lists(Hier<T> &H, const Params &P, cudaStream_t s, Mem &mem) {
+  const int nf = P.f_sweeps;
+  if (nf < 2 || nf > Level<T>::kMaxFLists) return;
+  const int m = 2 * nf - 3;
+  Mem tmp;
+  tmp.s = s;
+  int *cnt = tmp.alloc<int>((size_t)H.nlev * m);
+  std::vector<int *> bufs(H.nlev, nullptr);
+  for (int l = 0; l < H.nlev; ++l) {
+    Level<T> &L = H.lev[l];
+    if (L.coarsest || !L.nF) continue;
+    const int E = L.E, nF = L.nF;
+    unsigned char *ch = tmp.alloc<unsigned char>((size_t)nf * E);
+    for (int k = 1; k < nf; ++k) {
+      launch_pdl(k_fsweep_dep, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, (const signed char *)L.cf,
+                 k == 1 ? (const unsigned char *)nullptr : (const unsigned char *)(ch + (size_t)(k - 1) * E),
+                 ch + (size_t)k * E);
+      NAIR_LAUNCH_CHECK();
+    }
+    const long long tot = (long long)m * nF;
+    if (tot >= INT_MAX) continue;  // this level keeps the full F sweeps
+    int *flag = tmp.alloc<int>(tot), *pre = tmp.alloc<int>(tot + 1);
+    launch_pdl(k_fsweep_flags, dim3(grid(tot)), dim3(kThreads), 0, s, nF, nf, E, (const int *)L.fsweep,
+               (const unsigned char *)ch, flag);
+    NAIR_LAUNCH_CHECK();
+    exclusive_scan(flag, pre, (int)tot, s, tmp, false);
+    bufs[l] = mem.alloc<int>(tot);
+    launch_pdl(k_fsweep_scatter, dim3(grid(tot)), dim3(kThreads), 0, s, nF, m, (const int *)L.fsweep,
+               (const int *)flag, (const int *)pre, bufs[l], cnt + (size_t)l * m);
+    NAIR_LAUNCH_CHECK();
+  }
+  std::vector<int> h((size_t)H.nlev * m, 0);
+  NAIR_CK(cudaMemcpyAsync(h.data(), cnt, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s));
+  NAIR_CK(cudaStreamSynchronize(s));
+  for (int l = 0; l < H.nlev; ++l) {
+    Level<T> &L = H.lev[l];
+    if (!bufs[l]) continue;
+    L.nfl = nf;
+    L.fl[0] = L.fsweep;
+    L.fl_n[0] = L.nF;
+    for (int k = 1; k < nf; ++k) {
+      L.fl[k] = bufs[l] + (size_t)(k - 1) * L.nF;
+      L.fl_n[k] = h[(size_t)l * m + k - 1];
+    }
+    for (int k = 2; k < nf; ++k) {
+      const int t = nf - 1 + k - 2;
+      L.fq[k] = bufs[l] + (size_t)t * L.nF;
+      L.fq_n[k] = h[(size_t)l * m + t];
+    }
+  }
+}
+
 // extract rows `rowmap` (nrows of them) of A with the chosen column test
 // The output count stays on the device (out.nnzb = -1, buffers sized by the
 // upper bound A.nnzb, returned in *ub): no host round trip.
@@ -1718,6 +1827,7 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     // b^2 FMAs per row of the D^{-1} apply)
     build_l0scaled<T>(H.lev[0].A, H.lev[0].dinv, H.b, s, mem, H.l0c);
   }
+  build_fsweep_lists<T>(H, P, s, mem);
   // V-cycle vectors and complexities (Sec. 6: OC and CC in work units)
   const int b = H.b;
   double nnz0 = (double)H.lev[0].A.nnzb, oc = 0.0, cc = 0.0;

@@ -261,8 +261,14 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
   }
   // device-clock stamps only in V-cycles, where every sweep site runs once per cycle
   const bool stamp = H.clock.dev && P.cycle == 0;
+  // from a zero iterate the F sweeps after the first update only the rows whose
+  // inputs changed (fl[k]): the first sweep writes its F rows into both buffers,
+  // so a buffer lacks only the rows updated since it was last written -- fq[k]
+  // for sweep k >= 2, fl[f_sweeps - 1] for the first C sweep -- and those are copied
+  const int SF = P.f_sweeps;
+  const bool short_f = zero && SF >= 2 && L.nfl == SF;
   for (int k = 0; k < S; ++k) {
-    const int cls = k < P.f_sweeps ? 0 : 1, oth = 1 - cls, ob = k % 2;
+    const int cls = k < SF ? 0 : 1, oth = 1 - cls, ob = k % 2;
     RowArgs<T> a = row_args(L.A, b);
     a.x = in;
     a.ipc = (k == 0) ? ipc0 : nullptr;
@@ -272,11 +278,23 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
     a.nrows = nrow[cls];
     a.list = rows[cls];
     a.out = buf[ob];
-    if (buf_ver[ob][oth] != cur_ver[oth]) {
+    if (short_f && k >= 1 && k < SF) {
+      // the C rows of both buffers hold P x_c since the first sweep
+      a.nrows = L.fl_n[k];
+      a.list = L.fl[k];
+      if (k >= 2) {
+        a.ncopy = L.fq_n[k];
+        a.copy_list = L.fq[k];
+      }
+    } else if (short_f && k == SF) {
+      a.ncopy = L.fl_n[SF - 1];
+      a.copy_list = L.fl[SF - 1];
+    } else if (buf_ver[ob][oth] != cur_ver[oth]) {
       a.ncopy = nrow[oth];
       a.copy_list = rows[oth];
       if (k == 0 && zero) a.out2 = buf[1 - ob];  // both buffers then hold P x_c on that class
     }
+    if (short_f && k == 0) a.out2c = buf[1];
     if (stamp) {
       a.stamp = H.clock.dev + (size_t)l * S + k;
       a.ns = H.clock.nsites;
@@ -300,7 +318,13 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
     }
     cur_ver[cls] = k + 1;
     buf_ver[ob][cls] = k + 1;
-    if (a.ncopy) {
+    if (short_f && k < SF) {
+      // both buffers hold the C rows of the first sweep; the F rows of buf[ob]
+      // are current, those of the other buffer differ by fl[k]
+      buf_ver[1 - ob][oth] = buf_ver[ob][oth] = cur_ver[oth];
+    } else if (short_f && k == SF) {
+      buf_ver[ob][oth] = cur_ver[oth];
+    } else if (a.ncopy) {
       buf_ver[ob][oth] = cur_ver[oth];
       if (a.out2) buf_ver[1 - ob][oth] = cur_ver[oth];
     }
@@ -703,6 +727,8 @@ static void clock_init(const Hier<T> &H, const Params &P) {
   for (auto &sl : c.slot) NAIR_CK(cudaMallocHost(&sl, sizeof(unsigned long long) * 2 * c.nsites));
   c.count.assign(2 * H.nlev, 0);
   c.ms.assign(2 * H.nlev, 0.0);
+  c.site_count.assign(c.nsites, 0);
+  c.site_ms.assign(c.nsites, 0.0);
 }
 
 // queue a copy of the stamps of the cycle just enqueued into pinned slot q
@@ -725,8 +751,11 @@ static void clock_collect(const Hier<T> &H, const Params &P, int q) {
       const unsigned long long t0 = h[site], t1 = h[c.nsites + site];
       if (t1 == 0 || t0 == ~0ULL || t1 < t0) continue;
       const int cls = k < P.f_sweeps ? 0 : 1;
+      const double ms = (double)(t1 - t0) * 1e-6;
       c.count[2 * l + cls] += 1;
-      c.ms[2 * l + cls] += (double)(t1 - t0) * 1e-6;
+      c.ms[2 * l + cls] += ms;
+      c.site_count[site] += 1;
+      c.site_ms[site] += ms;
     }
 }
 

@@ -1,7 +1,8 @@
 """The benchmark's algorithmic-work accounting of the block-Jacobi sweeps, on
-CPU: `bench.level_work` reads a hierarchy's exported levels, so an oracle
+CPU: `bench.sweep_work` reads a hierarchy's exported levels, so an oracle
 hierarchy (same export layout as the GPU solver's) stands in for the GPU one.
-The counts are checked against sums written out here from the level arrays."""
+The counts are checked against sums written out here from the level arrays,
+and the shortened F-sweep row lists against full sweeps computed here."""
 import numpy as np
 import pytest
 
@@ -28,29 +29,69 @@ def test_l0_width_is_face_node_count():
     assert bench.l0_width(np.ones((3, 32, 32)), 32) == 0
 
 
-def test_level_work_counts(hier):
+def _level_arrays(lev):
+    rows = np.repeat(np.arange(lev["E"]), np.diff(lev["row_ptr"]))
+    return rows, lev["col"], lev["cf"], lev["col"] != rows
+
+
+def test_sweep_work_counts(hier):
     P, H = hier
-    b = P["b"]
-    work = bench.level_work(H, H.nlev, b)
+    b, SF = P["b"], 3
+    work = bench.sweep_work(H, H.nlev, b, SF, 1)
     assert H.nlev >= 3
     for l in range(H.nlev):
         lev = H.level(l)
         if lev["coarsest"]:
-            assert f"jacobi_F@L{l}" not in work
+            assert not any(key[0] == l for key in work)
             continue
-        rows = np.repeat(np.arange(lev["E"]), np.diff(lev["row_ptr"]))
-        off = lev["col"] != rows
-        for cls, name in ((0, "F"), (1, "C")):
-            sel = (lev["cf"][rows] == cls) & off
-            nrow = int(np.count_nonzero(lev["cf"] == cls))
-            flops, byts = work[f"jacobi_{name}@L{l}"]
+        rows, ci, cf, off = _level_arrays(lev)
+        masks = bench.f_sweep_rows(rows, ci, cf, off, SF)
+        for k, upd in enumerate(masks + [cf == 1]):
+            sel = upd[rows] & off
+            nrow = int(upd.sum())
+            if (l, k) not in work:  # nothing to update or copy
+                assert nrow == 0
+                continue
+            flops, byts = work[(l, k)]
             if l == 0:  # scaled, column-compressed couplings: b * W FMAs per block, no D^-1
-                W = P["p"] + 1
-                assert flops == 2.0 * int(sel.sum()) * b * W
+                assert flops == 2.0 * int(sel.sum()) * b * (P["p"] + 1)
             else:       # classical form: exact off-diagonal nonzeros plus b^2 per row for D^-1
                 nnz = int(np.count_nonzero(lev["vals"][sel].reshape(int(sel.sum()), -1)))
                 assert flops == 2.0 * (nnz + nrow * b * b)
-            assert byts > 0 and byts >= 16.0 * lev["E"] * b
+            assert byts >= 16.0 * nrow * b
+
+
+def test_f_sweep_rows_cover_every_changing_row(hier):
+    """Block-Jacobi F sweeps computed over all F rows: every F row outside the
+    list of sweep k keeps its value of sweep k - 1 bit for bit, and the lists
+    shrink (the premise of the shortened F sweeps)."""
+    P, H = hier
+    b, SF = P["b"], 4
+    rng = np.random.default_rng(5)
+    shrunk = 0
+    for l in range(H.nlev):
+        lev = H.level(l)
+        if lev["coarsest"]:
+            continue
+        rows, ci, cf, off = _level_arrays(lev)
+        masks = bench.f_sweep_rows(rows, ci, cf, off, SF)
+        A = lev["vals"]
+        dinv = lev["dinv"].reshape(-1, b, b)
+        f = rng.standard_normal((lev["E"], b))
+        x = rng.standard_normal((lev["E"], b))
+        F = np.flatnonzero(cf == 0)
+        for k in range(SF):
+            prod = np.einsum("prc,pc->pr", A[off], x[ci[off]])
+            acc = np.zeros_like(x)
+            np.add.at(acc, rows[off], prod)
+            new = x.copy()
+            new[F] = np.einsum("irc,ic->ir", dinv[F], f[F] - acc[F])
+            if k >= 1:
+                keep = (cf == 0) & ~masks[k]
+                assert np.array_equal(new[keep], x[keep]), (l, k)
+                shrunk += int(keep.sum())
+            x = new
+    assert shrunk > 0
 
 
 def test_hbm_peak_falls_back_without_measurement(monkeypatch, tmp_path):

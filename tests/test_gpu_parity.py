@@ -266,6 +266,32 @@ def test_adjoint_parity_and_gradients(nair, oracle_mod):
     assert np.allclose(gq.cpu().numpy(), ogq, rtol=1e-12, atol=1e-15 * np.abs(ogq).max())
 
 
+@pytest.mark.parametrize("name,N,p,k", [("C2", 12, 2, 2), ("C3", 6, 3, 1)])
+@pytest.mark.parametrize("fs,cs", [(2, 1), (4, 2), (5, 0), (8, 1), (9, 1)])
+def test_vcycle_sweep_counts_parity(nair, oracle_mod, name, N, p, k, fs, cs):
+    """Forward V-cycles with 2 to 9 F sweeps and 0 to 2 C sweeps against the
+    oracle, which updates every F row in every F sweep: the GPU cycle updates
+    only the rows whose inputs changed (up to 8 F sweeps; more use full sweeps).
+    As an F-cycle too, whose second visit of a level starts from a nonzero
+    iterate and sweeps every row."""
+    P = D.make_problem(name, N=N, p=p)
+    params = dict(neumann_degree=k, max_coarse=4, f_sweeps=fs, c_sweeps=cs)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), **params)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params)
+    f = D.rng.uniform(13, P["n"]) - 0.5
+    for rep in range(2):
+        z = S.vcycle(dev(f)).cpu().numpy()
+        zr = H.vcycle(f)
+        assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    S.close()
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), cycle_type="F", **params)
+    H.set_cycle("F")
+    z = S.vcycle(dev(f)).cpu().numpy()
+    zr = H.vcycle(f)
+    assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    S.close()
+
+
 @pytest.mark.parametrize("name,N,p,k", CASES)
 @pytest.mark.parametrize("fs,cs,graphs", [(0, 1, 1), (3, 0, 1), (1, 2, 0), (0, 1, 0)])
 def test_transposed_cycle_parity(nair, oracle_mod, name, N, p, k, fs, cs, graphs):
