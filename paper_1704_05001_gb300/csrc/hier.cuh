@@ -38,6 +38,13 @@ struct Level {
   int nfl = 0;
   int *fl[kMaxFLists] = {}, *fq[kMaxFLists] = {};
   int fl_n[kMaxFLists] = {}, fq_n[kMaxFLists] = {};
+  // scalar-row form of the off-diagonal blocks for the sweeps of levels >= 1:
+  // scalar row (i, r) lists, in ascending block order, the off-diagonal blocks
+  // p of row i whose row r has a nonzero (offsets srp[i b + r], block indices
+  // sp); perm_f[k] (for fl[k], or fsweep when k = 0) and perm_c (csweep) order
+  // each thread block's scalar rows by their number of entries
+  int *srp = nullptr, *sp = nullptr;
+  unsigned char *perm_f[kMaxFLists] = {}, *perm_c = nullptr;
   int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
   DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
   int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)
@@ -176,6 +183,8 @@ void scalar_matrix(const DBsr<double> &A, int b, const double *Dinv, const int *
 
 // rows of one class ordered by decreasing row length (sweep work list)
 int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem, Mem &tmp);
+// thread groups per row the row kernels use for nrows rows of avg blocks
+int rowop_groups(long long nrows, int b, double avg);
 
 // position of the diagonal block of every row
 void diag_positions(int E, const int *rp, const int *ci, int *out, cudaStream_t s);

@@ -46,6 +46,11 @@ struct RowArgs {
   const int *diag, *oci;
   const unsigned long long *ocols;
   const T *ov;
+  // scalar-row form of the sweep (k_sweep_rows): entries srp[i b + r] ..
+  // srp[i b + r + 1] of sp are the off-diagonal blocks of row i whose row r has
+  // a nonzero; perm orders each thread block's scalar rows by entry count
+  const int *srp, *sp;
+  const unsigned char *perm;
 };
 
 __device__ __forceinline__ unsigned long long global_clock() {
@@ -218,6 +223,119 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
     if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
   }
 }
+
+// Block-Jacobi sweep in scalar-row form (levels >= 1, whose off-diagonal
+// blocks keep about half of their rows zero): thread block c owns rows
+// list[c tpc ..], and its tpc x B scalar rows (i, r) are assigned to threads in
+// the order perm gives -- sorted by entry count, so that the threads of a warp
+// run loops of nearly equal length and the FP64 pipe is not spent on the zero
+// rows of the blocks.  Scalar row (i, r) accumulates sum_p A_p[r, :] x_{col p}
+// over its entries in ascending block order; then each thread of the natural
+// layout applies row r of D_ii^{-1} to f_i - that sum from shared memory.
+template <typename T, int B>
+__global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
+  pdl_launch_dependents();
+  if ((int)blockIdx.x >= a.comp_ctas) {  // copy segment, as in k_rowop
+    const long long g = (long long)(blockIdx.x - a.comp_ctas) * blockDim.x + threadIdx.x;
+    const bool in = g < (long long)a.ncopy * B;
+    const int row = in ? (int)(g / B) : 0, r = in ? (int)(g - (long long)row * B) : 0;
+    const int i = in ? a.copy_list[row] : 0;
+    const int J = (in && a.ipc) ? a.ipc[i] : i;
+    pdl_wait();
+    if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
+    if (in) {
+      const T v = a.ipc ? (J >= 0 ? a.x[(size_t)J * B + r] : (T)0) : a.x[(size_t)i * B + r];
+      a.out[(size_t)i * B + r] = v;
+      if (a.out2) a.out2[(size_t)i * B + r] = v;
+    }
+    if (a.stamp) {
+      __syncthreads();
+      if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
+    }
+    return;
+  }
+  __shared__ T sres[256];
+  const int base = blockIdx.x * a.tpc;
+  const int nact = min(a.tpc, a.nrows - base);  // rows of this thread block
+  const int t = threadIdx.x;
+  // sorted layout: this thread's scalar row
+  const bool act = t < nact * B;
+  const int enc = act ? (int)a.perm[(size_t)base * B + t] : 0;
+  const int team = enc / B, r = enc - team * B;
+  const int i = act ? a.list[base + team] : 0;
+  const int e0 = act ? a.srp[(size_t)i * B + r] : 0, e1 = act ? a.srp[(size_t)i * B + r + 1] : 0;
+  // natural layout: the D^{-1} row this thread applies.  For B <= 10 the
+  // thread block's D^{-1} blocks are staged in shared memory before the
+  // dependency wait; larger blocks are read after the loop
+  const int team2 = t / B, r2 = t - team2 * B;
+  const bool act2 = team2 < nact;
+  const int i2 = act2 ? a.list[base + team2] : 0;
+  constexpr bool kStage = B <= 10;
+  __shared__ T sd[kStage ? (256 / B) * B * B : 1];
+  if constexpr (kStage) {
+    for (int q = t; q < nact * B * B; q += blockDim.x) {
+      const int tm = q / (B * B);
+      sd[q] = a.dinv[(size_t)a.list[base + tm] * B * B + (q - tm * B * B)];
+    }
+  }
+  // the first entry's block and column do not change during the cycle
+  int p0 = -1, j0 = -1;
+  T va0[B];
+  if (e0 < e1) {
+    p0 = a.sp[e0];
+    j0 = a.ci[p0];
+    if (a.ipc) j0 = a.ipc[j0];
+    const T *av = a.v + (size_t)p0 * B * B + r * B;
+#pragma unroll
+    for (int c = 0; c < B; ++c) va0[c] = av[c];
+  }
+  pdl_wait();
+  if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
+  T acc = 0;
+  if (e0 < e1 && j0 >= 0) {
+    const T *xj = a.x + (size_t)j0 * B;
+    T vx[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) vx[c] = xj[c];
+#pragma unroll
+    for (int c = 0; c < B; ++c) acc = fma(va0[c], vx[c], acc);
+  }
+#pragma unroll 2
+  for (int e = e0 + 1; e < e1; ++e) {
+    const int p = a.sp[e];
+    int j = a.ci[p];
+    if (a.ipc) {
+      j = a.ipc[j];
+      if (j < 0) continue;
+    }
+    const T *av = a.v + (size_t)p * B * B + r * B;
+    const T *xj = a.x + (size_t)j * B;
+    T va[B], vx[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
+#pragma unroll
+    for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
+  }
+  if (act) sres[team * B + r] = a.f[(size_t)i * B + r] - acc;
+  __syncthreads();
+  if (act2) {
+    const T *d = kStage ? sd + (size_t)team2 * B * B + r2 * B : a.dinv + (size_t)i2 * B * B + r2 * B;
+    T s2 = 0;
+#pragma unroll
+    for (int c = 0; c < B; ++c) s2 = fma(d[c], sres[team2 * B + c], s2);
+    a.out[(size_t)i2 * B + r2] = s2;
+    if (a.out2c) a.out2c[(size_t)i2 * B + r2] = s2;
+  }
+  if (a.stamp) {
+    __syncthreads();
+    if (threadIdx.x == 0) atomicMax(a.stamp + a.ns, global_clock());
+  }
+}
+
+// host launcher of the scalar-row sweep (b in 3, 6, 10, 15, 21, 28); false if
+// there is no kernel for b
+template <typename T>
+bool launch_sweep_rows(RowArgs<T> a, cudaStream_t s);
 
 // Level-0 form of the row kernel: the diagonal block from the BSR values, the
 // off-diagonal blocks from their W nonzero columns (one team of B threads per

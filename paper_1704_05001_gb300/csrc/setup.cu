@@ -1473,6 +1473,106 @@ static void build_fsweep_lists(Hier<T> &H, const Params &P, cudaStream_t s, Mem 
   }
 }
 
+// ---------------------------------------------------------------------------
+// scalar-row form of the off-diagonal blocks (sweeps of levels >= 1)
+// ---------------------------------------------------------------------------
+// FILL = false: number of off-diagonal blocks of row i whose row r has a
+// nonzero; FILL = true: their block indices, ascending
+template <typename T, bool FILL>
+__global__ void k_srow_entries(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
+                               const T *__restrict__ v, const int *__restrict__ srp, int *__restrict__ cnt,
+                               int *__restrict__ sp) {
+  pdl_wait();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)E * b) return;
+  const int i = (int)(g / b), r = (int)(g - (long long)i * b);
+  int w = FILL ? srp[g] : 0;
+  for (int p = rp[i]; p < rp[i + 1]; ++p) {
+    if (ci[p] == i) continue;
+    const T *row = v + ((size_t)p * b + r) * b;
+    bool nz = false;
+    for (int c = 0; c < b; ++c) nz |= row[c] != (T)0;
+    if (nz) {
+      if (FILL) sp[w] = p;
+      ++w;
+    }
+  }
+  if (!FILL) cnt[g] = w;
+}
+
+// per thread block of a sweep list (tpc rows, tpc b scalar rows): the scalar
+// rows sorted by entry count, ties in natural order; perm[c tpc b + rank] = the
+// natural slot team b + r
+__global__ void k_srow_perm(int n, int b, int tpc, const int *__restrict__ list, const int *__restrict__ srp,
+                            unsigned char *__restrict__ perm) {
+  pdl_wait();
+  __shared__ int key[256];
+  const int base = blockIdx.x * tpc, nact = min(tpc, n - base), t = threadIdx.x, m = nact * b;
+  int k = 0;
+  if (t < m) {
+    const int team = t / b, r = t - team * b;
+    const size_t q = (size_t)list[base + team] * b + r;
+    k = srp[q + 1] - srp[q];
+    key[t] = k;
+  }
+  __syncthreads();
+  if (t >= m) return;
+  int rank = 0;
+  for (int u = 0; u < m; ++u) rank += (key[u] < k) || (key[u] == k && u < t);
+  perm[(size_t)base * b + rank] = (unsigned char)t;
+}
+
+static bool srow_supported(int b) {
+  return b == 3 || b == 6 || b == 10 || b == 15 || b == 21 || b == 28;
+}
+
+template <typename T>
+static unsigned char *srow_perm(int n, int b, double avg, const int *list, const int *srp, cudaStream_t s,
+                                Mem &mem) {
+  // only lists whose rows the row kernel would sweep with one thread group each
+  if (rowop_groups(n, b, avg) != 1) return nullptr;
+  const int tpc = 256 / b;
+  unsigned char *perm = mem.alloc<unsigned char>((size_t)std::max(n, 1) * b);
+  if (n > 0) {
+    launch_pdl(k_srow_perm, dim3(cdiv(n, tpc)), dim3(tpc * b), 0, s, n, b, tpc, list, srp, perm);
+    NAIR_LAUNCH_CHECK();
+  }
+  return perm;
+}
+
+// the scalar-row lists and permutations of every level >= 1 that sweeps
+template <typename T>
+static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
+  const int b = H.b;
+  // FP64 only: it trades the FP64 pipe's work on zero rows for a shuffled
+  // access pattern, which does not pay where FP32 arithmetic is cheap
+  if (!std::is_same<T, double>::value || !srow_supported(b)) return;
+  Mem tmp;
+  tmp.s = s;
+  for (int l = 1; l < H.nlev; ++l) {
+    Level<T> &L = H.lev[l];
+    if (L.coarsest) continue;
+    const long long n = (long long)L.E * b, ub = (long long)L.A.nnzb * b;
+    if (n + 1 >= INT_MAX || ub >= INT_MAX) continue;
+    const double avg = (double)L.A.nnzb / L.E;
+    if (rowop_groups(L.nF, b, avg) != 1 && rowop_groups(L.nC, b, avg) != 1) continue;
+    int *cnt = tmp.alloc<int>(n + 1);
+    launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, L.E, b, (const int *)L.A.rp,
+               (const int *)L.A.ci, (const T *)L.A.v, (const int *)nullptr, cnt, (int *)nullptr);
+    NAIR_LAUNCH_CHECK();
+    L.srp = mem.alloc<int>(n + 1);
+    exclusive_scan(cnt, L.srp, (int)n, s, tmp, false);
+    L.sp = mem.alloc<int>(std::max(ub, 1LL));
+    launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, L.E, b, (const int *)L.A.rp,
+               (const int *)L.A.ci, (const T *)L.A.v, (const int *)L.srp, (int *)nullptr, L.sp);
+    NAIR_LAUNCH_CHECK();
+    L.perm_f[0] = srow_perm<T>(L.nF, b, avg, L.fsweep, L.srp, s, mem);
+    for (int k = 1; k < L.nfl; ++k) L.perm_f[k] = srow_perm<T>(L.fl_n[k], b, avg, L.fl[k], L.srp, s, mem);
+    L.perm_c = srow_perm<T>(L.nC, b, avg, L.csweep, L.srp, s, mem);
+    tmp.release(cnt);
+  }
+}
+
 // extract rows `rowmap` (nrows of them) of A with the chosen column test
 // The output count stays on the device (out.nnzb = -1, buffers sized by the
 // upper bound A.nnzb, returned in *ub): no host round trip.
@@ -1828,6 +1928,7 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     build_l0scaled<T>(H.lev[0].A, H.lev[0].dinv, H.b, s, mem, H.l0c);
   }
   build_fsweep_lists<T>(H, P, s, mem);
+  build_sweep_rows<T>(H, s, mem);
   // V-cycle vectors and complexities (Sec. 6: OC and CC in work units)
   const int b = H.b;
   double nnz0 = (double)H.lev[0].A.nnzb, oc = 0.0, cc = 0.0;

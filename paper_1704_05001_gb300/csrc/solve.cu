@@ -74,19 +74,24 @@ static int sm_count() {
   return n;
 }
 
-template <typename T, int OP>
-void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
-  const int b = a.b;
-  // threads per row: enough block groups that each thread handles about two
-  // blocks of a long (coarse-level) row, keeping the serial chain short; on
-  // small levels more, until the rows fill about one wave of the GPU (those
-  // sweeps are bound by each thread's chain of dependent loads, not by
-  // throughput), up to about one group per block of an average row
+// threads per row of the row kernels: enough block groups that each thread
+// handles about two blocks of a long (coarse-level) row, keeping the serial
+// chain short; on small levels more, until the rows fill about one wave of the
+// GPU (those sweeps are bound by each thread's chain of dependent loads, not by
+// throughput), up to about one group per block of an average row
+int rowop_groups(long long nrows, int b, double avg) {
   int G = 1;
   if (avg > 4.0)
     while (G * 2 <= avg / 2 && G * 2 * b <= 256 && G < 32) G *= 2;
   const long long wave = (long long)sm_count() * 1536;
-  while (G < 32 && G * 2 * b <= 256 && G * 2 <= 2 * avg && (long long)a.nrows * b * G * 2 <= wave) G *= 2;
+  while (G < 32 && G * 2 * b <= 256 && G * 2 <= 2 * avg && nrows * b * G * 2 <= wave) G *= 2;
+  return G;
+}
+
+template <typename T, int OP>
+void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
+  const int b = a.b;
+  const int G = rowop_groups(a.nrows, b, avg);
   a.G = G;
   const int tsz = G * b;
   a.tpc = std::max(1, 256 / tsz);
@@ -109,6 +114,31 @@ void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   }
   NAIR_LAUNCH_CHECK();
 }
+template <typename T>
+bool launch_sweep_rows(RowArgs<T> a, cudaStream_t s) {
+  const int b = a.b;
+  a.G = 1;
+  a.tpc = 256 / b;
+  const int threads = a.tpc * b;
+  a.comp_ctas = cdiv(a.nrows, a.tpc);
+  int blocks = a.comp_ctas;
+  if (a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
+  const dim3 gr(blocks), bl(threads);
+  switch (b) {
+    case 3: if (blocks) launch_pdl(k_sweep_rows<T, 3>, gr, bl, 0, s, a); break;
+    case 6: if (blocks) launch_pdl(k_sweep_rows<T, 6>, gr, bl, 0, s, a); break;
+    case 10: if (blocks) launch_pdl(k_sweep_rows<T, 10>, gr, bl, 0, s, a); break;
+    case 15: if (blocks) launch_pdl(k_sweep_rows<T, 15>, gr, bl, 0, s, a); break;
+    case 21: if (blocks) launch_pdl(k_sweep_rows<T, 21>, gr, bl, 0, s, a); break;
+    case 28: if (blocks) launch_pdl(k_sweep_rows<T, 28>, gr, bl, 0, s, a); break;
+    default: return false;
+  }
+  NAIR_LAUNCH_CHECK();
+  return true;
+}
+template bool launch_sweep_rows<double>(RowArgs<double>, cudaStream_t);
+template bool launch_sweep_rows<float>(RowArgs<float>, cudaStream_t);
+
 template <typename T, int OP>
 void launch_rowop_l0(RowArgs<T> a, int W, cudaStream_t s) {
   const int b = a.b;
@@ -314,7 +344,16 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       a.ov = H.l0c.ov;
       launch_rowop_l0<T, OP_JACOBI>(a, H.l0c.W, s);
     } else {
-      launch_rowop<T, OP_JACOBI>(a, avg, s);
+      // scalar-row form where built: the permutation belongs to the row list in use
+      const unsigned char *perm = cls == 1 ? L.perm_c : L.perm_f[(short_f && k < SF) ? k : 0];
+      bool done = false;
+      if (L.srp && perm && rowop_groups(a.nrows, b, avg) == 1) {
+        a.srp = L.srp;
+        a.sp = L.sp;
+        a.perm = perm;
+        done = launch_sweep_rows<T>(a, s);
+      }
+      if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
     }
     cur_ver[cls] = k + 1;
     buf_ver[ob][cls] = k + 1;

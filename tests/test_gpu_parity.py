@@ -266,6 +266,32 @@ def test_adjoint_parity_and_gradients(nair, oracle_mod):
     assert np.allclose(gq.cpu().numpy(), ogq, rtol=1e-12, atol=1e-15 * np.abs(ogq).max())
 
 
+def test_scalar_row_sweeps_parity(nair, oracle_mod):
+    """A C2 problem large enough that the F and C sweeps of level 1 run with one
+    thread group per row, where FP64 sweeps take the scalar-row form (one thread
+    per row and component over the blocks whose row is nonzero, threads sorted
+    by entry count): V-cycles and the solve against the oracle."""
+    import torch
+    P = D.make_problem("C2", N=224)
+    params = dict(neumann_degree=2, max_coarse=4)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params)
+    L1 = H.level(1)
+    wave = torch.cuda.get_device_properties(0).multi_processor_count * 1536
+    avg = len(L1["col"]) / L1["E"]
+    assert avg <= 4.0 and min(L1["nF"], L1["nC"]) * P["b"] * 2 > wave  # one group per row
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), **params)
+    f = D.rng.uniform(17, P["n"]) - 0.5
+    for rep in range(2):
+        z = S.vcycle(dev(f)).cpu().numpy()
+        zr = H.vcycle(f)
+        assert np.linalg.norm(z - zr) <= 1e-12 * np.linalg.norm(zr)
+    x, rep = S.solve(dev(P["rhs"]))
+    ref = H.solve(P["rhs"])
+    assert rep["iterations"] == ref["iterations"]
+    assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    S.close()
+
+
 @pytest.mark.parametrize("name,N,p,k", [("C2", 12, 2, 2), ("C3", 6, 3, 1)])
 @pytest.mark.parametrize("fs,cs", [(2, 1), (4, 2), (5, 0), (8, 1), (9, 1)])
 def test_vcycle_sweep_counts_parity(nair, oracle_mod, name, N, p, k, fs, cs):
