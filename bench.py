@@ -153,7 +153,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
 # launch, averaged over the sweeps of one C2 V-cycle: dram__bytes_read.sum +
 # dram__bytes_write.sum); None whenever the kernel has changed since the capture.
-JACOBI_TRAFFIC = None
+JACOBI_TRAFFIC = 13.48e6
 
 
 def f_sweep_rows(rows, ci, cf, off, f_sweeps):
@@ -296,7 +296,7 @@ def roofline(nair, params, rp, ci, v, sweep_ms):
             "frac": achieved / FP64_PEAK_TFLOPS,
             "traffic": JACOBI_TRAFFIC,
             "algorithmic_bytes_per_launch": by / launches if launches else None,
-            "kernel": "k_rowop block-Jacobi sweep (FP64, all levels)",
+            "kernel": "block-Jacobi sweep: k_rowop, k_rowop_l0, k_sweep_rows (FP64, all levels)",
             "launches_per_step": None, "launches_timed": launches,
             "kernel_ms_timed": 1e3 * t,
             "hbm_achieved_gbs": by / t / 1e9 if t else 0.0,
