@@ -141,12 +141,15 @@ template void bsr_transpose<double>(const DBsr<double> &, int, DBsr<double> &, c
 template void bsr_transpose<float>(const DBsr<float> &, int, DBsr<float> &, cudaStream_t, Mem &);
 
 template <typename T>
-void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem) {
+void build_transposed(Hier<T> &H, int f_sweeps, cudaStream_t s, Mem &mem) {
   ProfScope ps("transpose_hierarchy", s);
   const int b = H.b;
   H.tlev.assign(H.nlev, TLevel<T>());
   Mem tmp;
   tmp.s = s;
+  const int nf = (f_sweeps >= 2 && f_sweeps <= Level<T>::kMaxFLists) ? f_sweeps : 0, m = nf ? 2 * (nf - 1) : 0;
+  int *lcnt = m ? tmp.alloc<int>((size_t)H.nlev * m) : nullptr;
+  std::vector<int *> lbufs(H.nlev, nullptr);
   for (int l = 0; l < H.nlev; ++l) {
     const Level<T> &L = H.lev[l];
     TLevel<T> &TL = H.tlev[l];
@@ -173,6 +176,8 @@ void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem) {
     const int nC = L.nC, nF = L.nF;
     TL.fsweep = sweep_list(nF, L.f2f, TL.At.rp, s, mem, tmp);
     TL.csweep = sweep_list(nC, L.c2f, TL.At.rp, s, mem, tmp);
+    if (nf)
+      lbufs[l] = fsweep_lists(E, nF, TL.At.rp, TL.At.ci, L.cf, TL.fsweep, nf, lcnt + (size_t)l * m, s, mem, tmp);
     // R_cf (nC rows, element columns) -> R_cf^T (element rows, nC columns)
     DBsr<T> R = L.R;
     R.nrows = nC;
@@ -197,9 +202,17 @@ void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem) {
     TL.r = mem.alloc<T>((size_t)E * b);
   }
   if (!H.lev[0].coarsest) build_l0comp<T>(H.tlev[0].At, H.tlev[0].diag, b, s, mem, H.tl0c);
+  std::vector<int> h((size_t)H.nlev * m, 0);
+  if (m) NAIR_CK(cudaMemcpyAsync(h.data(), lcnt, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s));
   NAIR_CK(cudaStreamSynchronize(s));
+  for (int l = 0; l < H.nlev; ++l) {
+    TLevel<T> &TL = H.tlev[l];
+    if (!lbufs[l]) continue;
+    TL.nfl = nf;
+    fsweep_assign(H.lev[l].nF, nf, lbufs[l], h.data() + (size_t)l * m, TL.fsweep, TL.fl, TL.fl_n, TL.fq, TL.fq_n);
+  }
 }
-template void build_transposed<double>(Hier<double> &, cudaStream_t, Mem &);
-template void build_transposed<float>(Hier<float> &, cudaStream_t, Mem &);
+template void build_transposed<double>(Hier<double> &, int, cudaStream_t, Mem &);
+template void build_transposed<float>(Hier<float> &, int, cudaStream_t, Mem &);
 
 }  // namespace nair

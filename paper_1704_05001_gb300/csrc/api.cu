@@ -468,8 +468,8 @@ static void build_transposed_handle(nair_handle *h) {
   NAIR_CK(cudaEventCreate(&e0));
   NAIR_CK(cudaEventCreate(&e1));
   NAIR_CK(cudaEventRecord(e0, s));
-  if (h->mixed) build_transposed<float>(h->h32, s, h->mem);
-  else build_transposed<double>(h->h64, s, h->mem);
+  if (h->mixed) build_transposed<float>(h->h32, h->P.f_sweeps, s, h->mem);
+  else build_transposed<double>(h->h64, h->P.f_sweeps, s, h->mem);
   h->bwd.b = h->b;
   if (!h->mixed && !h->scalar) {  // level 0 of the transposed hierarchy is A^T itself
     h->bwd.A = h->h64.tlev[0].At;

@@ -32,7 +32,7 @@ struct Level {
   // all lead to rows that kept their value in sweep k - 1 would recompute its
   // previous value from the same inputs: sweep k updates only the rows of
   // fl[k] (F rows with an F coupling to a row of fl[k - 1]; fl[0] = fsweep),
-  // in the order of fsweep.  fq[k] (k >= 2) holds the rows of fl[k - 1] that
+  // in the order of fsweep.  fq[k] (k >= 1) holds the rows of fl[k - 1] that
   // are not in fl[k].  Built for nfl = f_sweeps sweeps (0: not built).
   static constexpr int kMaxFLists = 8;
   int nfl = 0;
@@ -112,6 +112,12 @@ struct TLevel {
   int *diag = nullptr;         // position of the diagonal block of each row of At
   T *dinvT = nullptr;          // (D_ii^{-1})^T, the inverse diagonal blocks of A_l^T
   int *fsweep = nullptr, *csweep = nullptr;  // F / C rows ordered by At row length
+  // F sweeps after the first (they follow the C sweeps, which fix x_C): as
+  // Level::fl / fq, for the couplings of A^T; fq[1] lists the F rows the second
+  // F sweep copies into its buffer
+  int nfl = 0;
+  int *fl[Level<T>::kMaxFLists] = {}, *fq[Level<T>::kMaxFLists] = {};
+  int fl_n[Level<T>::kMaxFLists] = {}, fq_n[Level<T>::kMaxFLists] = {};
   DBsr<T> Rt;                  // R_cf^T: E rows (blocks on F rows only), nC columns
   int *cself = nullptr;        // element -> its coarse index (C) or -1 (F)
   int *pt_rp = nullptr, *pt_ci = nullptr;  // P^T: coarse J -> F elements with ip = J, ascending
@@ -170,7 +176,7 @@ void vcycle_t(const Hier<T> &H, const Params &P, const T *f, T *x, cudaStream_t 
 
 // the transposed form of a built hierarchy (adjoint solves without a second setup)
 template <typename T>
-void build_transposed(Hier<T> &H, cudaStream_t s, Mem &mem);
+void build_transposed(Hier<T> &H, int f_sweeps, cudaStream_t s, Mem &mem);
 
 // block transpose of a block-CSR matrix (each block transposed, rows sorted)
 template <typename T>
@@ -185,6 +191,15 @@ void scalar_matrix(const DBsr<double> &A, int b, const double *Dinv, const int *
 int *sweep_list(int n, const int *list, const int *rp, cudaStream_t s, Mem &mem, Mem &tmp);
 // thread groups per row the row kernels use for nrows rows of avg blocks
 int rowop_groups(long long nrows, int b, double avg);
+// row lists of F sweeps 1 .. nf - 1 that update only the F rows whose inputs
+// changed (matrix rp / ci, F rows fsweep): rows of sweep k, then for each k the
+// rows of sweep k - 1 not in sweep k, 2 (nf - 1) lists of nF slots in the
+// returned buffer, their lengths written to cnt on the device; null when the
+// level keeps full sweeps.  fsweep_assign sets fl / fq from the read-back lengths.
+int *fsweep_lists(int E, int nF, const int *rp, const int *ci, const signed char *cf, const int *fsweep, int nf,
+                  int *cnt, cudaStream_t s, Mem &mem, Mem &tmp);
+void fsweep_assign(int nF, int nf, int *buf, const int *hcnt, int *fsweep, int **fl, int *fl_n, int **fq,
+                   int *fq_n);
 
 // position of the diagonal block of every row
 void diag_positions(int E, const int *rp, const int *ci, int *out, cudaStream_t s);

@@ -1388,13 +1388,14 @@ __global__ void k_fsweep_dep(int E, const int *__restrict__ rp, const int *__res
   cur[i] = c;
 }
 
-// membership flags over the positions q of fsweep for m = 2 nf - 3 lists:
-// t < nf - 1: the rows of sweep t + 1; t >= nf - 1: the rows of sweep k - 1 not
-// in sweep k, k = t - nf + 3 (ch: nf rows of E flags, row k for sweep k >= 1)
+// membership flags over the positions q of fsweep for m = 2 (nf - 1) lists:
+// t < nf - 1: the rows of sweep k = t + 1; t >= nf - 1: the rows of sweep
+// k - 1 that are not in sweep k, k = t - nf + 2 (ch: nf rows of E flags, row k
+// for sweep k >= 1; sweep 0 holds every F row)
 __global__ void k_fsweep_flags(int nF, int nf, int E, const int *__restrict__ fsweep,
                                const unsigned char *__restrict__ ch, int *__restrict__ flag) {
   pdl_wait();
-  const int m = 2 * nf - 3;
+  const int m = 2 * (nf - 1);
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)m * nF) return;
   const int t = (int)(g / nF), q = (int)(g - (long long)t * nF), i = fsweep[q];
@@ -1402,8 +1403,8 @@ __global__ void k_fsweep_flags(int nF, int nf, int E, const int *__restrict__ fs
   if (t < nf - 1) {
     v = ch[(size_t)(t + 1) * E + i];
   } else {
-    const int k = t - nf + 3;
-    v = ch[(size_t)(k - 1) * E + i] && !ch[(size_t)k * E + i];
+    const int k = t - nf + 2;
+    v = (k == 1 || ch[(size_t)(k - 1) * E + i]) && !ch[(size_t)k * E + i];
   }
   flag[g] = v;
 }
@@ -1419,38 +1420,60 @@ __global__ void k_fsweep_scatter(int nF, int m, const int *__restrict__ fsweep, 
   out[(size_t)t * nF + pre[g] - pre[(size_t)t * nF]] = fsweep[q];
 }
 
+// the row lists of F sweeps 1 .. nf - 1 of one level (matrix rp / ci, its F
+// rows fsweep) into a new buffer of 2 (nf - 1) nF entries, list lengths to
+// cnt on the device; null when the level keeps full sweeps
+int *fsweep_lists(int E, int nF, const int *rp, const int *ci, const signed char *cf, const int *fsweep, int nf,
+                  int *cnt, cudaStream_t s, Mem &mem, Mem &tmp) {
+  const int m = 2 * (nf - 1);
+  const long long tot = (long long)m * nF;
+  if (nf < 2 || nF == 0 || tot >= INT_MAX) return nullptr;
+  unsigned char *ch = tmp.alloc<unsigned char>((size_t)nf * E);
+  for (int k = 1; k < nf; ++k) {
+    launch_pdl(k_fsweep_dep, dim3(grid(E)), dim3(kThreads), 0, s, E, rp, ci, cf,
+               k == 1 ? (const unsigned char *)nullptr : (const unsigned char *)(ch + (size_t)(k - 1) * E),
+               ch + (size_t)k * E);
+    NAIR_LAUNCH_CHECK();
+  }
+  int *flag = tmp.alloc<int>(tot), *pre = tmp.alloc<int>(tot + 1);
+  launch_pdl(k_fsweep_flags, dim3(grid(tot)), dim3(kThreads), 0, s, nF, nf, E, fsweep, (const unsigned char *)ch,
+             flag);
+  NAIR_LAUNCH_CHECK();
+  exclusive_scan(flag, pre, (int)tot, s, tmp, false);
+  int *buf = mem.alloc<int>(tot);
+  launch_pdl(k_fsweep_scatter, dim3(grid(tot)), dim3(kThreads), 0, s, nF, m, fsweep, (const int *)flag,
+             (const int *)pre, buf, cnt);
+  NAIR_LAUNCH_CHECK();
+  return buf;
+}
+
+// pointers and lengths of the lists in buf (hcnt: the 2 (nf - 1) lengths)
+void fsweep_assign(int nF, int nf, int *buf, const int *hcnt, int *fsweep, int **fl, int *fl_n, int **fq,
+                   int *fq_n) {
+  fl[0] = fsweep;
+  fl_n[0] = nF;
+  for (int k = 1; k < nf; ++k) {
+    fl[k] = buf + (size_t)(k - 1) * nF;
+    fl_n[k] = hcnt[k - 1];
+    fq[k] = buf + (size_t)(nf - 1 + k - 1) * nF;
+    fq_n[k] = hcnt[nf - 1 + k - 1];
+  }
+}
+
 // the lists of every non-coarsest level, with one read-back of their lengths
 template <typename T>
 static void build_fsweep_lists(Hier<T> &H, const Params &P, cudaStream_t s, Mem &mem) {
   const int nf = P.f_sweeps;
   if (nf < 2 || nf > Level<T>::kMaxFLists) return;
-  const int m = 2 * nf - 3;
+  const int m = 2 * (nf - 1);
   Mem tmp;
   tmp.s = s;
   int *cnt = tmp.alloc<int>((size_t)H.nlev * m);
   std::vector<int *> bufs(H.nlev, nullptr);
   for (int l = 0; l < H.nlev; ++l) {
     Level<T> &L = H.lev[l];
-    if (L.coarsest || !L.nF) continue;
-    const int E = L.E, nF = L.nF;
-    unsigned char *ch = tmp.alloc<unsigned char>((size_t)nf * E);
-    for (int k = 1; k < nf; ++k) {
-      launch_pdl(k_fsweep_dep, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, (const signed char *)L.cf,
-                 k == 1 ? (const unsigned char *)nullptr : (const unsigned char *)(ch + (size_t)(k - 1) * E),
-                 ch + (size_t)k * E);
-      NAIR_LAUNCH_CHECK();
-    }
-    const long long tot = (long long)m * nF;
-    if (tot >= INT_MAX) continue;  // this level keeps the full F sweeps
-    int *flag = tmp.alloc<int>(tot), *pre = tmp.alloc<int>(tot + 1);
-    launch_pdl(k_fsweep_flags, dim3(grid(tot)), dim3(kThreads), 0, s, nF, nf, E, (const int *)L.fsweep,
-               (const unsigned char *)ch, flag);
-    NAIR_LAUNCH_CHECK();
-    exclusive_scan(flag, pre, (int)tot, s, tmp, false);
-    bufs[l] = mem.alloc<int>(tot);
-    launch_pdl(k_fsweep_scatter, dim3(grid(tot)), dim3(kThreads), 0, s, nF, m, (const int *)L.fsweep,
-               (const int *)flag, (const int *)pre, bufs[l], cnt + (size_t)l * m);
-    NAIR_LAUNCH_CHECK();
+    if (L.coarsest) continue;
+    bufs[l] = fsweep_lists(L.E, L.nF, L.A.rp, L.A.ci, L.cf, L.fsweep, nf, cnt + (size_t)l * m, s, mem, tmp);
   }
   std::vector<int> h((size_t)H.nlev * m, 0);
   NAIR_CK(cudaMemcpyAsync(h.data(), cnt, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s));
@@ -1459,17 +1482,7 @@ static void build_fsweep_lists(Hier<T> &H, const Params &P, cudaStream_t s, Mem 
     Level<T> &L = H.lev[l];
     if (!bufs[l]) continue;
     L.nfl = nf;
-    L.fl[0] = L.fsweep;
-    L.fl_n[0] = L.nF;
-    for (int k = 1; k < nf; ++k) {
-      L.fl[k] = bufs[l] + (size_t)(k - 1) * L.nF;
-      L.fl_n[k] = h[(size_t)l * m + k - 1];
-    }
-    for (int k = 2; k < nf; ++k) {
-      const int t = nf - 1 + k - 2;
-      L.fq[k] = bufs[l] + (size_t)t * L.nF;
-      L.fq_n[k] = h[(size_t)l * m + t];
-    }
+    fsweep_assign(L.nF, nf, bufs[l], h.data() + (size_t)l * m, L.fsweep, L.fl, L.fl_n, L.fq, L.fq_n);
   }
 }
 

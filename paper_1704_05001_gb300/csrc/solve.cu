@@ -468,8 +468,13 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
     const int *rows[2] = {TL.fsweep, TL.csweep};
     int cur_ver[2] = {0, 0};  // version of each class (0 = the zero start)
     int buf_ver[2][2] = {{-1, -1}, {-1, -1}};
+    // F sweep m >= 1 updates only the rows of fl[m] (their F couplings reach a
+    // row updated in sweep m - 1; x_C is fixed) and copies fq[m] into its
+    // buffer, which holds every other F row current: the values of sweep m - 2,
+    // or for m = 1 none, fq[1] then being all F rows outside fl[1]
+    const bool tshort = P.f_sweeps >= 2 && TL.nfl == P.f_sweeps;
     for (int k = 0; k < S; ++k) {
-      const int cls = k < P.c_sweeps ? 1 : 0, oth = 1 - cls, ob = k % 2;
+      const int cls = k < P.c_sweeps ? 1 : 0, oth = 1 - cls, ob = k % 2, m = k - P.c_sweeps;
       ProfScope ps(cls == 0 ? "jacobi_tF" : "jacobi_tC", s, l);
       if (k == 0) {
         const long long tot = (long long)(nrow[cls] + nrow[oth]) * b;
@@ -489,7 +494,13 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
       a.nrows = nrow[cls];
       a.list = rows[cls];
       a.out = buf[ob];
-      if (buf_ver[ob][oth] != cur_ver[oth]) {
+      const bool short_f = tshort && cls == 0 && m >= 1 && buf_ver[ob][1] == cur_ver[1];
+      if (short_f) {
+        a.nrows = TL.fl_n[m];
+        a.list = TL.fl[m];
+        a.ncopy = TL.fq_n[m];
+        a.copy_list = TL.fq[m];
+      } else if (buf_ver[ob][oth] != cur_ver[oth]) {
         a.ncopy = nrow[oth];
         a.copy_list = rows[oth];
       }
@@ -501,7 +512,7 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
       }
       cur_ver[cls] = k + 1;
       buf_ver[ob][cls] = k + 1;
-      if (a.ncopy) buf_ver[ob][oth] = cur_ver[oth];
+      if (!short_f && a.ncopy) buf_ver[ob][oth] = cur_ver[oth];
     }
     ProfScope ps("resid_t", s, l);
     RowArgs<T> a = row_args(TL.At, b);

@@ -319,7 +319,7 @@ def test_vcycle_sweep_counts_parity(nair, oracle_mod, name, N, p, k, fs, cs):
 
 
 @pytest.mark.parametrize("name,N,p,k", CASES)
-@pytest.mark.parametrize("fs,cs,graphs", [(0, 1, 1), (3, 0, 1), (1, 2, 0), (0, 1, 0)])
+@pytest.mark.parametrize("fs,cs,graphs", [(0, 1, 1), (3, 0, 1), (1, 2, 0), (0, 1, 0), (4, 2, 1), (9, 1, 1)])
 def test_transposed_cycle_parity(nair, oracle_mod, name, N, p, k, fs, cs, graphs):
     """The transposed cycle of the forward hierarchy (R^T interpolation, P^T
     restriction, C then F pre-sweeps on A^T) against the oracle's, on a seeded
