@@ -291,12 +291,14 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
   }
   // device-clock stamps only in V-cycles, where every sweep site runs once per cycle
   const bool stamp = H.clock.dev && P.cycle == 0;
-  // from a zero iterate the F sweeps after the first update only the rows whose
-  // inputs changed (fl[k]): the first sweep writes its F rows into both buffers,
-  // so a buffer lacks only the rows updated since it was last written -- fq[k]
-  // for sweep k >= 2, fl[f_sweeps - 1] for the first C sweep -- and those are copied
+  // the F sweeps after the first update only the rows whose inputs changed
+  // (fl[k]; x_C is fixed while they run).  A buffer lacks only the rows updated
+  // since it was last written, and those are copied: fq[k] for sweep k >= 2,
+  // fl[f_sweeps - 1] for the first C sweep.  From a zero iterate the first
+  // sweep reads x_c and writes its F rows into both buffers; from a nonzero one
+  // it reads one of them, so sweep 1 copies the F rows outside its list (fq[1])
   const int SF = P.f_sweeps;
-  const bool short_f = zero && SF >= 2 && L.nfl == SF;
+  const bool short_f = SF >= 2 && L.nfl == SF;
   for (int k = 0; k < S; ++k) {
     const int cls = k < SF ? 0 : 1, oth = 1 - cls, ob = k % 2;
     RowArgs<T> a = row_args(L.A, b);
@@ -309,10 +311,10 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
     a.list = rows[cls];
     a.out = buf[ob];
     if (short_f && k >= 1 && k < SF) {
-      // the C rows of both buffers hold P x_c since the first sweep
+      // the C rows of both buffers are current since the first sweep
       a.nrows = L.fl_n[k];
       a.list = L.fl[k];
-      if (k >= 2) {
+      if (k >= 2 || !zero) {
         a.ncopy = L.fq_n[k];
         a.copy_list = L.fq[k];
       }
@@ -324,7 +326,7 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       a.copy_list = rows[oth];
       if (k == 0 && zero) a.out2 = buf[1 - ob];  // both buffers then hold P x_c on that class
     }
-    if (short_f && k == 0) a.out2c = buf[1];
+    if (short_f && zero && k == 0) a.out2c = buf[1];
     if (stamp) {
       a.stamp = H.clock.dev + (size_t)l * S + k;
       a.ns = H.clock.nsites;
