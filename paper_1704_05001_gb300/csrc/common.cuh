@@ -144,6 +144,9 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // (synchronises the stream to read it back when want_total is set)
 int exclusive_scan(const int *in, int *out, int n, cudaStream_t s, Mem &tmp, bool want_total = true);
 
+// rows per thread block of the scalar-row sweep with G threads per scalar row
+inline int sweep_rows_tpc(int b, int G) { return 256 / (b * G) > 1 ? 256 / (b * G) : 1; }
+
 // read one int from device memory (synchronising)
 int read_int(const int *p, cudaStream_t s);
 

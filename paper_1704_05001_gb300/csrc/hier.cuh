@@ -42,9 +42,10 @@ struct Level {
   // scalar row (i, r) lists, in ascending block order, the off-diagonal blocks
   // p of row i whose row r has a nonzero (offsets srp[i b + r], block indices
   // sp); perm_f[k] (for fl[k], or fsweep when k = 0) and perm_c (csweep) order
-  // each thread block's scalar rows by their number of entries
+  // the scalar rows of each thread block of *_tpc rows by their number of entries
   int *srp = nullptr, *sp = nullptr;
   unsigned char *perm_f[kMaxFLists] = {}, *perm_c = nullptr;
+  int perm_f_tpc[kMaxFLists] = {}, perm_c_tpc = 0;
   int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
   DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
   int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)

@@ -226,12 +226,14 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
 
 // Block-Jacobi sweep in scalar-row form (levels >= 1, whose off-diagonal
 // blocks keep about half of their rows zero): thread block c owns rows
-// list[c tpc ..], and its tpc x B scalar rows (i, r) are assigned to threads in
-// the order perm gives -- sorted by entry count, so that the threads of a warp
-// run loops of nearly equal length and the FP64 pipe is not spent on the zero
-// rows of the blocks.  Scalar row (i, r) accumulates sum_p A_p[r, :] x_{col p}
-// over its entries in ascending block order; then each thread of the natural
-// layout applies row r of D_ii^{-1} to f_i - that sum from shared memory.
+// list[c tpc ..], and its tpc x B scalar rows (i, r) are assigned, G threads
+// each, in the order perm gives -- sorted by entry count, so that the threads
+// of a warp run loops of nearly equal length and the FP64 pipe is not spent on
+// the zero rows of the blocks.  Thread g of scalar row (i, r) accumulates
+// sum_p A_p[r, :] x_{col p} over its entries g, g + G, ... in ascending block
+// order; the G partial sums are added by the pairwise tree of the row kernels;
+// then each thread of the natural layout applies row r of D_ii^{-1} to f_i -
+// that sum from shared memory.
 template <typename T, int B>
 __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
   pdl_launch_dependents();
@@ -255,15 +257,18 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
     return;
   }
   __shared__ T sres[256];
+  __shared__ T red[256];
+  const int G = a.G;
   const int base = blockIdx.x * a.tpc;
   const int nact = min(a.tpc, a.nrows - base);  // rows of this thread block
   const int t = threadIdx.x;
-  // sorted layout: this thread's scalar row
-  const bool act = t < nact * B;
-  const int enc = act ? (int)a.perm[(size_t)base * B + t] : 0;
+  // sorted layout: this thread's scalar row and its share g of the entries
+  const int slot = t / G, g = t - slot * G;
+  const bool act = slot < nact * B;
+  const int enc = act ? (int)a.perm[(size_t)base * B + slot] : 0;
   const int team = enc / B, r = enc - team * B;
   const int i = act ? a.list[base + team] : 0;
-  const int e0 = act ? a.srp[(size_t)i * B + r] : 0, e1 = act ? a.srp[(size_t)i * B + r + 1] : 0;
+  const int e0 = act ? a.srp[(size_t)i * B + r] + g : 0, e1 = act ? a.srp[(size_t)i * B + r + 1] : 0;
   // natural layout: the D^{-1} row this thread applies.  For B <= 10 the
   // thread block's D^{-1} blocks are staged in shared memory before the
   // dependency wait; larger blocks are read after the loop
@@ -279,10 +284,10 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
     }
   }
   // the first entry's block and column do not change during the cycle
-  int p0 = -1, j0 = -1;
+  int j0 = -1;
   T va0[B];
   if (e0 < e1) {
-    p0 = a.sp[e0];
+    const int p0 = a.sp[e0];
     j0 = a.ci[p0];
     if (a.ipc) j0 = a.ipc[j0];
     const T *av = a.v + (size_t)p0 * B * B + r * B;
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
     for (int c = 0; c < B; ++c) acc = fma(va0[c], vx[c], acc);
   }
 #pragma unroll 2
-  for (int e = e0 + 1; e < e1; ++e) {
+  for (int e = e0 + G; e < e1; e += G) {
     const int p = a.sp[e];
     int j = a.ci[p];
     if (a.ipc) {
@@ -316,7 +321,17 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
 #pragma unroll
     for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
   }
-  if (act) sres[team * B + r] = a.f[(size_t)i * B + r] - acc;
+  if (G > 1) {  // pairwise tree over the G partial sums of each scalar row
+    if (act) red[enc * G + g] = acc;
+    __syncthreads();
+    for (int h = G / 2; h > 0; h >>= 1) {
+      if (act && g < h) red[enc * G + g] += red[enc * G + g + h];
+      __syncthreads();
+    }
+    if (t < nact * B) sres[t] = a.f[(size_t)i2 * B + r2] - red[t * G];
+  } else if (act) {
+    sres[enc] = a.f[(size_t)i * B + r] - acc;
+  }
   __syncthreads();
   if (act2) {
     const T *d = kStage ? sd + (size_t)team2 * B * B + r2 * B : a.dinv + (size_t)i2 * B * B + r2 * B;
@@ -332,10 +347,11 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
   }
 }
 
-// host launcher of the scalar-row sweep (b in 3, 6, 10, 15, 21, 28); false if
-// there is no kernel for b
+// host launcher of the scalar-row sweep with G threads per scalar row and
+// tpc = max(1, 256 / (b G)) rows per thread block (b in 3, 6, 10, 15, 21, 28);
+// false if there is no kernel for b
 template <typename T>
-bool launch_sweep_rows(RowArgs<T> a, cudaStream_t s);
+bool launch_sweep_rows(RowArgs<T> a, int G, cudaStream_t s);
 
 // Level-0 form of the row kernel: the diagonal block from the BSR values, the
 // off-diagonal blocks from their W nonzero columns (one team of B threads per

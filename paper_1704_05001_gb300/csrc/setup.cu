@@ -1539,12 +1539,17 @@ static bool srow_supported(int b) {
   return b == 3 || b == 6 || b == 10 || b == 15 || b == 21 || b == 28;
 }
 
+// largest thread-group count per row that takes the scalar-row form: with 16
+// or more groups a thread already handles about one block of a row
+static constexpr int kSweepRowsMaxG = 8;
+
 template <typename T>
 static unsigned char *srow_perm(int n, int b, double avg, const int *list, const int *srp, cudaStream_t s,
-                                Mem &mem) {
-  // only lists whose rows the row kernel would sweep with one thread group each
-  if (rowop_groups(n, b, avg) != 1) return nullptr;
-  const int tpc = 256 / b;
+                                Mem &mem, int *tpc_out) {
+  const int G = rowop_groups(n, b, avg);
+  if (G > kSweepRowsMaxG) return nullptr;
+  const int tpc = sweep_rows_tpc(b, G);
+  *tpc_out = tpc;
   unsigned char *perm = mem.alloc<unsigned char>((size_t)std::max(n, 1) * b);
   if (n > 0) {
     launch_pdl(k_srow_perm, dim3(cdiv(n, tpc)), dim3(tpc * b), 0, s, n, b, tpc, list, srp, perm);
@@ -1568,7 +1573,7 @@ static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
     const long long n = (long long)L.E * b, ub = (long long)L.A.nnzb * b;
     if (n + 1 >= INT_MAX || ub >= INT_MAX) continue;
     const double avg = (double)L.A.nnzb / L.E;
-    if (rowop_groups(L.nF, b, avg) != 1 && rowop_groups(L.nC, b, avg) != 1) continue;
+    if (rowop_groups(L.nF, b, avg) > kSweepRowsMaxG && rowop_groups(L.nC, b, avg) > kSweepRowsMaxG) continue;
     int *cnt = tmp.alloc<int>(n + 1);
     launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, L.E, b, (const int *)L.A.rp,
                (const int *)L.A.ci, (const T *)L.A.v, (const int *)nullptr, cnt, (int *)nullptr);
@@ -1579,9 +1584,10 @@ static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
     launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, L.E, b, (const int *)L.A.rp,
                (const int *)L.A.ci, (const T *)L.A.v, (const int *)L.srp, (int *)nullptr, L.sp);
     NAIR_LAUNCH_CHECK();
-    L.perm_f[0] = srow_perm<T>(L.nF, b, avg, L.fsweep, L.srp, s, mem);
-    for (int k = 1; k < L.nfl; ++k) L.perm_f[k] = srow_perm<T>(L.fl_n[k], b, avg, L.fl[k], L.srp, s, mem);
-    L.perm_c = srow_perm<T>(L.nC, b, avg, L.csweep, L.srp, s, mem);
+    L.perm_f[0] = srow_perm<T>(L.nF, b, avg, L.fsweep, L.srp, s, mem, &L.perm_f_tpc[0]);
+    for (int k = 1; k < L.nfl; ++k)
+      L.perm_f[k] = srow_perm<T>(L.fl_n[k], b, avg, L.fl[k], L.srp, s, mem, &L.perm_f_tpc[k]);
+    L.perm_c = srow_perm<T>(L.nC, b, avg, L.csweep, L.srp, s, mem, &L.perm_c_tpc);
     tmp.release(cnt);
   }
 }

@@ -115,11 +115,11 @@ void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   NAIR_LAUNCH_CHECK();
 }
 template <typename T>
-bool launch_sweep_rows(RowArgs<T> a, cudaStream_t s) {
+bool launch_sweep_rows(RowArgs<T> a, int G, cudaStream_t s) {
   const int b = a.b;
-  a.G = 1;
-  a.tpc = 256 / b;
-  const int threads = a.tpc * b;
+  a.G = G;
+  a.tpc = sweep_rows_tpc(b, G);
+  const int threads = a.tpc * b * G;
   a.comp_ctas = cdiv(a.nrows, a.tpc);
   int blocks = a.comp_ctas;
   if (a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
@@ -136,8 +136,8 @@ bool launch_sweep_rows(RowArgs<T> a, cudaStream_t s) {
   NAIR_LAUNCH_CHECK();
   return true;
 }
-template bool launch_sweep_rows<double>(RowArgs<double>, cudaStream_t);
-template bool launch_sweep_rows<float>(RowArgs<float>, cudaStream_t);
+template bool launch_sweep_rows<double>(RowArgs<double>, int, cudaStream_t);
+template bool launch_sweep_rows<float>(RowArgs<float>, int, cudaStream_t);
 
 template <typename T, int OP>
 void launch_rowop_l0(RowArgs<T> a, int W, cudaStream_t s) {
@@ -346,14 +346,18 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       a.ov = H.l0c.ov;
       launch_rowop_l0<T, OP_JACOBI>(a, H.l0c.W, s);
     } else {
-      // scalar-row form where built: the permutation belongs to the row list in use
-      const unsigned char *perm = cls == 1 ? L.perm_c : L.perm_f[(short_f && k < SF) ? k : 0];
+      // scalar-row form where built: the permutation belongs to the row list in
+      // use and was sorted for the same thread groups per row
+      const int pk = (short_f && k < SF) ? k : 0;
+      const unsigned char *perm = cls == 1 ? L.perm_c : L.perm_f[pk];
+      const int ptpc = cls == 1 ? L.perm_c_tpc : L.perm_f_tpc[pk];
+      const int G = rowop_groups(a.nrows, b, avg);
       bool done = false;
-      if (L.srp && perm && rowop_groups(a.nrows, b, avg) == 1) {
+      if (L.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
         a.srp = L.srp;
         a.sp = L.sp;
         a.perm = perm;
-        done = launch_sweep_rows<T>(a, s);
+        done = launch_sweep_rows<T>(a, G, s);
       }
       if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
     }
