@@ -1562,8 +1562,10 @@ static unsigned char *srow_perm(int n, int b, double avg, const int *list, const
 template <typename T>
 static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
   const int b = H.b;
-  // FP64 only: it trades the FP64 pipe's work on zero rows for a shuffled
-  // access pattern, which does not pay where FP32 arithmetic is cheap
+  // FP64 only: it saves FP64 issue slots at the price of a shuffled access
+  // pattern and a longer setup; the FP32 sweeps are not bound by arithmetic
+  // and did not gain (mixed-precision setup + solve C3 40.0 -> 39.7 ms, C5
+  // 427.6 -> 434.7 ms)
   if (!std::is_same<T, double>::value || !srow_supported(b)) return;
   Mem tmp;
   tmp.s = s;
