@@ -147,7 +147,7 @@ void build_transposed(Hier<T> &H, int f_sweeps, cudaStream_t s, Mem &mem) {
   H.tlev.assign(H.nlev, TLevel<T>());
   Mem tmp;
   tmp.s = s;
-  const int nf = (f_sweeps >= 2 && f_sweeps <= Level<T>::kMaxFLists) ? f_sweeps : 0, m = nf ? 2 * (nf - 1) : 0;
+  const int nf = (f_sweeps >= 2 && f_sweeps <= kMaxFLists) ? f_sweeps : 0, m = nf ? 2 * (nf - 1) : 0;
   int *lcnt = m ? tmp.alloc<int>((size_t)H.nlev * m) : nullptr;
   std::vector<int *> lbufs(H.nlev, nullptr);
   for (int l = 0; l < H.nlev; ++l) {
@@ -211,6 +211,13 @@ void build_transposed(Hier<T> &H, int f_sweeps, cudaStream_t s, Mem &mem) {
     TL.nfl = nf;
     fsweep_assign(H.lev[l].nF, nf, lbufs[l], h.data() + (size_t)l * m, TL.fsweep, TL.fl, TL.fl_n, TL.fq, TL.fq_n);
   }
+  for (int l = 1; l < H.nlev; ++l) {
+    const Level<T> &L = H.lev[l];
+    TLevel<T> &TL = H.tlev[l];
+    if (L.coarsest) continue;
+    build_sweep_rows_level<T>(L.E, L.nF, L.nC, b, TL.At, TL.fsweep, TL.nfl, TL.fl, TL.fl_n, TL.csweep, TL.sr, s, mem);
+  }
+  NAIR_CK(cudaStreamSynchronize(s));
 }
 template void build_transposed<double>(Hier<double> &, int, cudaStream_t, Mem &);
 template void build_transposed<float>(Hier<float> &, int, cudaStream_t, Mem &);

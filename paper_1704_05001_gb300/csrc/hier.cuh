@@ -14,6 +14,20 @@ struct DBsr {
   T *v = nullptr;
 };
 
+// most F sweeps per cycle with their own row lists
+static constexpr int kMaxFLists = 8;
+
+// scalar-row form of a level's off-diagonal blocks for its FP64 sweeps:
+// scalar row (i, r) lists, in ascending block order, the off-diagonal blocks
+// p of row i whose row r has a nonzero (offsets srp[i b + r], block indices
+// sp); perm_f[k] (for F sweep k's rows, fsweep when k = 0) and perm_c (csweep)
+// order the scalar rows of each thread block of *_tpc rows by entry count
+struct SweepRows {
+  int *srp = nullptr, *sp = nullptr;
+  unsigned char *perm_f[kMaxFLists] = {}, *perm_c = nullptr;
+  int perm_f_tpc[kMaxFLists] = {}, perm_c_tpc = 0;
+};
+
 // One level of the hierarchy (Sec. 5).  Index spaces: elements 0..E-1 of the
 // level; F elements numbered 0..nF-1 and C elements 0..nC-1 in ascending
 // element order (the C numbering is the next level's element numbering).
@@ -34,18 +48,10 @@ struct Level {
   // fl[k] (F rows with an F coupling to a row of fl[k - 1]; fl[0] = fsweep),
   // in the order of fsweep.  fq[k] (k >= 1) holds the rows of fl[k - 1] that
   // are not in fl[k].  Built for nfl = f_sweeps sweeps (0: not built).
-  static constexpr int kMaxFLists = 8;
   int nfl = 0;
   int *fl[kMaxFLists] = {}, *fq[kMaxFLists] = {};
   int fl_n[kMaxFLists] = {}, fq_n[kMaxFLists] = {};
-  // scalar-row form of the off-diagonal blocks for the sweeps of levels >= 1:
-  // scalar row (i, r) lists, in ascending block order, the off-diagonal blocks
-  // p of row i whose row r has a nonzero (offsets srp[i b + r], block indices
-  // sp); perm_f[k] (for fl[k], or fsweep when k = 0) and perm_c (csweep) order
-  // the scalar rows of each thread block of *_tpc rows by their number of entries
-  int *srp = nullptr, *sp = nullptr;
-  unsigned char *perm_f[kMaxFLists] = {}, *perm_c = nullptr;
-  int perm_f_tpc[kMaxFLists] = {}, perm_c_tpc = 0;
+  SweepRows sr;  // levels >= 1, FP64
   int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
   DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
   int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)
@@ -117,8 +123,9 @@ struct TLevel {
   // Level::fl / fq, for the couplings of A^T; fq[1] lists the F rows the second
   // F sweep copies into its buffer
   int nfl = 0;
-  int *fl[Level<T>::kMaxFLists] = {}, *fq[Level<T>::kMaxFLists] = {};
-  int fl_n[Level<T>::kMaxFLists] = {}, fq_n[Level<T>::kMaxFLists] = {};
+  int *fl[kMaxFLists] = {}, *fq[kMaxFLists] = {};
+  int fl_n[kMaxFLists] = {}, fq_n[kMaxFLists] = {};
+  SweepRows sr;  // levels >= 1, FP64, for the rows of A^T
   DBsr<T> Rt;                  // R_cf^T: E rows (blocks on F rows only), nC columns
   int *cself = nullptr;        // element -> its coarse index (C) or -1 (F)
   int *pt_rp = nullptr, *pt_ci = nullptr;  // P^T: coarse J -> F elements with ip = J, ascending
@@ -201,6 +208,11 @@ int *fsweep_lists(int E, int nF, const int *rp, const int *ci, const signed char
                   int *cnt, cudaStream_t s, Mem &mem, Mem &tmp);
 void fsweep_assign(int nF, int nf, int *buf, const int *hcnt, int *fsweep, int **fl, int *fl_n, int **fq,
                    int *fq_n);
+// the scalar-row form of one level's matrix A for its sweep lists (FP64 and
+// the DG block sizes; otherwise sr stays empty and the sweeps use k_rowop)
+template <typename T>
+void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, int *fsweep, int nfl,
+                            int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s, Mem &mem);
 
 // position of the diagonal block of every row
 void diag_positions(int E, const int *rp, const int *ci, int *out, cudaStream_t s);

@@ -1464,7 +1464,7 @@ void fsweep_assign(int nF, int nf, int *buf, const int *hcnt, int *fsweep, int *
 template <typename T>
 static void build_fsweep_lists(Hier<T> &H, const Params &P, cudaStream_t s, Mem &mem) {
   const int nf = P.f_sweeps;
-  if (nf < 2 || nf > Level<T>::kMaxFLists) return;
+  if (nf < 2 || nf > kMaxFLists) return;
   const int m = 2 * (nf - 1);
   Mem tmp;
   tmp.s = s;
@@ -1558,39 +1558,46 @@ static unsigned char *srow_perm(int n, int b, double avg, const int *list, const
   return perm;
 }
 
-// the scalar-row lists and permutations of every level >= 1 that sweeps
 template <typename T>
-static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
-  const int b = H.b;
+void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, int *fsweep, int nfl,
+                            int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s, Mem &mem) {
   // FP64 only: it saves FP64 issue slots at the price of a shuffled access
   // pattern and a longer setup; the FP32 sweeps are not bound by arithmetic
   // and did not gain (mixed-precision setup + solve C3 40.0 -> 39.7 ms, C5
   // 427.6 -> 434.7 ms)
-  if (!std::is_same<T, double>::value || !srow_supported(b)) return;
+  if (!std::is_same<T, double>::value || !srow_supported(b) || E == 0) return;
+  const long long n = (long long)E * b, ub = (long long)A.nnzb * b;
+  if (n + 1 >= INT_MAX || ub >= INT_MAX) return;
+  const double avg = (double)A.nnzb / E;
+  if (rowop_groups(nF, b, avg) > kSweepRowsMaxG && rowop_groups(nC, b, avg) > kSweepRowsMaxG) return;
   Mem tmp;
   tmp.s = s;
+  int *cnt = tmp.alloc<int>(n + 1);
+  launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)A.rp,
+             (const int *)A.ci, (const T *)A.v, (const int *)nullptr, cnt, (int *)nullptr);
+  NAIR_LAUNCH_CHECK();
+  sr.srp = mem.alloc<int>(n + 1);
+  exclusive_scan(cnt, sr.srp, (int)n, s, tmp, false);
+  sr.sp = mem.alloc<int>(std::max(ub, 1LL));
+  launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)A.rp,
+             (const int *)A.ci, (const T *)A.v, (const int *)sr.srp, (int *)nullptr, sr.sp);
+  NAIR_LAUNCH_CHECK();
+  sr.perm_f[0] = srow_perm<T>(nF, b, avg, fsweep, sr.srp, s, mem, &sr.perm_f_tpc[0]);
+  for (int k = 1; k < nfl; ++k) sr.perm_f[k] = srow_perm<T>(fl_n[k], b, avg, fl[k], sr.srp, s, mem, &sr.perm_f_tpc[k]);
+  sr.perm_c = srow_perm<T>(nC, b, avg, csweep, sr.srp, s, mem, &sr.perm_c_tpc);
+}
+template void build_sweep_rows_level<double>(int, int, int, int, const DBsr<double> &, int *, int, int *const *,
+                                             const int *, int *, SweepRows &, cudaStream_t, Mem &);
+template void build_sweep_rows_level<float>(int, int, int, int, const DBsr<float> &, int *, int, int *const *,
+                                            const int *, int *, SweepRows &, cudaStream_t, Mem &);
+
+// the scalar-row lists and permutations of every level >= 1 that sweeps
+template <typename T>
+static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
   for (int l = 1; l < H.nlev; ++l) {
     Level<T> &L = H.lev[l];
     if (L.coarsest) continue;
-    const long long n = (long long)L.E * b, ub = (long long)L.A.nnzb * b;
-    if (n + 1 >= INT_MAX || ub >= INT_MAX) continue;
-    const double avg = (double)L.A.nnzb / L.E;
-    if (rowop_groups(L.nF, b, avg) > kSweepRowsMaxG && rowop_groups(L.nC, b, avg) > kSweepRowsMaxG) continue;
-    int *cnt = tmp.alloc<int>(n + 1);
-    launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, L.E, b, (const int *)L.A.rp,
-               (const int *)L.A.ci, (const T *)L.A.v, (const int *)nullptr, cnt, (int *)nullptr);
-    NAIR_LAUNCH_CHECK();
-    L.srp = mem.alloc<int>(n + 1);
-    exclusive_scan(cnt, L.srp, (int)n, s, tmp, false);
-    L.sp = mem.alloc<int>(std::max(ub, 1LL));
-    launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, L.E, b, (const int *)L.A.rp,
-               (const int *)L.A.ci, (const T *)L.A.v, (const int *)L.srp, (int *)nullptr, L.sp);
-    NAIR_LAUNCH_CHECK();
-    L.perm_f[0] = srow_perm<T>(L.nF, b, avg, L.fsweep, L.srp, s, mem, &L.perm_f_tpc[0]);
-    for (int k = 1; k < L.nfl; ++k)
-      L.perm_f[k] = srow_perm<T>(L.fl_n[k], b, avg, L.fl[k], L.srp, s, mem, &L.perm_f_tpc[k]);
-    L.perm_c = srow_perm<T>(L.nC, b, avg, L.csweep, L.srp, s, mem, &L.perm_c_tpc);
-    tmp.release(cnt);
+    build_sweep_rows_level<T>(L.E, L.nF, L.nC, H.b, L.A, L.fsweep, L.nfl, L.fl, L.fl_n, L.csweep, L.sr, s, mem);
   }
 }
 

@@ -349,13 +349,13 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       // scalar-row form where built: the permutation belongs to the row list in
       // use and was sorted for the same thread groups per row
       const int pk = (short_f && k < SF) ? k : 0;
-      const unsigned char *perm = cls == 1 ? L.perm_c : L.perm_f[pk];
-      const int ptpc = cls == 1 ? L.perm_c_tpc : L.perm_f_tpc[pk];
+      const unsigned char *perm = cls == 1 ? L.sr.perm_c : L.sr.perm_f[pk];
+      const int ptpc = cls == 1 ? L.sr.perm_c_tpc : L.sr.perm_f_tpc[pk];
       const int G = rowop_groups(a.nrows, b, avg);
       bool done = false;
-      if (L.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
-        a.srp = L.srp;
-        a.sp = L.sp;
+      if (L.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
+        a.srp = L.sr.srp;
+        a.sp = L.sr.sp;
         a.perm = perm;
         done = launch_sweep_rows<T>(a, G, s);
       }
@@ -514,7 +514,18 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
         l0_args(a, TL, H.tl0c);
         launch_rowop_l0<T, OP_JACOBI>(a, H.tl0c.W, s);
       } else {
-        launch_rowop<T, OP_JACOBI>(a, avg, s);
+        // scalar-row form of A^T where built, as in the forward cycle
+        const unsigned char *perm = cls == 1 ? TL.sr.perm_c : TL.sr.perm_f[short_f ? m : 0];
+        const int ptpc = cls == 1 ? TL.sr.perm_c_tpc : TL.sr.perm_f_tpc[short_f ? m : 0];
+        const int G = rowop_groups(a.nrows, b, avg);
+        bool done = false;
+        if (TL.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
+          a.srp = TL.sr.srp;
+          a.sp = TL.sr.sp;
+          a.perm = perm;
+          done = launch_sweep_rows<T>(a, G, s);
+        }
+        if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
       }
       cur_ver[cls] = k + 1;
       buf_ver[ob][cls] = k + 1;
