@@ -153,7 +153,7 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
 # launch, averaged over the sweeps of one C2 V-cycle: dram__bytes_read.sum +
 # dram__bytes_write.sum); None whenever the kernel has changed since the capture.
-JACOBI_TRAFFIC = 13.48e6
+JACOBI_TRAFFIC = 13.04e6
 
 
 def f_sweep_rows(rows, ci, cf, off, f_sweeps):
