@@ -61,10 +61,27 @@ def test_sweep_work_counts(hier):
             assert byts >= 16.0 * nrow * b
 
 
-def test_f_sweep_rows_cover_every_changing_row(hier):
+def _transpose_level(lev, b):
+    """Block transpose of a level matrix with its inverse diagonal blocks:
+    (A^T)_ji = (A_ij)^T, rows sorted by column, (D_ii^{-1})^T."""
+    E = lev["E"]
+    rows = np.repeat(np.arange(E), np.diff(lev["row_ptr"]))
+    order = np.lexsort((rows, lev["col"]))
+    trows, tcols = lev["col"][order], rows[order]
+    t = dict(lev)
+    t["row_ptr"] = np.concatenate(([0], np.cumsum(np.bincount(trows, minlength=E)))).astype(np.int32)
+    t["col"] = tcols.astype(np.int32)
+    t["vals"] = np.ascontiguousarray(lev["vals"][order].transpose(0, 2, 1))
+    t["dinv"] = np.ascontiguousarray(lev["dinv"].reshape(-1, b, b).transpose(0, 2, 1))
+    return t
+
+
+@pytest.mark.parametrize("transposed", [False, True])
+def test_f_sweep_rows_cover_every_changing_row(hier, transposed):
     """Block-Jacobi F sweeps computed over all F rows: every F row outside the
     list of sweep k keeps its value of sweep k - 1 bit for bit, and the lists
-    shrink (the premise of the shortened F sweeps)."""
+    shrink (the premise of the shortened F sweeps), for A and for A^T (the
+    transposed cycle's F sweeps, with A's C/F split)."""
     P, H = hier
     b, SF = P["b"], 4
     rng = np.random.default_rng(5)
@@ -73,6 +90,8 @@ def test_f_sweep_rows_cover_every_changing_row(hier):
         lev = H.level(l)
         if lev["coarsest"]:
             continue
+        if transposed:
+            lev = _transpose_level(lev, b)
         rows, ci, cf, off = _level_arrays(lev)
         masks = bench.f_sweep_rows(rows, ci, cf, off, SF)
         A = lev["vals"]
