@@ -63,6 +63,8 @@ def _load():
             lib.orc_block_inverse.argtypes = [I, P, P]
             lib.orc_transpose.argtypes = [I, I, P, P, P, P, P, P]
             lib.orc_gradients.argtypes = [I, I, P, P, P, P, P]
+            lib.orc_filter.argtypes = [I, I, P, P, P, D]
+            lib.orc_filter.restype = I
             _lib = lib
     return _lib
 
@@ -80,7 +82,8 @@ class use_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("orc_setup", "orc_setup_scalar", "orc_free", "orc_num_levels", "orc_level_sizes", "orc_level_get",
-                     "orc_solve", "orc_vcycle", "orc_solve_t", "orc_vcycle_t", "orc_set_cycle", "orc_block_inverse", "orc_transpose", "orc_gradients"):
+                     "orc_solve", "orc_vcycle", "orc_solve_t", "orc_vcycle_t", "orc_set_cycle", "orc_block_inverse", "orc_transpose", "orc_gradients",
+                     "orc_filter"):
             getattr(lib, name).argtypes = getattr(self._saved, name).argtypes
             getattr(lib, name).restype = getattr(self._saved, name).restype
         _lib = lib
@@ -237,6 +240,16 @@ def block_inverse(A):
     if st:
         raise OracleError(st, "block inverse")
     return X
+
+
+def filter_blocks(row_ptr, col, vals, tol):
+    """The block filter alone (Sec. 5.2): a copy of the square block-CSR matrix
+    without the off-diagonal blocks X_ij with ||X_ij||_F^2 <= tol^2 ||X_ii||_F^2."""
+    rp = np.array(row_ptr, dtype=np.int32)
+    ci = np.array(col, dtype=np.int32)
+    v = np.array(vals, dtype=np.float64)
+    kept = _load().orc_filter(len(rp) - 1, v.shape[-1], _p(rp), _p(ci), _p(v), float(tol))
+    return rp, ci[:kept].copy(), v[:kept].copy()
 
 
 def transpose(row_ptr, col, vals):

@@ -1238,6 +1238,31 @@ int orc_level_get(void *h, int l, int which, void *out) {
 /* block inverse exported for the pins */
 int orc_block_inverse(int b, const double *A, double *X) { return gj_inverse(b, A, X); }
 
+/* a8 alone, exported for the pins: the filter of Sec. 5.2 (block form) applied
+ * in place to a square block-CSR matrix (nrows block rows, b x b blocks) with
+ * tolerance tol.  rp, ci and v are overwritten with the kept blocks, in their
+ * original order; returns the new number of blocks. */
+int orc_filter(int nrows, int b, int *rp, int *ci, double *v, double tol) {
+  size_t bb = (size_t)b * b;
+  int nnzb = rp[nrows];
+  Bsr M;
+  M.nrows = nrows;
+  M.ncols = nrows;
+  M.rp = (int *)malloc(sizeof(int) * (nrows + 1));
+  M.ci = (int *)malloc(sizeof(int) * (nnzb ? nnzb : 1));
+  M.v = (double *)malloc(sizeof(double) * bb * (nnzb ? nnzb : 1));
+  memcpy(M.rp, rp, sizeof(int) * (nrows + 1));
+  memcpy(M.ci, ci, sizeof(int) * nnzb);
+  memcpy(M.v, v, sizeof(double) * bb * nnzb);
+  filter_bsr(b, &M, tol * tol);
+  int kept = M.rp[nrows];
+  memcpy(rp, M.rp, sizeof(int) * (nrows + 1));
+  memcpy(ci, M.ci, sizeof(int) * kept);
+  memcpy(v, M.v, sizeof(double) * bb * kept);
+  bsr_free(&M);
+  return kept;
+}
+
 /* ---------------------------------------------------------------------------
  * Adjoint helpers: block transpose of A, and the gradients of J = w . x with
  * respect to the element absorption and the nodal source when A(sigma) has

@@ -65,6 +65,24 @@ MUTATIONS = [
     ("scalar: explicit zeros stored", "if (blk[c] != 0.0) {", "if (1) {"),
     ("scalar: D^-1 not applied before the cycle", "block_diag_apply(E, H->bo, H->Do, v, t, 0);",
      "memcpy(t, v, sizeof(double) * n);"),
+    ("filter: strict < instead of inclusive <=", "!(block_norm2(b, M->v + (size_t)p * bb) <= thr)",
+     "!(block_norm2(b, M->v + (size_t)p * bb) < thr)"),
+    ("filter: threshold from the row's largest block",
+     "if (M->ci[p] == i) dn = block_norm2(b, M->v + (size_t)p * bb);",
+     "dn = fmax(dn, block_norm2(b, M->v + (size_t)p * bb));"),
+    ("filter: diagonal block not exempt", "int keep = (M->ci[p] == i) || !(", "int keep = !("),
+    # R_cf has no diagonal block, so a filter of R_cf takes its row's largest block as the scale
+    ("filter: R_cf filtered as well", "spgemm(b, nC, nF, &Acf, NULL, &L->Delta, NULL, NULL, 1, &L->Rcf);",
+     "spgemm(b, nC, nF, &Acf, NULL, &L->Delta, NULL, NULL, 1, &L->Rcf);\n"
+     "    for (int c = 0; c < nC; ++c) {\n"
+     "      double mx = 0.0;\n"
+     "      for (int p = L->Rcf.rp[c]; p < L->Rcf.rp[c + 1]; ++p) mx = fmax(mx, block_norm2(b, L->Rcf.v + (size_t)p * bb));\n"
+     "      for (int p = L->Rcf.rp[c]; p < L->Rcf.rp[c + 1]; ++p)\n"
+     "        if (block_norm2(b, L->Rcf.v + (size_t)p * bb) <= tol2 * mx) memset(L->Rcf.v + (size_t)p * bb, 0, sizeof(double) * bb);\n"
+     "    }"),
+    ("filter: only the last Neumann iterate filtered", "if (targets & 1) filter_bsr(b, &Tn, tol2);",
+     "if ((targets & 1) && t == k - 1) filter_bsr(b, &Tn, tol2);"),
+    ("filter: coarse operator left unfiltered", "if (targets & 2) filter_bsr(b, &Nx->A, tol2);", ";"),
     ("scalar adjoint: D^-1 not transposed", "block_diag_apply(E, H->bo, H->Do, t, z, 1);",
      "block_diag_apply(E, H->bo, H->Do, t, z, 0);"),
 ]
@@ -90,6 +108,11 @@ PINS = [
     lambda o: pins.test_scalar_scaled_matrix(o, "C2", 4, 2),
     lambda o: pins.test_scalar_exact_under_ideal_settings(o, 1),
     lambda o: pins.test_scalar_preconditioner_composition(o, "C2", 4, 2, 2),
+    lambda o: pins.test_filter_rule_boundary_by_hand(o),
+    lambda o: pins.test_filter_threshold_is_the_diagonal_block(o),
+    lambda o: pins.test_filter_keeps_diagonal_block(o),
+    lambda o: pins.test_filter_targets_in_the_hierarchy(o, 3),
+    lambda o: pins.test_filter_targets_in_the_hierarchy(o, 1),
 ]
 
 

@@ -305,6 +305,185 @@ def test_galerkin_product_and_wap_identity(oracle_lib, name, p, k):
     assert np.max(np.abs((K_dense - KA) - dR @ np.linalg.inv(Aff) @ dP)) <= 1e-10 * scale
 
 
+# -----------------------------------------------------------------------------
+# a8: filtering (Sec. 5.2, block form: drop X_ij when ||X_ij||_F^2 <= tol^2 ||X_ii||_F^2)
+# -----------------------------------------------------------------------------
+
+def bsr_rows(rows):
+    """Block-CSR arrays from a list of block rows [[(col, block), ...], ...]."""
+    rp, col, vals = [0], [], []
+    for r in rows:
+        for j, blk in r:
+            col.append(j)
+            vals.append(np.asarray(blk, dtype=np.float64))
+        rp.append(len(col))
+    return np.array(rp, dtype=np.int32), np.array(col, dtype=np.int32), np.array(vals)
+
+
+def test_filter_rule_boundary_by_hand(oracle_lib):
+    """tol = 0.5 (tol^2 = 0.25 exactly) and identity diagonal blocks
+    (||X_ii||^2 = 2) put the threshold at exactly 0.5.  Row 0's coupling
+    [[.5, .5], [0, 0]] has ||X||^2 = 0.5, on the threshold: dropped, the rule is
+    inclusive.  Row 1's [[.5, .5 + 2^-53], [0, 0]] has ||X||^2 = 0.5 + 2^-53
+    (the rounded sum), one ulp above: kept.  Kept blocks are copied bit for bit."""
+    I2 = np.eye(2)
+    up = np.nextafter(0.5, 1.0)
+    assert up == 0.5 + 2.0 ** -53
+    X0 = np.array([[0.5, 0.5], [0.0, 0.0]])
+    X1 = np.array([[0.5, up], [0.0, 0.0]])
+    rp, col, vals = bsr_rows([[(0, I2), (1, X0)], [(0, X1), (1, I2)]])
+    rp2, ci2, v2 = oracle_lib.filter_blocks(rp, col, vals, 0.5)
+    assert rp2.tolist() == [0, 1, 3]
+    assert ci2.tolist() == [0, 0, 1]
+    assert np.array_equal(v2, np.array([I2, X1, I2]))
+
+
+def test_filter_threshold_is_the_diagonal_block(oracle_lib):
+    """The threshold scales with the row's own diagonal block, not with the
+    row's largest block.  tol = 0.6 (tol^2 = 0.36), b = 1:
+      row 0: diagonal 1, couplings 100, 2, 0.5 -> threshold 0.36: keeps 100 and 2
+             (4 > 0.36), drops 0.5 (0.25 <= 0.36); a threshold from the largest
+             block (0.36 * 1e4) would drop 2 as well;
+      row 1: diagonal 10, coupling 5 -> threshold 36: drops 5 (25 <= 36); a
+             threshold from the largest off-diagonal block (0.36 * 25) would keep it."""
+    rp, col, vals = bsr_rows([
+        [(0, [[1.0]]), (1, [[100.0]]), (2, [[2.0]]), (3, [[0.5]])],
+        [(0, [[5.0]]), (1, [[10.0]])],
+        [(2, [[1.0]])],
+        [(3, [[1.0]])],
+    ])
+    rp2, ci2, v2 = oracle_lib.filter_blocks(rp, col, vals, 0.6)
+    assert rp2.tolist() == [0, 3, 4, 5, 6]
+    assert ci2.tolist() == [0, 1, 2, 1, 2, 3]
+    assert v2.ravel().tolist() == [1.0, 100.0, 2.0, 10.0, 1.0, 1.0]
+
+
+def test_filter_keeps_diagonal_block(oracle_lib):
+    """The diagonal block is never dropped, however small.  tol = 2 (tol^2 = 4):
+      row 0: diagonal 1e-3 I (||.||^2 = 2e-6, below its own threshold 8e-6),
+             couplings 1e-3 I (dropped: 2e-6 <= 8e-6) and I (kept);
+      row 1: a zero diagonal block (threshold 0) and a zero coupling (dropped:
+             0 <= 0); the diagonal stays;
+      row 2: the diagonal alone."""
+    I2 = np.eye(2)
+    Z2 = np.zeros((2, 2))
+    rp, col, vals = bsr_rows([
+        [(0, 1e-3 * I2), (1, 1e-3 * I2), (2, I2)],
+        [(0, Z2), (1, Z2)],
+        [(2, I2)],
+    ])
+    rp2, ci2, v2 = oracle_lib.filter_blocks(rp, col, vals, 2.0)
+    assert rp2.tolist() == [0, 2, 3, 4]
+    assert ci2.tolist() == [0, 2, 1, 2]
+    assert np.array_equal(v2, np.array([1e-3 * I2, I2, Z2, I2]))
+
+
+def block_norms2(M, b):
+    """Squared Frobenius norm of every b x b block of a dense matrix."""
+    nr, nc = M.shape[0] // b, M.shape[1] // b
+    return (M.reshape(nr, b, nc, b) ** 2).sum(axis=(1, 3))
+
+
+def filter_dense(M, pattern, b, tol):
+    """The filtering rule on a dense square block matrix with its block pattern:
+    returns the kept pattern and the matrix with the dropped blocks zeroed.
+    Also returns the smallest relative distance of a stored off-diagonal
+    block's squared norm to its threshold (the margin of the decisions)."""
+    nrm = block_norms2(M, b)
+    n = nrm.shape[0]
+    thr = tol * tol * np.diag(nrm)[:, None]
+    off = pattern & ~np.eye(n, dtype=bool)
+    drop = off & (nrm <= thr)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rel = np.abs(nrm - thr) / np.where(thr > 0, thr, 1.0)
+    margin = float(rel[off].min()) if off.any() else np.inf
+    keep = pattern & ~drop
+    mask = np.kron(keep, np.ones((b, b), dtype=bool))
+    return keep, np.where(mask, M, 0.0), margin
+
+
+def block_pattern(rp, col, nr, nc):
+    S = np.zeros((nr, nc), dtype=bool)
+    for i in range(nr):
+        S[i, col[rp[i]:rp[i + 1]]] = True
+    return S
+
+
+@pytest.mark.parametrize("targets", [0, 1, 2, 3])
+def test_filter_targets_in_the_hierarchy(oracle_lib, targets):
+    """Which matrices are filtered (Sec. 5.2, block form; the filter_targets
+    bits): each Neumann iterate T_{t+1} = D^{-1} + L T_t when bit 0 is set, the
+    coarse operator A_{l+1} when bit 1 is set, and R_cf = -A_cf Delta never.
+    Delta, R_cf and K are rebuilt here in numpy from A, the splitting, the
+    strength flags and P: block patterns by boolean products of the structure,
+    values by dense products, the rule applied to each filtered matrix.  tol =
+    0.5 makes the filter drop blocks of both Delta and K on this problem, and
+    every decision lies at least 1e-6 (relative) away from its threshold."""
+    tol = 0.5
+    k = 2
+    P = tiny("C2", N=6, p=2)
+    b = P["b"]
+    H = two_level(oracle_lib, P, neumann_degree=k, filter_targets=targets, filter_tol=tol, theta=0.1)
+    lev = H.level(0)
+    A = bsr_dense(P["row_ptr"], P["col"], P["vals"])
+    cf, strong, rp, col = lev["cf"], lev["strong"].astype(bool), lev["row_ptr"], lev["col"]
+    F, C, fd, cd = dof_sets(cf, b)
+    nF, nC = len(F), len(C)
+    SA = block_pattern(rp, col, lev["E"], lev["E"])
+    # Horner with the rule applied to every iterate when bit 0 is set
+    Lm = dense_L(A, cf, strong, rp, col, b)
+    SL = np.abs(block_norms2(Lm, b)) > 0
+    SL |= block_pattern(lev["L_rp"], lev["L_ci"], nF, nF)  # structural zero blocks as well
+    Dg = np.zeros((nF * b, nF * b))
+    for a, i in enumerate(F):
+        Dg[a * b:(a + 1) * b, a * b:(a + 1) * b] = np.linalg.inv(A[i * b:(i + 1) * b, i * b:(i + 1) * b])
+    eyeF = np.eye(nF, dtype=bool)
+    T, ST = Dg.copy(), eyeF.copy()
+    dropped_delta = 0
+    for _ in range(k):
+        T = Dg + Lm @ T
+        ST = eyeF | ((SL.astype(int) @ ST.astype(int)) > 0)
+        if targets & 1:
+            keep, T, margin = filter_dense(T, ST, b, tol)
+            assert margin > 1e-6
+            dropped_delta += int(ST.sum() - keep.sum())
+            ST = keep
+    SD = block_pattern(lev["D_rp"], lev["D_ci"], nF, nF)
+    assert np.array_equal(SD, ST)
+    Delta = bsr_dense(lev["D_rp"], lev["D_ci"], lev["D_v"], nF, nF)
+    assert np.max(np.abs(Delta - T)) <= 1e-12 * np.abs(T).max()
+    assert (dropped_delta > 0) == bool(targets & 1)
+    # R_cf = -A_cf Delta over all its structural blocks: never filtered
+    SAcf = SA[np.ix_(C, F)]
+    SR = (SAcf.astype(int) @ SD.astype(int)) > 0
+    assert np.array_equal(block_pattern(lev["R_rp"], lev["R_ci"], nC, nF), SR)
+    Acf = A[np.ix_(cd, fd)]
+    Rn = -Acf @ Delta
+    Rcf = bsr_dense(lev["R_rp"], lev["R_ci"], lev["R_v"], nC, nF)
+    assert np.max(np.abs(Rcf - Rn)) <= 1e-12 * np.abs(Rn).max()
+    # K = (AP)_C + R_cf (AP)_F, filtered when bit 1 is set
+    W = np.zeros((lev["E"] * b, nC * b))
+    SP = np.zeros((lev["E"], nC), dtype=bool)
+    for i in range(lev["E"]):
+        J = lev["ipc"][i]
+        if J >= 0:
+            W[i * b:(i + 1) * b, J * b:(J + 1) * b] = np.eye(b)
+            SP[i, J] = True
+    AP = A @ W
+    SAP = (SA.astype(int) @ SP.astype(int)) > 0
+    Kd = AP[cd] + Rcf @ AP[fd]
+    SK = SAP[C] | ((SR.astype(int) @ SAP[F].astype(int)) > 0)
+    nK = int(SK.sum())
+    if targets & 2:
+        SK, Kd, margin = filter_dense(Kd, SK, b, tol)
+        assert margin > 1e-6
+    assert (int(SK.sum()) < nK) == bool(targets & 2)
+    L1 = H.level(1)
+    assert np.array_equal(block_pattern(L1["row_ptr"], L1["col"], nC, nC), SK)
+    K = bsr_dense(L1["row_ptr"], L1["col"], L1["vals"], nC, nC)
+    assert np.max(np.abs(K - Kd)) <= 1e-12 * np.abs(Kd).max()
+
+
 def test_chain_closed_form(oracle_lib):
     """1D upwind chain: R_ideal and the Schur complement have closed forms
     R_{c,f} = c^{c-f} and K_{c,c'} = -c^{c-c'} (c' the previous C point)."""
