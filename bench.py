@@ -4,12 +4,14 @@ A step is one pass of the whole hot path on one synthetic problem that is
 already resident in HBM: the nAIR setup (diagonal-block inverses, strength,
 C/F splitting, Neumann Delta, R, P, K = R A P on every level) followed by the
 FGMRES solve preconditioned by V-cycles, to ||b - A x|| / ||b|| <= 1e-10.
-The headline workload is the P2 DG transport problem on a 256 x 256 x 2
-mesh with rotating flow and log-normal absorption (786,432 unknowns, FP64).
-value = unknowns / (setup + solve time) in MDOF/s, summed over ranks.
+The headline workload is the largest one that fits one GPU: the P3 DG
+transport problem on a 512 x 512 x 2 jittered mesh with rotating flow and
+log-normal absorption (5,242,880 unknowns, FP64).  value = unknowns / (setup +
+solve time) in MDOF/s, summed over ranks, from the mean step time of the timed
+steps (their median is reported beside it).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nair|reference]
-                    [--workload C2] [--precision fp64|mixed]
+                    [--workload C5] [--precision fp64|mixed] [--variant-steps V]
 
 With N > 1 (torchrun) every rank solves its own replica of the problem on its
 own GPU with no communication on the data path (the solve does not shard).
@@ -45,9 +47,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nair", choices=["nair", "reference"])
-    ap.add_argument("--workload", default="C2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="C5", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--variant-steps", type=int, default=3,
+                    help="timed steps of each variant (after one warm-up)")
     ap.add_argument("--vcycles", type=int, default=0,
                     help="profiling aid: build the hierarchy (no CUDA graph) and apply this many "
                          "V-cycles to the right-hand side instead of benchmarking")
@@ -112,48 +116,68 @@ def make_inputs(workload):
     return P
 
 
+def oracle_sample(workload):
+    """Mesh size of the bounded oracle sample: the same configuration on a mesh
+    whose setup + solve takes a few seconds on the host cores."""
+    cfg = dgtransport.CONFIGS[workload]
+    dofs_per_cell = 2 * (cfg["p"] + 1) * (cfg["p"] + 2) // 2
+    Ns = cfg["N"]
+    while Ns > 16 and Ns * Ns * dofs_per_cell > 200_000:
+        Ns //= 2
+    return Ns
+
+
+def _host_threads():
+    return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
+
+
 def run_reference(args, rank, world):
-    """FP64 CPU oracle (single host thread) on a bounded sample of the workload."""
+    """The FP64 CPU oracle as it stands, built with OpenMP (rows in parallel) and
+    run on all host cores, on a bounded sample of the workload."""
+    if world > 1 and rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     import oracle
     oracle.build()
-    if rank != 0:
-        return
-    # bounded sample: the same configuration on a coarser mesh (setup + solve)
-    cfg = dgtransport.CONFIGS[args.workload]
-    Ns = max(16, cfg["N"] // 4)
+    path = oracle.build_omp()
+    Ns = oracle_sample(args.workload)
     P = dgtransport.make_problem(args.workload, N=Ns)
     k = P["neumann_degree"]
     times = []
-    for it in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        H = oracle.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=k)
-        r = H.solve(P["rhs"])
-        t1 = time.perf_counter()
-        del H
-        if it >= args.warmup:
-            times.append(t1 - t0)
+    with oracle.use_library(path):
+        for it in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            H = oracle.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=k)
+            r = H.solve(P["rhs"])
+            t1 = time.perf_counter()
+            del H
+            if it >= args.warmup:
+                times.append(t1 - t0)
     tot = sum(times)
     value = P["n"] * len(times) / tot / 1e6
-    sample = f"{args.workload} configuration on a {Ns}x{Ns}x2 mesh ({P['n']} DOFs), setup+solve, {r['iterations']} iterations"
+    cores = _host_threads()
+    sample = (f"{args.workload} configuration on a {Ns}x{Ns}x2 mesh ({P['n']} DOFs), setup+solve, "
+              f"{r['iterations']} iterations, OpenMP build on {cores} host threads")
     line = {"impl": "reference", "metric": "nAIR setup+solve MDOF/s to 1e-10 rel. residual",
             "value": value, "unit": "MDOF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "sample_dofs": P["n"]},
-            "cpu_baseline": {"value": value, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "MDOF/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "MDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# FP64 pipe of one GB300: 1.25 TFLOP/s dense FP64 (nominal figure of the part; an
-# FMA-throughput probe on the box measured 1.249 TFLOP/s).
-FP64_PEAK_TFLOPS = 1.25
+# Nominal FP64 rate of one GB300 (2 FMA per clock per SM x 152 SMs x 2.07 GHz),
+# used only when the live probe (nair_fp64_peak) fails.
+FP64_NOMINAL_TFLOPS = 1.25
 
-# DRAM traffic of the block-Jacobi sweep kernel from an ncu capture (bytes per
-# launch, averaged over the sweeps of one C2 V-cycle: dram__bytes_read.sum +
-# dram__bytes_write.sum); None whenever the kernel has changed since the capture.
-JACOBI_TRAFFIC = 13.04e6
+# DRAM traffic of the block-Jacobi sweep kernels per launch (dram__bytes_read.sum
+# + dram__bytes_write.sum from one ncu capture, averaged over the sweeps of one
+# V-cycle), by workload, with the profile that records it; a workload is left out
+# whenever the kernels have changed since its capture.
+SWEEP_TRAFFIC = {}
 
 
 def f_sweep_rows(rows, ci, cf, off, f_sweeps):
@@ -258,15 +282,18 @@ def hbm_peak_gbs():
         return 6800.0, "fallback"
 
 
-def roofline(nair, params, rp, ci, v, sweep_ms):
+def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
     """Roofline of the dominant kernel, the block-Jacobi sweep (all levels).
 
     sweep_ms maps (level, sweep k of the cycle) to (sweeps, total ms) stamped on
-    the device inside the timed steps; the algorithmic work of each sweep comes
-    from the hierarchy (rebuilt once, untimed, to read its level sizes)."""
+    the device in untimed steps run right after the timed ones; the algorithmic
+    work of each sweep comes from the hierarchy (rebuilt once, untimed, to read
+    its level sizes).  FP64 sweeps are bound by the FP64 pipe (fp64_peak: the
+    live FMA-throughput probe, TFLOP/s, and its source); FP32 sweeps by HBM."""
     S = nair.NairSolver(rp, ci, v, **params)
     work = sweep_work(S, S.num_levels(), S.b, S.f_sweeps, max(S.params.c_sweeps, 0))
     S.close()
+    peak, peak_src = fp64_peak
     fl = by = t = 0.0
     launches = 0
     per_level = {}
@@ -283,27 +310,35 @@ def roofline(nair, params, rp, ci, v, sweep_ms):
         a[1] += byts * n
         a[2] += ms * 1e-3
         a[3] += n
-    achieved = fl / t / 1e12 if t else 0.0
     hbm_peak, hbm_src = hbm_peak_gbs()
     by_level = []
     for l in sorted(per_level):
         lf, lb, lt, ln = per_level[l]
         if lt:
             by_level.append({"level": l, "sweeps": ln, "us_per_sweep": round(1e6 * lt / ln, 2),
-                             "tflops": round(lf / lt / 1e12, 4), "frac_fp64": round(lf / lt / 1e12 / FP64_PEAK_TFLOPS, 3),
+                             "tflops": round(lf / lt / 1e12, 4), "frac_fp64": round(lf / lt / 1e12 / peak, 3),
                              "gbs": round(lb / lt / 1e9, 1), "frac_hbm": round(lb / lt / 1e9 / hbm_peak, 3)})
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": JACOBI_TRAFFIC,
-            "algorithmic_bytes_per_launch": by / launches if launches else None,
-            "kernel": "block-Jacobi sweep: k_rowop, k_rowop_l0, k_sweep_rows (FP64, all levels)",
-            "launches_per_step": None, "launches_timed": launches,
-            "kernel_ms_timed": 1e3 * t,
-            "hbm_achieved_gbs": by / t / 1e9 if t else 0.0,
-            "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
-            "by_level": by_level,
-            "how": "device-clock stamps (first thread block past the dependency wait to last "
-                   "thread block done) on every sweep inside the timed steps"}
+    fp64 = params.get("precision", "fp64") == "fp64"
+    tflops = fl / t / 1e12 if t else 0.0
+    gbs = by / t / 1e9 if t else 0.0
+    traffic = SWEEP_TRAFFIC.get(workload) if fp64 else None
+    out = {"bound": "alu" if fp64 else "hbm",
+           "achieved": tflops if fp64 else gbs, "peak": peak if fp64 else hbm_peak,
+           "unit": "TFLOP/s" if fp64 else "GB/s",
+           "frac": (tflops / peak) if fp64 else (gbs / hbm_peak),
+           "peak_source": (peak_src if fp64 else f"{hbm_src}: MEASURED_PEAKS.json hbm_gbs"),
+           "traffic": traffic[0] if traffic else None,
+           "traffic_source": traffic[1] if traffic else "no capture of the current kernels on this workload",
+           "algorithmic_bytes_per_launch": by / launches if launches else None,
+           "kernel": "block-Jacobi sweep: k_rowop, k_rowop_l0, k_sweep_rows (all levels)",
+           "launches_per_step": None, "launches_stamped": launches,
+           "kernel_ms_stamped": 1e3 * t,
+           "tflops_achieved": tflops, "fp64_peak_tflops": peak,
+           "hbm_achieved_gbs": gbs, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+           "by_level": by_level,
+           "how": "device-clock stamps (first thread block past the dependency wait to last "
+                  "thread block done) on every sweep, in untimed steps after the timed ones"}
+    return out
 
 
 def aggregate_ranks(total_ms, steps, dofs, world, device):
@@ -399,88 +434,113 @@ def measure_second_workload(nair, flush, stream, steps, device):
 
 def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps):
     """The mixed-precision form and the adjoint (forward + A^T solve) timed beside
-    the FP64 solver on the same workload and tolerance."""
+    the FP64 solver on the same workload and tolerance, the F-cycle and Neumann
+    degree 3 of the scaling study, scalar nAIR, the C2 workload, and the second
+    workload (the paper's flows and a batched angle sweep)."""
     import torch
+    dev = bvec.device
     n = P["n"]
-    w = torch.from_numpy(dgtransport.functional_weights(n)).to(bvec.device)
+    w = torch.from_numpy(dgtransport.functional_weights(n)).to(dev)
+    mass = torch.from_numpy(np.ascontiguousarray(P["mass"])).to(dev)
     res = {}
     xref = x64.clone()
 
-    def fwd(prec):
+    def run(extra, adjoint=False, mode="transposed"):
         def f():
-            S = nair.NairSolver(rp, ci, v, **dict(params, precision=prec))
+            S = nair.NairSolver(rp, ci, v, **dict(params, **extra, adjoint_mode=mode))
             xx, rep = S.solve(bvec)
+            out = (xx, rep)
+            if adjoint:
+                lam, repa = S.adjoint_solve(w)
+                out = (xx, rep, lam, repa)
             S.close()
-            return xx, rep
+            return out
         return f
 
-    def fwd_adj(prec, mode="transposed"):
-        def f():
-            S = nair.NairSolver(rp, ci, v, **dict(params, precision=prec, adjoint_mode=mode))
-            xx, rep = S.solve(bvec)
-            lam, repa = S.adjoint_solve(w)
-            S.close()
-            return xx, lam, rep, repa
-        return f
+    def timed(fn):
+        fn()
+        return timed_steps(fn, steps, flush, stream)
 
-    for prec in ("fp64", "mixed"):
-        fwd(prec)()
-        ms, (xx, rep) = timed_steps(fwd(prec), steps, flush, stream)
-        res[f"forward_{prec}"] = {"ms_per_step": ms, "mdof_s": n / (ms * 1e-3) / 1e6,
-                                 "setup_ms": rep["setup_ms"], "solve_ms": rep["solve_ms"],
-                                 "iterations": rep["iterations"], "rel_res": rep["rel_res"],
-                                 "rel_diff_vs_fp64": float((xx - xref).norm() / xref.norm())}
-    # the F-cycle and Neumann degree 3 of the scaling study (Sec. 6), and scalar nAIR
-    for label, extra in (("forward_vcycle_k3_fp64", dict(neumann_degree=3)),
+    for label, extra in (("forward_mixed", dict(precision="mixed")),
+                         # Neumann degrees 2 to 4 and the F-cycle of the scaling study (Sec. 6)
+                         ("forward_vcycle_k2_fp64", dict(neumann_degree=2)),
+                         ("forward_vcycle_k3_fp64", dict(neumann_degree=3)),
+                         ("forward_vcycle_k3_mixed", dict(neumann_degree=3, precision="mixed")),
+                         ("forward_vcycle_k4_fp64", dict(neumann_degree=4)),
                          ("forward_fcycle_k3_fp64", dict(neumann_degree=3, cycle_type="F")),
                          ("forward_fcycle_k3_mixed", dict(neumann_degree=3, cycle_type="F", precision="mixed")),
                          # scalar nAIR (block-diagonal scaling, coarsening by degree of freedom)
                          ("forward_scalar_fp64", dict(scalar=1)),
                          ("forward_scalar_mixed", dict(scalar=1, precision="mixed"))):
-        def fk(extra=extra):
-            S = nair.NairSolver(rp, ci, v, **dict(params, **extra))
-            xx, rep = S.solve(bvec)
-            S.close()
-            return xx, rep
-        fk()
-        ms, (xx, rep) = timed_steps(fk, steps, flush, stream)
+        ms, (xx, rep) = timed(run(extra))
         res[label] = {"ms_per_step": ms, "mdof_s": n / (ms * 1e-3) / 1e6, "setup_ms": rep["setup_ms"],
                       "solve_ms": rep["solve_ms"], "iterations": rep["iterations"], "rel_res": rep["rel_res"],
                       "cycle_complexity": rep["cycle_complexity"], "op_complexity": rep["op_complexity"],
                       "rel_diff_vs_fp64": float((xx - xref).norm() / xref.norm())}
-    res.update(measure_second_workload(nair, flush, stream, steps, bvec.device))
-    lam_ref = None
-    # the adjoint through the transposed forward hierarchy (default), and by a
-    # second hierarchy built on A^T
-    for prec, mode, label in (("fp64", "transposed", "forward_adjoint_fp64"),
-                              ("mixed", "transposed", "forward_adjoint_mixed"),
-                              ("fp64", "rebuild", "forward_adjoint_rebuild_fp64")):
-        fwd_adj(prec, mode)()
-        ms, (xx, lam, rep, repa) = timed_steps(fwd_adj(prec, mode), steps, flush, stream)
-        if lam_ref is None:
-            lam_ref = lam.clone()
+    # the adjoint through the transposed forward hierarchy (default), also in
+    # mixed precision, and by a second hierarchy built on A^T; gradients of
+    # J = w . x (Eq. transport: dJ/dq = M^T lambda, dJ/dsigma_e = -lambda_e^T M_e x_e)
+    ref = None
+    for label, extra, mode in (("forward_adjoint_fp64", {}, "transposed"),
+                               ("forward_adjoint_mixed", dict(precision="mixed"), "transposed"),
+                               ("forward_adjoint_rebuild_fp64", {}, "rebuild")):
+        ms, (xx, rep, lam, repa) = timed(run(extra, adjoint=True, mode=mode))
+        gs, gq = nair.gradients(mass, lam, xx)
+        if ref is None:
+            ref = (lam.clone(), gs.clone(), gq.clone())
         res[label] = {
-            "ms_per_step": ms, "adjoint_setup_ms": repa["setup_ms"], "adjoint_solve_ms": repa["solve_ms"],
-            "adjoint_iterations": repa["iterations"], "adjoint_rel_res": repa["rel_res"],
-            "lambda_rel_diff_vs_fp64": float((lam - lam_ref).norm() / lam_ref.norm())}
+            "ms_per_step": ms, "setup_ms": rep["setup_ms"], "solve_ms": rep["solve_ms"],
+            "iterations": rep["iterations"], "adjoint_setup_ms": repa["setup_ms"],
+            "adjoint_solve_ms": repa["solve_ms"], "adjoint_iterations": repa["iterations"],
+            "adjoint_rel_res": repa["rel_res"],
+            "lambda_rel_diff_vs_fp64": float((lam - ref[0]).norm() / ref[0].norm()),
+            "grad_sigma_rel_diff_vs_fp64": float((gs - ref[1]).norm() / ref[1].norm()),
+            "grad_q_rel_diff_vs_fp64": float((gq - ref[2]).norm() / ref[2].norm())}
+    # the C2 workload (P2 DG, 256 x 256 x 2, rotating flow), FP64 and mixed
+    P2 = dgtransport.make_problem("C2")
+    c2 = [torch.from_numpy(np.ascontiguousarray(P2[k2])).to(dev) for k2 in ("row_ptr", "col", "vals", "rhs")]
+    for prec in ("fp64", "mixed"):
+        def f2(prec=prec):
+            S = nair.NairSolver(*c2[:3], neumann_degree=P2["neumann_degree"], precision=prec)
+            xx, rep = S.solve(c2[3])
+            S.close()
+            return xx, rep
+        ms, (xx, rep) = timed(f2)
+        res[f"C2_forward_{prec}"] = {"dofs": P2["n"], "ms_per_step": ms, "mdof_s": P2["n"] / (ms * 1e-3) / 1e6,
+                                     "setup_ms": rep["setup_ms"], "solve_ms": rep["solve_ms"],
+                                     "iterations": rep["iterations"], "rel_res": rep["rel_res"]}
+    res.update(measure_second_workload(nair, flush, stream, steps, dev))
     return res
 
 
 def cpu_baseline(workload):
-    """The oracle as it stands, one host thread, on a bounded sample (~10-30 s)."""
+    """The oracle as it stands on a bounded sample of the workload (the same
+    configuration on a coarser mesh): one setup + solve of its OpenMP build on
+    all host threads (the reported value), and of its single-threaded build."""
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
     import oracle
     oracle.build()
-    cfg = dgtransport.CONFIGS[workload]
-    # the full workload when it is small enough for ~10-30 s of one host thread
-    Ns = cfg["N"] if cfg["N"] * cfg["N"] * (cfg["p"] + 1) ** 2 <= 256 * 256 * 9 else cfg["N"] // 2
+    path = oracle.build_omp()
+    Ns = min(dgtransport.CONFIGS[workload]["N"], 2 * oracle_sample(workload))
     P = dgtransport.make_problem(workload, N=Ns)
-    t0 = time.perf_counter()
-    H = oracle.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=P["neumann_degree"])
-    r = H.solve(P["rhs"])
-    t = time.perf_counter() - t0
-    return {"value": P["n"] / t / 1e6, "unit": "MDOF/s", "cores": 1, "kind": "oracle",
+    k = P["neumann_degree"]
+
+    def once():
+        t0 = time.perf_counter()
+        H = oracle.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=k)
+        r = H.solve(P["rhs"])
+        del H
+        return time.perf_counter() - t0, r["iterations"]
+
+    with oracle.use_library(path):
+        t_all, its = once()
+    t_one, _ = once()
+    cores = _host_threads()
+    return {"value": P["n"] / t_all / 1e6, "unit": "MDOF/s", "cores": cores, "kind": "oracle",
             "sample": f"one setup+solve of the {workload} configuration on a {Ns}x{Ns}x2 mesh "
-                      f"({P['n']} DOFs, {r['iterations']} iterations, {t:.1f} s)"}
+                      f"({P['n']} DOFs, {its} iterations): OpenMP build on {cores} host threads "
+                      f"{t_all:.1f} s, single-threaded build {t_one:.1f} s",
+            "single_thread": {"value": P["n"] / t_one / 1e6, "unit": "MDOF/s", "cores": 1}}
 
 
 def main():
@@ -489,8 +549,6 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if world > 1 and rank != 0:
-            return
         run_reference(args, rank, world)
         return
 
@@ -525,30 +583,34 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    sweep_ms = {}
-    timed = {"on": False}
+    fp64_peak = (FP64_NOMINAL_TFLOPS, "nominal (probe failed)")
+    if not args.no_extras:
+        try:
+            tf, mhz = nair.fp64_peak()
+            fp64_peak = (tf, f"measured live by nair_fp64_peak (FP64 FMA-chain kernel, SM clock {mhz:.0f} MHz)")
+        except Exception as e:  # noqa: BLE001 - a failed probe leaves the nominal figure, said so
+            fp64_peak = (FP64_NOMINAL_TFLOPS, f"nominal (probe failed: {e})")
 
-    def step():
-        s = nair.NairSolver(rp, ci, v, **dict(params, sweep_timing=1 if timed["on"] else 0))
+    def step(stamps=None):
+        s = nair.NairSolver(rp, ci, v, **dict(params, sweep_timing=1 if stamps is not None else 0))
         x.zero_()
         _, rep = s.solve(bvec, x)
-        if timed["on"]:
+        if stamps is not None:
             for key, (n, ms) in s.sweep_site_timing().items():
-                c, m = sweep_ms.get(key, (0, 0.0))
-                sweep_ms[key] = (c + n, m + ms)
+                c, m = stamps.get(key, (0, 0.0))
+                stamps[key] = (c + n, m + ms)
         s.close()
         return rep
 
     for _ in range(args.warmup):
         rep = step()
     launches0 = nair.kernel_launches()
-    timed["on"] = not args.no_extras
     sampler = ClockSampler(local)
     sampler.start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    total_ms = 0.0
+    step_ms = []
     setup_ms = solve_ms = 0.0
     reps = []
     for _ in range(args.steps):
@@ -560,7 +622,7 @@ def main():
         rep = step()
         e1.record(stream)
         torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
+        step_ms.append(e0.elapsed_time(e1))
         setup_ms += rep["setup_ms"]
         solve_ms += rep["solve_ms"]
         reps.append(rep)
@@ -568,9 +630,14 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    timed["on"] = False
     launches = (nair.kernel_launches() - launches0) // max(1, args.steps)
-    ms, value = aggregate_ranks(total_ms, args.steps, P["n"], world, dev)
+    ms, value = aggregate_ranks(sum(step_ms), args.steps, P["n"], world, dev)
+
+    # device-clock stamps of every sweep, in separate untimed steps
+    sweep_ms = {}
+    if not args.no_extras:
+        for _ in range(min(args.steps, 3)):
+            step(sweep_ms)
 
     # end to end through the public API from pinned host buffers
     e2e = None
@@ -609,7 +676,8 @@ def main():
 
     variants = None
     if not args.no_extras:
-        variants = measure_variants(nair, params, rp, ci, v, bvec, P, x, flush, stream, args.steps)
+        variants = measure_variants(nair, params, rp, ci, v, bvec, P, x, flush, stream,
+                                    max(1, args.variant_steps))
 
     if rank != 0:
         return
@@ -623,6 +691,7 @@ def main():
         "config": {"workload": WORKLOADS[args.workload], "dofs": P["n"], "precision": args.precision,
                    "neumann_degree": k, "l2": "flushed between steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "ms_per_step_median": float(np.median(step_ms)), "ms_per_step_all": [round(t, 3) for t in step_ms],
         "setup_ms": setup_ms / args.steps, "solve_ms": solve_ms / args.steps,
         "iterations": last["iterations"], "levels": last["levels"], "rel_res": last["rel_res"],
         "op_complexity": last["op_complexity"], "cycle_complexity": last["cycle_complexity"],
@@ -631,8 +700,8 @@ def main():
     if variants:
         line["variants"] = variants
     if not args.no_extras:
-        line["roofline"] = roofline(nair, params, rp, ci, v, sweep_ms)
-        line["roofline"]["launches_per_step"] = line["roofline"]["launches_timed"] // args.steps
+        line["roofline"] = roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, args.workload)
+        line["roofline"]["launches_per_step"] = line["roofline"]["launches_stamped"] // max(1, min(args.steps, 3))
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -218,8 +218,11 @@ nair_status nair_block_inverse(int32_t nblk, int32_t b, const double *A, double 
  * forbid cudaMalloc after start-up, code that must not synchronise the device
  * the way cudaMalloc/cudaFree can).  The paper has no counterpart: this is a
  * deployment variant.  The entry point allocates nothing; its status words live
- * in a 32 KB array that the library reserves in device memory on every GPU that
- * loads it, until the process exits.  One call handles at most 8192 thread
+ * in a 32 KB array in the library's device code, which CUDA sets up on a GPU
+ * when it loads that code there (under lazy module loading, the default, at the
+ * library's first kernel call on that GPU; with CUDA_MODULE_LOADING=EAGER at
+ * start-up) and keeps until the process exits: make one warm-up call before a
+ * caching allocator takes the whole device.  One call handles at most 8192 thread
  * blocks of max(1, 256 / b) matrix blocks each (for example 344064 blocks of
  * size 6, 73728 of size 28); larger calls return INVALID_ARG and launch
  * nothing.  The first call on a device looks up the array's device address
@@ -252,6 +255,18 @@ nair_status nair_gradients(int32_t E, int32_t b, const double *M, const double *
 /* Total number of kernels this library has launched in the process so far
  * (a diagnostic counter; every launch site increments it). */
 nair_status nair_kernel_launches(int64_t *count);
+
+/* Measured FP64 throughput of the current GPU, in TFLOP/s (two flops per fused
+ * multiply-add), written to *tflops.  A diagnostic with no counterpart in the
+ * paper: the denominator of the roofline of the FP64-bound kernels.  It
+ * launches eight 256-thread blocks per SM on `stream` and reports the best of
+ * three timed launches after one warm-up (CUDA events).  mode 0: each thread
+ * runs sixteen independent fma chains of `iters` steps (1..1000000); mode 1:
+ * each warp runs four independent chains of FP64 tensor-core products
+ * (mma.sync m8n8k4); mode 2: both in one loop.  *sm_mhz (may be NULL)
+ * receives the SM clock during that launch, from one block's clock64() cycles
+ * over its %globaltimer nanoseconds.  Synchronises the stream. */
+nair_status nair_fp64_peak(int32_t mode, int32_t iters, double *tflops, double *sm_mhz, void *stream);
 
 /* Device time of the block-Jacobi sweeps of the forward hierarchy, recorded
  * when the handle was set up with sweep_timing = 1: for level `level` and class

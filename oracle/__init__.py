@@ -36,6 +36,21 @@ def build(force=False):
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build_omp(force=False):
+    """The same source built with OpenMP, for timing the oracle on all host
+    cores (rows in parallel, each row's arithmetic unchanged; dot products in
+    fixed chunks).  Not used by the parity tests."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fopenmp",
+               "-shared", "-o", _LIB_OMP + ".tmp", _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(_LIB_OMP + ".tmp", _LIB_OMP)
+    return _LIB_OMP
+
+
 def _load():
     global _lib
     with _lock:

@@ -26,6 +26,12 @@
  *   inner block index in ascending order; squared block norms s = fma(x, x, s)
  *   over the block in row-major order; Gauss-Jordan inverses as below.
  * Build with -ffp-contract=off so that the compiler adds no contraction.
+ *
+ * The parity build is single-threaded.  A second build with -fopenmp exists
+ * only to time the oracle on all host cores: its pragmas split loops whose
+ * iterations write disjoint rows (every row's arithmetic is unchanged), and its
+ * dot products add fixed contiguous chunks in order, so it is deterministic
+ * but rounds dot products differently from the single-threaded build.
  */
 #include <math.h>
 #include <stdint.h>
@@ -779,6 +785,7 @@ static void block_diag_apply(int E, int b, const double *D, const double *x, dou
  * ------------------------------------------------------------------------- */
 static void spmv(int b, const Bsr *A, const double *x, double *y) {
   size_t bb = (size_t)b * b;
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < A->nrows; ++i)
     for (int r = 0; r < b; ++r) {
       double s = 0.0;
@@ -799,6 +806,7 @@ static void jacobi(int b, const Level *L, int which, const double *f, double *x,
   size_t bb = (size_t)b * b;
   const Bsr *A = &L->A;
   memcpy(tmp, x, sizeof(double) * (size_t)A->nrows * b);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < A->nrows; ++i) {
     if (L->cf[i] != which) continue;
     double res[32];
@@ -849,6 +857,7 @@ static void cycle(const Hier *H, int l, int type, const double *f, double *x, in
     spmv(b, &L->A, x, r);
     for (size_t k = 0; k < n; ++k) r[k] = f[k] - r[k];
   }
+#pragma omp parallel for schedule(static)
   for (int c = 0; c < nC; ++c) {
     int i = L->c2f[c];
     for (int rr = 0; rr < b; ++rr) {
@@ -863,6 +872,7 @@ static void cycle(const Hier *H, int l, int type, const double *f, double *x, in
   }
   cycle(H, l + 1, type, fc, xc, 1);
   if (type == 1) cycle(H, l + 1, 0, fc, xc, 0);
+#pragma omp parallel for schedule(static)
   for (int i = 0; i < L->A.nrows; ++i)
     for (int rr = 0; rr < b; ++rr) {
       double v = L->ipc[i] >= 0 ? xc[(size_t)L->ipc[i] * b + rr] : 0.0;
@@ -1058,9 +1068,24 @@ static void precond_apply(const Hier *H, const double *v, double *z) {
 }
 
 static double dot(size_t n, const double *a, const double *b) {
+#ifdef _OPENMP
+  /* multi-threaded timing build: 64 contiguous chunks, then their sums in order */
+  double part[64];
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < 64; ++c) {
+    size_t lo = n * (size_t)c / 64, hi = n * (size_t)(c + 1) / 64;
+    double t = 0.0;
+    for (size_t i = lo; i < hi; ++i) t += a[i] * b[i];
+    part[c] = t;
+  }
+  double s = 0.0;
+  for (int c = 0; c < 64; ++c) s += part[c];
+  return s;
+#else
   double s = 0.0;
   for (size_t i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
+#endif
 }
 
 /* Flexible GMRES(m), right preconditioned by one V-cycle, classical Gram-Schmidt
@@ -1116,6 +1141,7 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
         }
         for (int k = 0; k <= j; ++k) {
           const double *vk = V + (size_t)k * n;
+#pragma omp parallel for schedule(static)
           for (size_t i = 0; i < n; ++i) w[i] -= hc[k] * vk[i];
         }
       }
@@ -1123,6 +1149,7 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
       Hm[(size_t)(j + 1) * m + j] = hn;
       if (hn != 0.0) {
         double *vn = V + (size_t)(j + 1) * n;
+#pragma omp parallel for schedule(static)
         for (size_t i = 0; i < n; ++i) vn[i] = w[i] / hn;
       }
       for (int k = 0; k < j; ++k) {
@@ -1151,6 +1178,7 @@ int orc_solve(void *h, const double *bvec, double *x, int f_sweeps, int c_sweeps
     }
     for (int k = 0; k < j; ++k) {
       const double *zk = Z + (size_t)k * n;
+#pragma omp parallel for schedule(static)
       for (size_t i = 0; i < n; ++i) x[i] += y[k] * zk[i];
     }
     memset(Hm, 0, sizeof(double) * (size_t)(m + 1) * m);

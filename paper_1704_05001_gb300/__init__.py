@@ -67,7 +67,8 @@ EXPORTS = ["nair_default_params", "nair_setup", "nair_solve", "nair_adjoint_solv
            "nair_free", "nair_num_levels", "nair_level_sizes", "nair_get_level", "nair_block_inverse",
            "nair_assemble_sigma", "nair_mass_apply", "nair_gradients", "nair_kernel_launches",
            "nair_profile", "nair_profile_entry", "nair_block_inverse_noalloc", "nair_sweep_timing",
-           "nair_setup_batch", "nair_solve_batch", "nair_adjoint_solve_batch", "nair_last_error"]
+           "nair_setup_batch", "nair_solve_batch", "nair_adjoint_solve_batch", "nair_fp64_peak",
+           "nair_last_error"]
 
 
 def lib():
@@ -101,6 +102,7 @@ def lib():
     L.nair_mass_apply.argtypes = [I32, I32, P, P, P, P]
     L.nair_gradients.argtypes = [I32, I32, P, P, P, P, P, P]
     L.nair_kernel_launches.argtypes = [ctypes.POINTER(I64)]
+    L.nair_fp64_peak.argtypes = [I32, I32, ctypes.POINTER(D), ctypes.POINTER(D), P]
     L.nair_profile.argtypes = [I32]
     L.nair_sweep_timing.argtypes = [P, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(D)]
     L.nair_profile_entry.argtypes = [I32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(I64),
@@ -138,6 +140,19 @@ def kernel_launches():
     c = ctypes.c_int64(0)
     _check(lib().nair_kernel_launches(ctypes.byref(c)), "nair_kernel_launches")
     return c.value
+
+
+FP64_FMA, FP64_MMA, FP64_BOTH = 0, 1, 2
+
+
+def fp64_peak(mode=FP64_FMA, iters=40000):
+    """Measured FP64 throughput of the current GPU (nair_fp64_peak): fma chains
+    (mode 0), FP64 tensor-core mma chains (1) or both at once (2).  Returns
+    (TFLOP/s, SM clock in MHz during the measurement)."""
+    t = ctypes.c_double(0)
+    mhz = ctypes.c_double(0)
+    _check(lib().nair_fp64_peak(mode, iters, ctypes.byref(t), ctypes.byref(mhz), _stream()), "nair_fp64_peak")
+    return t.value, mhz.value
 
 
 def profile(enable=True):

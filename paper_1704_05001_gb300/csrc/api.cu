@@ -368,6 +368,98 @@ nair_status nair_kernel_launches(int64_t *count) {
   return NAIR_OK;
 }
 
+// FP64 throughput probe.  mode 0: sixteen independent fma chains per thread;
+// mode 1: four independent FP64 tensor-core chains per warp (mma.sync m8n8k4,
+// 256 fused multiply-adds per warp instruction); mode 2: both in the same
+// loop, to see whether the two paths add up.  Block 0's first thread records
+// the SM clock cycles and the nanoseconds the block ran, from which the host
+// derives the SM clock under this load.  The final test is never true for
+// these inputs; it keeps the chains live.
+__global__ void __launch_bounds__(256) k_fp64_rate(int mode, int iters, double a, double c, double *sink,
+                                                   long long *clk) {
+  long long c0 = 0, t0 = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c0 = clock64();
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  }
+  double x[16], acc[4][2];
+  const double fa = 1.0 + 1e-3 * (threadIdx.x & 31), fb = 0.999;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = 1e-3 * threadIdx.x + k;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    if (mode != 1) {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) x[k] = fma(x[k], a, c);
+    }
+    if (mode != 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                     : "+d"(acc[k][0]), "+d"(acc[k][1])
+                     : "d"(fa), "d"(fb));
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) s += x[k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s += acc[k][0] + acc[k][1];
+  if (s == -1.0) *sink = s;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    long long t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    clk[0] = clock64() - c0;
+    clk[1] = t1 - t0;
+  }
+}
+
+nair_status nair_fp64_peak(int32_t mode, int32_t iters, double *tflops, double *sm_mhz, void *stream) {
+  NAIR_API_BEGIN
+  if (!tflops || mode < 0 || mode > 2 || iters < 1 || iters > 1000000)
+    return set_error(NAIR_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  NAIR_CK(cudaGetDevice(&dev));
+  NAIR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  Mem tmp;
+  tmp.s = s;
+  double *sink = tmp.alloc<double>(1);
+  long long *clk = tmp.alloc<long long>(2);
+  cudaEvent_t e0, e1;
+  NAIR_CK(cudaEventCreate(&e0));
+  NAIR_CK(cudaEventCreate(&e1));
+  const int blocks = sms * 8;
+  // fused multiply-adds per thread and iteration: 16 fma; 4 mma x 256 / 32 lanes
+  const double per_thread = (mode != 1 ? 16.0 : 0.0) + (mode != 0 ? 32.0 : 0.0);
+  double best = 0.0, mhz = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {
+    NAIR_CK(cudaEventRecord(e0, s));
+    k_fp64_rate<<<blocks, 256, 0, s>>>(mode, iters, 0.999999, 1e-6, sink, clk);
+    NAIR_LAUNCH_CHECK();
+    NAIR_CK(cudaEventRecord(e1, s));
+    NAIR_CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    NAIR_CK(cudaEventElapsedTime(&ms, e0, e1));
+    long long hc[2] = {0, 0};
+    NAIR_CK(cudaMemcpyAsync(hc, clk, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    NAIR_CK(cudaStreamSynchronize(s));
+    const double flops = 2.0 * per_thread * 256.0 * blocks * (double)iters;
+    const double rate = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+    if (rep > 0 && rate > best) {
+      best = rate;
+      mhz = hc[1] > 0 ? 1e3 * (double)hc[0] / (double)hc[1] : 0.0;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *tflops = best;
+  if (sm_mhz) *sm_mhz = mhz;
+  return NAIR_OK;
+  NAIR_API_END
+}
+
 nair_status nair_setup(const nair_bsr *A, const nair_params *p, nair_handle **out) {
   NAIR_API_BEGIN
   if (!A || !p || !out) return set_error(NAIR_ERR_INVALID_ARG, "null argument");

@@ -5,8 +5,12 @@
 // the whole device, solvers embedded in applications that forbid cudaMalloc
 // after start-up, or host code that must not synchronise the device the way
 // cudaMalloc/cudaFree can.  nair_block_inverse_noalloc does the same work with
-// its status words in a fixed array that lives in this file's device memory:
-// the library itself reserves it when it is loaded, on every GPU it touches,
+// its status words in a fixed array that lives in this file's device memory.
+// CUDA sets that array up on a GPU when it loads the library's device code
+// there: at the first kernel call of the library on that GPU under lazy module
+// loading (the default of recent CUDA releases), at start-up with
+// CUDA_MODULE_LOADING=EAGER.  A caller whose caching allocator later takes the
+// whole device should therefore make one warm-up call first.  The array stays
 // until the process exits.
 //
 // The array holds one status word per thread block of the launch plus one
@@ -18,6 +22,7 @@
 // clearing between calls.  Calls that overlap on the GPU share the array and
 // race; order them on one stream.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdio>
 
@@ -32,11 +37,14 @@ constexpr int kNoallocMaxDevices = 64;
 // status words of the thread blocks of the last call, then the result word
 static __device__ __align__(256) int g_noalloc_scratch[kNoallocMaxCtas + 1];
 
-int *g_scratch_ptr[kNoallocMaxDevices] = {nullptr};
+// device address of the array per device; host threads may look it up at the
+// same time (each stores the same value), so the cache is atomic
+std::atomic<int *> g_scratch_ptr[kNoallocMaxDevices] = {};
 
 // same Gauss-Jordan arithmetic as the allocating kernel (one thread per block
-// row, partial pivoting, fma elimination, IEEE division); each thread block
-// stores 1 in its own status word if one of its blocks met a zero pivot, else 0
+// row, partial pivoting, fma elimination, the pivot row multiplied by one
+// correctly rounded reciprocal 1/d per step); each thread block stores 1 in
+// its own status word if one of its blocks met a zero or NaN pivot, else 0
 __global__ void k_block_inverse_noalloc(int nblk, int b, int bpc, const double *__restrict__ A,
                                         double *__restrict__ out, int *__restrict__ status) {
   extern __shared__ double sm[];
@@ -124,7 +132,8 @@ int *scratch_address(nair_status *st, const char **msg) {
     *msg = "nair_block_inverse_noalloc: no usable current device";
     return nullptr;
   }
-  if (!g_scratch_ptr[dev]) {
+  int *cached = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!cached) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -133,9 +142,10 @@ int *scratch_address(nair_status *st, const char **msg) {
       *msg = "nair_block_inverse_noalloc: cudaGetSymbolAddress of the scratch array failed";
       return nullptr;
     }
-    g_scratch_ptr[dev] = static_cast<int *>(p);
+    cached = static_cast<int *>(p);
+    g_scratch_ptr[dev].store(cached, std::memory_order_release);
   }
-  return g_scratch_ptr[dev];
+  return cached;
 }
 
 }  // namespace

@@ -154,3 +154,81 @@ def test_c5_full_forward_adjoint_mixed_vs_fp64(nair):
     assert np.linalg.norm(xm - x64) <= 1e-8 * np.linalg.norm(x64)
     assert np.linalg.norm(gsm - gs64) <= 1e-8 * np.linalg.norm(gs64)
     assert np.linalg.norm(gqm - gq64) <= 1e-8 * np.linalg.norm(gq64)
+
+
+@pytest.mark.parametrize("name", ["C3", "C5"])
+def test_full_mixed_hierarchy_per_result_error(nair, name):
+    """The FP32 hierarchy of mixed precision against the FP64 hierarchy at full
+    size: the same C/F splittings and patterns on every level, level 0's A
+    within the FP32 rounding (2^-24 per row) and D^{-1} within 2e-6, coarse A,
+    R_cf and D^{-1} within 5e-3 per row (measured up to 1.3e-3), one FP32 cycle
+    within 5e-6 of the FP64 cycle (measured 1.3e-6), and the same FGMRES
+    iteration count."""
+    from test_gpu_parity import level_diffs
+    P = D.make_problem(name)
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    k = P["neumann_degree"]
+    S64 = nair.NairSolver(*args, neumann_degree=k)
+    S32 = nair.NairSolver(*args, neumann_degree=k, precision="mixed")
+    assert S32.num_levels() == S64.num_levels()
+    diffs = level_diffs(S32, S64)
+    assert all(d["cf"] == 0 and d["pattern"] == 0 for d in diffs), diffs
+    assert diffs[0]["A"] <= 2.0 ** -24 and diffs[0]["Dinv"] <= 2e-6, diffs[0]
+    for d in diffs:
+        for key in ("A", "Dinv", "R"):
+            if key in d:
+                assert d[key] <= 5e-3, (key, d)
+    f = D.rng.uniform(7, P["n"]) - 0.5
+    z64 = S64.vcycle(dev(f))
+    z32 = S32.vcycle(dev(f))
+    assert float((z32 - z64).norm() / z64.norm()) <= 5e-6
+    rhs = dev(P["rhs"])
+    _, r64 = S64.solve(rhs)
+    _, r32 = S32.solve(rhs)
+    assert r32["iterations"] <= r64["iterations"] + 1, (r32["iterations"], r64["iterations"])
+    S32.close()
+    S64.close()
+
+
+def test_c4_full_gradients_against_tangent_solves(nair):
+    """C4 at its stated size (P2, 256 x 256 x 2, rotating flow, log-normal
+    sigma_t): the adjoint gradients of J = w . x (NairSolve backward, FGMRES on
+    A^T with the transposed cycle, solves to 1e-13) against forward tangent
+    solves on 16 seeded coordinates (8 in q, 8 in sigma_t):
+        dJ/dq_i = w . A^{-1} (M e_i),   dJ/dsigma_e = -w . A^{-1} (E_e M_e x_e),
+    E_e placing element e's block.  J is linear in q, so the first is the
+    central difference of any step; the second is its step -> 0 limit.  A
+    central difference with step 1e-6 cannot be resolved at this size in FP64:
+    it moves J (about 2e5) by about 1e-13 (q) to 1e-11 (sigma_t) relative, below
+    the error of a solve to 1e-13; that check runs on the small meshes."""
+    P = D.make_problem("C4", keep_parts=True)
+    n, E, b = P["n"], P["E"], P["b"]
+    w = dev(D.functional_weights(n))
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals0"]), dev(P["diag_pos"]), dev(P["mass"]))
+    params = dict(neumann_degree=2, tol=1e-13)
+    q = dev(P["q"]).requires_grad_(True)
+    sig = dev(P["sigma"]).requires_grad_(True)
+    x = nair.NairSolve.apply(q, sig, *args, params)
+    (w * x).sum().backward()
+    xs = x.detach()
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), **params)
+    iq, isg = D.fd_coordinates(n, E, count=8)
+    mass = P["mass"]
+    for i in iq:
+        e, c = divmod(int(i), b)
+        t = np.zeros(n)
+        t[e * b:(e + 1) * b] = mass[e][:, c]
+        dx, rep = S.solve(dev(t))
+        assert rep["rel_res"] <= 1e-12
+        ref = float((w * dx).sum())
+        assert abs(float(q.grad[i]) - ref) <= 1e-6 * abs(ref) + 1e-14, (int(i), float(q.grad[i]), ref)
+    xe = xs.cpu().numpy()
+    for e in isg:
+        e = int(e)
+        t = np.zeros(n)
+        t[e * b:(e + 1) * b] = -mass[e] @ xe[e * b:(e + 1) * b]
+        dx, rep = S.solve(dev(t))
+        assert rep["rel_res"] <= 1e-12
+        ref = float((w * dx).sum())
+        assert abs(float(sig.grad[e]) - ref) <= 1e-6 * abs(ref) + 1e-14, (e, float(sig.grad[e]), ref)
+    S.close()

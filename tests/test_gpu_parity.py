@@ -583,3 +583,114 @@ def test_mixed_precision_accuracy(nair, name, N, p, k):
     l32, a32 = S32.adjoint_solve(w)
     assert a64["rel_res"] <= 1e-10 and a32["rel_res"] <= 1e-10
     assert float((l32 - l64).norm() / l64.norm()) <= 1e-8
+
+
+def level_diffs(S32, S64):
+    """Per level of two hierarchies of the same matrix: C/F and pattern
+    difference counts, and the largest per-row relative difference of A_l,
+    R_cf and D^{-1} (values compared only where the patterns agree)."""
+    out = []
+    for l in range(min(S32.num_levels(), S64.num_levels())):
+        g, o = S32.level(l), S64.level(l)
+        d = {"level": l, "cf": 0, "pattern": 0}
+        same_pattern = np.array_equal(g["row_ptr"], o["row_ptr"]) and np.array_equal(g["col"], o["col"])
+        d["pattern"] = 0 if same_pattern else 1
+        if same_pattern:
+            d["A"] = rel_rows(g["vals"], o["vals"])
+            d["Dinv"] = rel_rows(g["dinv"], o["dinv"])
+        if not o["coarsest"] and not g["coarsest"]:
+            d["cf"] = int(np.count_nonzero(g["cf"] != o["cf"]))
+            if d["cf"] == 0 and np.array_equal(g["R_ci"], o["R_ci"]) and np.array_equal(g["R_rp"], o["R_rp"]):
+                d["R"] = rel_rows(g["R_v"], o["R_v"])
+            else:
+                d["pattern"] += 1
+        out.append(d)
+    return out
+
+
+@pytest.mark.parametrize("name,N,p,k", [("C3", 16, 6, 1), ("C5", 24, 3, 2)])
+def test_mixed_precision_per_result_error(nair, oracle_mod, name, N, p, k):
+    """Per-result error of the FP32 forms against FP64 (mixed precision: setup
+    from the FP32-rounded matrix, D^{-1} computed in FP64 from the FP32 blocks
+    and stored in FP32).  Level by level the FP32 hierarchy has the FP64
+    hierarchy's C/F splittings and patterns; level 0's A is the FP32 rounding
+    (<= 2^-24 per row, relative) and its D^{-1} carries cond(D_ii) times that
+    (<= 2e-6); the coarse A, R_cf and D^{-1} stay within 1e-4 per row (measured
+    up to 4.2e-5).  One FP32 cycle (forward and transposed) on a seeded vector
+    is within 5e-6 of the oracle's FP64 cycle (measured up to 6e-7) -- the
+    identity in its place would be off by O(1) -- and FGMRES needs at most one
+    more iteration than in FP64 (measured: the same count)."""
+    P = D.make_problem(name, N=N, p=p)
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]))
+    params = dict(neumann_degree=k)
+    S64 = nair.NairSolver(*args, **params)
+    S32 = nair.NairSolver(*args, precision="mixed", **params)
+    assert S32.num_levels() == S64.num_levels()
+    diffs = level_diffs(S32, S64)
+    assert all(d["cf"] == 0 and d["pattern"] == 0 for d in diffs), diffs
+    assert diffs[0]["A"] <= 2.0 ** -24 and diffs[0]["Dinv"] <= 2e-6, diffs[0]
+    for d in diffs:
+        for key in ("A", "Dinv", "R"):
+            if key in d:
+                assert d[key] <= 1e-4, (key, d)
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], **params)
+    f = D.rng.uniform(7, P["n"]) - 0.5
+    zo = H.vcycle(f)
+    z32 = S32.vcycle(dev(f)).cpu().numpy()
+    z64 = S64.vcycle(dev(f)).cpu().numpy()
+    assert np.linalg.norm(z64 - zo) <= 1e-12 * np.linalg.norm(zo)
+    assert np.linalg.norm(z32 - zo) <= 5e-6 * np.linalg.norm(zo)
+    assert np.linalg.norm(f - zo) > 1e-2 * np.linalg.norm(zo)   # the bound rules out the identity
+    zto = H.vcycle(f, transposed=True)
+    zt32 = S32.adjoint_vcycle(dev(f)).cpu().numpy()
+    assert np.linalg.norm(zt32 - zto) <= 5e-6 * np.linalg.norm(zto)
+    rhs = dev(P["rhs"])
+    _, r64 = S64.solve(rhs)
+    _, r32 = S32.solve(rhs)
+    assert r32["iterations"] <= r64["iterations"] + 1, (r32["iterations"], r64["iterations"])
+    S32.close()
+    S64.close()
+
+
+def test_c4_gradients_against_oracle_solutions(nair, oracle_mod):
+    """C4 on a 24 x 24 x 2 mesh: the GPU gradients (NairSolve backward) against
+    the oracle's gradient formula applied to the oracle's own forward solution
+    and its own adjoint solution (FGMRES on A^T with the transposed cycle), all
+    solves to 1e-13."""
+    P = D.make_problem("C4", N=24, keep_parts=True)
+    n = P["n"]
+    w = D.functional_weights(n)
+    args = (dev(P["row_ptr"]), dev(P["col"]), dev(P["vals0"]), dev(P["diag_pos"]), dev(P["mass"]))
+    params = dict(neumann_degree=2, tol=1e-13)
+    q = dev(P["q"]).requires_grad_(True)
+    sig = dev(P["sigma"]).requires_grad_(True)
+    x = nair.NairSolve.apply(q, sig, *args, params)
+    (dev(w) * x).sum().backward()
+    H = oracle_mod.Hierarchy(P["row_ptr"], P["col"], P["vals"], neumann_degree=2)
+    xo = H.solve(P["rhs"], tol=1e-13)["x"]
+    lo = H.solve(w, transposed=True, tol=1e-13)["x"]
+    gs_o, gq_o = oracle_mod.gradients(P["mass"], lo, xo)
+    gs, gq = sig.grad.cpu().numpy(), q.grad.cpu().numpy()
+    assert np.linalg.norm(gs - gs_o) <= 1e-9 * np.linalg.norm(gs_o)
+    assert np.linalg.norm(gq - gq_o) <= 1e-9 * np.linalg.norm(gq_o)
+
+
+def test_nan_rhs_is_breakdown_and_handle_recovers(nair):
+    """A NaN in the right-hand side (made on the host) ends the forward solve
+    with NAIR_ERR_BREAKDOWN, an infinity in w ends the adjoint solve the same
+    way, and the handle then solves a finite system as before."""
+    P = D.make_problem("C2", N=8)
+    S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), neumann_degree=2)
+    _, good = S.solve(dev(P["rhs"]))
+    bad = P["rhs"].copy()
+    bad[17] = np.nan
+    _, rep = S.solve(dev(bad), check=False)
+    assert rep["status"] == 4
+    wbad = D.functional_weights(P["n"])
+    wbad[3] = np.inf
+    _, repa = S.adjoint_solve(dev(wbad), check=False)
+    assert repa["status"] == 4
+    x, again = S.solve(dev(P["rhs"]))
+    assert again["status"] == 0 and again["rel_res"] <= 1e-10
+    assert again["iterations"] == good["iterations"]
+    S.close()

@@ -49,6 +49,50 @@ def test_noalloc_matches_allocating_entry_point_twice(lib, b):
         assert torch.equal(got, ref)
 
 
+@pytest.mark.parametrize("b", [3, 6, 10, 28, 32])
+def test_noalloc_matches_on_pivot_ties_and_signed_zeros(lib, b):
+    """Small-integer blocks with signed zeros: equal |entries| in a pivot column,
+    zero diagonals that force row exchanges, and -0.0 against +0.0.  The two
+    kernels pick pivots and exchange rows in different ways, so these are the
+    inputs where they could part; they must still agree bit for bit, and on
+    which calls report a zero pivot."""
+    r = np.random.default_rng(300 + b)
+    A = r.integers(-2, 3, size=(400, b, b)).astype(np.float64)
+    A[r.random(A.shape) < 0.2] = -0.0
+    A[::7, np.arange(b), np.arange(b)] = 0.0   # zero diagonals on every seventh block
+    good = []
+    for k in range(len(A)):
+        st, _ = _call(lib, "nair_block_inverse", torch.from_numpy(A[k:k + 1]).cuda())
+        if st == 0:
+            good.append(k)
+    assert len(good) > 100
+    X = torch.from_numpy(A[good]).cuda()
+    for _ in range(2):
+        st0, ref = _call(lib, "nair_block_inverse", X)
+        st1, got = _call(lib, "nair_block_inverse_noalloc", X)
+        assert st0 == 0 and st1 == 0, lib.lib().nair_last_error()
+        assert torch.equal(got.view(torch.int64), ref.view(torch.int64))
+
+
+@pytest.mark.parametrize("b", [3, 6, 28, 32])
+def test_noalloc_singular_and_nan_blocks_match_status(lib, b):
+    """All-ones blocks (rank one) and blocks holding a NaN: both entry points
+    report SINGULAR_BLOCK; one regular block alone gives OK from both."""
+    for fill in (1.0, float("nan")):
+        A = np.ones((40, b, b)) if fill == 1.0 else np.eye(b)[None].repeat(40, axis=0) * 2.0
+        if fill != 1.0:
+            A[17, b // 2, b // 2] = fill
+        X = torch.from_numpy(A).cuda()
+        st0, _ = _call(lib, "nair_block_inverse", X)
+        st1, _ = _call(lib, "nair_block_inverse_noalloc", X)
+        assert st0 == 2 and st1 == 2
+    X = torch.from_numpy(np.eye(b)[None] * 3.0).cuda()
+    st0, ref = _call(lib, "nair_block_inverse", X)
+    st1, got = _call(lib, "nair_block_inverse_noalloc", X)
+    assert st0 == 0 and st1 == 0
+    assert torch.equal(got, ref)
+
+
 def test_noalloc_reports_singular_then_recovers(lib):
     r = np.random.default_rng(7)
     A = r.standard_normal((500, 6, 6)) + 3 * np.eye(6)
