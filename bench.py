@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--variant-steps", type=int, default=3,
                     help="timed steps of each variant (after one warm-up)")
+    ap.add_argument("--neumann-degree", type=int, default=0,
+                    help="profiling aid: this Neumann degree instead of the workload's")
+    ap.add_argument("--mesh", type=int, default=0,
+                    help="profiling aid: the workload on an N x N x 2 mesh instead of its own")
     ap.add_argument("--vcycles", type=int, default=0,
                     help="profiling aid: build the hierarchy (no CUDA graph) and apply this many "
                          "V-cycles to the right-hand side instead of benchmarking")
@@ -111,9 +115,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs(workload):
-    P = dgtransport.make_problem(workload)
-    return P
+def make_inputs(workload, mesh=0):
+    return dgtransport.make_problem(workload, N=mesh or None)
 
 
 def oracle_sample(workload):
@@ -467,6 +470,11 @@ def measure_variants(nair, params, rp, ci, v, bvec, P, x64, flush, stream, steps
                          ("forward_vcycle_k3_fp64", dict(neumann_degree=3)),
                          ("forward_vcycle_k3_mixed", dict(neumann_degree=3, precision="mixed")),
                          ("forward_vcycle_k4_fp64", dict(neumann_degree=4)),
+                         ("forward_vcycle_k5_fp64", dict(neumann_degree=5)),
+                         ("forward_vcycle_k6_fp64", dict(neumann_degree=6)),
+                         ("forward_vcycle_k7_fp64", dict(neumann_degree=7)),
+                         ("forward_vcycle_k8_fp64", dict(neumann_degree=8)),
+                         ("forward_fcycle_k4_fp64", dict(neumann_degree=4, cycle_type="F")),
                          ("forward_fcycle_k3_fp64", dict(neumann_degree=3, cycle_type="F")),
                          ("forward_fcycle_k3_mixed", dict(neumann_degree=3, cycle_type="F", precision="mixed")),
                          # scalar nAIR (block-diagonal scaling, coarsening by degree of freedom)
@@ -562,8 +570,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    P = make_inputs(args.workload)
-    k = P["neumann_degree"]
+    P = make_inputs(args.workload, args.mesh)
+    k = args.neumann_degree or P["neumann_degree"]
     params = dict(neumann_degree=k, precision=args.precision)
     if args.vcycles:
         S = nair.NairSolver(torch.from_numpy(P["row_ptr"]).to(dev), torch.from_numpy(P["col"]).to(dev),

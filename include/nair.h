@@ -15,7 +15,10 @@
  *   - "device" pointers are CUDA global-memory addresses on the current device;
  *     "host" pointers are ordinary CPU memory.  The caller owns every pointer
  *     it passes; the library copies what it keeps and retains no caller
- *     pointer after a call returns.
+ *     pointer after a call returns.  The device vectors of the solves and
+ *     cycles (b, x, w, lambda, f) must start on a 16-byte boundary (as every
+ *     cudaMalloc'd or torch-allocated buffer does); a misaligned vector is
+ *     rejected with NAIR_ERR_INVALID_ARG before any work is queued.
  *   - Work is ordered on the stream given in nair_params (NULL = the legacy
  *     default stream).  Calls that return sizes or statuses synchronise that
  *     stream.

@@ -536,9 +536,15 @@ static nair_status solve_impl(nair_handle *h, const double *b, double *x, nair_i
   return st;
 }
 
+// the row kernels read vectors with 16-byte loads where the block size
+// allows it, so caller vectors must start on a 16-byte boundary
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+static const char *kAlignMsg = "device vectors must be 16-byte aligned";
+
 nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *info) {
   NAIR_API_BEGIN
   if (!h || !b || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(b) || !aligned16(x)) return set_error(NAIR_ERR_INVALID_ARG, kAlignMsg);
   return solve_impl(h, b, x, info, false);
   NAIR_API_END
 }
@@ -546,6 +552,7 @@ nair_status nair_solve(nair_handle *h, const double *b, double *x, nair_info *in
 nair_status nair_vcycle(nair_handle *h, const double *f, double *x) {
   NAIR_API_BEGIN
   if (!h || !f || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(f) || !aligned16(x)) return set_error(NAIR_ERR_INVALID_ARG, kAlignMsg);
   if (h->mixed) precond<float>(h->h32, h->P, f, x, h->s, h->n);
   else precond<double>(h->h64, h->P, f, x, h->s, h->n);
   NAIR_CK(cudaStreamSynchronize(h->s));
@@ -606,6 +613,7 @@ static void build_adjoint(nair_handle *h) {
 nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lam, nair_info *info) {
   NAIR_API_BEGIN
   if (!h || !w || !lam) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(w) || !aligned16(lam)) return set_error(NAIR_ERR_INVALID_ARG, kAlignMsg);
   if (h->raw.adjoint_mode == NAIR_ADJOINT_REBUILD) {
     if (!h->adj) build_adjoint(h);
     return nair_solve(h->adj, w, lam, info);
@@ -618,6 +626,7 @@ nair_status nair_adjoint_solve(nair_handle *h, const double *w, double *lam, nai
 nair_status nair_adjoint_vcycle(nair_handle *h, const double *f, double *x) {
   NAIR_API_BEGIN
   if (!h || !f || !x) return set_error(NAIR_ERR_INVALID_ARG, "null argument");
+  if (!aligned16(f) || !aligned16(x)) return set_error(NAIR_ERR_INVALID_ARG, kAlignMsg);
   if (!h->tbuilt) build_transposed_handle(h);
   if (h->mixed) precond<float>(h->h32, h->P, f, x, h->s, h->n, true);
   else precond<double>(h->h64, h->P, f, x, h->s, h->n, true);

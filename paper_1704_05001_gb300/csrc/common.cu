@@ -119,6 +119,9 @@ void *Mem::raw(size_t bytes) {
     fail(e == cudaErrorMemoryAllocation ? NAIR_ERR_OOM : NAIR_ERR_CUDA, buf);
   }
   ptrs.push_back(p);
+  // the row kernels read rows with 16-byte loads from offsets that are
+  // multiples of 16 bytes; they rely on the allocator's 256-byte alignment
+  if ((uintptr_t)p & 255u) fail(NAIR_ERR_CUDA, "device allocation not 256-byte aligned");
   return p;
 }
 

@@ -20,10 +20,14 @@ static constexpr int kMaxFLists = 8;
 // scalar-row form of a level's off-diagonal blocks for its FP64 sweeps:
 // scalar row (i, r) lists, in ascending block order, the off-diagonal blocks
 // p of row i whose row r has a nonzero (offsets srp[i b + r], block indices
-// sp); perm_f[k] (for F sweep k's rows, fsweep when k = 0) and perm_c (csweep)
+// sp).  The entries are also packed for the sweeps: sj[e] is entry e's block
+// column and sv[e b .. e b + b) row r of its block (values of the level's
+// type), so a sweep streams its values and loads one index per entry.
+// perm_f[k] (for F sweep k's rows, fsweep when k = 0) and perm_c (csweep)
 // order the scalar rows of each thread block of *_tpc rows by entry count
 struct SweepRows {
-  int *srp = nullptr, *sp = nullptr;
+  int *srp = nullptr, *sp = nullptr, *sj = nullptr;
+  void *sv = nullptr;
   unsigned char *perm_f[kMaxFLists] = {}, *perm_c = nullptr;
   int perm_f_tpc[kMaxFLists] = {}, perm_c_tpc = 0;
 };
@@ -54,6 +58,7 @@ struct Level {
   SweepRows sr;  // levels >= 1, FP64
   int *ipc = nullptr;      // element -> coarse column of P (C: itself, F: one-point source) or -1
   DBsr<T> R;               // R_cf, nC rows, columns = element indices (solve form)
+  SweepRows rr;            // scalar-row form of R_cf for the restriction (FP64; perm_c: all rows)
   int *R_ci_f = nullptr;   // R_cf columns as F indices (export form)
   // kept only with keep_setup_data
   unsigned char *strong = nullptr;
@@ -208,6 +213,10 @@ int *fsweep_lists(int E, int nF, const int *rp, const int *ci, const signed char
                   int *cnt, cudaStream_t s, Mem &mem, Mem &tmp);
 void fsweep_assign(int nF, int nf, int *buf, const int *hcnt, int *fsweep, int **fl, int *fl_n, int **fq,
                    int *fq_n);
+// the scalar-row form of R_cf (nC rows, element columns) for the restriction
+// (FP64 and the DG block sizes; otherwise rr stays empty)
+template <typename T>
+void build_restrict_rows(int nC, int b, const DBsr<T> &R, SweepRows &rr, cudaStream_t s, Mem &mem);
 // the scalar-row form of one level's matrix A for its sweep lists (FP64 and
 // the DG block sizes; otherwise sr stays empty and the sweeps use k_rowop)
 template <typename T>

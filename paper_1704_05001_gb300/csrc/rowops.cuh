@@ -46,12 +46,60 @@ struct RowArgs {
   const int *diag, *oci;
   const unsigned long long *ocols;
   const T *ov;
-  // scalar-row form of the sweep (k_sweep_rows): entries srp[i b + r] ..
-  // srp[i b + r + 1] of sp are the off-diagonal blocks of row i whose row r has
-  // a nonzero; perm orders each thread block's scalar rows by entry count
-  const int *srp, *sp;
+  // scalar-row form (k_scalar_rows): entries srp[i b + r] ..
+  // srp[i b + r + 1] are the off-diagonal blocks of row i whose row r has a
+  // nonzero, packed: sj[e] the block column, sv[e b ..] row r of the block;
+  // perm orders each thread block's scalar rows by entry count
+  const int *srp, *sj;
+  const T *sv;
   const unsigned char *perm;
 };
+
+// B consecutive values from p into registers, as 16-byte loads where the
+// row's size allows it (the callers' rows start on 16-byte boundaries then:
+// every row offset is a multiple of B values and the arrays are allocated
+// with 256-byte alignment)
+template <typename T, int B>
+__device__ __forceinline__ void load_row(const T *__restrict__ p, T (&o)[B]) {
+  if constexpr (sizeof(T) == 8 && B % 2 == 0) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int c = 0; c < B / 2; ++c) {
+      const double2 t = q[c];
+      o[2 * c] = t.x;
+      o[2 * c + 1] = t.y;
+    }
+  } else if constexpr (sizeof(T) == 4 && B % 4 == 0) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int c = 0; c < B / 4; ++c) {
+      const float4 t = q[c];
+      o[4 * c] = t.x;
+      o[4 * c + 1] = t.y;
+      o[4 * c + 2] = t.z;
+      o[4 * c + 3] = t.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && B % 2 == 0) {
+    const float2 *q = reinterpret_cast<const float2 *>(p);
+#pragma unroll
+    for (int c = 0; c < B / 2; ++c) {
+      const float2 t = q[c];
+      o[2 * c] = t.x;
+      o[2 * c + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < B; ++c) o[c] = p[c];
+  }
+}
+
+// the same values with scalar loads (prologue loads held across the
+// dependency wait, where 16-byte loads cost registers)
+template <typename T, int B>
+__device__ __forceinline__ void load_row_scalar(const T *__restrict__ p, T (&o)[B]) {
+#pragma unroll
+  for (int c = 0; c < B; ++c) o[c] = p[c];
+}
 
 __device__ __forceinline__ unsigned long long global_clock() {
   unsigned long long t;
@@ -81,10 +129,8 @@ __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int p0, int p1, in
   T acc = 0;
   if constexpr (B > 0) {
     if (p0 < p1 && j0 >= 0 && p0 != skip) {
-      const T *xj = a.x + (size_t)j0 * B;
       T vx[B];
-#pragma unroll
-      for (int c = 0; c < B; ++c) vx[c] = xj[c];
+      load_row<T, B>(a.x + (size_t)j0 * B, vx);
 #pragma unroll
       for (int c = 0; c < B; ++c) acc = fma(va0[c], vx[c], acc);
     }
@@ -96,11 +142,9 @@ __device__ __forceinline__ T row_partial(const RowArgs<T> &a, int p0, int p1, in
         j = a.ipc[j];
         if (j < 0) continue;
       }
-      const T *av = a.v + (size_t)p * bb + r * B;
-      const T *xj = a.x + (size_t)j * B;
       T va[B], vx[B];
-#pragma unroll
-      for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
+      load_row_scalar<T, B>(a.v + (size_t)p * bb + r * B, va);
+      load_row_scalar<T, B>(a.x + (size_t)j * B, vx);
 #pragma unroll
       for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
     }
@@ -160,14 +204,10 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
     if (p0 < p1) {
       j0 = a.ci[p0];
       if (a.ipc) j0 = a.ipc[j0];
-      const T *av = a.v + (size_t)p0 * B * B + r * B;
-#pragma unroll
-      for (int c = 0; c < B; ++c) va0[c] = av[c];
+      load_row_scalar<T, B>(a.v + (size_t)p0 * B * B + r * B, va0);
     }
-    if (OP == OP_JACOBI && active && g == 0) {
-      const T *d = a.dinv + (size_t)i * B * B + r * B;
-#pragma unroll
-      for (int c = 0; c < B; ++c) dv[c] = d[c];
+    if constexpr (OP == OP_JACOBI) {
+      if (active && g == 0) load_row_scalar<T, B>(a.dinv + (size_t)i * B * B + r * B, dv);
     }
   }
   // JACOBI works in the classical form x_i = D_ii^{-1} (f_i - sum_{j != i} A_ij x_j):
@@ -224,20 +264,23 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
   }
 }
 
-// Block-Jacobi sweep in scalar-row form (levels >= 1, whose off-diagonal
-// blocks keep about half of their rows zero): thread block c owns rows
-// list[c tpc ..], and its tpc x B scalar rows (i, r) are assigned, G threads
-// each, in the order perm gives -- sorted by entry count, so that the threads
-// of a warp run loops of nearly equal length and the FP64 pipe is not spent on
-// the zero rows of the blocks.  Thread g of scalar row (i, r) accumulates
-// sum_p A_p[r, :] x_{col p} over its entries g, g + G, ... in ascending block
-// order; the G partial sums are added by the pairwise tree of the row kernels;
-// then each thread of the natural layout applies row r of D_ii^{-1} to f_i -
-// that sum from shared memory.
-template <typename T, int B>
-__global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
+// Scalar-row form of the coarse-level row kernels (levels >= 1, whose
+// off-diagonal blocks -- and the blocks of R_cf -- keep about half of their
+// rows zero): thread block c owns rows list[c tpc ..] (rows c tpc .. when list
+// is null), and its tpc x B scalar rows (i, r) are assigned, G threads each,
+// in the order perm gives -- sorted by entry count, so that the threads of a
+// warp run loops of nearly equal length and the FP64 pipe is not spent on the
+// zero rows of the blocks.  Thread g of scalar row (i, r) accumulates
+// sum_e sv_e . x_{sj_e} over its packed entries g, g + G, ... in ascending
+// block order; the G partial sums are added by the pairwise tree of the row
+// kernels.  Then each thread of the natural layout finishes component r of
+// row i:
+//   OP_JACOBI: row r of D_ii^{-1} applied to f_i - sum (from shared memory);
+//   OP_RESTRICT: f_c = f_{c2f[i]} + sum, the restriction f_c = f_C + R_cf f_F.
+template <typename T, int B, int OP>
+__global__ void __launch_bounds__(256) k_scalar_rows(RowArgs<T> a) {
   pdl_launch_dependents();
-  if ((int)blockIdx.x >= a.comp_ctas) {  // copy segment, as in k_rowop
+  if (OP == OP_JACOBI && (int)blockIdx.x >= a.comp_ctas) {  // copy segment, as in k_rowop
     const long long g = (long long)(blockIdx.x - a.comp_ctas) * blockDim.x + threadIdx.x;
     const bool in = g < (long long)a.ncopy * B;
     const int row = in ? (int)(g / B) : 0, r = in ? (int)(g - (long long)row * B) : 0;
@@ -267,15 +310,16 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
   const bool act = slot < nact * B;
   const int enc = act ? (int)a.perm[(size_t)base * B + slot] : 0;
   const int team = enc / B, r = enc - team * B;
-  const int i = act ? a.list[base + team] : 0;
+  const int i = act ? (a.list ? a.list[base + team] : base + team) : 0;
   const int e0 = act ? a.srp[(size_t)i * B + r] + g : 0, e1 = act ? a.srp[(size_t)i * B + r + 1] : 0;
-  // natural layout: the D^{-1} row this thread applies.  For B <= 10 the
-  // thread block's D^{-1} blocks are staged in shared memory before the
-  // dependency wait; larger blocks are read after the loop
+  // natural layout: the row and component this thread finishes.  For the
+  // sweep with B <= 10 the thread block's D^{-1} blocks are staged in shared
+  // memory before the dependency wait; larger blocks are read after the loop
   const int team2 = t / B, r2 = t - team2 * B;
   const bool act2 = team2 < nact;
-  const int i2 = act2 ? a.list[base + team2] : 0;
-  constexpr bool kStage = B <= 10;
+  const int i2 = act2 ? (a.list ? a.list[base + team2] : base + team2) : 0;
+  const int own = (OP == OP_RESTRICT && act2) ? a.c2f[i2] : i2;  // row of f this component takes
+  constexpr bool kStage = OP == OP_JACOBI && B <= 10;
   __shared__ T sd[kStage ? (256 / B) * B * B : 1];
   if constexpr (kStage) {
     for (int q = t; q < nact * B * B; q += blockDim.x) {
@@ -283,41 +327,38 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
       sd[q] = a.dinv[(size_t)a.list[base + tm] * B * B + (q - tm * B * B)];
     }
   }
-  // the first entry's block and column do not change during the cycle
+  // the first entry's values and column do not change during the cycle
   int j0 = -1;
   T va0[B];
   if (e0 < e1) {
-    const int p0 = a.sp[e0];
-    j0 = a.ci[p0];
+    j0 = a.sj[e0];
     if (a.ipc) j0 = a.ipc[j0];
-    const T *av = a.v + (size_t)p0 * B * B + r * B;
-#pragma unroll
-    for (int c = 0; c < B; ++c) va0[c] = av[c];
+    load_row_scalar<T, B>(a.sv + (size_t)e0 * B, va0);
   }
   pdl_wait();
   if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
   T acc = 0;
   if (e0 < e1 && j0 >= 0) {
-    const T *xj = a.x + (size_t)j0 * B;
     T vx[B];
-#pragma unroll
-    for (int c = 0; c < B; ++c) vx[c] = xj[c];
+    load_row<T, B>(a.x + (size_t)j0 * B, vx);
 #pragma unroll
     for (int c = 0; c < B; ++c) acc = fma(va0[c], vx[c], acc);
   }
 #pragma unroll 2
   for (int e = e0 + G; e < e1; e += G) {
-    const int p = a.sp[e];
-    int j = a.ci[p];
+    int j = a.sj[e];
     if (a.ipc) {
       j = a.ipc[j];
       if (j < 0) continue;
     }
-    const T *av = a.v + (size_t)p * B * B + r * B;
-    const T *xj = a.x + (size_t)j * B;
     T va[B], vx[B];
-#pragma unroll
-    for (int c = 0; c < B; ++c) { va[c] = av[c]; vx[c] = xj[c]; }
+    if constexpr (B >= 10) {  // 16-byte loads; for smaller rows they cost spills
+      load_row<T, B>(a.sv + (size_t)e * B, va);
+      load_row<T, B>(a.x + (size_t)j * B, vx);
+    } else {
+      load_row_scalar<T, B>(a.sv + (size_t)e * B, va);
+      load_row_scalar<T, B>(a.x + (size_t)j * B, vx);
+    }
 #pragma unroll
     for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
   }
@@ -328,18 +369,25 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
       if (act && g < h) red[enc * G + g] += red[enc * G + g + h];
       __syncthreads();
     }
-    if (t < nact * B) sres[t] = a.f[(size_t)i2 * B + r2] - red[t * G];
+    if (OP == OP_RESTRICT) {
+      if (act2) a.out[(size_t)i2 * B + r2] = a.f[(size_t)own * B + r2] + red[t * G];
+    } else if (t < nact * B) {
+      sres[t] = a.f[(size_t)i2 * B + r2] - red[t * G];
+    }
   } else if (act) {
-    sres[enc] = a.f[(size_t)i * B + r] - acc;
+    if (OP == OP_RESTRICT) a.out[(size_t)i * B + r] = a.f[(size_t)a.c2f[i] * B + r] + acc;
+    else sres[enc] = a.f[(size_t)i * B + r] - acc;
   }
-  __syncthreads();
-  if (act2) {
-    const T *d = kStage ? sd + (size_t)team2 * B * B + r2 * B : a.dinv + (size_t)i2 * B * B + r2 * B;
-    T s2 = 0;
+  if constexpr (OP == OP_JACOBI) {
+    __syncthreads();
+    if (act2) {
+      const T *d = kStage ? sd + (size_t)team2 * B * B + r2 * B : a.dinv + (size_t)i2 * B * B + r2 * B;
+      T s2 = 0;
 #pragma unroll
-    for (int c = 0; c < B; ++c) s2 = fma(d[c], sres[team2 * B + c], s2);
-    a.out[(size_t)i2 * B + r2] = s2;
-    if (a.out2c) a.out2c[(size_t)i2 * B + r2] = s2;
+      for (int c = 0; c < B; ++c) s2 = fma(d[c], sres[team2 * B + c], s2);
+      a.out[(size_t)i2 * B + r2] = s2;
+      if (a.out2c) a.out2c[(size_t)i2 * B + r2] = s2;
+    }
   }
   if (a.stamp) {
     __syncthreads();
@@ -347,11 +395,11 @@ __global__ void __launch_bounds__(256) k_sweep_rows(RowArgs<T> a) {
   }
 }
 
-// host launcher of the scalar-row sweep with G threads per scalar row and
-// tpc = max(1, 256 / (b G)) rows per thread block (b in 3, 6, 10, 15, 21, 28);
-// false if there is no kernel for b
-template <typename T>
-bool launch_sweep_rows(RowArgs<T> a, int G, cudaStream_t s);
+// host launcher of the scalar-row kernels (OP_JACOBI, OP_RESTRICT) with G
+// threads per scalar row and tpc = max(1, 256 / (b G)) rows per thread block
+// (b in 3, 6, 10, 15, 21, 28); false if there is no kernel for b
+template <typename T, int OP>
+bool launch_scalar_rows(RowArgs<T> a, int G, cudaStream_t s);
 
 // Level-0 form of the row kernel: the diagonal block from the BSR values, the
 // off-diagonal blocks from their W nonzero columns (one team of B threads per
@@ -392,23 +440,13 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
   int j0 = -1;
   unsigned long long cols0 = 0;
   if (active) {
-    if constexpr (kDiag) {
-      const T *dp = a.v + (size_t)a.diag[i] * B * B + r * B;
-#pragma unroll
-      for (int c = 0; c < B; ++c) dv[c] = dp[c];
-    }
-    if (OP == OP_JACOBI) {
-      const T *dd = a.dinv + (size_t)i * B * B + r * B;
-#pragma unroll
-      for (int c = 0; c < B; ++c) drow[c] = dd[c];
-    }
+    if constexpr (kDiag) load_row_scalar<T, B>(a.v + (size_t)a.diag[i] * B * B + r * B, dv);
+    if constexpr (OP == OP_JACOBI) load_row_scalar<T, B>(a.dinv + (size_t)i * B * B + r * B, drow);
     if (q0 < q1) {
       j0 = a.oci[q0];
       if (a.ipc) j0 = a.ipc[j0];
       cols0 = a.ocols[q0];
-      const T *o = a.ov + (size_t)q0 * B * W + r * W;
-#pragma unroll
-      for (int w = 0; w < W; ++w) ov0[w] = o[w];
+      load_row_scalar<T, W>(a.ov + (size_t)q0 * B * W + r * W, ov0);
     }
   }
   // ---- wait for the producer of x and f
@@ -417,10 +455,8 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
   T acc = 0;
   if (active) {
     if constexpr (kDiag) {  // SPMV / RESID: x is never read through ipc
-      const T *xi = a.x + (size_t)i * B;
       T xv[B];
-#pragma unroll
-      for (int c = 0; c < B; ++c) xv[c] = xi[c];
+      load_row<T, B>(a.x + (size_t)i * B, xv);
 #pragma unroll
       for (int c = 0; c < B; ++c) acc = fma(dv[c], xv[c], acc);
     }
@@ -436,11 +472,12 @@ __global__ void __launch_bounds__(256) k_rowop_l0(RowArgs<T> a) {
         if (j < 0) continue;
       }
       const unsigned long long cols = a.ocols[q];
-      const T *o = a.ov + (size_t)q * B * W + r * W;
       const T *xj = a.x + (size_t)j * B;
       T ovq[W], xq[W];
+      if constexpr (OP == OP_JACOBI) load_row_scalar<T, W>(a.ov + (size_t)q * B * W + r * W, ovq);
+      else load_row<T, W>(a.ov + (size_t)q * B * W + r * W, ovq);
 #pragma unroll
-      for (int w = 0; w < W; ++w) { ovq[w] = o[w]; xq[w] = xj[(cols >> (8 * w)) & 255u]; }
+      for (int w = 0; w < W; ++w) xq[w] = xj[(cols >> (8 * w)) & 255u];
 #pragma unroll
       for (int w = 0; w < W; ++w) acc = fma(ovq[w], xq[w], acc);
     }

@@ -1489,19 +1489,20 @@ static void build_fsweep_lists(Hier<T> &H, const Params &P, cudaStream_t s, Mem 
 // ---------------------------------------------------------------------------
 // scalar-row form of the off-diagonal blocks (sweeps of levels >= 1)
 // ---------------------------------------------------------------------------
-// FILL = false: number of off-diagonal blocks of row i whose row r has a
-// nonzero; FILL = true: their block indices, ascending
+// FILL = false: number of blocks of row i (the off-diagonal ones when
+// skip_diag is set) whose row r has a nonzero; FILL = true: their block
+// indices, ascending
 template <typename T, bool FILL>
 __global__ void k_srow_entries(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
                                const T *__restrict__ v, const int *__restrict__ srp, int *__restrict__ cnt,
-                               int *__restrict__ sp) {
+                               int *__restrict__ sp, int skip_diag) {
   pdl_wait();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)E * b) return;
   const int i = (int)(g / b), r = (int)(g - (long long)i * b);
   int w = FILL ? srp[g] : 0;
   for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    if (ci[p] == i) continue;
+    if (skip_diag && ci[p] == i) continue;
     const T *row = v + ((size_t)p * b + r) * b;
     bool nz = false;
     for (int c = 0; c < b; ++c) nz |= row[c] != (T)0;
@@ -1513,9 +1514,27 @@ __global__ void k_srow_entries(int E, int b, const int *__restrict__ rp, const i
   if (!FILL) cnt[g] = w;
 }
 
-// per thread block of a sweep list (tpc rows, tpc b scalar rows): the scalar
-// rows sorted by entry count, ties in natural order; perm[c tpc b + rank] = the
-// natural slot team b + r
+// packed entries: for scalar row g = (i, r), each entry e's block column sj[e]
+// and row r of its block, sv[e b .. e b + b)
+template <typename T>
+__global__ void k_srow_pack(long long n, int b, const int *__restrict__ srp, const int *__restrict__ sp,
+                            const int *__restrict__ ci, const T *__restrict__ v, int *__restrict__ sj,
+                            T *__restrict__ sv) {
+  pdl_wait();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n) return;
+  const int r = (int)(g % b);
+  for (int e = srp[g]; e < srp[g + 1]; ++e) {
+    const int p = sp[e];
+    sj[e] = ci[p];
+    const T *row = v + ((size_t)p * b + r) * b;
+    for (int c = 0; c < b; ++c) sv[(size_t)e * b + c] = row[c];
+  }
+}
+
+// per thread block of a row list (tpc rows, tpc b scalar rows; rows base ..
+// when list is null): the scalar rows sorted by entry count, ties in natural
+// order; perm[c tpc b + rank] = the natural slot team b + r
 __global__ void k_srow_perm(int n, int b, int tpc, const int *__restrict__ list, const int *__restrict__ srp,
                             unsigned char *__restrict__ perm) {
   pdl_wait();
@@ -1524,7 +1543,7 @@ __global__ void k_srow_perm(int n, int b, int tpc, const int *__restrict__ list,
   int k = 0;
   if (t < m) {
     const int team = t / b, r = t - team * b;
-    const size_t q = (size_t)list[base + team] * b + r;
+    const size_t q = (size_t)(list ? list[base + team] : base + team) * b + r;
     k = srp[q + 1] - srp[q];
     key[t] = k;
   }
@@ -1558,6 +1577,45 @@ static unsigned char *srow_perm(int n, int b, double avg, const int *list, const
   return perm;
 }
 
+// entry lists and packed entries of the scalar-row form of the E x b scalar
+// rows of M (its off-diagonal blocks when skip_diag is set)
+template <typename T>
+static void srow_pack(int E, int b, const DBsr<T> &M, bool skip_diag, SweepRows &sr, cudaStream_t s, Mem &mem) {
+  const long long n = (long long)E * b;
+  Mem tmp;
+  tmp.s = s;
+  int *cnt = tmp.alloc<int>(n + 1);
+  launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)M.rp,
+             (const int *)M.ci, (const T *)M.v, (const int *)nullptr, cnt, (int *)nullptr, (int)skip_diag);
+  NAIR_LAUNCH_CHECK();
+  sr.srp = mem.alloc<int>(n + 1);
+  const int ne = exclusive_scan(cnt, sr.srp, (int)n, s, tmp, true);
+  sr.sp = mem.alloc<int>(std::max(ne, 1));
+  launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)M.rp,
+             (const int *)M.ci, (const T *)M.v, (const int *)sr.srp, (int *)nullptr, sr.sp, (int)skip_diag);
+  NAIR_LAUNCH_CHECK();
+  sr.sj = mem.alloc<int>(std::max(ne, 1));
+  T *sv = mem.alloc<T>((size_t)std::max(ne, 1) * b);
+  sr.sv = sv;
+  launch_pdl(k_srow_pack<T>, dim3(grid(n)), dim3(kThreads), 0, s, n, b, (const int *)sr.srp, (const int *)sr.sp,
+             (const int *)M.ci, (const T *)M.v, sr.sj, sv);
+  NAIR_LAUNCH_CHECK();
+}
+
+template <typename T>
+void build_restrict_rows(int nC, int b, const DBsr<T> &R, SweepRows &rr, cudaStream_t s, Mem &mem) {
+  // FP64 only, as the sweeps
+  if (!std::is_same<T, double>::value || !srow_supported(b) || nC == 0) return;
+  const long long n = (long long)nC * b, ub = (long long)R.nnzb * b;
+  if (n + 1 >= INT_MAX || ub >= INT_MAX) return;
+  const double avg = (double)R.nnzb / nC;
+  if (rowop_groups(nC, b, avg) > kSweepRowsMaxG) return;
+  srow_pack<T>(nC, b, R, false, rr, s, mem);
+  rr.perm_c = srow_perm<T>(nC, b, avg, nullptr, rr.srp, s, mem, &rr.perm_c_tpc);
+}
+template void build_restrict_rows<double>(int, int, const DBsr<double> &, SweepRows &, cudaStream_t, Mem &);
+template void build_restrict_rows<float>(int, int, const DBsr<float> &, SweepRows &, cudaStream_t, Mem &);
+
 template <typename T>
 void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, int *fsweep, int nfl,
                             int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s, Mem &mem) {
@@ -1570,18 +1628,7 @@ void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, int 
   if (n + 1 >= INT_MAX || ub >= INT_MAX) return;
   const double avg = (double)A.nnzb / E;
   if (rowop_groups(nF, b, avg) > kSweepRowsMaxG && rowop_groups(nC, b, avg) > kSweepRowsMaxG) return;
-  Mem tmp;
-  tmp.s = s;
-  int *cnt = tmp.alloc<int>(n + 1);
-  launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)A.rp,
-             (const int *)A.ci, (const T *)A.v, (const int *)nullptr, cnt, (int *)nullptr);
-  NAIR_LAUNCH_CHECK();
-  sr.srp = mem.alloc<int>(n + 1);
-  exclusive_scan(cnt, sr.srp, (int)n, s, tmp, false);
-  sr.sp = mem.alloc<int>(std::max(ub, 1LL));
-  launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)A.rp,
-             (const int *)A.ci, (const T *)A.v, (const int *)sr.srp, (int *)nullptr, sr.sp);
-  NAIR_LAUNCH_CHECK();
+  srow_pack<T>(E, b, A, true, sr, s, mem);
   sr.perm_f[0] = srow_perm<T>(nF, b, avg, fsweep, sr.srp, s, mem, &sr.perm_f_tpc[0]);
   for (int k = 1; k < nfl; ++k) sr.perm_f[k] = srow_perm<T>(fl_n[k], b, avg, fl[k], sr.srp, s, mem, &sr.perm_f_tpc[k]);
   sr.perm_c = srow_perm<T>(nC, b, avg, csweep, sr.srp, s, mem, &sr.perm_c_tpc);
@@ -1594,9 +1641,11 @@ template void build_sweep_rows_level<float>(int, int, int, int, const DBsr<float
 // the scalar-row lists and permutations of every level >= 1 that sweeps
 template <typename T>
 static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
-  for (int l = 1; l < H.nlev; ++l) {
+  for (int l = 0; l < H.nlev; ++l) {
     Level<T> &L = H.lev[l];
     if (L.coarsest) continue;
+    build_restrict_rows<T>(L.nC, H.b, L.R, L.rr, s, mem);
+    if (l == 0) continue;
     build_sweep_rows_level<T>(L.E, L.nF, L.nC, H.b, L.A, L.fsweep, L.nfl, L.fl, L.fl_n, L.csweep, L.sr, s, mem);
   }
 }

@@ -114,30 +114,32 @@ void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   }
   NAIR_LAUNCH_CHECK();
 }
-template <typename T>
-bool launch_sweep_rows(RowArgs<T> a, int G, cudaStream_t s) {
+template <typename T, int OP>
+bool launch_scalar_rows(RowArgs<T> a, int G, cudaStream_t s) {
   const int b = a.b;
   a.G = G;
   a.tpc = sweep_rows_tpc(b, G);
   const int threads = a.tpc * b * G;
   a.comp_ctas = cdiv(a.nrows, a.tpc);
   int blocks = a.comp_ctas;
-  if (a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
+  if (OP == OP_JACOBI && a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
   const dim3 gr(blocks), bl(threads);
   switch (b) {
-    case 3: if (blocks) launch_pdl(k_sweep_rows<T, 3>, gr, bl, 0, s, a); break;
-    case 6: if (blocks) launch_pdl(k_sweep_rows<T, 6>, gr, bl, 0, s, a); break;
-    case 10: if (blocks) launch_pdl(k_sweep_rows<T, 10>, gr, bl, 0, s, a); break;
-    case 15: if (blocks) launch_pdl(k_sweep_rows<T, 15>, gr, bl, 0, s, a); break;
-    case 21: if (blocks) launch_pdl(k_sweep_rows<T, 21>, gr, bl, 0, s, a); break;
-    case 28: if (blocks) launch_pdl(k_sweep_rows<T, 28>, gr, bl, 0, s, a); break;
+    case 3: if (blocks) launch_pdl(k_scalar_rows<T, 3, OP>, gr, bl, 0, s, a); break;
+    case 6: if (blocks) launch_pdl(k_scalar_rows<T, 6, OP>, gr, bl, 0, s, a); break;
+    case 10: if (blocks) launch_pdl(k_scalar_rows<T, 10, OP>, gr, bl, 0, s, a); break;
+    case 15: if (blocks) launch_pdl(k_scalar_rows<T, 15, OP>, gr, bl, 0, s, a); break;
+    case 21: if (blocks) launch_pdl(k_scalar_rows<T, 21, OP>, gr, bl, 0, s, a); break;
+    case 28: if (blocks) launch_pdl(k_scalar_rows<T, 28, OP>, gr, bl, 0, s, a); break;
     default: return false;
   }
   NAIR_LAUNCH_CHECK();
   return true;
 }
-template bool launch_sweep_rows<double>(RowArgs<double>, int, cudaStream_t);
-template bool launch_sweep_rows<float>(RowArgs<float>, int, cudaStream_t);
+template bool launch_scalar_rows<double, OP_JACOBI>(RowArgs<double>, int, cudaStream_t);
+template bool launch_scalar_rows<float, OP_JACOBI>(RowArgs<float>, int, cudaStream_t);
+template bool launch_scalar_rows<double, OP_RESTRICT>(RowArgs<double>, int, cudaStream_t);
+template bool launch_scalar_rows<float, OP_RESTRICT>(RowArgs<float>, int, cudaStream_t);
 
 template <typename T, int OP>
 void launch_rowop_l0(RowArgs<T> a, int W, cudaStream_t s) {
@@ -239,7 +241,19 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
     a.f = rhs;
     a.c2f = L.c2f;
     a.out = N.f;
-    launch_rowop<T, OP_RESTRICT>(a, L.nC ? (double)L.R.nnzb / L.nC : 0.0, s);
+    const double avgR = L.nC ? (double)L.R.nnzb / L.nC : 0.0;
+    // scalar-row form of R_cf where built (its permutation was sorted for the
+    // same thread groups per row)
+    const int G = rowop_groups(a.nrows, b, avgR);
+    bool done = false;
+    if (L.rr.srp && L.rr.perm_c && sweep_rows_tpc(b, G) == L.rr.perm_c_tpc) {
+      a.srp = L.rr.srp;
+      a.sj = L.rr.sj;
+      a.sv = static_cast<const T *>(L.rr.sv);
+      a.perm = L.rr.perm_c;
+      done = launch_scalar_rows<T, OP_RESTRICT>(a, G, s);
+    }
+    if (!done) launch_rowop<T, OP_RESTRICT>(a, avgR, s);
   }
   vcyc<T>(H, P, l + 1, type, N.f, N.x, true, s);
   if (type == 1) vcyc<T>(H, P, l + 1, 0, N.f, N.x, false, s);
@@ -355,9 +369,10 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       bool done = false;
       if (L.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
         a.srp = L.sr.srp;
-        a.sp = L.sr.sp;
+        a.sj = L.sr.sj;
+        a.sv = static_cast<const T *>(L.sr.sv);
         a.perm = perm;
-        done = launch_sweep_rows<T>(a, G, s);
+        done = launch_scalar_rows<T, OP_JACOBI>(a, G, s);
       }
       if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
     }
@@ -521,9 +536,10 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
         bool done = false;
         if (TL.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
           a.srp = TL.sr.srp;
-          a.sp = TL.sr.sp;
+          a.sj = TL.sr.sj;
+          a.sv = static_cast<const T *>(TL.sr.sv);
           a.perm = perm;
-          done = launch_sweep_rows<T>(a, G, s);
+          done = launch_scalar_rows<T, OP_JACOBI>(a, G, s);
         }
         if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
       }
