@@ -29,10 +29,10 @@ CONFIGS = {
     "C4": dict(N=256, p=2, flow=("rot",), sigma="lognormal", jitter=0.0,
                order="natural", neumann_degree=2),
     # P3, 512x512x2 jittered, rotating b, log-normal sigma_t; Neumann degree not
-    # stated for this workload: 3, the fastest measured setup + solve (with
-    # degree 1 GMRES(50) stalls near 1e-7; degree 2 needs 166 iterations)
+    # stated for this workload: 6, the fastest measured setup + solve of the
+    # degrees 2 to 8 (with degree 1 GMRES(50) stalls near 1e-7)
     "C5": dict(N=512, p=3, flow=("rot",), sigma="lognormal", jitter=0.2,
-               order="natural", neumann_degree=3),
+               order="natural", neumann_degree=6),
     # second workload: the paper's non-constant flows b1, b2, b3 (Sec. 6.2) on a
     # P2, 256x256x2 jittered mesh, sigma_t = 1, Neumann degree 1 (paper default),
     # elements in flow order where the flow graph has none

@@ -327,13 +327,15 @@ __global__ void __launch_bounds__(256) k_scalar_rows(RowArgs<T> a) {
       sd[q] = a.dinv[(size_t)a.list[base + tm] * B * B + (q - tm * B * B)];
     }
   }
-  // the first entry's values and column do not change during the cycle
-  int j0 = -1;
+  // the first entry's values and the first two columns do not change during
+  // the cycle: loaded before the dependency wait
+  int j0 = -1, jn = 0;
   T va0[B];
   if (e0 < e1) {
     j0 = a.sj[e0];
     if (a.ipc) j0 = a.ipc[j0];
     load_row_scalar<T, B>(a.sv + (size_t)e0 * B, va0);
+    if (e0 + G < e1) jn = a.sj[e0 + G];
   }
   pdl_wait();
   if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
@@ -344,9 +346,12 @@ __global__ void __launch_bounds__(256) k_scalar_rows(RowArgs<T> a) {
 #pragma unroll
     for (int c = 0; c < B; ++c) acc = fma(va0[c], vx[c], acc);
   }
+  // each entry's column was loaded one entry ahead, so the gather of x starts
+  // at once and the next column's load overlaps it
 #pragma unroll 2
   for (int e = e0 + G; e < e1; e += G) {
-    int j = a.sj[e];
+    int j = jn;
+    if (e + G < e1) jn = a.sj[e + G];
     if (a.ipc) {
       j = a.ipc[j];
       if (j < 0) continue;

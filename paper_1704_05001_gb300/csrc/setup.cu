@@ -760,6 +760,59 @@ __global__ void k_spgemm_pairs(long long total, int b, const int *__restrict__ p
   ov[g] = negate ? -acc : acc;
 }
 
+// The same products with the block size as a template parameter (DG blocks up
+// to 10): the operands of pair k + 1 (row r of its left block, column c of its
+// right block) are loaded before the fma chain of pair k, so each thread keeps
+// one pair's loads in flight while it computes.  The chain is unchanged.
+template <typename T, int B>
+__global__ void __launch_bounds__(kThreads) k_spgemm_pairs_b(long long total, const int *__restrict__ pbeg,
+                                                             const int2 *__restrict__ pairs, const int *__restrict__ iq,
+                                                             const T *__restrict__ lv, const T *__restrict__ rv,
+                                                             const T *__restrict__ iv, int negate, T *__restrict__ ov) {
+  pdl_wait();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  constexpr int bb = B * B;
+  const long long blk = g / bb;
+  const int rc = (int)(g - blk * bb), r = rc / B, c = rc - r * B;
+  const int q0 = iq[blk];
+  T acc = q0 >= 0 ? iv[(size_t)q0 * bb + rc] : (T)0;
+  int k = pbeg[blk];
+  const int k1 = pbeg[blk + 1];
+  T na[B], nb[B];
+  if (k < k1) {
+    const int2 pq = pairs[k];
+    const T *a = lv + (size_t)pq.x * bb + r * B;
+    const T *bv = rv + (size_t)pq.y * bb + c;
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+      na[t] = a[t];
+      nb[t] = bv[t * B];
+    }
+  }
+  for (; k < k1; ++k) {
+    T ca[B], cb[B];
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+      ca[t] = na[t];
+      cb[t] = nb[t];
+    }
+    if (k + 1 < k1) {
+      const int2 pq = pairs[k + 1];
+      const T *a = lv + (size_t)pq.x * bb + r * B;
+      const T *bv = rv + (size_t)pq.y * bb + c;
+#pragma unroll
+      for (int t = 0; t < B; ++t) {
+        na[t] = a[t];
+        nb[t] = bv[t * B];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < B; ++t) acc = fma_rn(ca[t], cb[t], acc);
+  }
+  ov[g] = negate ? -acc : acc;
+}
+
 // ---------------------------------------------------------------------------
 // a8: filtering.  Drop X_ij (j != i) when ||X_ij||^2 <= tol^2 ||X_ii||^2
 // ---------------------------------------------------------------------------
@@ -1277,7 +1330,13 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
   out.v = mem.alloc<T>((size_t)out.nnzb * b * b);
   const long long total = (long long)out.nnzb * b * b;
   if (total) {
-    launch_pdl(k_spgemm_pairs<T>, dim3(grid(total)), dim3(kThreads), 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    const dim3 gr(grid(total)), bl(kThreads);
+    switch (b) {
+      case 3: launch_pdl(k_spgemm_pairs_b<T, 3>, gr, bl, 0, s, total, pbeg, pairs, iq, lv, rv, iv, negate, out.v); break;
+      case 6: launch_pdl(k_spgemm_pairs_b<T, 6>, gr, bl, 0, s, total, pbeg, pairs, iq, lv, rv, iv, negate, out.v); break;
+      case 10: launch_pdl(k_spgemm_pairs_b<T, 10>, gr, bl, 0, s, total, pbeg, pairs, iq, lv, rv, iv, negate, out.v); break;
+      default: launch_pdl(k_spgemm_pairs<T>, gr, bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v); break;
+    }
     NAIR_LAUNCH_CHECK();
   }
   tmp.release(pairs);
