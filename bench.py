@@ -178,9 +178,16 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 # DRAM traffic of the block-Jacobi sweep kernels per launch (dram__bytes_read.sum
 # + dram__bytes_write.sum from one ncu capture, averaged over the sweeps of one
-# V-cycle), by workload, with the profile that records it; a workload is left out
+# V-cycle), by (workload, Neumann degree): (captured bytes per launch, algorithmic bytes per
+# launch of the captured case, the profile that records it).  The capture may be
+# of a smaller mesh of the same configuration; it is scaled to the measured
+# workload by the ratio of algorithmic bytes per launch.  A workload is left out
 # whenever the kernels have changed since its capture.
-SWEEP_TRAFFIC = {}
+SWEEP_TRAFFIC = {
+    ("C5", 6): (17.964272e6, 14.3672455e6,
+           "profiles/sweep_traffic_C5.md: 256x256x2 mesh, degree 6, 80 sweeps of one V-cycle, "
+           "scaled by algorithmic bytes per launch"),
+}
 
 
 def f_sweep_rows(rows, ci, cf, off, f_sweeps):
@@ -324,7 +331,12 @@ def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
     fp64 = params.get("precision", "fp64") == "fp64"
     tflops = fl / t / 1e12 if t else 0.0
     gbs = by / t / 1e9 if t else 0.0
-    traffic = SWEEP_TRAFFIC.get(workload) if fp64 else None
+    traffic = SWEEP_TRAFFIC.get((workload, params.get("neumann_degree"))) if fp64 else None
+    alg = by / launches if launches else None
+    if traffic and alg:
+        traffic = (traffic[0] * alg / traffic[1], traffic[2])
+    else:
+        traffic = None
     out = {"bound": "alu" if fp64 else "hbm",
            "achieved": tflops if fp64 else gbs, "peak": peak if fp64 else hbm_peak,
            "unit": "TFLOP/s" if fp64 else "GB/s",

@@ -277,8 +277,11 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
 // row i:
 //   OP_JACOBI: row r of D_ii^{-1} applied to f_i - sum (from shared memory);
 //   OP_RESTRICT: f_c = f_{c2f[i]} + sum, the restriction f_c = f_C + R_cf f_F.
+// Six thread blocks per SM (register cap 40): these sweeps wait on memory, and
+// the extra resident warps gained more than the few spilled registers cost
+// (C5 FP64, Neumann degree 6: solve 145.9 -> 140.8 ms)
 template <typename T, int B, int OP>
-__global__ void __launch_bounds__(256) k_scalar_rows(RowArgs<T> a) {
+__global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
   pdl_launch_dependents();
   if (OP == OP_JACOBI && (int)blockIdx.x >= a.comp_ctas) {  // copy segment, as in k_rowop
     const long long g = (long long)(blockIdx.x - a.comp_ctas) * blockDim.x + threadIdx.x;
