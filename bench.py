@@ -183,11 +183,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # of a smaller mesh of the same configuration; it is scaled to the measured
 # workload by the ratio of algorithmic bytes per launch.  A workload is left out
 # whenever the kernels have changed since its capture.
-SWEEP_TRAFFIC = {
-    ("C5", 6): (17.964272e6, 14.3672455e6,
-           "profiles/sweep_traffic_C5.md: 256x256x2 mesh, degree 6, 80 sweeps of one V-cycle, "
-           "scaled by algorithmic bytes per launch"),
-}
+SWEEP_TRAFFIC = {}
 
 
 def f_sweep_rows(rows, ci, cf, off, f_sweeps):
@@ -205,7 +201,11 @@ def f_sweep_rows(rows, ci, cf, off, f_sweeps):
     return masks
 
 
-def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1):
+# block sizes with the packed scalar-row form of the coarse FP64 sweeps
+SROW_SIZES = (3, 6, 10, 15, 21, 28)
+
+
+def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False):
     """Algorithmic work of every block-Jacobi sweep of a cycle from a zero
     iterate, {(level, k): (flops, bytes)} for sweep k (F sweeps first).
 
@@ -222,7 +222,11 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1):
 
     Level 0 with column-compressed coupling blocks (W of b columns) sweeps with
     the couplings scaled in advance, x_i = g_i - sum_j (D_ii^{-1} A_ij) x_j with
-    g = D^{-1} f: b W FMAs per coupling block and no D^{-1} apply."""
+    g = D^{-1} f: b W FMAs per coupling block and no D^{-1} apply.
+
+    With split (levels >= 1 in the FP64 scalar-row form), the first F sweep
+    also writes h = f - A_FC x_C for its rows, and the later F sweeps, during
+    which x_C does not change, read h and sum only the F-column couplings."""
     work = {}
     for l in range(nlev):
         lev = S.level(l)
@@ -251,6 +255,9 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1):
                 else:
                     copy = fm[f_sweeps - 1] if short else (cf == 0)
             sel = upd[rows] & off
+            fpart = split and l >= 1 and short and 1 <= k < f_sweeps
+            if fpart:  # later F sweeps: the F-column couplings only
+                sel = sel & (cf[ci] == 0)
             nrow, ncopy = int(upd.sum()), int(copy.sum())
             nblk = int(sel.sum())
             xcols = len(np.unique(ci[sel]))
@@ -262,6 +269,8 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1):
                 flops = 2.0 * (nnz + nrow * b * b)
                 byts = 8.0 * nnz + 4.0 * nblk + 8.0 * nrow * b * (b + 1)
             byts += 8.0 * b * xcols + 8.0 * b * (nrow + ncopy) * dual + 8.0 * b * ncopy
+            if split and l >= 1 and short and k == 0:  # h written
+                byts += 8.0 * b * nrow
             if nrow or ncopy:
                 work[(l, k)] = (flops, byts)
     return work
@@ -301,7 +310,9 @@ def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
     its level sizes).  FP64 sweeps are bound by the FP64 pipe (fp64_peak: the
     live FMA-throughput probe, TFLOP/s, and its source); FP32 sweeps by HBM."""
     S = nair.NairSolver(rp, ci, v, **params)
-    work = sweep_work(S, S.num_levels(), S.b, S.f_sweeps, max(S.params.c_sweeps, 0))
+    fp64 = params.get("precision", "fp64") == "fp64"
+    work = sweep_work(S, S.num_levels(), S.b, S.f_sweeps, max(S.params.c_sweeps, 0),
+                      split=fp64 and S.b in SROW_SIZES)
     S.close()
     peak, peak_src = fp64_peak
     fl = by = t = 0.0
@@ -328,7 +339,6 @@ def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
             by_level.append({"level": l, "sweeps": ln, "us_per_sweep": round(1e6 * lt / ln, 2),
                              "tflops": round(lf / lt / 1e12, 4), "frac_fp64": round(lf / lt / 1e12 / peak, 3),
                              "gbs": round(lb / lt / 1e9, 1), "frac_hbm": round(lb / lt / 1e9 / hbm_peak, 3)})
-    fp64 = params.get("precision", "fp64") == "fp64"
     tflops = fl / t / 1e12 if t else 0.0
     gbs = by / t / 1e9 if t else 0.0
     traffic = SWEEP_TRAFFIC.get((workload, params.get("neumann_degree"))) if fp64 else None

@@ -215,7 +215,8 @@ void build_transposed(Hier<T> &H, int f_sweeps, cudaStream_t s, Mem &mem) {
     const Level<T> &L = H.lev[l];
     TLevel<T> &TL = H.tlev[l];
     if (L.coarsest) continue;
-    build_sweep_rows_level<T>(L.E, L.nF, L.nC, b, TL.At, TL.fsweep, TL.nfl, TL.fl, TL.fl_n, TL.csweep, TL.sr, s, mem);
+    build_sweep_rows_level<T>(L.E, L.nF, L.nC, b, TL.At, nullptr, TL.fsweep, TL.nfl, TL.fl, TL.fl_n, TL.csweep, TL.sr,
+                              s, mem);
   }
   NAIR_CK(cudaStreamSynchronize(s));
 }

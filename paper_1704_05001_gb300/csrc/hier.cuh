@@ -28,6 +28,7 @@ static constexpr int kMaxFLists = 8;
 struct SweepRows {
   int *srp = nullptr, *sp = nullptr, *sj = nullptr;
   void *sv = nullptr;
+  int *srs = nullptr;  // per scalar row of an F row: where its F-column entries start (C columns first)
   unsigned char *perm_f[kMaxFLists] = {}, *perm_c = nullptr;
   int perm_f_tpc[kMaxFLists] = {}, perm_c_tpc = 0;
 };
@@ -68,8 +69,9 @@ struct Level {
   int n = 0;
   T *ainv = nullptr;
   // cycle vectors: right-hand side, iterate, second sweep buffer, residual;
-  // level 0 with scaled couplings also g = D^{-1} f
-  T *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr, *g = nullptr;
+  // level 0 with scaled couplings also g = D^{-1} f; levels >= 1 in the
+  // scalar-row form also h = f_F - A_FC x_C for the F sweeps of a cycle
+  T *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr, *g = nullptr, *h = nullptr;
 };
 
 // Level-0 off-diagonal blocks restricted to their nonzero columns.  An upwind
@@ -220,8 +222,9 @@ void build_restrict_rows(int nC, int b, const DBsr<T> &R, SweepRows &rr, cudaStr
 // the scalar-row form of one level's matrix A for its sweep lists (FP64 and
 // the DG block sizes; otherwise sr stays empty and the sweeps use k_rowop)
 template <typename T>
-void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, int *fsweep, int nfl,
-                            int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s, Mem &mem);
+void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, const signed char *cf, int *fsweep,
+                            int nfl, int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s,
+                            Mem &mem);
 
 // position of the diagonal block of every row
 void diag_positions(int E, const int *rp, const int *ci, int *out, cudaStream_t s);

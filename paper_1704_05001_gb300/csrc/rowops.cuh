@@ -53,6 +53,14 @@ struct RowArgs {
   const int *srp, *sj;
   const T *sv;
   const unsigned char *perm;
+  // F sweeps with the C part of the F rows summed once (k_scalar_rows, OP_JACOBI):
+  // the entries of an F row's scalar row list its C columns first, up to srs,
+  // then its F columns.  fmode 1 (the first F sweep of a cycle): h = f - the C
+  // part, stored, then the F part subtracted; fmode 2 (later F sweeps, x_C
+  // unchanged): h read back and only the F part summed; fmode 0: every entry
+  const int *srs;
+  T *h;
+  int fmode;
 };
 
 // B consecutive values from p into registers, as 16-byte loads where the
@@ -280,7 +288,7 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
 // Six thread blocks per SM (register cap 40): these sweeps wait on memory, and
 // the extra resident warps gained more than the few spilled registers cost
 // (C5 FP64, Neumann degree 6: solve 145.9 -> 140.8 ms)
-template <typename T, int B, int OP>
+template <typename T, int B, int OP, int FM = 0>
 __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
   pdl_launch_dependents();
   if (OP == OP_JACOBI && (int)blockIdx.x >= a.comp_ctas) {  // copy segment, as in k_rowop
@@ -314,7 +322,16 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
   const int enc = act ? (int)a.perm[(size_t)base * B + slot] : 0;
   const int team = enc / B, r = enc - team * B;
   const int i = act ? (a.list ? a.list[base + team] : base + team) : 0;
-  const int e0 = act ? a.srp[(size_t)i * B + r] + g : 0, e1 = act ? a.srp[(size_t)i * B + r + 1] : 0;
+  // entry ranges: A = every entry (fmode 0), the C part (1) or the F part (2);
+  // B = the F part in fmode 1, else empty
+  int s0 = 0, sm = 0, s1 = 0;
+  if (act) {
+    const size_t q = (size_t)i * B + r;
+    s0 = a.srp[q];
+    s1 = a.srp[q + 1];
+    sm = FM ? a.srs[q] : s0;
+  }
+  const int e0 = (FM == 2 ? sm : s0) + g, e1 = FM == 1 ? sm : s1;
   // natural layout: the row and component this thread finishes.  For the
   // sweep with B <= 10 the thread block's D^{-1} blocks are staged in shared
   // memory before the dependency wait; larger blocks are read after the loop
@@ -370,6 +387,41 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
 #pragma unroll
     for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
   }
+  T accB = 0;
+  if constexpr (OP == OP_JACOBI && FM == 1) {  // the F part of the first F sweep
+#pragma unroll 2
+    for (int e = sm + g; e < s1; e += G) {
+      int j = a.sj[e];
+      if (a.ipc) {
+        j = a.ipc[j];
+        if (j < 0) continue;
+      }
+      T va[B], vx[B];
+      if constexpr (B >= 10) {
+        load_row<T, B>(a.sv + (size_t)e * B, va);
+        load_row<T, B>(a.x + (size_t)j * B, vx);
+      } else {
+        load_row_scalar<T, B>(a.sv + (size_t)e * B, va);
+        load_row_scalar<T, B>(a.x + (size_t)j * B, vx);
+      }
+#pragma unroll
+      for (int c = 0; c < B; ++c) accB = fma(va[c], vx[c], accB);
+    }
+  }
+  // f_i - the row's sum: with the C part kept in h (stored in fmode 1, read
+  // back in fmode 2)
+  auto residual = [&](int row, int comp, T sumA, T sumB) -> T {
+    const size_t q = (size_t)row * B + comp;
+    if constexpr (FM == 1) {
+      const T hv = a.f[q] - sumA;
+      a.h[q] = hv;
+      return hv - sumB;
+    } else if constexpr (FM == 2) {
+      return a.h[q] - sumA;
+    } else {
+      return a.f[q] - sumA;
+    }
+  };
   if (G > 1) {  // pairwise tree over the G partial sums of each scalar row
     if (act) red[enc * G + g] = acc;
     __syncthreads();
@@ -377,14 +429,25 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
       if (act && g < h) red[enc * G + g] += red[enc * G + g + h];
       __syncthreads();
     }
-    if (OP == OP_RESTRICT) {
+    T sumB = 0;
+    if (OP == OP_JACOBI && FM == 1) {  // the same tree for the F part
+      const T sumA = (t < nact * B) ? red[t * G] : (T)0;
+      __syncthreads();
+      if (act) red[enc * G + g] = accB;
+      __syncthreads();
+      for (int h = G / 2; h > 0; h >>= 1) {
+        if (act && g < h) red[enc * G + g] += red[enc * G + g + h];
+        __syncthreads();
+      }
+      if (t < nact * B) sres[t] = residual(i2, r2, sumA, red[t * G]);
+    } else if (OP == OP_RESTRICT) {
       if (act2) a.out[(size_t)i2 * B + r2] = a.f[(size_t)own * B + r2] + red[t * G];
     } else if (t < nact * B) {
-      sres[t] = a.f[(size_t)i2 * B + r2] - red[t * G];
+      sres[t] = residual(i2, r2, red[t * G], sumB);
     }
   } else if (act) {
     if (OP == OP_RESTRICT) a.out[(size_t)i * B + r] = a.f[(size_t)a.c2f[i] * B + r] + acc;
-    else sres[enc] = a.f[(size_t)i * B + r] - acc;
+    else sres[enc] = residual(i, r, acc, accB);
   }
   if constexpr (OP == OP_JACOBI) {
     __syncthreads();

@@ -1552,25 +1552,34 @@ static void build_fsweep_lists(Hier<T> &H, const Params &P, cudaStream_t s, Mem 
 // ---------------------------------------------------------------------------
 // FILL = false: number of blocks of row i (the off-diagonal ones when
 // skip_diag is set) whose row r has a nonzero; FILL = true: their block
-// indices, ascending
+// indices, ascending.  With cf, an F row lists its blocks in C columns first
+// and then those in F columns (each part ascending), and srs receives the
+// position where the F part starts (the row's start for C rows)
 template <typename T, bool FILL>
 __global__ void k_srow_entries(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
                                const T *__restrict__ v, const int *__restrict__ srp, int *__restrict__ cnt,
-                               int *__restrict__ sp, int skip_diag) {
+                               int *__restrict__ sp, int skip_diag, const signed char *__restrict__ cf,
+                               int *__restrict__ srs) {
   pdl_wait();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)E * b) return;
   const int i = (int)(g / b), r = (int)(g - (long long)i * b);
+  const bool split = cf && cf[i] == 0;
   int w = FILL ? srp[g] : 0;
-  for (int p = rp[i]; p < rp[i + 1]; ++p) {
-    if (skip_diag && ci[p] == i) continue;
-    const T *row = v + ((size_t)p * b + r) * b;
-    bool nz = false;
-    for (int c = 0; c < b; ++c) nz |= row[c] != (T)0;
-    if (nz) {
-      if (FILL) sp[w] = p;
-      ++w;
+  if (FILL && srs) srs[g] = w;
+  for (int pass = 0; pass < (split ? 2 : 1); ++pass) {
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      if (skip_diag && ci[p] == i) continue;
+      if (split && (cf[ci[p]] == 1) != (pass == 0)) continue;  // pass 0: C columns, pass 1: F columns
+      const T *row = v + ((size_t)p * b + r) * b;
+      bool nz = false;
+      for (int c = 0; c < b; ++c) nz |= row[c] != (T)0;
+      if (nz) {
+        if (FILL) sp[w] = p;
+        ++w;
+      }
     }
+    if (FILL && srs && split && pass == 0) srs[g] = w;
   }
   if (!FILL) cnt[g] = w;
 }
@@ -1594,10 +1603,11 @@ __global__ void k_srow_pack(long long n, int b, const int *__restrict__ srp, con
 }
 
 // per thread block of a row list (tpc rows, tpc b scalar rows; rows base ..
-// when list is null): the scalar rows sorted by entry count, ties in natural
-// order; perm[c tpc b + rank] = the natural slot team b + r
+// when list is null): the scalar rows sorted by entry count (counted from srs
+// when given: the F part a later F sweep sums), ties in natural order;
+// perm[c tpc b + rank] = the natural slot team b + r
 __global__ void k_srow_perm(int n, int b, int tpc, const int *__restrict__ list, const int *__restrict__ srp,
-                            unsigned char *__restrict__ perm) {
+                            const int *__restrict__ srs, unsigned char *__restrict__ perm) {
   pdl_wait();
   __shared__ int key[256];
   const int base = blockIdx.x * tpc, nact = min(tpc, n - base), t = threadIdx.x, m = nact * b;
@@ -1605,7 +1615,7 @@ __global__ void k_srow_perm(int n, int b, int tpc, const int *__restrict__ list,
   if (t < m) {
     const int team = t / b, r = t - team * b;
     const size_t q = (size_t)(list ? list[base + team] : base + team) * b + r;
-    k = srp[q + 1] - srp[q];
+    k = srp[q + 1] - (srs ? srs[q] : srp[q]);
     key[t] = k;
   }
   __syncthreads();
@@ -1625,14 +1635,14 @@ static constexpr int kSweepRowsMaxG = 8;
 
 template <typename T>
 static unsigned char *srow_perm(int n, int b, double avg, const int *list, const int *srp, cudaStream_t s,
-                                Mem &mem, int *tpc_out) {
+                                Mem &mem, int *tpc_out, const int *srs = nullptr) {
   const int G = rowop_groups(n, b, avg);
   if (G > kSweepRowsMaxG) return nullptr;
   const int tpc = sweep_rows_tpc(b, G);
   *tpc_out = tpc;
   unsigned char *perm = mem.alloc<unsigned char>((size_t)std::max(n, 1) * b);
   if (n > 0) {
-    launch_pdl(k_srow_perm, dim3(cdiv(n, tpc)), dim3(tpc * b), 0, s, n, b, tpc, list, srp, perm);
+    launch_pdl(k_srow_perm, dim3(cdiv(n, tpc)), dim3(tpc * b), 0, s, n, b, tpc, list, srp, srs, perm);
     NAIR_LAUNCH_CHECK();
   }
   return perm;
@@ -1641,19 +1651,23 @@ static unsigned char *srow_perm(int n, int b, double avg, const int *list, const
 // entry lists and packed entries of the scalar-row form of the E x b scalar
 // rows of M (its off-diagonal blocks when skip_diag is set)
 template <typename T>
-static void srow_pack(int E, int b, const DBsr<T> &M, bool skip_diag, SweepRows &sr, cudaStream_t s, Mem &mem) {
+static void srow_pack(int E, int b, const DBsr<T> &M, bool skip_diag, const signed char *cf, SweepRows &sr,
+                      cudaStream_t s, Mem &mem) {
   const long long n = (long long)E * b;
   Mem tmp;
   tmp.s = s;
   int *cnt = tmp.alloc<int>(n + 1);
   launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)M.rp,
-             (const int *)M.ci, (const T *)M.v, (const int *)nullptr, cnt, (int *)nullptr, (int)skip_diag);
+             (const int *)M.ci, (const T *)M.v, (const int *)nullptr, cnt, (int *)nullptr, (int)skip_diag, cf,
+             (int *)nullptr);
   NAIR_LAUNCH_CHECK();
   sr.srp = mem.alloc<int>(n + 1);
   const int ne = exclusive_scan(cnt, sr.srp, (int)n, s, tmp, true);
   sr.sp = mem.alloc<int>(std::max(ne, 1));
+  if (cf) sr.srs = mem.alloc<int>(n);
   launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)M.rp,
-             (const int *)M.ci, (const T *)M.v, (const int *)sr.srp, (int *)nullptr, sr.sp, (int)skip_diag);
+             (const int *)M.ci, (const T *)M.v, (const int *)sr.srp, (int *)nullptr, sr.sp, (int)skip_diag, cf,
+             sr.srs);
   NAIR_LAUNCH_CHECK();
   sr.sj = mem.alloc<int>(std::max(ne, 1));
   T *sv = mem.alloc<T>((size_t)std::max(ne, 1) * b);
@@ -1671,15 +1685,16 @@ void build_restrict_rows(int nC, int b, const DBsr<T> &R, SweepRows &rr, cudaStr
   if (n + 1 >= INT_MAX || ub >= INT_MAX) return;
   const double avg = (double)R.nnzb / nC;
   if (rowop_groups(nC, b, avg) > kSweepRowsMaxG) return;
-  srow_pack<T>(nC, b, R, false, rr, s, mem);
+  srow_pack<T>(nC, b, R, false, nullptr, rr, s, mem);
   rr.perm_c = srow_perm<T>(nC, b, avg, nullptr, rr.srp, s, mem, &rr.perm_c_tpc);
 }
 template void build_restrict_rows<double>(int, int, const DBsr<double> &, SweepRows &, cudaStream_t, Mem &);
 template void build_restrict_rows<float>(int, int, const DBsr<float> &, SweepRows &, cudaStream_t, Mem &);
 
 template <typename T>
-void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, int *fsweep, int nfl,
-                            int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s, Mem &mem) {
+void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, const signed char *cf, int *fsweep,
+                            int nfl, int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s,
+                            Mem &mem) {
   // FP64 only: it saves FP64 issue slots at the price of a shuffled access
   // pattern and a longer setup; the FP32 sweeps are not bound by arithmetic
   // and did not gain (mixed-precision setup + solve C3 40.0 -> 39.7 ms, C5
@@ -1689,15 +1704,17 @@ void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, int 
   if (n + 1 >= INT_MAX || ub >= INT_MAX) return;
   const double avg = (double)A.nnzb / E;
   if (rowop_groups(nF, b, avg) > kSweepRowsMaxG && rowop_groups(nC, b, avg) > kSweepRowsMaxG) return;
-  srow_pack<T>(E, b, A, true, sr, s, mem);
+  srow_pack<T>(E, b, A, true, cf, sr, s, mem);
   sr.perm_f[0] = srow_perm<T>(nF, b, avg, fsweep, sr.srp, s, mem, &sr.perm_f_tpc[0]);
-  for (int k = 1; k < nfl; ++k) sr.perm_f[k] = srow_perm<T>(fl_n[k], b, avg, fl[k], sr.srp, s, mem, &sr.perm_f_tpc[k]);
+  // the later F sweeps sum only the F part of their rows: sorted by its length
+  for (int k = 1; k < nfl; ++k)
+    sr.perm_f[k] = srow_perm<T>(fl_n[k], b, avg, fl[k], sr.srp, s, mem, &sr.perm_f_tpc[k], sr.srs);
   sr.perm_c = srow_perm<T>(nC, b, avg, csweep, sr.srp, s, mem, &sr.perm_c_tpc);
 }
-template void build_sweep_rows_level<double>(int, int, int, int, const DBsr<double> &, int *, int, int *const *,
-                                             const int *, int *, SweepRows &, cudaStream_t, Mem &);
-template void build_sweep_rows_level<float>(int, int, int, int, const DBsr<float> &, int *, int, int *const *,
-                                            const int *, int *, SweepRows &, cudaStream_t, Mem &);
+template void build_sweep_rows_level<double>(int, int, int, int, const DBsr<double> &, const signed char *, int *,
+                                             int, int *const *, const int *, int *, SweepRows &, cudaStream_t, Mem &);
+template void build_sweep_rows_level<float>(int, int, int, int, const DBsr<float> &, const signed char *, int *,
+                                            int, int *const *, const int *, int *, SweepRows &, cudaStream_t, Mem &);
 
 // the scalar-row lists and permutations of every level >= 1 that sweeps
 template <typename T>
@@ -1707,7 +1724,10 @@ static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
     if (L.coarsest) continue;
     build_restrict_rows<T>(L.nC, H.b, L.R, L.rr, s, mem);
     if (l == 0) continue;
-    build_sweep_rows_level<T>(L.E, L.nF, L.nC, H.b, L.A, L.fsweep, L.nfl, L.fl, L.fl_n, L.csweep, L.sr, s, mem);
+    build_sweep_rows_level<T>(L.E, L.nF, L.nC, H.b, L.A, L.cf, L.fsweep, L.nfl, L.fl, L.fl_n, L.csweep, L.sr, s,
+                              mem);
+    // the C part of the F rows, summed once per cycle by the first F sweep
+    if (L.sr.srs && L.nfl >= 2) L.h = mem.alloc<T>((size_t)L.E * H.b);
   }
 }
 

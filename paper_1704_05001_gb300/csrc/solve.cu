@@ -114,6 +114,19 @@ void launch_rowop(RowArgs<T> a, double avg, cudaStream_t s) {
   }
   NAIR_LAUNCH_CHECK();
 }
+// the scalar-row kernel for block size b and F-sweep mode FM
+template <typename T, int OP, int FM>
+static void launch_scalar_rows_b(const RowArgs<T> &a, int b, dim3 gr, dim3 bl, cudaStream_t s) {
+  switch (b) {
+    case 3: launch_pdl(k_scalar_rows<T, 3, OP, FM>, gr, bl, 0, s, a); break;
+    case 6: launch_pdl(k_scalar_rows<T, 6, OP, FM>, gr, bl, 0, s, a); break;
+    case 10: launch_pdl(k_scalar_rows<T, 10, OP, FM>, gr, bl, 0, s, a); break;
+    case 15: launch_pdl(k_scalar_rows<T, 15, OP, FM>, gr, bl, 0, s, a); break;
+    case 21: launch_pdl(k_scalar_rows<T, 21, OP, FM>, gr, bl, 0, s, a); break;
+    default: launch_pdl(k_scalar_rows<T, 28, OP, FM>, gr, bl, 0, s, a); break;
+  }
+}
+
 template <typename T, int OP>
 bool launch_scalar_rows(RowArgs<T> a, int G, cudaStream_t s) {
   const int b = a.b;
@@ -124,16 +137,13 @@ bool launch_scalar_rows(RowArgs<T> a, int G, cudaStream_t s) {
   int blocks = a.comp_ctas;
   if (OP == OP_JACOBI && a.ncopy > 0) blocks += cdiv((long long)a.ncopy * b, threads);
   const dim3 gr(blocks), bl(threads);
-  switch (b) {
-    case 3: if (blocks) launch_pdl(k_scalar_rows<T, 3, OP>, gr, bl, 0, s, a); break;
-    case 6: if (blocks) launch_pdl(k_scalar_rows<T, 6, OP>, gr, bl, 0, s, a); break;
-    case 10: if (blocks) launch_pdl(k_scalar_rows<T, 10, OP>, gr, bl, 0, s, a); break;
-    case 15: if (blocks) launch_pdl(k_scalar_rows<T, 15, OP>, gr, bl, 0, s, a); break;
-    case 21: if (blocks) launch_pdl(k_scalar_rows<T, 21, OP>, gr, bl, 0, s, a); break;
-    case 28: if (blocks) launch_pdl(k_scalar_rows<T, 28, OP>, gr, bl, 0, s, a); break;
-    default: return false;
+  if (b != 3 && b != 6 && b != 10 && b != 15 && b != 21 && b != 28) return false;
+  if (blocks) {
+    if (OP == OP_JACOBI && a.fmode == 1) launch_scalar_rows_b<T, OP_JACOBI, 1>(a, b, gr, bl, s);
+    else if (OP == OP_JACOBI && a.fmode == 2) launch_scalar_rows_b<T, OP_JACOBI, 2>(a, b, gr, bl, s);
+    else launch_scalar_rows_b<T, OP, 0>(a, b, gr, bl, s);
+    NAIR_LAUNCH_CHECK();
   }
-  NAIR_LAUNCH_CHECK();
   return true;
 }
 template bool launch_scalar_rows<double, OP_JACOBI>(RowArgs<double>, int, cudaStream_t);
@@ -313,6 +323,10 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
   // it reads one of them, so sweep 1 copies the F rows outside its list (fq[1])
   const int SF = P.f_sweeps;
   const bool short_f = SF >= 2 && L.nfl == SF;
+  // the first F sweep (scalar-row form) keeps f - A_FC x_C in L.h for the
+  // later F sweeps, which then sum only the F-column part (x_C is fixed while
+  // the F sweeps run)
+  bool have_h = false;
   for (int k = 0; k < S; ++k) {
     const int cls = k < SF ? 0 : 1, oth = 1 - cls, ob = k % 2;
     RowArgs<T> a = row_args(L.A, b);
@@ -372,7 +386,13 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
         a.sj = L.sr.sj;
         a.sv = static_cast<const T *>(L.sr.sv);
         a.perm = perm;
+        if (cls == 0 && L.h && L.sr.srs && (k == 0 || have_h)) {
+          a.srs = L.sr.srs;
+          a.h = L.h;
+          a.fmode = k == 0 ? 1 : 2;
+        }
         done = launch_scalar_rows<T, OP_JACOBI>(a, G, s);
+        if (done && k == 0 && a.fmode == 1) have_h = true;
       }
       if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
     }

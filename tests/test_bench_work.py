@@ -34,10 +34,14 @@ def _level_arrays(lev):
     return rows, lev["col"], lev["cf"], lev["col"] != rows
 
 
-def test_sweep_work_counts(hier):
+@pytest.mark.parametrize("split", [False, True])
+def test_sweep_work_counts(hier, split):
+    """With split, the F sweeps after the first on levels >= 1 count only their
+    F-column couplings (x_C does not change while they run), and the first F
+    sweep there also writes h = f - A_FC x_C."""
     P, H = hier
     b, SF = P["b"], 3
-    work = bench.sweep_work(H, H.nlev, b, SF, 1)
+    work = bench.sweep_work(H, H.nlev, b, SF, 1, split=split)
     assert H.nlev >= 3
     for l in range(H.nlev):
         lev = H.level(l)
@@ -48,6 +52,8 @@ def test_sweep_work_counts(hier):
         masks = bench.f_sweep_rows(rows, ci, cf, off, SF)
         for k, upd in enumerate(masks + [cf == 1]):
             sel = upd[rows] & off
+            if split and l >= 1 and 1 <= k < SF:
+                sel = sel & (cf[ci] == 0)
             nrow = int(upd.sum())
             if (l, k) not in work:  # nothing to update or copy
                 assert nrow == 0
