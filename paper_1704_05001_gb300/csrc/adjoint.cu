@@ -215,8 +215,11 @@ void build_transposed(Hier<T> &H, int f_sweeps, cudaStream_t s, Mem &mem) {
     const Level<T> &L = H.lev[l];
     TLevel<T> &TL = H.tlev[l];
     if (L.coarsest) continue;
-    build_sweep_rows_level<T>(L.E, L.nF, L.nC, b, TL.At, nullptr, TL.fsweep, TL.nfl, TL.fl, TL.fl_n, TL.csweep, TL.sr,
+    build_sweep_rows_level<T>(L.E, L.nF, L.nC, b, TL.At, L.cf, TL.fsweep, TL.nfl, TL.fl, TL.fl_n, TL.csweep, TL.sr,
                               s, mem);
+    // the F sweeps follow the C sweeps, so x_C is fixed while they run: the
+    // first keeps f - (A^T)_FC x_C for the others, as in the forward cycle
+    if (TL.sr.srs && TL.nfl >= 2) TL.h = mem.alloc<T>((size_t)L.E * b);
   }
   NAIR_CK(cudaStreamSynchronize(s));
 }

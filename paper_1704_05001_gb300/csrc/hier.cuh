@@ -137,6 +137,7 @@ struct TLevel {
   int *cself = nullptr;        // element -> its coarse index (C) or -1 (F)
   int *pt_rp = nullptr, *pt_ci = nullptr;  // P^T: coarse J -> F elements with ip = J, ascending
   T *r = nullptr;              // residual after the pre-relaxation
+  T *h = nullptr;              // f - (A^T)_FC x_C for the F sweeps (scalar-row levels)
   T *ainvT = nullptr;          // coarsest level: (A_c^{-1})^T
 };
 

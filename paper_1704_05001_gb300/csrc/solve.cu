@@ -514,6 +514,7 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
     // buffer, which holds every other F row current: the values of sweep m - 2,
     // or for m = 1 none, fq[1] then being all F rows outside fl[1]
     const bool tshort = P.f_sweeps >= 2 && TL.nfl == P.f_sweeps;
+    bool have_h = false;  // h = f - (A^T)_FC x_C formed by this cycle's first F sweep
     for (int k = 0; k < S; ++k) {
       const int cls = k < P.c_sweeps ? 1 : 0, oth = 1 - cls, ob = k % 2, m = k - P.c_sweeps;
       ProfScope ps(cls == 0 ? "jacobi_tF" : "jacobi_tC", s, l);
@@ -559,7 +560,15 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
           a.sj = TL.sr.sj;
           a.sv = static_cast<const T *>(TL.sr.sv);
           a.perm = perm;
+          // the first F sweep over all F rows forms h; later ones sum the F part
+          const bool full = a.nrows == L.nF;
+          if (cls == 0 && TL.h && TL.sr.srs && (have_h || full)) {
+            a.srs = TL.sr.srs;
+            a.h = TL.h;
+            a.fmode = have_h ? 2 : 1;
+          }
           done = launch_scalar_rows<T, OP_JACOBI>(a, G, s);
+          if (done && a.fmode == 1) have_h = true;
         }
         if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
       }
