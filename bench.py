@@ -183,7 +183,11 @@ FP64_NOMINAL_TFLOPS = 1.25
 # of a smaller mesh of the same configuration; it is scaled to the measured
 # workload by the ratio of algorithmic bytes per launch.  A workload is left out
 # whenever the kernels have changed since its capture.
-SWEEP_TRAFFIC = {}
+SWEEP_TRAFFIC = {
+    ("C5", 6): (16.595536e6, 11.72450465e6,
+                "profiles/sweep_traffic_C5.md: 256x256x2 mesh, degree 6, 80 sweeps of one V-cycle, "
+                "scaled by algorithmic bytes per launch"),
+}
 
 
 def f_sweep_rows(rows, ci, cf, off, f_sweeps):
@@ -355,7 +359,7 @@ def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
            "traffic": traffic[0] if traffic else None,
            "traffic_source": traffic[1] if traffic else "no capture of the current kernels on this workload",
            "algorithmic_bytes_per_launch": by / launches if launches else None,
-           "kernel": "block-Jacobi sweep: k_rowop, k_rowop_l0, k_sweep_rows (all levels)",
+           "kernel": "block-Jacobi sweep: k_rowop, k_rowop_l0, k_scalar_rows (all levels)",
            "launches_per_step": None, "launches_stamped": launches,
            "kernel_ms_stamped": 1e3 * t,
            "tflops_achieved": tflops, "fp64_peak_tflops": peak,

@@ -47,7 +47,7 @@ __global__ void k_scale_blocks(long long total, int b, const int *__restrict__ b
 // scalar row (i, r): its nonzeros over the blocks of row i in ascending column
 // order; FILL = false counts them, FILL = true writes them at srp[i b + r]
 template <bool FILL>
-__global__ void k_scalar_rows(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
+__global__ void k_expand_scalar(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
                               const double *__restrict__ S, const int *__restrict__ srp, int *__restrict__ cnt,
                               int *__restrict__ sci, double *__restrict__ sv) {
   pdl_wait();
@@ -89,7 +89,7 @@ void scalar_matrix(const DBsr<double> &A, int b, const double *Dinv, const int *
   launch_pdl(k_scale_blocks, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, brow, diag, Dinv, A.v, S);
   NAIR_LAUNCH_CHECK();
   int *cnt = tmp.alloc<int>(n + 1);
-  launch_pdl(k_scalar_rows<false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, A.rp, A.ci, S, nullptr, cnt, nullptr, nullptr);
+  launch_pdl(k_expand_scalar<false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, A.rp, A.ci, S, nullptr, cnt, nullptr, nullptr);
   NAIR_LAUNCH_CHECK();
   out.nrows = out.ncols = (int)n;
   out.rp = mem.alloc<int>(n + 1);
@@ -97,7 +97,7 @@ void scalar_matrix(const DBsr<double> &A, int b, const double *Dinv, const int *
   out.nnzb = nnz;
   out.ci = mem.alloc<int>(nnz);
   out.v = mem.alloc<double>(nnz);
-  launch_pdl(k_scalar_rows<true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, A.rp, A.ci, S, out.rp, nullptr, out.ci, out.v);
+  launch_pdl(k_expand_scalar<true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, A.rp, A.ci, S, out.rp, nullptr, out.ci, out.v);
   NAIR_LAUNCH_CHECK();
 }
 
