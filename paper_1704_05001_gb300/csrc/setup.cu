@@ -736,29 +736,53 @@ __global__ void k_spgemm_warp(SpgemmIdx X, int *__restrict__ cnt, int *__restric
 }
 
 // numeric phase over the recorded pairs: the start value, then one fma chain over
-// the pairs in order (left entry ascending) and t ascending.  Eight thread
-// blocks per SM (register cap 32): the chains wait on loads, and the extra
-// resident warps gained more than the spilled registers cost (C5 FP64 setup
-// with Neumann degree 6: 96.3 -> 92.9 ms)
-template <typename T>
-__global__ void __launch_bounds__(256, 8) k_spgemm_pairs(long long total, int b, const int *__restrict__ pbeg,
-                               const int2 *__restrict__ pairs, const int *__restrict__ iq,
-                               const T *__restrict__ lv, const T *__restrict__ rv,
-                               const T *__restrict__ iv, int negate, T *__restrict__ ov) {
+// the pairs in order (left entry ascending) and t ascending.  B = 0 takes the
+// block size b at run time, with eight thread blocks per SM (register cap 32):
+// the chains wait on loads, and the extra resident warps gained more than the
+// spilled registers cost (C5 FP64 setup with Neumann degree 6: 96.3 -> 92.9
+// ms).  For B > 0 the index arithmetic divides by constants and each pair's 2B
+// loads are issued before its fma chain, the next pair's indices one pair
+// ahead; six thread blocks per SM keep it free of spills (C5 FP64 setup 93.8
+// -> 93.1 ms, two boxes; 60 registers and four blocks per SM: 96.1 ms)
+template <typename T, int B>
+__global__ void __launch_bounds__(256, B ? 6 : 8) k_spgemm_pairs(long long total, int b_rt,
+                               const int *__restrict__ pbeg, const int2 *__restrict__ pairs,
+                               const int *__restrict__ iq, const T *__restrict__ lv,
+                               const T *__restrict__ rv, const T *__restrict__ iv, int negate,
+                               T *__restrict__ ov) {
   pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
+  const int b = B ? B : b_rt;
   const int bb = b * b;
   const long long blk = g / bb;
   const int rc = (int)(g - blk * bb), r = rc / b, c = rc - r * b;
   const int q0 = iq[blk];
   T acc = q0 >= 0 ? iv[(size_t)q0 * bb + rc] : (T)0;
+  int k = pbeg[blk];
   const int k1 = pbeg[blk + 1];
-  for (int k = pbeg[blk]; k < k1; ++k) {
-    const int2 pq = pairs[k];
-    const T *a = lv + (size_t)pq.x * bb + r * b;
-    const T *bv = rv + (size_t)pq.y * bb + c;
-    for (int t = 0; t < b; ++t) acc = fma_rn(a[t], bv[t * b], acc);
+  if constexpr (B > 0) {
+    int2 pq = k < k1 ? pairs[k] : make_int2(0, 0);
+    for (; k < k1; ++k) {
+      const T *a = lv + (size_t)pq.x * bb + r * B;
+      const T *bv = rv + (size_t)pq.y * bb + c;
+      T av[B], bw[B];
+#pragma unroll
+      for (int t = 0; t < B; ++t) {
+        av[t] = a[t];
+        bw[t] = bv[t * B];
+      }
+      if (k + 1 < k1) pq = pairs[k + 1];
+#pragma unroll
+      for (int t = 0; t < B; ++t) acc = fma_rn(av[t], bw[t], acc);
+    }
+  } else {
+    for (; k < k1; ++k) {
+      const int2 pq = pairs[k];
+      const T *a = lv + (size_t)pq.x * bb + r * b;
+      const T *bv = rv + (size_t)pq.y * bb + c;
+      for (int t = 0; t < b; ++t) acc = fma_rn(a[t], bv[t * b], acc);
+    }
   }
   ov[g] = negate ? -acc : acc;
 }
@@ -1338,7 +1362,10 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
     if (row_form && b == 3) launch_pdl(k_spgemm_rows<T, 3>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     else if (row_form && b == 6) launch_pdl(k_spgemm_rows<T, 6>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     else if (row_form) launch_pdl(k_spgemm_rows<T, 10>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
-    else launch_pdl(k_spgemm_pairs<T>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    else if (b == 10) launch_pdl(k_spgemm_pairs<T, 10>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    else if (b == 6) launch_pdl(k_spgemm_pairs<T, 6>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    else if (b == 3) launch_pdl(k_spgemm_pairs<T, 3>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    else launch_pdl(k_spgemm_pairs<T, 0>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     NAIR_LAUNCH_CHECK();
   }
   tmp.release(pairs);
