@@ -682,16 +682,26 @@ def main():
         h2d = sum(t2.numel() * t2.element_size() for t2 in hp.values())
         d2h = xh.numel() * xh.element_size()
 
-        def e2e_step():
+        h2d_ms = [0.0]
+
+        def e2e_step(timed=False):
+            if timed:
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
             drp = hp["row_ptr"].to(dev, non_blocking=True)
             dci = hp["col"].to(dev, non_blocking=True)
             dv = hp["vals"].to(dev, non_blocking=True)
             db = hp["rhs"].to(dev, non_blocking=True)
+            if timed:
+                c1.record(stream)
             s = nair.NairSolver(drp, dci, dv, **params)
             xx, _ = s.solve(db)
             xh.copy_(xx, non_blocking=True)
             s.close()
             torch.cuda.synchronize()
+            if timed:
+                h2d_ms[0] += c0.elapsed_time(c1)
 
         e2e_step()
         e2e_ms = 0.0
@@ -701,12 +711,15 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            e2e_step()
+            e2e_step(timed=True)
             e1.record(stream)
             torch.cuda.synchronize()
             e2e_ms += e0.elapsed_time(e1)
         e2e = {"value": world * P["n"] / (e2e_ms / args.steps * 1e-3) / 1e6, "unit": "MDOF/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               # the host-to-device copies alone (CUDA events around them, same steps)
+               "h2d_ms_per_step": h2d_ms[0] / args.steps,
+               "h2d_gbs": h2d / (h2d_ms[0] / args.steps * 1e-3) / 1e9 if h2d_ms[0] > 0 else None}
 
     variants = None
     if not args.no_extras:

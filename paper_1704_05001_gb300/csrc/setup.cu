@@ -743,13 +743,21 @@ __global__ void k_spgemm_warp(SpgemmIdx X, int *__restrict__ cnt, int *__restric
 // ms).  For B > 0 the index arithmetic divides by constants and each pair's 2B
 // loads are issued before its fma chain, the next pair's indices one pair
 // ahead; six thread blocks per SM keep it free of spills (C5 FP64 setup 93.8
-// -> 93.1 ms, two boxes; 60 registers and four blocks per SM: 96.1 ms)
+// -> 93.1 ms, two boxes; 60 registers and four blocks per SM: 96.1 ms).  With
+// masks, a pair takes only the inner indices t where column t of its left
+// block and row t of its right block hold a nonzero: the skipped terms are
+// exact zeros (finite operands), so each sum is unchanged but for the sign of
+// a zero.  The coupling blocks of the DG operator are nonzero only on the
+// shared face, and that structure persists down the hierarchy (C5, 32x32x2
+// mesh: 40 % of L's and A_cf's level-0 terms kept, 48-72 % of the Galerkin
+// product's on every level); C5 FP64 setup 93.0 -> 85.0 ms
 template <typename T, int B>
 __global__ void __launch_bounds__(256, B ? 6 : 8) k_spgemm_pairs(long long total, int b_rt,
                                const int *__restrict__ pbeg, const int2 *__restrict__ pairs,
                                const int *__restrict__ iq, const T *__restrict__ lv,
                                const T *__restrict__ rv, const T *__restrict__ iv, int negate,
-                               T *__restrict__ ov) {
+                               T *__restrict__ ov, const unsigned *__restrict__ lmask,
+                               const unsigned *__restrict__ rmask) {
   pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= total) return;
@@ -762,19 +770,31 @@ __global__ void __launch_bounds__(256, B ? 6 : 8) k_spgemm_pairs(long long total
   int k = pbeg[blk];
   const int k1 = pbeg[blk + 1];
   if constexpr (B > 0) {
+    constexpr unsigned kFull = (1u << B) - 1u;
     int2 pq = k < k1 ? pairs[k] : make_int2(0, 0);
     for (; k < k1; ++k) {
       const T *a = lv + (size_t)pq.x * bb + r * B;
       const T *bv = rv + (size_t)pq.y * bb + c;
-      T av[B], bw[B];
+      // inner indices t with a nonzero in column t of the left block and in
+      // row t of the right one; the others add exact zeros
+      const unsigned m = (lmask ? lmask[pq.x] : kFull) & (rmask ? rmask[pq.y] >> 16 : kFull) & kFull;
+      if (m == kFull) {
+        T av[B], bw[B];
 #pragma unroll
-      for (int t = 0; t < B; ++t) {
-        av[t] = a[t];
-        bw[t] = bv[t * B];
+        for (int t = 0; t < B; ++t) {
+          av[t] = a[t];
+          bw[t] = bv[t * B];
+        }
+        if (k + 1 < k1) pq = pairs[k + 1];
+#pragma unroll
+        for (int t = 0; t < B; ++t) acc = fma_rn(av[t], bw[t], acc);
+      } else {
+        if (k + 1 < k1) pq = pairs[k + 1];
+        for (unsigned mm = m; mm; mm &= mm - 1u) {
+          const int t = __ffs(mm) - 1;
+          acc = fma_rn(a[t], bv[t * B], acc);
+        }
       }
-      if (k + 1 < k1) pq = pairs[k + 1];
-#pragma unroll
-      for (int t = 0; t < B; ++t) acc = fma_rn(av[t], bw[t], acc);
     }
   } else {
     for (; k < k1; ++k) {
@@ -785,6 +805,37 @@ __global__ void __launch_bounds__(256, B ? 6 : 8) k_spgemm_pairs(long long total
     }
   }
   ov[g] = negate ? -acc : acc;
+}
+
+// nonzero pattern of each b x b block (b <= 16): bit c for a nonzero in
+// column c, bit 16 + r for one in row r.  Thread per block row; blocks from
+// *nblk on (when given) are skipped.  mask must be zero on entry.
+template <typename T>
+__global__ void k_block_masks(long long rows, int b, const T *__restrict__ v, const int *__restrict__ nblk,
+                              unsigned *__restrict__ mask) {
+  pdl_wait();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= rows) return;
+  const long long blk = g / b;
+  if (nblk && blk >= *nblk) return;
+  const int r = (int)(g - blk * b);
+  const T *row = v + (size_t)g * b;
+  unsigned cols = 0;
+  for (int c = 0; c < b; ++c)
+    if (row[c] != (T)0) cols |= 1u << c;
+  if (cols) atomicOr(&mask[blk], cols | (1u << (16 + r)));
+}
+
+// the masks of k_block_masks for up to cap blocks (null where the pair kernel
+// takes no masks: FP32, or b not 3, 6 or 10)
+template <typename T>
+static unsigned *block_masks(int b, int cap, const T *v, const int *nblk, cudaStream_t s, Mem &tmp) {
+  if (sizeof(T) != 8 || !(b == 3 || b == 6 || b == 10) || cap <= 0) return nullptr;
+  unsigned *m = tmp.alloc<unsigned>(cap);
+  NAIR_CK(cudaMemsetAsync(m, 0, sizeof(unsigned) * cap, s));
+  launch_pdl(k_block_masks<T>, dim3(std::max(1, cdiv((long long)cap * b, kThreads))), dim3(kThreads), 0, s, (long long)cap * b, b, v, nblk, m);
+  NAIR_LAUNCH_CHECK();
+  return m;
 }
 
 // The same products with one thread per output block row (DG blocks up to
@@ -1304,7 +1355,8 @@ static void spgemm_rowwise(int b, const SpgemmIdx &X, int left_nnz, const T *lv,
 
 template <typename T>
 static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T *rv, const T *iv,
-                   int negate, int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out) {
+                   int negate, int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out,
+                   const unsigned *lmask = nullptr, const unsigned *rmask = nullptr) {
   ProfScope ps("spgemm", s);
   const int nrows = X.nrows;
   int *cnt = tmp.alloc<int>(nrows + 1), *pcnt = tmp.alloc<int>(nrows + 1);
@@ -1362,10 +1414,11 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
     if (row_form && b == 3) launch_pdl(k_spgemm_rows<T, 3>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     else if (row_form && b == 6) launch_pdl(k_spgemm_rows<T, 6>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     else if (row_form) launch_pdl(k_spgemm_rows<T, 10>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
-    else if (b == 10) launch_pdl(k_spgemm_pairs<T, 10>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
-    else if (b == 6) launch_pdl(k_spgemm_pairs<T, 6>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
-    else if (b == 3) launch_pdl(k_spgemm_pairs<T, 3>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
-    else launch_pdl(k_spgemm_pairs<T, 0>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
+    else if (b == 10) launch_pdl(k_spgemm_pairs<T, 10>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
+    else if (b == 6) launch_pdl(k_spgemm_pairs<T, 6>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
+    else if (b == 3) launch_pdl(k_spgemm_pairs<T, 3>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
+    else launch_pdl(k_spgemm_pairs<T, 0>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v,
+                                (const unsigned *)nullptr, (const unsigned *)nullptr);
     NAIR_LAUNCH_CHECK();
   }
   tmp.release(pairs);
@@ -1898,14 +1951,18 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     NAIR_CK(cudaMemcpyAsync(Tk.v, Dg.v, sizeof(T) * nF * bb, cudaMemcpyDeviceToDevice, s));
   }
   const T tol2 = (T)(P.filter_tol * P.filter_tol);
+  // zero columns of the L blocks (the face columns of A's couplings): the
+  // products skip them
+  unsigned *lm_mask = block_masks<T>(b, lub, Lm.v, Lm.rp + nF, s, tmp);
   for (int t = 0; t < P.k; ++t) {
     SpgemmIdx X{nF, Lm.rp, Lm.ci, nullptr, Tk.rp, Tk.ci, Dg.rp, Dg.rp, nullptr};
     DBsr<T> Tn;
-    spgemm<T>(b, X, lub, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn);
+    spgemm<T>(b, X, lub, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn, lm_mask);
     if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn, true);
     release_bsr(mem, Tk);
     Tk = Tn;
   }
+  if (lm_mask) tmp.release(lm_mask);
   tmp.release(Dg.v);
   tmp.release(Dg.rp);
   ps_neu.end();
@@ -1922,7 +1979,9 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   }
   {
     SpgemmIdx X{nC, Acf.rp, Acf.ci, nullptr, Tk.rp, Tk.ci, nullptr, nullptr, nullptr};
-    spgemm<T>(b, X, aub, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R);
+    unsigned *acf_mask = block_masks<T>(b, aub, Acf.v, Acf.rp + nC, s, tmp);
+    spgemm<T>(b, X, aub, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R, acf_mask);
+    if (acf_mask) tmp.release(acf_mask);
   }
   L.R_ci_f = L.R.ci;
   L.R.ci = mem.alloc<int>(L.R.nnzb);
@@ -1965,7 +2024,11 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   Level<T> nx;
   {
     SpgemmIdx X{nC, L.R.rp, L.R.ci, nullptr, AP.rp, AP.ci, AP.rp, AP.ci, L.c2f};
-    spgemm<T>(b, X, L.R.nnzb, L.R.v, AP.v, AP.v, 0, nC, s, mem, tmp, nx.A);
+    unsigned *r_mask = block_masks<T>(b, L.R.nnzb, L.R.v, (const int *)nullptr, s, tmp);
+    unsigned *ap_mask = block_masks<T>(b, nnzb, AP.v, AP.rp + E, s, tmp);
+    spgemm<T>(b, X, L.R.nnzb, L.R.v, AP.v, AP.v, 0, nC, s, mem, tmp, nx.A, r_mask, ap_mask);
+    if (ap_mask) tmp.release(ap_mask);
+    if (r_mask) tmp.release(r_mask);
     if (P.filter_targets & 2) filter<T>(b, tol2, s, mem, tmp, nx.A);
   }
   nx.E = nC;
