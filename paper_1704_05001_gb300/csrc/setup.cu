@@ -788,12 +788,22 @@ __global__ void __launch_bounds__(256, B ? 6 : 8) k_spgemm_pairs(long long total
         if (k + 1 < k1) pq = pairs[k + 1];
 #pragma unroll
         for (int t = 0; t < B; ++t) acc = fma_rn(av[t], bw[t], acc);
-      } else {
+      } else if (m) {
         if (k + 1 < k1) pq = pairs[k + 1];
-        for (unsigned mm = m; mm; mm &= mm - 1u) {
-          const int t = __ffs(mm) - 1;
-          acc = fma_rn(a[t], bv[t * B], acc);
+        // the next term's operands are loaded while the current one is added
+        unsigned mm = m;
+        int t = __ffs(mm) - 1;
+        T an = a[t], bn = bv[t * B];
+        for (mm &= mm - 1u; mm; mm &= mm - 1u) {
+          const T ac = an, bc = bn;
+          t = __ffs(mm) - 1;
+          an = a[t];
+          bn = bv[t * B];
+          acc = fma_rn(ac, bc, acc);
         }
+        acc = fma_rn(an, bn, acc);
+      } else if (k + 1 < k1) {
+        pq = pairs[k + 1];
       }
     }
   } else {
@@ -805,6 +815,68 @@ __global__ void __launch_bounds__(256, B ? 6 : 8) k_spgemm_pairs(long long total
     }
   }
   ov[g] = negate ? -acc : acc;
+}
+
+// position of the (n + 1)-th set bit of m (n < popcount(m))
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+  for (int i = 0; i < n; ++i) m &= m - 1u;
+  return __ffs(m) - 1;
+}
+
+// Warp per output block, for products whose left blocks have zero rows (R_cf,
+// A_cf): the block's b x b sums stay in shared memory, and for each pair the
+// lanes take the outputs (r, c) with r a nonzero row of the left block and c
+// a nonzero column of the right block, ceil(nr nc / 32) at a time, each an
+// fma chain over the inner indices of the pair's mask.  Each output sees the
+// same nonzero terms in the same order as in k_spgemm_pairs (pairs in order,
+// t ascending); the terms left out are exact zeros.  lmask is required.  The
+// blocks of R_cf and A_cf keep about 60 % of their rows zero (the rows of
+// element DOFs off the shared faces), which the thread-per-output form can
+// skip only where a whole warp's rows are zero (about 12 % of the 4-row
+// windows); here a pair costs ceil(nr nc / 32) fma chains instead of about
+// three.  C5 FP64 setup 84.9 -> 77.0 ms (the Neumann products, whose L
+// blocks have full rows, stay with k_spgemm_pairs).
+template <typename T, int B>
+__global__ void __launch_bounds__(256) k_spgemm_wblk(int nblk, const int *__restrict__ pbeg,
+                                                     const int2 *__restrict__ pairs, const int *__restrict__ iq,
+                                                     const T *__restrict__ lv, const T *__restrict__ rv,
+                                                     const T *__restrict__ iv, int negate, T *__restrict__ ov,
+                                                     const unsigned *__restrict__ lmask,
+                                                     const unsigned *__restrict__ rmask) {
+  pdl_wait();
+  constexpr int bb = B * B;
+  constexpr unsigned kFull = (1u << B) - 1u;
+  __shared__ T sacc[8][bb];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int blk = blockIdx.x * 8 + wid;
+  if (blk >= nblk) return;  // the whole warp; no block-wide barrier follows
+  T *acc = sacc[wid];
+  const int q0 = iq[blk];
+  for (int rc = lane; rc < bb; rc += 32) acc[rc] = q0 >= 0 ? iv[(size_t)q0 * bb + rc] : (T)0;
+  __syncwarp();
+  const int k1 = pbeg[blk + 1];
+  for (int k = pbeg[blk]; k < k1; ++k) {
+    const int2 pq = pairs[k];
+    const unsigned ml = lmask[pq.x], mr = rmask ? rmask[pq.y] : (kFull | (kFull << 16));
+    const unsigned tm = ml & (mr >> 16) & kFull;
+    const unsigned rows = (ml >> 16) & kFull, cols = mr & kFull;
+    const int nc = __popc(cols), nw = __popc(rows) * nc;
+    if (tm) {
+      const T *a0 = lv + (size_t)pq.x * bb, *b0 = rv + (size_t)pq.y * bb;
+      for (int idx = lane; idx < nw; idx += 32) {
+        const int ri = idx / nc, ci = idx - ri * nc;
+        const int r = nth_set_bit(rows, ri), c = nth_set_bit(cols, ci);
+        T sum = acc[r * B + c];
+        for (unsigned mm = tm; mm; mm &= mm - 1u) {
+          const int t = __ffs(mm) - 1;
+          sum = fma_rn(a0[r * B + t], b0[t * B + c], sum);
+        }
+        acc[r * B + c] = sum;
+      }
+    }
+    __syncwarp();
+  }
+  for (int rc = lane; rc < bb; rc += 32) ov[(size_t)blk * bb + rc] = negate ? -acc[rc] : acc[rc];
 }
 
 // nonzero pattern of each b x b block (b <= 16): bit c for a nonzero in
@@ -1356,7 +1428,7 @@ static void spgemm_rowwise(int b, const SpgemmIdx &X, int left_nnz, const T *lv,
 template <typename T>
 static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T *rv, const T *iv,
                    int negate, int ncols, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &out,
-                   const unsigned *lmask = nullptr, const unsigned *rmask = nullptr) {
+                   const unsigned *lmask = nullptr, const unsigned *rmask = nullptr, bool by_block = false) {
   ProfScope ps("spgemm", s);
   const int nrows = X.nrows;
   int *cnt = tmp.alloc<int>(nrows + 1), *pcnt = tmp.alloc<int>(nrows + 1);
@@ -1414,7 +1486,12 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
     if (row_form && b == 3) launch_pdl(k_spgemm_rows<T, 3>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     else if (row_form && b == 6) launch_pdl(k_spgemm_rows<T, 6>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
     else if (row_form) launch_pdl(k_spgemm_rows<T, 10>, gr, bl, 0, s, rows, pbeg, pairs, iq, lv, rv, iv, negate, out.v);
-    else if (b == 10) launch_pdl(k_spgemm_pairs<T, 10>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
+    else if (by_block && lmask && (b == 3 || b == 6 || b == 10)) {
+      const dim3 gw(cdiv(out.nnzb, 8));
+      if (b == 10) launch_pdl(k_spgemm_wblk<T, 10>, gw, bl, 0, s, out.nnzb, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
+      else if (b == 6) launch_pdl(k_spgemm_wblk<T, 6>, gw, bl, 0, s, out.nnzb, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
+      else launch_pdl(k_spgemm_wblk<T, 3>, gw, bl, 0, s, out.nnzb, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
+    } else if (b == 10) launch_pdl(k_spgemm_pairs<T, 10>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
     else if (b == 6) launch_pdl(k_spgemm_pairs<T, 6>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
     else if (b == 3) launch_pdl(k_spgemm_pairs<T, 3>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v, lmask, rmask);
     else launch_pdl(k_spgemm_pairs<T, 0>, dim3(grid(total)), bl, 0, s, total, b, pbeg, pairs, iq, lv, rv, iv, negate, out.v,
@@ -1980,7 +2057,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   {
     SpgemmIdx X{nC, Acf.rp, Acf.ci, nullptr, Tk.rp, Tk.ci, nullptr, nullptr, nullptr};
     unsigned *acf_mask = block_masks<T>(b, aub, Acf.v, Acf.rp + nC, s, tmp);
-    spgemm<T>(b, X, aub, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R, acf_mask);
+    spgemm<T>(b, X, aub, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R, acf_mask, nullptr, true);
     if (acf_mask) tmp.release(acf_mask);
   }
   L.R_ci_f = L.R.ci;
@@ -2026,7 +2103,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     SpgemmIdx X{nC, L.R.rp, L.R.ci, nullptr, AP.rp, AP.ci, AP.rp, AP.ci, L.c2f};
     unsigned *r_mask = block_masks<T>(b, L.R.nnzb, L.R.v, (const int *)nullptr, s, tmp);
     unsigned *ap_mask = block_masks<T>(b, nnzb, AP.v, AP.rp + E, s, tmp);
-    spgemm<T>(b, X, L.R.nnzb, L.R.v, AP.v, AP.v, 0, nC, s, mem, tmp, nx.A, r_mask, ap_mask);
+    spgemm<T>(b, X, L.R.nnzb, L.R.v, AP.v, AP.v, 0, nC, s, mem, tmp, nx.A, r_mask, ap_mask, true);
     if (ap_mask) tmp.release(ap_mask);
     if (r_mask) tmp.release(r_mask);
     if (P.filter_targets & 2) filter<T>(b, tol2, s, mem, tmp, nx.A);
