@@ -577,6 +577,7 @@ struct SpgemmIdx {
   const int *lrp, *lci, *rmap;
   const int *rrp, *rci;
   const int *irp, *ici, *imap;
+  const int *rsrc;  // right entry q -> its block in the right value array (null: q)
 };
 
 template <bool FILL>
@@ -649,7 +650,7 @@ __global__ void k_spgemm_numeric(long long total, int b, SpgemmIdx X, const T *_
     int q = find_sorted(X.rci, X.rrp[m], X.rrp[m + 1], j);
     if (q < 0) continue;
     const T *a = lv + (size_t)p * bb + r * b;
-    const T *bv = rv + (size_t)q * bb + c;
+    const T *bv = rv + (size_t)(X.rsrc ? X.rsrc[q] : q) * bb + c;
     for (int t = 0; t < b; ++t) acc = fma_rn(a[t], bv[t * b], acc);
   }
   ov[g] = negate ? -acc : acc;
@@ -721,7 +722,8 @@ __global__ void k_spgemm_warp(SpgemmIdx X, int *__restrict__ cnt, int *__restric
     for (int c = 0; c < kMergeChunks; ++c) {
       const bool mt = cur[c] < end[c] && X.rci[cur[c]] == jmin;
       const unsigned ball = __ballot_sync(0xffffffffu, mt);
-      if (FILL && mt) pairs[pw + __popc(ball & ((1u << lane) - 1u))] = make_int2(l0 + c * 32 + lane, cur[c]);
+      if (FILL && mt)
+        pairs[pw + __popc(ball & ((1u << lane) - 1u))] = make_int2(l0 + c * 32 + lane, X.rsrc ? X.rsrc[cur[c]] : cur[c]);
       pw += __popc(ball);
       if (mt) ++cur[c];
     }
@@ -1511,8 +1513,12 @@ static void spgemm(int b, const SpgemmIdx &X, int left_nnz, const T *lv, const T
 
 // With defer, the kept count stays on the device (M.nnzb = -1, the buffers sized
 // by the unfiltered count): no host round trip.
+// With keep_src, the kept blocks are not copied: M keeps its value array, and
+// *keep_src (allocated in mem, released by the caller) maps each kept entry to
+// its block there.
 template <typename T>
-static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M, bool defer = false) {
+static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M, bool defer = false,
+                   int **keep_src = nullptr) {
   const int nrows = M.nrows;
   ProfScope ps("filter", s);
   const int ub = M.nnzb;
@@ -1529,9 +1535,21 @@ static void filter(int b, T tol2, cudaStream_t s, Mem &mem, Mem &tmp, DBsr<T> &M
   const int nn = exclusive_scan(cnt, nrp, nrows, s, tmp, !defer);
   const int cap = defer ? ub : nn;
   int *nci = mem.alloc<int>(cap);
-  int *src = tmp.alloc<int>(cap);
+  int *src = keep_src ? mem.alloc<int>(cap) : tmp.alloc<int>(cap);
   launch_pdl(k_filter_compact, dim3(grid(nrows)), dim3(kThreads), 0, s, nrows, M.rp, M.ci, newpos, nrp, nci, src);
   NAIR_LAUNCH_CHECK();
+  if (keep_src) {
+    mem.release(M.rp);
+    mem.release(M.ci);
+    tmp.release(nrm);
+    tmp.release(cnt);
+    tmp.release(newpos);
+    M.rp = nrp;
+    M.ci = nci;
+    M.nnzb = defer ? -1 : nn;
+    *keep_src = src;
+    return;
+  }
   T *nv = mem.alloc<T>((size_t)cap * b * b);
   long long total = (long long)cap * b * b;
   if (total) {
@@ -2031,13 +2049,20 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   // zero columns of the L blocks (the face columns of A's couplings): the
   // products skip them
   unsigned *lm_mask = block_masks<T>(b, lub, Lm.v, Lm.rp + nF, s, tmp);
+  // the filtered iterates keep the product's value array: tk_src maps their
+  // entries into it, so no kept block is copied (the next product reads the
+  // blocks through the map; C5 FP64 setup 77.0 -> 73.8 ms)
+  int *tk_src = nullptr;
   for (int t = 0; t < P.k; ++t) {
-    SpgemmIdx X{nF, Lm.rp, Lm.ci, nullptr, Tk.rp, Tk.ci, Dg.rp, Dg.rp, nullptr};
+    SpgemmIdx X{nF, Lm.rp, Lm.ci, nullptr, Tk.rp, Tk.ci, Dg.rp, Dg.rp, nullptr, tk_src};
     DBsr<T> Tn;
+    int *tn_src = nullptr;
     spgemm<T>(b, X, lub, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn, lm_mask);
-    if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn, true);
+    if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn, true, &tn_src);
     release_bsr(mem, Tk);
+    if (tk_src) mem.release(tk_src);
     Tk = Tn;
+    tk_src = tn_src;
   }
   if (lm_mask) tmp.release(lm_mask);
   tmp.release(Dg.v);
@@ -2055,7 +2080,7 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     NAIR_LAUNCH_CHECK();
   }
   {
-    SpgemmIdx X{nC, Acf.rp, Acf.ci, nullptr, Tk.rp, Tk.ci, nullptr, nullptr, nullptr};
+    SpgemmIdx X{nC, Acf.rp, Acf.ci, nullptr, Tk.rp, Tk.ci, nullptr, nullptr, nullptr, tk_src};
     unsigned *acf_mask = block_masks<T>(b, aub, Acf.v, Acf.rp + nC, s, tmp);
     spgemm<T>(b, X, aub, Acf.v, Tk.v, (const T *)nullptr, 1, nF, s, mem, tmp, L.R, acf_mask, nullptr, true);
     if (acf_mask) tmp.release(acf_mask);
@@ -2112,11 +2137,25 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
   if (P.keep) {
     Lm.nnzb = read_int(Lm.rp + nF, s);
     if (Tk.nnzb < 0) Tk.nnzb = read_int(Tk.rp + nF, s);
+    if (tk_src) {  // Delta's kept blocks, contiguous for the export
+      T *dv = mem.alloc<T>((size_t)std::max(Tk.nnzb, 1) * bb);
+      const long long tk_tot = (long long)Tk.nnzb * bb;
+      if (tk_tot) {
+        launch_pdl(k_copy_blocks<T>, dim3(grid(tk_tot)), dim3(kThreads), 0, s, tk_tot, b, (const int *)tk_src,
+                   (const T *)Tk.v, dv, (const int *)nullptr);
+        NAIR_LAUNCH_CHECK();
+      }
+      mem.release(Tk.v);
+      mem.release(tk_src);
+      tk_src = nullptr;
+      Tk.v = dv;
+    }
     L.L = Lm;
     L.Delta = Tk;
   } else {
     release_bsr(mem, Lm);
     release_bsr(mem, Tk);
+    if (tk_src) mem.release(tk_src);
   }
   tmp.release_all();
   H.lev.push_back(nx);
