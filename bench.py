@@ -184,7 +184,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # workload by the ratio of algorithmic bytes per launch.  A workload is left out
 # whenever the kernels have changed since its capture.
 SWEEP_TRAFFIC = {
-    ("C5", 6): (16.595536e6, 11.72450465e6,
+    ("C5", 6): (14.391e6, 10.1194e6,
                 "profiles/sweep_traffic_C5.md: 256x256x2 mesh, degree 6, 80 sweeps of one V-cycle, "
                 "scaled by algorithmic bytes per launch"),
 }
@@ -209,7 +209,7 @@ def f_sweep_rows(rows, ci, cf, off, f_sweeps):
 SROW_SIZES = (3, 6, 10, 15, 21, 28)
 
 
-def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False):
+def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False, ymode=False):
     """Algorithmic work of every block-Jacobi sweep of a cycle from a zero
     iterate, {(level, k): (flops, bytes)} for sweep k (F sweeps first).
 
@@ -230,7 +230,14 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False):
 
     With split (levels >= 1 in the FP64 scalar-row form), the first F sweep
     also writes h = f - A_FC x_C for its rows, and the later F sweeps, during
-    which x_C does not change, read h and sum only the F-column couplings."""
+    which x_C does not change, read h and sum only the F-column couplings.
+
+    With ymode as well (one C sweep), those levels' F sweeps iterate on
+    y_F = D_FF x_F: no F sweep reads or applies D^{-1}; the later ones sum the
+    right-scaled couplings A_ij D_jj^{-1}, whose nonzero rows are full (b
+    nonzeros each); the C sweep takes the same scaled blocks for its F columns
+    and converts every F row, x_F = D_FF^{-1} y_F (b^2 FMAs, the D^{-1} block
+    and y read, x written)."""
     work = {}
     for l in range(nlev):
         lev = S.level(l)
@@ -238,6 +245,7 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False):
             continue
         rp, ci, vals, cf = lev["row_ptr"], lev["col"], lev["vals"], lev["cf"]
         nnz_block = np.count_nonzero(vals.reshape(len(vals), -1), axis=1)
+        nzr_block = np.count_nonzero(np.any(vals != 0, axis=2), axis=1)
         rows = np.repeat(np.arange(lev["E"]), np.diff(rp))
         off = ci != rows
         W = l0_width(vals[off], b) if l == 0 else 0
@@ -260,14 +268,26 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False):
                     copy = fm[f_sweeps - 1] if short else (cf == 0)
             sel = upd[rows] & off
             fpart = split and l >= 1 and short and 1 <= k < f_sweeps
+            ylev = ymode and split and l >= 1 and short and c_sweeps == 1
             if fpart:  # later F sweeps: the F-column couplings only
                 sel = sel & (cf[ci] == 0)
+            if ylev and k == f_sweeps:  # the C sweep converts every F row
+                copy = cf == 0
             nrow, ncopy = int(upd.sum()), int(copy.sum())
             nblk = int(sel.sum())
             xcols = len(np.unique(ci[sel]))
             if W:
                 flops = 2.0 * nblk * b * W
                 byts = 8.0 * nblk * b * W + 4.0 * nblk + 8.0 * nrow * b
+            elif ylev:
+                scaled = sel & (cf[ci] == 0) if k >= 1 else np.zeros_like(sel)
+                nnz = int(nnz_block[sel & ~scaled].sum()) + b * int(nzr_block[scaled].sum())
+                if k < f_sweeps:
+                    flops = 2.0 * nnz
+                    byts = 8.0 * nnz + 4.0 * nblk + 8.0 * nrow * b
+                else:
+                    flops = 2.0 * (nnz + (nrow + ncopy) * b * b)
+                    byts = 8.0 * nnz + 4.0 * nblk + 8.0 * nrow * b * (b + 1) + 8.0 * ncopy * b * b
             else:
                 nnz = int(nnz_block[sel].sum())
                 flops = 2.0 * (nnz + nrow * b * b)
@@ -316,7 +336,7 @@ def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
     S = nair.NairSolver(rp, ci, v, **params)
     fp64 = params.get("precision", "fp64") == "fp64"
     work = sweep_work(S, S.num_levels(), S.b, S.f_sweeps, max(S.params.c_sweeps, 0),
-                      split=fp64 and S.b in SROW_SIZES)
+                      split=fp64 and S.b in SROW_SIZES, ymode=fp64 and S.b in SROW_SIZES)
     S.close()
     peak, peak_src = fp64_peak
     fl = by = t = 0.0

@@ -27,8 +27,12 @@ static constexpr int kMaxFLists = 8;
 // order the scalar rows of each thread block of *_tpc rows by entry count
 struct SweepRows {
   int *srp = nullptr, *sp = nullptr, *sj = nullptr;
+  int ne = 0;  // packed entries
   void *sv = nullptr;
   int *srs = nullptr;  // per scalar row of an F row: where its F-column entries start (C columns first)
+  // with the F sweeps in the scaled variable y_F = D_FF x_F: the entries with an
+  // F column scaled from the right, row r of A_ij D_jj^{-1}; the others as in sv
+  void *sv2 = nullptr;
   unsigned char *perm_f[kMaxFLists] = {}, *perm_c = nullptr;
   int perm_f_tpc[kMaxFLists] = {}, perm_c_tpc = 0;
 };
@@ -72,6 +76,9 @@ struct Level {
   // level 0 with scaled couplings also g = D^{-1} f; levels >= 1 in the
   // scalar-row form also h = f_F - A_FC x_C for the F sweeps of a cycle
   T *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr, *g = nullptr, *h = nullptr;
+  // F sweeps in y_F = D_FF x_F (sr.sv2 built): the F sweeps of a cycle apply no
+  // D^{-1}; the C sweep reads y_F through sr.sv2 and converts x_F = D^{-1} y_F
+  int ymode = 0;
 };
 
 // Level-0 off-diagonal blocks restricted to their nonzero columns.  An upwind

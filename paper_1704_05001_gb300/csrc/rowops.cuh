@@ -300,7 +300,16 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
     pdl_wait();
     if (a.stamp && threadIdx.x == 0) atomicMin(a.stamp, global_clock());
     if (in) {
-      const T v = a.ipc ? (J >= 0 ? a.x[(size_t)J * B + r] : (T)0) : a.x[(size_t)i * B + r];
+      T v;
+      if constexpr (FM == 5) {  // an F row's x = D^{-1} y from the scaled iterate
+        const T *d = a.dinv + ((size_t)i * B + r) * B;
+        const T *y = a.x + (size_t)i * B;
+        v = 0;
+#pragma unroll
+        for (int c = 0; c < B; ++c) v = fma(d[c], y[c], v);
+      } else {
+        v = a.ipc ? (J >= 0 ? a.x[(size_t)J * B + r] : (T)0) : a.x[(size_t)i * B + r];
+      }
       a.out[(size_t)i * B + r] = v;
       if (a.out2) a.out2[(size_t)i * B + r] = v;
     }
@@ -310,6 +319,11 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
     }
     return;
   }
+  // F sweep modes: 1, 3 the first (h = f - C part stored, then the F part),
+  // 2, 4 the later ones (h - F part); 3, 4 leave the result in y = D x (no
+  // D^{-1}); 5 is the C sweep after them (D^{-1} applied to its rows, the F
+  // rows copied as x = D^{-1} y)
+  constexpr bool kFirst = FM == 1 || FM == 3, kLater = FM == 2 || FM == 4, kNoInv = FM == 3 || FM == 4;
   __shared__ T sres[256];
   __shared__ T red[256];
   const int G = a.G;
@@ -331,7 +345,7 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
     s1 = a.srp[q + 1];
     sm = FM ? a.srs[q] : s0;
   }
-  const int e0 = (FM == 2 ? sm : s0) + g, e1 = FM == 1 ? sm : s1;
+  const int e0 = (kLater ? sm : s0) + g, e1 = kFirst ? sm : s1;
   // natural layout: the row and component this thread finishes.  For the
   // sweep with B <= 10 the thread block's D^{-1} blocks are staged in shared
   // memory before the dependency wait; larger blocks are read after the loop
@@ -339,7 +353,7 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
   const bool act2 = team2 < nact;
   const int i2 = act2 ? (a.list ? a.list[base + team2] : base + team2) : 0;
   const int own = (OP == OP_RESTRICT && act2) ? a.c2f[i2] : i2;  // row of f this component takes
-  constexpr bool kStage = OP == OP_JACOBI && B <= 10;
+  constexpr bool kStage = OP == OP_JACOBI && B <= 10 && !kNoInv;
   __shared__ T sd[kStage ? (256 / B) * B * B : 1];
   if constexpr (kStage) {
     for (int q = t; q < nact * B * B; q += blockDim.x) {
@@ -388,7 +402,7 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
     for (int c = 0; c < B; ++c) acc = fma(va[c], vx[c], acc);
   }
   T accB = 0;
-  if constexpr (OP == OP_JACOBI && FM == 1) {  // the F part of the first F sweep
+  if constexpr (OP == OP_JACOBI && kFirst) {  // the F part of the first F sweep
 #pragma unroll 2
     for (int e = sm + g; e < s1; e += G) {
       int j = a.sj[e];
@@ -412,11 +426,11 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
   // back in fmode 2)
   auto residual = [&](int row, int comp, T sumA, T sumB) -> T {
     const size_t q = (size_t)row * B + comp;
-    if constexpr (FM == 1) {
+    if constexpr (kFirst) {
       const T hv = a.f[q] - sumA;
       a.h[q] = hv;
       return hv - sumB;
-    } else if constexpr (FM == 2) {
+    } else if constexpr (kLater) {
       return a.h[q] - sumA;
     } else {
       return a.f[q] - sumA;
@@ -430,7 +444,7 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
       __syncthreads();
     }
     T sumB = 0;
-    if (OP == OP_JACOBI && FM == 1) {  // the same tree for the F part
+    if (OP == OP_JACOBI && kFirst) {  // the same tree for the F part
       const T sumA = (t < nact * B) ? red[t * G] : (T)0;
       __syncthreads();
       if (act) red[enc * G + g] = accB;
@@ -446,10 +460,25 @@ __global__ void __launch_bounds__(256, 6) k_scalar_rows(RowArgs<T> a) {
       sres[t] = residual(i2, r2, red[t * G], sumB);
     }
   } else if (act) {
-    if (OP == OP_RESTRICT) a.out[(size_t)i * B + r] = a.f[(size_t)a.c2f[i] * B + r] + acc;
-    else sres[enc] = residual(i, r, acc, accB);
+    if (OP == OP_RESTRICT) {
+      a.out[(size_t)i * B + r] = a.f[(size_t)a.c2f[i] * B + r] + acc;
+    } else if (kNoInv) {  // y of this scalar row: no exchange needed
+      const T y = residual(i, r, acc, accB);
+      a.out[(size_t)i * B + r] = y;
+      if (a.out2c) a.out2c[(size_t)i * B + r] = y;
+    } else {
+      sres[enc] = residual(i, r, acc, accB);
+    }
   }
-  if constexpr (OP == OP_JACOBI) {
+  if constexpr (OP == OP_JACOBI && kNoInv) {
+    if (G > 1) {
+      __syncthreads();
+      if (act2) {
+        a.out[(size_t)i2 * B + r2] = sres[t];
+        if (a.out2c) a.out2c[(size_t)i2 * B + r2] = sres[t];
+      }
+    }
+  } else if constexpr (OP == OP_JACOBI) {
     __syncthreads();
     if (act2) {
       const T *d = kStage ? sd + (size_t)team2 * B * B + r2 * B : a.dinv + (size_t)i2 * B * B + r2 * B;

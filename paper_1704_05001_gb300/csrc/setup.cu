@@ -1838,6 +1838,7 @@ static void srow_pack(int E, int b, const DBsr<T> &M, bool skip_diag, const sign
   NAIR_LAUNCH_CHECK();
   sr.srp = mem.alloc<int>(n + 1);
   const int ne = exclusive_scan(cnt, sr.srp, (int)n, s, tmp, true);
+  sr.ne = ne;
   sr.sp = mem.alloc<int>(std::max(ne, 1));
   if (cf) sr.srs = mem.alloc<int>(n);
   launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)M.rp,
@@ -1891,9 +1892,31 @@ template void build_sweep_rows_level<double>(int, int, int, int, const DBsr<doub
 template void build_sweep_rows_level<float>(int, int, int, int, const DBsr<float> &, const signed char *, int *,
                                             int, int *const *, const int *, int *, SweepRows &, cudaStream_t, Mem &);
 
+// sv2[e b + c] = sum_t sv[e b + t] dinv[j][t][c] (fma, t ascending) for an
+// entry e whose column j = sj[e] is an F element; sv[e b + c] otherwise
+template <typename T>
+__global__ void k_srow_scale(long long tot, int b, const int *__restrict__ sj, const T *__restrict__ sv,
+                             const T *__restrict__ dinv, const signed char *__restrict__ cf, T *__restrict__ sv2) {
+  pdl_wait();
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= tot) return;
+  const long long e = g / b;
+  const int c = (int)(g - e * b);
+  const int j = sj[e];
+  if (cf[j] != 0) {
+    sv2[g] = sv[g];
+    return;
+  }
+  const T *row = sv + (size_t)e * b;
+  const T *dc = dinv + (size_t)j * b * b + c;
+  T acc = 0;
+  for (int t = 0; t < b; ++t) acc = fma_rn(row[t], dc[(size_t)t * b], acc);
+  sv2[g] = acc;
+}
+
 // the scalar-row lists and permutations of every level >= 1 that sweeps
 template <typename T>
-static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
+static void build_sweep_rows(Hier<T> &H, const Params &P, cudaStream_t s, Mem &mem) {
   for (int l = 0; l < H.nlev; ++l) {
     Level<T> &L = H.lev[l];
     if (L.coarsest) continue;
@@ -1903,6 +1926,25 @@ static void build_sweep_rows(Hier<T> &H, cudaStream_t s, Mem &mem) {
                               mem);
     // the C part of the F rows, summed once per cycle by the first F sweep
     if (L.sr.srs && L.nfl >= 2) L.h = mem.alloc<T>((size_t)L.E * H.b);
+    // F sweeps in y_F = D_FF x_F where every sweep of the cycle takes the
+    // scalar-row form (one F sweep list per sweep, one C sweep): the first F
+    // sweep stores y = f_F - A_FC x_C - A_FF x_F, each later one y = h -
+    // sum_j (A_ij D_jj^{-1}) y_j, so no F sweep applies D^{-1}; the C sweep
+    // reads y_F through the same scaled blocks and writes x_F = D_FF^{-1} y_F
+    bool all_rows = L.h && L.nfl == P.f_sweeps && P.f_sweeps >= 2 && P.c_sweeps == 1 && L.sr.perm_c;
+    for (int k = 0; all_rows && k < L.nfl; ++k) all_rows = L.sr.perm_f[k] != nullptr;
+    if (all_rows) {
+      const long long ne = L.sr.ne;
+      T *sv2 = mem.alloc<T>((size_t)std::max(ne, 1LL) * H.b);
+      const long long tot = ne * H.b;
+      if (tot) {
+        launch_pdl(k_srow_scale<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, H.b, (const int *)L.sr.sj,
+                   (const T *)L.sr.sv, (const T *)L.dinv, (const signed char *)L.cf, sv2);
+        NAIR_LAUNCH_CHECK();
+      }
+      L.sr.sv2 = sv2;
+      L.ymode = 1;
+    }
   }
 }
 
@@ -2058,7 +2100,9 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     DBsr<T> Tn;
     int *tn_src = nullptr;
     spgemm<T>(b, X, lub, Lm.v, Tk.v, Dg.v, 0, nF, s, mem, tmp, Tn, lm_mask);
-    if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn, true, &tn_src);
+    // (for b = 1 the copy is cheaper than the extra index load in the merge:
+    // scalar nAIR setup 973 -> 997 ms with the map)
+    if (P.filter_targets & 1) filter<T>(b, tol2, s, mem, tmp, Tn, true, b >= 3 ? &tn_src : nullptr);
     release_bsr(mem, Tk);
     if (tk_src) mem.release(tk_src);
     Tk = Tn;
@@ -2292,7 +2336,7 @@ void build_hierarchy(const DBsr<T> &A0, const Params &P, cudaStream_t s, Mem &me
     build_l0scaled<T>(H.lev[0].A, H.lev[0].dinv, H.b, s, mem, H.l0c);
   }
   build_fsweep_lists<T>(H, P, s, mem);
-  build_sweep_rows<T>(H, s, mem);
+  build_sweep_rows<T>(H, P, s, mem);
   // V-cycle vectors and complexities (Sec. 6: OC and CC in work units)
   const int b = H.b;
   double nnz0 = (double)H.lev[0].A.nnzb, oc = 0.0, cc = 0.0;

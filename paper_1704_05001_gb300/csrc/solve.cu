@@ -141,7 +141,16 @@ bool launch_scalar_rows(RowArgs<T> a, int G, cudaStream_t s) {
   if (blocks) {
     if (OP == OP_JACOBI && a.fmode == 1) launch_scalar_rows_b<T, OP_JACOBI, 1>(a, b, gr, bl, s);
     else if (OP == OP_JACOBI && a.fmode == 2) launch_scalar_rows_b<T, OP_JACOBI, 2>(a, b, gr, bl, s);
-    else launch_scalar_rows_b<T, OP, 0>(a, b, gr, bl, s);
+    else if (OP == OP_JACOBI && a.fmode >= 3) {
+      // the sweeps in y_F = D_FF x_F (FP64 levels only)
+      if constexpr (std::is_same<T, double>::value) {
+        if (a.fmode == 3) launch_scalar_rows_b<T, OP_JACOBI, 3>(a, b, gr, bl, s);
+        else if (a.fmode == 4) launch_scalar_rows_b<T, OP_JACOBI, 4>(a, b, gr, bl, s);
+        else launch_scalar_rows_b<T, OP_JACOBI, 5>(a, b, gr, bl, s);
+      } else {
+        fail(NAIR_ERR_UNSUPPORTED, "scaled F sweeps outside FP64");
+      }
+    } else launch_scalar_rows_b<T, OP, 0>(a, b, gr, bl, s);
     NAIR_LAUNCH_CHECK();
   }
   return true;
@@ -327,6 +336,12 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
   // later F sweeps, which then sum only the F-column part (x_C is fixed while
   // the F sweeps run)
   bool have_h = false;
+  // F sweeps in y_F = D_FF x_F (set up where every sweep takes the scalar-row
+  // form): y^1 = h - A_FF x_F^0 with h = f_F - A_FC x_C, y^{k+1} = h - sum_j
+  // (A_ij D_jj^{-1}) y^k_j, the same block-Jacobi iterates as x = D^{-1} y, with
+  // no D^{-1} applied per sweep; the C sweep reads y_F through the scaled
+  // blocks and its copy part writes x_F = D_FF^{-1} y_F for every F row
+  const bool ymode = L.ymode && short_f && S == SF + 1 && L.sr.sv2;
   for (int k = 0; k < S; ++k) {
     const int cls = k < SF ? 0 : 1, oth = 1 - cls, ob = k % 2;
     RowArgs<T> a = row_args(L.A, b);
@@ -347,8 +362,8 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
         a.copy_list = L.fq[k];
       }
     } else if (short_f && k == SF) {
-      a.ncopy = L.fl_n[SF - 1];
-      a.copy_list = L.fl[SF - 1];
+      a.ncopy = ymode ? L.nF : L.fl_n[SF - 1];
+      a.copy_list = ymode ? L.fsweep : L.fl[SF - 1];
     } else if (buf_ver[ob][oth] != cur_ver[oth]) {
       a.ncopy = nrow[oth];
       a.copy_list = rows[oth];
@@ -386,7 +401,12 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
         a.sj = L.sr.sj;
         a.sv = static_cast<const T *>(L.sr.sv);
         a.perm = perm;
-        if (cls == 0 && L.h && L.sr.srs && (k == 0 || have_h)) {
+        if (ymode) {
+          a.srs = L.sr.srs;
+          a.h = L.h;
+          a.fmode = cls == 1 ? 5 : (k == 0 ? 3 : 4);
+          if (a.fmode != 3) a.sv = static_cast<const T *>(L.sr.sv2);
+        } else if (cls == 0 && L.h && L.sr.srs && (k == 0 || have_h)) {
           a.srs = L.sr.srs;
           a.h = L.h;
           a.fmode = k == 0 ? 1 : 2;
@@ -394,6 +414,7 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
         done = launch_scalar_rows<T, OP_JACOBI>(a, G, s);
         if (done && k == 0 && a.fmode == 1) have_h = true;
       }
+      if (!done && ymode) fail(NAIR_ERR_UNSUPPORTED, "scaled F sweeps without the scalar-row form");
       if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
     }
     cur_ver[cls] = k + 1;
@@ -620,10 +641,12 @@ template void vcycle_t<float>(const Hier<float> &, const Params &, const float *
 // ---------------------------------------------------------------------------
 
 static constexpr int kDotGroup = 8;
-// four thread blocks per SM keep enough loads in flight for the FP64 dot
-// products over the Krylov basis (C5 FP64 solve 135.2 -> 134.5 ms against two;
-// six: 137.1 ms)
+// Thread blocks of the dot products over the Krylov basis: four per SM on
+// long vectors (C5, 5.2 M unknowns: FP64 solve 135.2 -> 134.5 ms against two;
+// six: 137.1 ms), two on shorter ones, where four leave each thread only a few
+// elements (C2, 0.79 M unknowns: 31.3 -> 32.3 ms with four)
 static constexpr int kDotCtas = 608;
+static int dot_ctas(long long n) { return n >= (1LL << 22) ? kDotCtas : kDotCtas / 2; }
 
 // partial[k * G + cta] = sum over this CTA's elements of V_k . w, k < nv.
 // Vectors are taken NQ at a time with NQ a compile-time count, so no FP64
@@ -802,9 +825,10 @@ Krylov::~Krylov() {
 static void multidot(Krylov &K, long long n, int nv, const double *V, const double *w, double *out,
                      cudaStream_t s) {
   ProfScope ps("multidot", s);
-  k_multidot<<<kDotCtas, kThreads, 0, s>>>(n, nv, V, n, w, K.partial);
+  const int G = dot_ctas(n);
+  k_multidot<<<G, kThreads, 0, s>>>(n, nv, V, n, w, K.partial);
   NAIR_LAUNCH_CHECK();
-  k_reduce_partials<<<nv, 32, 0, s>>>(nv, kDotCtas, K.partial, out);
+  k_reduce_partials<<<nv, 32, 0, s>>>(nv, G, K.partial, out);
   NAIR_LAUNCH_CHECK();
 }
 

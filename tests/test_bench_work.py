@@ -67,6 +67,43 @@ def test_sweep_work_counts(hier, split):
             assert byts >= 16.0 * nrow * b
 
 
+def test_sweep_work_counts_scaled_f_sweeps(hier):
+    """With ymode, the F sweeps on levels >= 1 apply no D^-1: the first sums
+    the exact nonzeros of its couplings, the later ones b per nonzero row of
+    the right-scaled F couplings A_ij D_jj^-1; the C sweep takes the scaled
+    blocks for its F columns and converts every F row (b^2 FMAs each)."""
+    P, H = hier
+    b, SF = P["b"], 3
+    work = bench.sweep_work(H, H.nlev, b, SF, 1, split=True, ymode=True)
+    base = bench.sweep_work(H, H.nlev, b, SF, 1, split=True)
+    for l in range(H.nlev):
+        lev = H.level(l)
+        if lev["coarsest"]:
+            continue
+        rows, ci, cf, off = _level_arrays(lev)
+        masks = bench.f_sweep_rows(rows, ci, cf, off, SF)
+        vals = lev["vals"]
+        nzr = np.count_nonzero(np.any(vals != 0, axis=2), axis=1)
+        nnzb = np.count_nonzero(vals.reshape(len(vals), -1), axis=1)
+        for k, upd in enumerate(masks + [cf == 1]):
+            if (l, k) not in work:
+                continue
+            if l == 0:
+                assert work[(l, k)] == base[(l, k)]
+                continue
+            sel = upd[rows] & off
+            if 1 <= k < SF:
+                sel = sel & (cf[ci] == 0)
+            fcol = sel & (cf[ci] == 0) if k >= 1 else np.zeros_like(sel)
+            nnz = int(nnzb[sel & ~fcol].sum()) + b * int(nzr[fcol].sum())
+            flops, byts = work[(l, k)]
+            if k < SF:
+                assert flops == 2.0 * nnz
+            else:
+                assert flops == 2.0 * (nnz + (int((cf == 1).sum()) + int((cf == 0).sum())) * b * b)
+            assert byts >= 16.0 * int(upd.sum()) * b
+
+
 def _transpose_level(lev, b):
     """Block transpose of a level matrix with its inverse diagonal blocks:
     (A^T)_ji = (A_ij)^T, rows sorted by column, (D_ii^{-1})^T."""
