@@ -769,19 +769,24 @@ __global__ void k_update(long long n, int nv, const double *__restrict__ Z, long
   x[i] = a;
 }
 
+// out = w / d as w times the correctly rounded 1 / d: an FP64 division per
+// element costs a dozen FP64-pipe instructions, which made the normalisation
+// FP64-bound (81 us per C5 basis vector; within 1.5 ulp of the quotient)
 __global__ void k_div(long long n, const double *__restrict__ w, double d, double *__restrict__ out) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = w[i] / d;
+  const double inv = 1.0 / d;
+  if (i < n) out[i] = w[i] * inv;
 }
 
-// out = w / ||w|| from the squared norm on the device (IEEE sqrt and division,
-// the values the host would compute); zero when the norm is zero (breakdown:
-// the host ends the cycle at this column and never uses out)
+// out = w / ||w|| from the squared norm on the device (IEEE sqrt, then the
+// scaling by its reciprocal as in k_div); zero when the norm is zero
+// (breakdown: the host ends the cycle at this column and never uses out)
 __global__ void k_div_norm(long long n, const double *__restrict__ w, const double *__restrict__ nrm2,
                            double *__restrict__ out) {
   const double d = sqrt(*nrm2);  // once per thread: a grid-stride loop over the vector
+  const double inv = d != 0.0 ? 1.0 / d : 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    out[i] = d != 0.0 ? w[i] / d : 0.0;
+    out[i] = w[i] * inv;
 }
 
 template <typename A, typename B>
