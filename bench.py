@@ -205,7 +205,7 @@ def f_sweep_rows(rows, ci, cf, off, f_sweeps):
     return masks
 
 
-# block sizes with the packed scalar-row form of the coarse FP64 sweeps
+# block sizes with the packed scalar-row form of the coarse sweeps
 SROW_SIZES = (3, 6, 10, 15, 21, 28)
 
 
@@ -228,7 +228,7 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False, ymode=False):
     the couplings scaled in advance, x_i = g_i - sum_j (D_ii^{-1} A_ij) x_j with
     g = D^{-1} f: b W FMAs per coupling block and no D^{-1} apply.
 
-    With split (levels >= 1 in the FP64 scalar-row form), the first F sweep
+    With split (levels >= 1 in the scalar-row form), the first F sweep
     also writes h = f - A_FC x_C for its rows, and the later F sweeps, during
     which x_C does not change, read h and sum only the F-column couplings.
 
@@ -336,7 +336,7 @@ def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
     S = nair.NairSolver(rp, ci, v, **params)
     fp64 = params.get("precision", "fp64") == "fp64"
     work = sweep_work(S, S.num_levels(), S.b, S.f_sweeps, max(S.params.c_sweeps, 0),
-                      split=fp64 and S.b in SROW_SIZES, ymode=fp64 and S.b in SROW_SIZES)
+                      split=S.b in SROW_SIZES, ymode=S.b in SROW_SIZES)
     S.close()
     peak, peak_src = fp64_peak
     fl = by = t = 0.0

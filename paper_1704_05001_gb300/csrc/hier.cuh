@@ -17,7 +17,7 @@ struct DBsr {
 // most F sweeps per cycle with their own row lists
 static constexpr int kMaxFLists = 8;
 
-// scalar-row form of a level's off-diagonal blocks for its FP64 sweeps:
+// scalar-row form of a level's off-diagonal blocks for its sweeps:
 // scalar row (i, r) lists, in ascending block order, the off-diagonal blocks
 // p of row i whose row r has a nonzero (offsets srp[i b + r], block indices
 // sp).  The entries are also packed for the sweeps: sj[e] is entry e's block
@@ -227,8 +227,8 @@ void fsweep_assign(int nF, int nf, int *buf, const int *hcnt, int *fsweep, int *
 // (FP64 and the DG block sizes; otherwise rr stays empty)
 template <typename T>
 void build_restrict_rows(int nC, int b, const DBsr<T> &R, SweepRows &rr, cudaStream_t s, Mem &mem);
-// the scalar-row form of one level's matrix A for its sweep lists (FP64 and
-// the DG block sizes; otherwise sr stays empty and the sweeps use k_rowop)
+// the scalar-row form of one level's matrix A for its sweep lists (the DG
+// block sizes; otherwise sr stays empty and the sweeps use k_rowop)
 template <typename T>
 void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, const signed char *cf, int *fsweep,
                             int nfl, int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s,

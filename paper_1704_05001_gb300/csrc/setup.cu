@@ -1855,7 +1855,7 @@ static void srow_pack(int E, int b, const DBsr<T> &M, bool skip_diag, const sign
 
 template <typename T>
 void build_restrict_rows(int nC, int b, const DBsr<T> &R, SweepRows &rr, cudaStream_t s, Mem &mem) {
-  // FP64 only, as the sweeps
+  // FP64 only (the FP32 restriction keeps the block-row kernel)
   if (!std::is_same<T, double>::value || !srow_supported(b) || nC == 0) return;
   const long long n = (long long)nC * b, ub = (long long)R.nnzb * b;
   if (n + 1 >= INT_MAX || ub >= INT_MAX) return;
@@ -1871,11 +1871,11 @@ template <typename T>
 void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, const signed char *cf, int *fsweep,
                             int nfl, int *const *fl, const int *fl_n, int *csweep, SweepRows &sr, cudaStream_t s,
                             Mem &mem) {
-  // FP64 only: it saves FP64 issue slots at the price of a shuffled access
-  // pattern and a longer setup; the FP32 sweeps are not bound by arithmetic
-  // and did not gain (mixed-precision setup + solve C3 40.0 -> 39.7 ms, C5
-  // 427.6 -> 434.7 ms)
-  if (!std::is_same<T, double>::value || !srow_supported(b) || E == 0) return;
+  // FP64 and FP32: it saves FP64 issue slots at the price of a shuffled
+  // access pattern and a longer setup.  In FP32 alone it did not gain (mixed
+  // precision, C5 at Neumann degree 2: 427.6 -> 434.7 ms); with the F sweeps
+  // in y = D x it does (degree 6: setup + solve 141.7 -> 132.9 ms)
+  if (!srow_supported(b) || E == 0) return;
   const long long n = (long long)E * b, ub = (long long)A.nnzb * b;
   if (n + 1 >= INT_MAX || ub >= INT_MAX) return;
   const double avg = (double)A.nnzb / E;

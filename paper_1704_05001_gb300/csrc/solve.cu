@@ -141,16 +141,10 @@ bool launch_scalar_rows(RowArgs<T> a, int G, cudaStream_t s) {
   if (blocks) {
     if (OP == OP_JACOBI && a.fmode == 1) launch_scalar_rows_b<T, OP_JACOBI, 1>(a, b, gr, bl, s);
     else if (OP == OP_JACOBI && a.fmode == 2) launch_scalar_rows_b<T, OP_JACOBI, 2>(a, b, gr, bl, s);
-    else if (OP == OP_JACOBI && a.fmode >= 3) {
-      // the sweeps in y_F = D_FF x_F (FP64 levels only)
-      if constexpr (std::is_same<T, double>::value) {
-        if (a.fmode == 3) launch_scalar_rows_b<T, OP_JACOBI, 3>(a, b, gr, bl, s);
-        else if (a.fmode == 4) launch_scalar_rows_b<T, OP_JACOBI, 4>(a, b, gr, bl, s);
-        else launch_scalar_rows_b<T, OP_JACOBI, 5>(a, b, gr, bl, s);
-      } else {
-        fail(NAIR_ERR_UNSUPPORTED, "scaled F sweeps outside FP64");
-      }
-    } else launch_scalar_rows_b<T, OP, 0>(a, b, gr, bl, s);
+    else if (OP == OP_JACOBI && a.fmode == 3) launch_scalar_rows_b<T, OP_JACOBI, 3>(a, b, gr, bl, s);
+    else if (OP == OP_JACOBI && a.fmode == 4) launch_scalar_rows_b<T, OP_JACOBI, 4>(a, b, gr, bl, s);
+    else if (OP == OP_JACOBI && a.fmode == 5) launch_scalar_rows_b<T, OP_JACOBI, 5>(a, b, gr, bl, s);
+    else launch_scalar_rows_b<T, OP, 0>(a, b, gr, bl, s);
     NAIR_LAUNCH_CHECK();
   }
   return true;
