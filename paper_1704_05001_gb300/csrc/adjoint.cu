@@ -220,6 +220,14 @@ void build_transposed(Hier<T> &H, int f_sweeps, cudaStream_t s, Mem &mem) {
     // the F sweeps follow the C sweeps, so x_C is fixed while they run: the
     // first keeps f - (A^T)_FC x_C for the others, as in the forward cycle
     if (TL.sr.srs && TL.nfl >= 2) TL.h = mem.alloc<T>((size_t)L.E * b);
+    // F sweeps in y_F = D_FF^T x_F where each of them takes the scalar-row
+    // form (the C sweeps come first and see x_F = 0)
+    bool all_rows = TL.h && TL.nfl == nf && nf >= 2;
+    for (int k = 0; all_rows && k < TL.nfl; ++k) all_rows = TL.sr.perm_f[k] != nullptr;
+    if (all_rows) {
+      scale_srow_entries<T>(TL.sr, b, (const T *)TL.dinvT, L.cf, s, mem);
+      TL.ymode = 1;
+    }
   }
   NAIR_CK(cudaStreamSynchronize(s));
 }

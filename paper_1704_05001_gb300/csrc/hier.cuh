@@ -139,13 +139,16 @@ struct TLevel {
   int nfl = 0;
   int *fl[kMaxFLists] = {}, *fq[kMaxFLists] = {};
   int fl_n[kMaxFLists] = {}, fq_n[kMaxFLists] = {};
-  SweepRows sr;  // levels >= 1, FP64, for the rows of A^T
+  SweepRows sr;  // levels >= 1, for the rows of A^T
   DBsr<T> Rt;                  // R_cf^T: E rows (blocks on F rows only), nC columns
   int *cself = nullptr;        // element -> its coarse index (C) or -1 (F)
   int *pt_rp = nullptr, *pt_ci = nullptr;  // P^T: coarse J -> F elements with ip = J, ascending
   T *r = nullptr;              // residual after the pre-relaxation
   T *h = nullptr;              // f - (A^T)_FC x_C for the F sweeps (scalar-row levels)
   T *ainvT = nullptr;          // coarsest level: (A_c^{-1})^T
+  // F sweeps in y_F = D_FF^T x_F (sr.sv2 built), as Level::ymode; x_F =
+  // D_FF^{-T} y_F is formed after the last F sweep
+  int ymode = 0;
 };
 
 template <typename T>
@@ -227,6 +230,10 @@ void fsweep_assign(int nF, int nf, int *buf, const int *hcnt, int *fsweep, int *
 // (FP64 and the DG block sizes; otherwise rr stays empty)
 template <typename T>
 void build_restrict_rows(int nC, int b, const DBsr<T> &R, SweepRows &rr, cudaStream_t s, Mem &mem);
+// sr.sv2: the packed entries with an F column j (cf[j] == 0) scaled from the
+// right by dinv_j (row r of the block times dinv_j), the others copied
+template <typename T>
+void scale_srow_entries(SweepRows &sr, int b, const T *dinv, const signed char *cf, cudaStream_t s, Mem &mem);
 // the scalar-row form of one level's matrix A for its sweep lists (the DG
 // block sizes; otherwise sr stays empty and the sweeps use k_rowop)
 template <typename T>

@@ -1881,7 +1881,10 @@ void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, cons
   const double avg = (double)A.nnzb / E;
   if (rowop_groups(nF, b, avg) > kSweepRowsMaxG && rowop_groups(nC, b, avg) > kSweepRowsMaxG) return;
   srow_pack<T>(E, b, A, true, cf, sr, s, mem);
-  sr.perm_f[0] = srow_perm<T>(nF, b, avg, fsweep, sr.srp, s, mem, &sr.perm_f_tpc[0]);
+  // F sweeps: thread groups per scalar row sized for half a row (the first
+  // F sweep's rows too: C5 FP64 solve 112.5 -> 110.8 ms; for a quarter of a
+  // row the later sweeps were slower, 113.1 ms)
+  sr.perm_f[0] = srow_perm<T>(nF, b, 0.5 * avg, fsweep, sr.srp, s, mem, &sr.perm_f_tpc[0]);
   // the later F sweeps sum only the F part of their rows: sorted by its length,
   // their thread groups per row sized for half a row (C5 FP64 solve 119.4 ->
   // 112.4 ms, mixed 80.2 -> 75.5 ms, adjoint 211.8 -> 204.8 ms)
@@ -1916,6 +1919,21 @@ __global__ void k_srow_scale(long long tot, int b, const int *__restrict__ sj, c
   sv2[g] = acc;
 }
 
+template <typename T>
+void scale_srow_entries(SweepRows &sr, int b, const T *dinv, const signed char *cf, cudaStream_t s, Mem &mem) {
+  const long long ne = sr.ne;
+  T *sv2 = mem.alloc<T>((size_t)std::max(ne, 1LL) * b);
+  const long long tot = ne * b;
+  if (tot) {
+    launch_pdl(k_srow_scale<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, (const int *)sr.sj,
+               (const T *)sr.sv, dinv, cf, sv2);
+    NAIR_LAUNCH_CHECK();
+  }
+  sr.sv2 = sv2;
+}
+template void scale_srow_entries<double>(SweepRows &, int, const double *, const signed char *, cudaStream_t, Mem &);
+template void scale_srow_entries<float>(SweepRows &, int, const float *, const signed char *, cudaStream_t, Mem &);
+
 // the scalar-row lists and permutations of every level >= 1 that sweeps
 template <typename T>
 static void build_sweep_rows(Hier<T> &H, const Params &P, cudaStream_t s, Mem &mem) {
@@ -1936,15 +1954,7 @@ static void build_sweep_rows(Hier<T> &H, const Params &P, cudaStream_t s, Mem &m
     bool all_rows = L.h && L.nfl == P.f_sweeps && P.f_sweeps >= 2 && P.c_sweeps == 1 && L.sr.perm_c;
     for (int k = 0; all_rows && k < L.nfl; ++k) all_rows = L.sr.perm_f[k] != nullptr;
     if (all_rows) {
-      const long long ne = L.sr.ne;
-      T *sv2 = mem.alloc<T>((size_t)std::max(ne, 1LL) * H.b);
-      const long long tot = ne * H.b;
-      if (tot) {
-        launch_pdl(k_srow_scale<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, H.b, (const int *)L.sr.sj,
-                   (const T *)L.sr.sv, (const T *)L.dinv, (const signed char *)L.cf, sv2);
-        NAIR_LAUNCH_CHECK();
-      }
-      L.sr.sv2 = sv2;
+      scale_srow_entries<T>(L.sr, H.b, L.dinv, L.cf, s, mem);
       L.ymode = 1;
     }
   }

@@ -388,8 +388,8 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       const int pk = (short_f && k < SF) ? k : 0;
       const unsigned char *perm = cls == 1 ? L.sr.perm_c : L.sr.perm_f[pk];
       const int ptpc = cls == 1 ? L.sr.perm_c_tpc : L.sr.perm_f_tpc[pk];
-      // the later F sweeps' lists sum about half of each row (its F part)
-      const int G = rowop_groups(a.nrows, b, (cls == 0 && pk >= 1) ? 0.5 * avg : avg);
+      // F sweep lists: groups sized for half a row, as at setup
+      const int G = rowop_groups(a.nrows, b, cls == 0 ? 0.5 * avg : avg);
       bool done = false;
       if (L.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
         a.srp = L.sr.srp;
@@ -494,6 +494,33 @@ static void l0_args(RowArgs<T> &a, const TLevel<T> &TL, const L0Comp<T> &C) {
   a.ov = C.ov;
 }
 
+// the end of the y-form F sweeps of the transposed cycle: out_F = D_ii^{-T} y_i
+// for the F rows (flist), out_C = y_C copied for the C rows (clist)
+template <typename T>
+__global__ void k_convert_t(int nF, int b, const int *__restrict__ flist, const T *__restrict__ dinvT,
+                            const T *__restrict__ y, int nC, const int *__restrict__ clist, T *__restrict__ out) {
+  pdl_launch_dependents();
+  pdl_wait();
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long na = (long long)nF * b;
+  if (g < na) {
+    const int k = (int)(g / b), r = (int)(g - (long long)k * b);
+    const int i = flist[k];
+    const T *d = dinvT + (size_t)i * b * b + r * b;
+    const T *yi = y + (size_t)i * b;
+    T acc = 0;
+    for (int c = 0; c < b; ++c) acc = fma(d[c], yi[c], acc);
+    out[(size_t)i * b + r] = acc;
+    return;
+  }
+  g -= na;
+  if (g < (long long)nC * b) {
+    const int k = (int)(g / b), r = (int)(g - (long long)k * b);
+    const size_t o = (size_t)clist[k] * b + r;
+    out[o] = y[o];
+  }
+}
+
 template <typename T>
 static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out, cudaStream_t s) {
   const Level<T> &L = H.lev[l];
@@ -519,8 +546,14 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
   if (S == 0) {
     NAIR_CK(cudaMemsetAsync(out, 0, sizeof(T) * (size_t)L.E * b, s));
   } else {
-    // the sweeps alternate between two buffers and end in out
-    T *buf[2] = {(S % 2 == 1) ? out : L.x2, (S % 2 == 1) ? L.x2 : out};
+    // F sweeps in y_F = D_FF^T x_F (as in the forward cycle): the first stores
+    // h and y = h (x_F = 0 after the C sweeps), the later ones y = h - sum_j
+    // ((A^T)_ij D_jj^{-T}) y_j with no D^{-T}, and a last pass writes x_F =
+    // D_FF^{-T} y_F into out before the residual
+    const bool ymode = TL.ymode && P.f_sweeps >= 2 && TL.nfl == P.f_sweeps && P.c_sweeps >= 1 && TL.sr.sv2;
+    const int Sp = S + (ymode ? 1 : 0);
+    // the sweeps (and the conversion) alternate between two buffers and end in out
+    T *buf[2] = {(Sp % 2 == 1) ? out : L.x2, (Sp % 2 == 1) ? L.x2 : out};
     const int nrow[2] = {L.nF, L.nC};
     const int *rows[2] = {TL.fsweep, TL.csweep};
     int cur_ver[2] = {0, 0};  // version of each class (0 = the zero start)
@@ -569,7 +602,7 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
         // scalar-row form of A^T where built, as in the forward cycle
         const unsigned char *perm = cls == 1 ? TL.sr.perm_c : TL.sr.perm_f[short_f ? m : 0];
         const int ptpc = cls == 1 ? TL.sr.perm_c_tpc : TL.sr.perm_f_tpc[short_f ? m : 0];
-        const int G = rowop_groups(a.nrows, b, (cls == 0 && short_f && m >= 1) ? 0.5 * avg : avg);
+        const int G = rowop_groups(a.nrows, b, cls == 0 ? 0.5 * avg : avg);
         bool done = false;
         if (TL.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
           a.srp = TL.sr.srp;
@@ -581,16 +614,25 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
           if (cls == 0 && TL.h && TL.sr.srs && (have_h || full)) {
             a.srs = TL.sr.srs;
             a.h = TL.h;
-            a.fmode = have_h ? 2 : 1;
+            a.fmode = ymode ? (have_h ? 4 : 3) : (have_h ? 2 : 1);
+            if (a.fmode == 4) a.sv = static_cast<const T *>(TL.sr.sv2);
           }
           done = launch_scalar_rows<T, OP_JACOBI>(a, G, s);
-          if (done && a.fmode == 1) have_h = true;
+          if (done && (a.fmode == 1 || a.fmode == 3)) have_h = true;
         }
+        if (!done && ymode && cls == 0) fail(NAIR_ERR_UNSUPPORTED, "scaled F sweeps without the scalar-row form");
         if (!done) launch_rowop<T, OP_JACOBI>(a, avg, s);
       }
       cur_ver[cls] = k + 1;
       buf_ver[ob][cls] = k + 1;
       if (!short_f && a.ncopy) buf_ver[ob][oth] = cur_ver[oth];
+    }
+    if (ymode) {
+      ProfScope ps("convert_t", s, l);
+      const long long tot = (long long)(L.nF + L.nC) * b;
+      launch_pdl(k_convert_t<T>, dim3(grid(tot)), dim3(kThreads), 0, s, L.nF, b, (const int *)TL.fsweep,
+                 (const T *)TL.dinvT, (const T *)buf[(S - 1) % 2], L.nC, (const int *)TL.csweep, out);
+      NAIR_LAUNCH_CHECK();
     }
     ProfScope ps("resid_t", s, l);
     RowArgs<T> a = row_args(TL.At, b);
