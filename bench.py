@@ -205,11 +205,8 @@ def f_sweep_rows(rows, ci, cf, off, f_sweeps):
     return masks
 
 
-# block sizes with the packed scalar-row form of the coarse sweeps
-SROW_SIZES = (3, 6, 10, 15, 21, 28)
 
-
-def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False, ymode=False):
+def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False, ymode=False, forms=None):
     """Algorithmic work of every block-Jacobi sweep of a cycle from a zero
     iterate, {(level, k): (flops, bytes)} for sweep k (F sweeps first).
 
@@ -237,7 +234,11 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False, ymode=False):
     right-scaled couplings A_ij D_jj^{-1}, whose nonzero rows are full (b
     nonzeros each); the C sweep takes the same scaled blocks for its F columns
     and converts every F row, x_F = D_FF^{-1} y_F (b^2 FMAs, the D^{-1} block
-    and y read, x written)."""
+    and y read, x written).
+
+    forms (the library's nair_sweep_forms per level, when given) replaces
+    split and ymode level by level: split where a level takes the scalar-row
+    form (2 or 3), ymode where its F sweeps run in y (3)."""
     work = {}
     for l in range(nlev):
         lev = S.level(l)
@@ -267,8 +268,10 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False, ymode=False):
                 else:
                     copy = fm[f_sweeps - 1] if short else (cf == 0)
             sel = upd[rows] & off
-            fpart = split and l >= 1 and short and 1 <= k < f_sweeps
-            ylev = ymode and split and l >= 1 and short and c_sweeps == 1
+            lsplit = (forms[l] in (2, 3)) if forms is not None else split
+            fpart = lsplit and l >= 1 and short and 1 <= k < f_sweeps
+            ylev = ((forms[l] == 3) if forms is not None else (ymode and split)) and l >= 1 and short \
+                and c_sweeps == 1
             if fpart:  # later F sweeps: the F-column couplings only
                 sel = sel & (cf[ci] == 0)
             if ylev and k == f_sweeps:  # the C sweep converts every F row
@@ -293,7 +296,7 @@ def sweep_work(S, nlev, b, f_sweeps, c_sweeps=1, split=False, ymode=False):
                 flops = 2.0 * (nnz + nrow * b * b)
                 byts = 8.0 * nnz + 4.0 * nblk + 8.0 * nrow * b * (b + 1)
             byts += 8.0 * b * xcols + 8.0 * b * (nrow + ncopy) * dual + 8.0 * b * ncopy
-            if split and l >= 1 and short and k == 0:  # h written
+            if lsplit and l >= 1 and short and k == 0:  # h written
                 byts += 8.0 * b * nrow
             if nrow or ncopy:
                 work[(l, k)] = (flops, byts)
@@ -336,7 +339,7 @@ def roofline(nair, params, rp, ci, v, sweep_ms, fp64_peak, workload):
     S = nair.NairSolver(rp, ci, v, **params)
     fp64 = params.get("precision", "fp64") == "fp64"
     work = sweep_work(S, S.num_levels(), S.b, S.f_sweeps, max(S.params.c_sweeps, 0),
-                      split=S.b in SROW_SIZES, ymode=S.b in SROW_SIZES)
+                      forms=S.sweep_forms())
     S.close()
     peak, peak_src = fp64_peak
     fl = by = t = 0.0

@@ -191,6 +191,17 @@ nair_status nair_adjoint_solve_batch(nair_handle *const *h, int32_t count, const
  * before the first adjoint solve or in NAIR_ADJOINT_TRANSPOSED mode). */
 nair_status nair_num_levels(const nair_handle *h, int32_t adjoint, int32_t *levels);
 
+/* Relaxation form of each level (a diagnostic for checks and measurement):
+ * forms[l] for l < min(cap, levels) of the forward hierarchy's cycle
+ * (transposed == 0) or of its transposed cycle (transposed == 1, available
+ * after the first adjoint solve in NAIR_ADJOINT_TRANSPOSED mode; INVALID_ARG
+ * before).  Values: -1 the coarsest level (direct solve), 0 block-row kernel,
+ * 1 level-0 column-compressed coupling blocks, 2 packed scalar rows, 3 packed
+ * scalar rows with the F sweeps iterating on y_F = D_FF x_F (transposed:
+ * D_FF^T x_F), which apply D^{-1} once per cycle instead of once per sweep.
+ * `levels` is nair_num_levels(h, 0); forms must hold cap int32 values. */
+nair_status nair_sweep_forms(const nair_handle *h, int32_t transposed, int32_t cap, int32_t *forms);
+
 /* Sizes of one level, 10 int64 values:
  *   E, nnzb(A), nC, nF, nnzb(L), nnzb(Delta), nnzb(R_cf), nnzb(AP), coarsest flag, setup rounds of C/F. */
 nair_status nair_level_sizes(const nair_handle *h, int32_t adjoint, int32_t level, int64_t *sizes);

@@ -68,7 +68,7 @@ EXPORTS = ["nair_default_params", "nair_setup", "nair_solve", "nair_adjoint_solv
            "nair_assemble_sigma", "nair_mass_apply", "nair_gradients", "nair_kernel_launches",
            "nair_profile", "nair_profile_entry", "nair_block_inverse_noalloc", "nair_sweep_timing",
            "nair_setup_batch", "nair_solve_batch", "nair_adjoint_solve_batch", "nair_fp64_peak",
-           "nair_last_error"]
+           "nair_last_error", "nair_sweep_forms"]
 
 
 def lib():
@@ -95,6 +95,7 @@ def lib():
     L.nair_free.restype = None
     L.nair_num_levels.argtypes = [P, I32, ctypes.POINTER(I32)]
     L.nair_level_sizes.argtypes = [P, I32, I32, P]
+    L.nair_sweep_forms.argtypes = [P, I32, I32, P]
     L.nair_get_level.argtypes = [P, I32, I32, I32, P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
     L.nair_block_inverse.argtypes = [I32, I32, P, P, P]
     L.nair_block_inverse_noalloc.argtypes = [I32, I32, P, P, P]
@@ -304,6 +305,16 @@ class NairSolver:
         n = ctypes.c_int32(0)
         _check(lib().nair_num_levels(self._h, int(adjoint), ctypes.byref(n)), "nair_num_levels")
         return n.value
+
+    def sweep_forms(self, transposed=False):
+        """Relaxation form per level: -1 coarsest, 0 block-row kernel, 1 level-0
+        column-compressed blocks, 2 packed scalar rows, 3 scalar rows with the F
+        sweeps in y = D x (nair_sweep_forms)."""
+        n = self.num_levels()
+        out = np.zeros(max(n, 1), dtype=np.int32)
+        _check(lib().nair_sweep_forms(self._h, int(transposed), n, out.ctypes.data_as(ctypes.c_void_p)),
+               "nair_sweep_forms")
+        return [int(v) for v in out[:n]]
 
     def sizes(self, level, adjoint=False):
         out = np.zeros(10, dtype=np.int64)

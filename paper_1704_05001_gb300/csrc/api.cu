@@ -758,6 +758,37 @@ static void sizes_t(const Hier<T> &H, int l, int64_t *o) {
   o[9] = L.cf_rounds;
 }
 
+template <typename T>
+static void sweep_forms_t(const Hier<T> &H, bool transposed, int cap, int32_t *forms) {
+  for (int l = 0; l < H.nlev && l < cap; ++l) {
+    const Level<T> &L = H.lev[l];
+    int f = 0;
+    if (L.coarsest) {
+      f = -1;
+    } else if (!transposed) {
+      if (l == 0 && H.l0c.W > 0) f = 1;
+      else if (L.ymode) f = 3;
+      else if (L.sr.srp) f = 2;
+    } else {
+      const TLevel<T> &TL = H.tlev[l];
+      if (l == 0 && H.tl0c.W > 0) f = 1;
+      else if (TL.ymode) f = 3;
+      else if (TL.sr.srp) f = 2;
+    }
+    forms[l] = f;
+  }
+}
+
+nair_status nair_sweep_forms(const nair_handle *h, int32_t transposed, int32_t cap, int32_t *forms) {
+  NAIR_API_BEGIN
+  if (!h || !forms || cap < 0) return set_error(NAIR_ERR_INVALID_ARG, "null handle or forms, or negative cap");
+  if (transposed && !h->tbuilt) return set_error(NAIR_ERR_INVALID_ARG, "transposed cycle not built yet");
+  if (h->mixed) sweep_forms_t(h->h32, transposed != 0, cap, forms);
+  else sweep_forms_t(h->h64, transposed != 0, cap, forms);
+  return NAIR_OK;
+  NAIR_API_END
+}
+
 nair_status nair_level_sizes(const nair_handle *h0, int32_t adjoint, int32_t level, int64_t *sizes) {
   NAIR_API_BEGIN
   const nair_handle *h = pick(h0, adjoint);

@@ -270,7 +270,8 @@ def test_scalar_row_sweeps_parity(nair, oracle_mod):
     """A C2 problem large enough that the F and C sweeps of level 1 run with one
     thread group per row, where FP64 sweeps take the scalar-row form (one thread
     per row and component over the blocks whose row is nonzero, threads sorted
-    by entry count): V-cycles and the solve against the oracle."""
+    by entry count) and the F sweeps iterate on y = D x: V-cycles, the solve
+    and the transposed cycle (its F sweeps on y = D^T x) against the oracle."""
     import torch
     P = D.make_problem("C2", N=224)
     params = dict(neumann_degree=2, max_coarse=4)
@@ -280,6 +281,8 @@ def test_scalar_row_sweeps_parity(nair, oracle_mod):
     avg = len(L1["col"]) / L1["E"]
     assert avg <= 4.0 and min(L1["nF"], L1["nC"]) * P["b"] * 2 > wave  # one group per row
     S = nair.NairSolver(dev(P["row_ptr"]), dev(P["col"]), dev(P["vals"]), **params)
+    forms = S.sweep_forms()
+    assert forms[0] == 1 and forms[1] == 3, forms  # level 1: scalar rows, F sweeps in y
     f = D.rng.uniform(17, P["n"]) - 0.5
     for rep in range(2):
         z = S.vcycle(dev(f)).cpu().numpy()
@@ -289,6 +292,11 @@ def test_scalar_row_sweeps_parity(nair, oracle_mod):
     ref = H.solve(P["rhs"])
     assert rep["iterations"] == ref["iterations"]
     assert np.max(np.abs(rep["history"] - ref["history"])) <= 1e-12
+    for rep in range(2):
+        zt = S.adjoint_vcycle(dev(f)).cpu().numpy()
+        zr = H.vcycle(f, transposed=True)
+        assert np.linalg.norm(zt - zr) <= 1e-12 * np.linalg.norm(zr)
+    assert S.sweep_forms(transposed=True)[1] == 3
     S.close()
 
 
