@@ -1734,7 +1734,7 @@ template <typename T, bool FILL>
 __global__ void k_srow_entries(int E, int b, const int *__restrict__ rp, const int *__restrict__ ci,
                                const T *__restrict__ v, const int *__restrict__ srp, int *__restrict__ cnt,
                                int *__restrict__ sp, int skip_diag, const signed char *__restrict__ cf,
-                               int *__restrict__ srs) {
+                               int *__restrict__ srs, unsigned char *__restrict__ nzb) {
   pdl_wait();
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= (long long)E * b) return;
@@ -1746,9 +1746,17 @@ __global__ void k_srow_entries(int E, int b, const int *__restrict__ rp, const i
     for (int p = rp[i]; p < rp[i + 1]; ++p) {
       if (skip_diag && ci[p] == i) continue;
       if (split && (cf[ci[p]] == 1) != (pass == 0)) continue;  // pass 0: C columns, pass 1: F columns
-      const T *row = v + ((size_t)p * b + r) * b;
+      // the counting pass reads the values and keeps one flag per block row
+      // (p, r) for the filling pass, which then reads no values (C5 FP64
+      // setup 75.3 -> 73.8 ms)
       bool nz = false;
-      for (int c = 0; c < b; ++c) nz |= row[c] != (T)0;
+      if (FILL) {
+        nz = nzb[(size_t)p * b + r] != 0;
+      } else {
+        const T *row = v + ((size_t)p * b + r) * b;
+        for (int c = 0; c < b; ++c) nz |= row[c] != (T)0;
+        nzb[(size_t)p * b + r] = nz;
+      }
       if (nz) {
         if (FILL) sp[w] = p;
         ++w;
@@ -1832,9 +1840,10 @@ static void srow_pack(int E, int b, const DBsr<T> &M, bool skip_diag, const sign
   Mem tmp;
   tmp.s = s;
   int *cnt = tmp.alloc<int>(n + 1);
+  unsigned char *nzb = tmp.alloc<unsigned char>((size_t)std::max(M.nnzb, 1) * b);
   launch_pdl(k_srow_entries<T, false>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)M.rp,
              (const int *)M.ci, (const T *)M.v, (const int *)nullptr, cnt, (int *)nullptr, (int)skip_diag, cf,
-             (int *)nullptr);
+             (int *)nullptr, nzb);
   NAIR_LAUNCH_CHECK();
   sr.srp = mem.alloc<int>(n + 1);
   const int ne = exclusive_scan(cnt, sr.srp, (int)n, s, tmp, true);
@@ -1843,7 +1852,7 @@ static void srow_pack(int E, int b, const DBsr<T> &M, bool skip_diag, const sign
   if (cf) sr.srs = mem.alloc<int>(n);
   launch_pdl(k_srow_entries<T, true>, dim3(grid(n)), dim3(kThreads), 0, s, E, b, (const int *)M.rp,
              (const int *)M.ci, (const T *)M.v, (const int *)sr.srp, (int *)nullptr, sr.sp, (int)skip_diag, cf,
-             sr.srs);
+             sr.srs, nzb);
   NAIR_LAUNCH_CHECK();
   sr.sj = mem.alloc<int>(std::max(ne, 1));
   T *sv = mem.alloc<T>((size_t)std::max(ne, 1) * b);
