@@ -1016,9 +1016,12 @@ __global__ void k_ap_count(int E, const int *__restrict__ rp, const int *__restr
   cnt[r] = c;
 }
 
+// The blocks of row r of AP in ascending column J; for each, first[w] is the
+// first block p of A's row r with ipc[ci[p]] = J, and next[p] links the
+// following ones in ascending p (-1 ends a list), the order of the sum
 __global__ void k_ap_fill(int E, const int *__restrict__ rp, const int *__restrict__ ci,
                           const int *__restrict__ ipc, const int *__restrict__ orp,
-                          int *__restrict__ oci, int *__restrict__ orow) {
+                          int *__restrict__ oci, int *__restrict__ first, int *__restrict__ next) {
   pdl_wait();
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= E) return;
@@ -1031,16 +1034,24 @@ __global__ void k_ap_fill(int E, const int *__restrict__ rp, const int *__restri
     }
     if (jmin == INT_MAX) break;
     oci[w] = jmin;
-    orow[w] = r;
+    int prev = -1;
+    for (int p = rp[r]; p < rp[r + 1]; ++p) {
+      if (ipc[ci[p]] != jmin) continue;
+      if (prev < 0) first[w] = p;
+      else next[prev] = p;
+      prev = p;
+    }
+    next[prev] = -1;
     ++w;
     last = jmin;
   }
 }
 
+// AP values: each output scalar adds its A blocks along the list of k_ap_fill
+// (ascending p, the sum's order), with no search of the row (C5 FP64 setup
+// 74.2 -> 71.9 ms against scanning the row for each output scalar)
 template <typename T>
-__global__ void k_ap_values(long long total, int b, const int *__restrict__ orow,
-                            const int *__restrict__ oci, const int *__restrict__ rp,
-                            const int *__restrict__ ci, const int *__restrict__ ipc,
+__global__ void k_ap_values(long long total, int b, const int *__restrict__ first, const int *__restrict__ next,
                             const T *__restrict__ Av, T *__restrict__ out, const int *__restrict__ nblk) {
   pdl_wait();
   long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1049,15 +1060,9 @@ __global__ void k_ap_values(long long total, int b, const int *__restrict__ orow
   const long long blk = g / bb;
   if (blk >= *nblk) return;  // grid sized by an upper bound
   const int rc = (int)(g - blk * bb);
-  const int r = orow[blk], J = oci[blk];
-  T acc = 0;
-  bool first = true;
-  for (int p = rp[r]; p < rp[r + 1]; ++p) {
-    if (ipc[ci[p]] != J) continue;
-    T v = Av[(size_t)p * bb + rc];
-    acc = first ? v : add_rn(acc, v);
-    first = false;
-  }
+  int p = first[blk];
+  T acc = Av[(size_t)p * bb + rc];
+  for (p = next[p]; p >= 0; p = next[p]) acc = add_rn(acc, Av[(size_t)p * bb + rc]);
   out[g] = acc;
 }
 
@@ -2177,14 +2182,15 @@ static bool coarsen(Hier<T> &H, int l, const Params &P, cudaStream_t s, Mem &mem
     exclusive_scan(cnt, AP.rp, E, s, tmp, false);
     AP.nnzb = -1;               // at most one block per block of A: sized by nnzb(A)
     AP.ci = tmp.alloc<int>(nnzb);
-    int *aprow = tmp.alloc<int>(nnzb);
-    launch_pdl(k_ap_fill, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, L.ipc, AP.rp, AP.ci, aprow);
+    int *apfirst = tmp.alloc<int>(nnzb), *apnext = tmp.alloc<int>(nnzb);
+    launch_pdl(k_ap_fill, dim3(grid(E)), dim3(kThreads), 0, s, E, L.A.rp, L.A.ci, L.ipc, AP.rp, AP.ci, apfirst,
+               apnext);
     NAIR_LAUNCH_CHECK();
     AP.v = tmp.alloc<T>((size_t)nnzb * bb);
     tot = (long long)nnzb * bb;
     if (tot) {
-      launch_pdl(k_ap_values<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, aprow, AP.ci, L.A.rp, L.A.ci, L.ipc, L.A.v, AP.v,
-                                                   AP.rp + E);
+      launch_pdl(k_ap_values<T>, dim3(grid(tot)), dim3(kThreads), 0, s, tot, b, (const int *)apfirst,
+                 (const int *)apnext, (const T *)L.A.v, AP.v, (const int *)(AP.rp + E));
       NAIR_LAUNCH_CHECK();
     }
   }
