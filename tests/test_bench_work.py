@@ -104,6 +104,24 @@ def test_sweep_work_counts_scaled_f_sweeps(hier):
             assert byts >= 16.0 * int(upd.sum()) * b
 
 
+def test_sweep_work_forms_select_the_accounting_per_level(hier):
+    """forms (the library's per-level relaxation form) picks the accounting
+    level by level: form 3 counts as split + ymode, form 2 as split only, and
+    form 0 (block-row kernel) as neither."""
+    P, H = hier
+    b, SF = P["b"], 3
+    n = H.nlev
+    plain = bench.sweep_work(H, n, b, SF, 1)
+    split = bench.sweep_work(H, n, b, SF, 1, split=True)
+    yform = bench.sweep_work(H, n, b, SF, 1, split=True, ymode=True)
+    forms = [1] + [3 if l % 3 == 1 else 2 if l % 3 == 2 else 0 for l in range(1, n)]
+    mixed = bench.sweep_work(H, n, b, SF, 1, forms=forms)
+    assert set(mixed) == set(plain)
+    for (l, k), w in mixed.items():
+        ref = plain if l == 0 or forms[l] == 0 else split if forms[l] == 2 else yform
+        assert w == ref[(l, k)], (l, k)
+
+
 def _transpose_level(lev, b):
     """Block transpose of a level matrix with its inverse diagonal blocks:
     (A^T)_ji = (A_ij)^T, rows sorted by column, (D_ii^{-1})^T."""
