@@ -57,7 +57,11 @@ struct RowArgs {
   // the entries of an F row's scalar row list its C columns first, up to srs,
   // then its F columns.  fmode 1 (the first F sweep of a cycle): h = f - the C
   // part, stored, then the F part subtracted; fmode 2 (later F sweeps, x_C
-  // unchanged): h read back and only the F part summed; fmode 0: every entry
+  // unchanged): h read back and only the F part summed; fmode 0: every entry.
+  // fmodes 3 and 4 are 1 and 2 with the F rows iterating on y = D x (no
+  // D^{-1} applied; 4 reads sv = the right-scaled entries A_ij D_jj^{-1});
+  // fmode 5 is the C sweep after them (sv = the scaled entries for its F
+  // columns), whose copy part writes the F rows as x = D^{-1} y
   const int *srs;
   T *h;
   int fmode;
@@ -284,6 +288,8 @@ __global__ void __launch_bounds__(256) k_rowop(RowArgs<T> a) {
 // kernels.  Then each thread of the natural layout finishes component r of
 // row i:
 //   OP_JACOBI: row r of D_ii^{-1} applied to f_i - sum (from shared memory);
+//     in the F sweeps of the y form (FM 3, 4) the result is y_i = h_i - sum
+//     itself, written by the thread that summed it when G = 1 (no exchange);
 //   OP_RESTRICT: f_c = f_{c2f[i]} + sum, the restriction f_c = f_C + R_cf f_F.
 // Six thread blocks per SM (register cap 40): these sweeps wait on memory, and
 // the extra resident warps gained more than the few spilled registers cost
