@@ -1897,13 +1897,16 @@ void build_sweep_rows_level(int E, int nF, int nC, int b, const DBsr<T> &A, cons
   srow_pack<T>(E, b, A, true, cf, sr, s, mem);
   // F sweeps: thread groups per scalar row sized for half a row (the first
   // F sweep's rows too: C5 FP64 solve 112.5 -> 110.8 ms; for a quarter of a
-  // row the later sweeps were slower, 113.1 ms)
-  sr.perm_f[0] = srow_perm<T>(nF, b, 0.5 * avg, fsweep, sr.srp, s, mem, &sr.perm_f_tpc[0]);
+  // row the later sweeps were slower, 113.1 ms).  Blocks larger than 10 keep
+  // the full-row sizing: their scalar rows are long already (C3, b = 28:
+  // solve 30.0 -> 28.1 ms with it)
+  const double favg = b <= 10 ? 0.5 * avg : avg;
+  sr.perm_f[0] = srow_perm<T>(nF, b, favg, fsweep, sr.srp, s, mem, &sr.perm_f_tpc[0]);
   // the later F sweeps sum only the F part of their rows: sorted by its length,
   // their thread groups per row sized for half a row (C5 FP64 solve 119.4 ->
   // 112.4 ms, mixed 80.2 -> 75.5 ms, adjoint 211.8 -> 204.8 ms)
   for (int k = 1; k < nfl; ++k)
-    sr.perm_f[k] = srow_perm<T>(fl_n[k], b, 0.5 * avg, fl[k], sr.srp, s, mem, &sr.perm_f_tpc[k], sr.srs);
+    sr.perm_f[k] = srow_perm<T>(fl_n[k], b, favg, fl[k], sr.srp, s, mem, &sr.perm_f_tpc[k], sr.srs);
   sr.perm_c = srow_perm<T>(nC, b, avg, csweep, sr.srp, s, mem, &sr.perm_c_tpc);
 }
 template void build_sweep_rows_level<double>(int, int, int, int, const DBsr<double> &, const signed char *, int *,

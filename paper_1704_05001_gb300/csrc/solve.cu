@@ -389,7 +389,7 @@ static void vcyc(const Hier<T> &H, const Params &P, int l, int type, const T *f,
       const unsigned char *perm = cls == 1 ? L.sr.perm_c : L.sr.perm_f[pk];
       const int ptpc = cls == 1 ? L.sr.perm_c_tpc : L.sr.perm_f_tpc[pk];
       // F sweep lists: groups sized for half a row, as at setup
-      const int G = rowop_groups(a.nrows, b, cls == 0 ? 0.5 * avg : avg);
+      const int G = rowop_groups(a.nrows, b, (cls == 0 && b <= 10) ? 0.5 * avg : avg);
       bool done = false;
       if (L.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
         a.srp = L.sr.srp;
@@ -602,7 +602,7 @@ static void vcyc_t(const Hier<T> &H, const Params &P, int l, const T *f, T *out,
         // scalar-row form of A^T where built, as in the forward cycle
         const unsigned char *perm = cls == 1 ? TL.sr.perm_c : TL.sr.perm_f[short_f ? m : 0];
         const int ptpc = cls == 1 ? TL.sr.perm_c_tpc : TL.sr.perm_f_tpc[short_f ? m : 0];
-        const int G = rowop_groups(a.nrows, b, cls == 0 ? 0.5 * avg : avg);
+        const int G = rowop_groups(a.nrows, b, (cls == 0 && b <= 10) ? 0.5 * avg : avg);
         bool done = false;
         if (TL.sr.srp && perm && sweep_rows_tpc(b, G) == ptpc) {
           a.srp = TL.sr.srp;
